@@ -1,0 +1,170 @@
+"""Seeded synthetic inputs for the similarity join (shared by tests, bench, oracle).
+
+This module holds no arithmetic of the join itself: it only draws embeddings.
+Every array is a deterministic function of (seed, stream, shape), drawn with
+NumPy's counter-based Philox generator in fixed-size row chunks, so the result
+does not depend on the number of threads used.
+
+Recipes (the workloads of the join, stated in the design doc):
+  * clustered: K centres uniform on the unit sphere (normalised Gaussians);
+    each row picks a centre (iid uniform, or Zipf(s) over the centre ranks),
+    adds isotropic Gaussian noise whose TOTAL expected squared norm is
+    sigma^2 (per-coordinate std sigma/sqrt(d)), and is renormalised in FP64
+    before rounding to float32.
+  * near duplicates: a seeded fraction of rows i < min(nA, nB) gets
+    b_{pi(i)} = normalise(a_i + n), ||n|| ~ sigma_dup (total), pi a seeded
+    permutation of B's rows.
+  * one-hot / multi-attribute one-hot: the relational encoding of Sec. 3.1 of
+    the paper (mat(A)_ij = 1 iff a_i.ID = v_j), optionally one block per
+    attribute scaled by 1/sqrt(#attributes).
+"""
+from __future__ import annotations
+
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+CHUNK = 8192  # rows per RNG chunk; part of the recipe (changing it changes data)
+
+
+def _rng(seed: int, stream: int, chunk: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(np.random.SeedSequence([seed, stream, chunk])))
+
+
+def _threads() -> int:
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def _normalise_rows(x64: np.ndarray) -> np.ndarray:
+    n = np.sqrt(np.einsum("ij,ij->i", x64, x64))
+    n[n == 0] = 1.0
+    return (x64 / n[:, None]).astype(np.float32)
+
+
+def centres(n_clusters: int, d: int, seed: int) -> np.ndarray:
+    """n_clusters unit vectors, uniform on the sphere (float64)."""
+    out = np.empty((n_clusters, d), np.float64)
+    for c0 in range(0, n_clusters, CHUNK):
+        c1 = min(n_clusters, c0 + CHUNK)
+        g = _rng(seed, 1000, c0 // CHUNK).standard_normal((c1 - c0, d))
+        out[c0:c1] = g / np.linalg.norm(g, axis=1, keepdims=True)
+    return out
+
+
+def assignments(n: int, n_clusters: int, seed: int, stream: int,
+                zipf_s: float | None = None) -> np.ndarray:
+    """Centre index per row: iid uniform, or Zipf(zipf_s) over ranks 1..K."""
+    rng = _rng(seed, 2000 + stream, 0)
+    if zipf_s is None:
+        return rng.integers(0, n_clusters, size=n, dtype=np.int64)
+    ranks = np.arange(1, n_clusters + 1, dtype=np.float64)
+    cdf = np.cumsum(ranks ** (-float(zipf_s)))
+    cdf /= cdf[-1]
+    u = rng.random(n)
+    r = np.minimum(np.searchsorted(cdf, u, side="right"), n_clusters - 1)
+    perm = _rng(seed, 3000, 0).permutation(n_clusters)  # rank -> centre id
+    return perm[r]
+
+
+def clustered(n: int, d: int, n_clusters: int, sigma: float = 0.1, seed: int = 0,
+              stream: int = 0, zipf_s: float | None = None,
+              noise_mode: str = "total", C: np.ndarray | None = None) -> np.ndarray:
+    """n x d float32 unit rows drawn around shared centres (see module doc)."""
+    if C is None:
+        C = centres(n_clusters, d, seed)
+    asg = assignments(n, n_clusters, seed, stream, zipf_s)
+    if noise_mode == "total":
+        std = sigma / np.sqrt(d)
+    elif noise_mode == "per_coord":
+        std = sigma
+    else:
+        raise ValueError("noise_mode must be 'total' or 'per_coord'")
+    out = np.empty((n, d), np.float32)
+
+    def work(ci):
+        r0 = ci * CHUNK
+        r1 = min(n, r0 + CHUNK)
+        g = _rng(seed, 10 + stream, ci).standard_normal((r1 - r0, d), dtype=np.float32)
+        x = C[asg[r0:r1]] + std * g.astype(np.float64)
+        out[r0:r1] = _normalise_rows(x)
+
+    nchunks = (n + CHUNK - 1) // CHUNK
+    with ThreadPoolExecutor(_threads()) as ex:
+        list(ex.map(work, range(nchunks)))
+    return out
+
+
+def add_near_duplicates(A: np.ndarray, B: np.ndarray, frac: float, sigma: float,
+                        seed: int = 0) -> np.ndarray:
+    """Return (pairs) and overwrite rows of B with noisy copies of rows of A.
+
+    pairs[:, 0] = i (row of A), pairs[:, 1] = pi(i) (row of B).
+    """
+    n = min(A.shape[0], B.shape[0])
+    d = A.shape[1]
+    rng = _rng(seed, 4000, 0)
+    m = int(round(frac * n))
+    src = np.sort(rng.choice(n, size=m, replace=False))
+    perm = rng.permutation(B.shape[0])
+    dst = perm[src]
+    std = sigma / np.sqrt(d)
+    for c0 in range(0, m, CHUNK):
+        c1 = min(m, c0 + CHUNK)
+        g = _rng(seed, 4001, c0 // CHUNK).standard_normal((c1 - c0, d))
+        B[dst[c0:c1]] = _normalise_rows(A[src[c0:c1]].astype(np.float64) + std * g)
+    return np.stack([src, dst], axis=1)
+
+
+def paired(n: int, d: int, n_clusters: int, sigma: float = 0.1, sigma_pair: float = 0.02,
+           seed: int = 0):
+    """(A, B) with b_i a near duplicate of a_i (positives on the diagonal)."""
+    A = clustered(n, d, n_clusters, sigma, seed, stream=0)
+    std = sigma_pair / np.sqrt(d)
+    B = np.empty_like(A)
+    for c0 in range(0, n, CHUNK):
+        c1 = min(n, c0 + CHUNK)
+        g = _rng(seed, 5000, c0 // CHUNK).standard_normal((c1 - c0, d))
+        B[c0:c1] = _normalise_rows(A[c0:c1].astype(np.float64) + std * g)
+    return A, B
+
+
+def one_hot(keys: np.ndarray, n_values: int) -> np.ndarray:
+    """mat(X)_ij = 1 iff key_i == v_j (Sec. 3.1), float32."""
+    keys = np.asarray(keys, dtype=np.int64)
+    out = np.zeros((keys.shape[0], n_values), np.float32)
+    out[np.arange(keys.shape[0]), keys] = 1.0
+    return out
+
+
+def multi_attr_one_hot(key_cols, domains) -> np.ndarray:
+    """One one-hot block per attribute, each scaled by 1/sqrt(#attributes).
+
+    With 4 attributes the scale is exactly 1/2, so <a, b> = (#equal attributes)/4.
+    """
+    na = len(domains)
+    scale = np.float32(1.0 / np.sqrt(na))
+    blocks = [one_hot(k, v) * scale for k, v in zip(key_cols, domains)]
+    return np.ascontiguousarray(np.concatenate(blocks, axis=1))
+
+
+def keys(n: int, n_distinct: int, seed: int, stream: int) -> np.ndarray:
+    """n uniform keys in [0, n_distinct)."""
+    return _rng(seed, 6000 + stream, 0).integers(0, n_distinct, size=n, dtype=np.int64)
+
+
+def unit_rows(n: int, d: int, seed: int, stream: int) -> np.ndarray:
+    """n iid uniform unit vectors (float32)."""
+    out = np.empty((n, d), np.float32)
+    for c0 in range(0, n, CHUNK):
+        c1 = min(n, c0 + CHUNK)
+        out[c0:c1] = _normalise_rows(_rng(seed, 7000 + stream, c0 // CHUNK)
+                                     .standard_normal((c1 - c0, d)))
+    return out
+
+
+def log_uniform_sizes(n_jobs: int, lo: int, hi: int, seed: int, stream: int) -> np.ndarray:
+    """Integer sizes log-uniform in [lo, hi]."""
+    u = _rng(seed, 8000 + stream, 0).random(n_jobs)
+    return np.minimum(hi, np.floor(np.exp(np.log(lo) + u * (np.log(hi + 1) - np.log(lo))))
+                      ).astype(np.int64)
