@@ -1,0 +1,184 @@
+/*
+ * sj.h -- C ABI of the GB300 embedding similarity join library (libsj.so).
+ *
+ * The operation.  The paper (Sec. 3.1, "Two-way natural join") evaluates a
+ * join of tables A and B as the matrix product C = mat(A) mat(B)^T and keeps
+ * (a_i, b_j) exactly when C_ij > 0; its Sec. 3.2 turns C back into pairs with
+ * nonzero(C).  This library evaluates that product over real-valued,
+ * unit-norm embeddings: C_ij = s_ij = <a_i, b_j>, the exact real dot product
+ * of the stored float32 rows, and returns
+ *
+ *   top-k   : for every left row i, the k right rows j with the largest s_ij,
+ *             ordered by (s_ij desc, j asc), padded with (-1, -inf) when
+ *             k > nB;
+ *   threshold: every pair with s_ij >= tau, ordered by (i asc, j asc).
+ *
+ * Every emitted index set and order is the one the exact scores define, and
+ * every emitted score is s_ij rounded to nearest-even float32, whatever
+ * precision the tensor-core scoring runs in (cfg.prec): candidates near a
+ * decision are rescored with a compensated FP32 dot product and, where even
+ * that cannot decide, with an exact fixed-point accumulation.
+ *
+ * Memory.  Row-major float32 matrices, row i at A + i*d.  Every array pointer
+ * may be DEVICE memory (used in place) or HOST memory (pageable or pinned;
+ * staged through the handle's workspace with copies inside the call).  The
+ * caller owns all arrays; the handle owns only its workspace, grown on demand
+ * up to cfg.workspace_limit bytes and kept between calls.
+ *
+ * Synchronisation.  Work is queued on cfg.stream; every call returns after
+ * that stream has drained the call's work (so status codes that depend on
+ * device-side checks, and the stats, are final on return).  One handle must
+ * not be used by two host threads at once.
+ *
+ * Errors.  Calls return a status code and never abort, trap or print.  Input
+ * validation (finite values, |  ||x||^2 - 1 | <= 1e-5 per row) runs on the
+ * device inside the call.  Device-side waits are bounded; a wait that gives up
+ * returns SJ_ERR_TIMEOUT and leaves the context usable.
+ */
+#ifndef SJ_H_
+#define SJ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SJ_OK = 0,
+  SJ_ERR_INVALID_ARG = 1,   /* null pointer, bad size, k < 1, d < 1, NaN tau */
+  SJ_ERR_NONFINITE = 2,     /* an input row holds NaN or Inf */
+  SJ_ERR_NOT_UNIT_NORM = 3, /* an input row has | ||x||^2 - 1 | > 1e-5 */
+  SJ_ERR_CAPACITY = 4,      /* output buffer too small; *n_out = required count */
+  SJ_ERR_OOM = 5,           /* workspace allocation failed or over the limit */
+  SJ_ERR_CUDA = 6,          /* a CUDA runtime/driver call failed */
+  SJ_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+  SJ_ERR_UNSUPPORTED = 8,   /* configuration not supported on this device */
+  SJ_ERR_INTERNAL = 9       /* internal consistency check failed */
+} sj_status;
+
+/* Precision of the tensor-core scoring pass.  The emitted results do not
+ * depend on it (see above); only speed and candidate counts do. */
+typedef enum {
+  SJ_FP32 = 0,     /* CUDA-core FP32 FMA tiles (no tensor cores) */
+  SJ_BF16 = 1,     /* bfloat16 operands, FP32 accumulation in TMEM */
+  SJ_FP8_E4M3 = 2  /* e4m3 with a power-of-two scale per row (reserved) */
+} sj_precision;
+
+/* cfg.flags */
+#define SJ_FLAG_SYM_INFONCE 0x1u   /* contrastive: add the column (B->A) term */
+#define SJ_FLAG_DEBUG_TIMEOUT 0x100u /* test hook: device waits give up at once */
+
+typedef struct {
+  int device;             /* CUDA device ordinal */
+  void *stream;           /* cudaStream_t; NULL = the legacy default stream */
+  sj_precision prec;      /* scoring precision */
+  int64_t d;              /* embedding width, >= 1 */
+  uint32_t flags;         /* SJ_FLAG_* */
+  size_t workspace_limit; /* bytes; 0 = no limit */
+} sj_config;
+
+/* One threshold result. 24 bytes; _pad is written as 0. */
+typedef struct {
+  int64_t i;
+  int64_t j;
+  float score;
+  int32_t _pad;
+} sj_pair;
+
+/* Per-call statistics (optional; pass NULL to skip).  Times come from CUDA
+ * events on cfg.stream. */
+typedef struct {
+  double ms_prepare;         /* validation + quantisation/packing (+ staging) */
+  double ms_score;           /* tensor-core / FFMA scoring with fused filter */
+  double ms_select;          /* rescoring, exact resolution, ordering, output */
+  double ms_total;           /* whole call */
+  int64_t n_candidates;      /* pairs that passed the low-precision filter */
+  int64_t n_rescored;        /* pairs rescored with the compensated FP32 dot */
+  int64_t n_exact;           /* pairs evaluated with the exact accumulator */
+  int64_t n_overflow_rows;   /* rows whose candidate list needed a second pass */
+  int64_t n_pairs;           /* threshold: pairs emitted */
+  double margin_max;         /* reserved (0) */
+  double max_abs_err_lowprec;/* max |s~ - s| seen over rescored top-k candidates */
+  int64_t n_launches;        /* kernels this call launched */
+} sj_stats;
+
+typedef struct sj_handle sj_handle;
+
+/* Create a handle bound to cfg->device.  Allocates no workspace yet.
+ * Errors: SJ_ERR_INVALID_ARG (null, d < 1), SJ_ERR_UNSUPPORTED (device is not
+ * compute capability 10.3 for SJ_BF16/SJ_FP8_E4M3), SJ_ERR_CUDA. */
+sj_status sj_create(sj_handle **h, const sj_config *cfg);
+
+/* Free the handle and its workspace.  NULL is accepted. */
+sj_status sj_destroy(sj_handle *h);
+
+/* Top-k join.  A: nA x d, B: nB x d float32 (device or host).  Outputs
+ * out_idx[nA*k] (int64) and out_score[nA*k] (float32), row i at i*k, ordered
+ * (score desc, j asc) with (-1, -inf) padding.  nA == 0 or nB == 0 is valid.
+ * A == B (self-join) is allowed; the diagonal is included.
+ * Errors: SJ_ERR_INVALID_ARG, SJ_ERR_NONFINITE, SJ_ERR_NOT_UNIT_NORM,
+ * SJ_ERR_OOM, SJ_ERR_CUDA, SJ_ERR_TIMEOUT.  Outputs are undefined on error. */
+sj_status sj_topk(sj_handle *h, const float *A, int64_t nA, const float *B,
+                  int64_t nB, int32_t k, int64_t *out_idx, float *out_score,
+                  sj_stats *st);
+
+/* Threshold join: all (i, j) with s_ij >= tau, sorted by (i, j), written to
+ * out[0 .. *n_out).  If more than `capacity` pairs qualify the call returns
+ * SJ_ERR_CAPACITY with *n_out = the required count and out undefined.
+ * Same input rules and errors as sj_topk. */
+sj_status sj_threshold(sj_handle *h, const float *A, int64_t nA, const float *B,
+                       int64_t nB, double tau, sj_pair *out, int64_t capacity,
+                       int64_t *n_out, sj_stats *st);
+
+/* One job of a batch: an independent join with its own sizes and outputs.
+ * topk_idx/topk_score may be NULL (no top-k); pairs may be NULL (no
+ * threshold).  All pointers follow the same device/host rule. */
+typedef struct {
+  const float *A;
+  int64_t nA;
+  const float *B;
+  int64_t nB;
+  int32_t k;
+  double tau;
+  int64_t *topk_idx;
+  float *topk_score;
+  sj_pair *pairs;
+  int64_t capacity;
+  int64_t *n_out;
+} sj_job;
+
+/* Run n_jobs independent joins (same d and precision).  A job that asks for
+ * both parts (top-k outputs and n_out) gets them from ONE scoring pass.
+ * Results per job are exactly those of sj_topk / sj_threshold.  Returns the
+ * first error; a job over capacity sets its *n_out and the call returns
+ * SJ_ERR_CAPACITY after finishing the other jobs. */
+sj_status sj_batch(sj_handle *h, const sj_job *jobs, int32_t n_jobs, sj_stats *st);
+
+/* Contrastive (InfoNCE) join over N paired rows, positives on the diagonal:
+ * S = A B^T / T, l_i = logsumexp_j S_ij, loss = (1/N) sum_i (l_i - S_ii)
+ * (with SJ_FLAG_SYM_INFONCE also the column term, averaged).  A, B: N x d
+ * bfloat16 (raw 16-bit patterns), DEVICE memory.  Writes loss[0] (device
+ * float) and lse[N] (2N with the symmetric flag: rows then columns).
+ * Errors: SJ_ERR_INVALID_ARG, SJ_ERR_UNSUPPORTED, SJ_ERR_CUDA, SJ_ERR_OOM. */
+sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t N,
+                             float T, float *loss, float *lse);
+
+/* Backward of sj_contrastive_fwd: given lse from the forward and the upstream
+ * gradient grad_loss[0] (device float), writes dA, dB (N x d float32, device)
+ * by recomputing the score tiles (no N x N matrix is stored). */
+sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, float T,
+                      const float *lse, const float *grad_loss, float *dA, float *dB);
+
+/* Static description of a status code. */
+const char *sj_status_string(sj_status s);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int sj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SJ_H_ */

@@ -1,0 +1,609 @@
+// finalize.cu -- from low-precision candidates to exact results.
+//
+// Top-k (per left row, one CTA):
+//   1. theta = (k-th best s~ over all splits) - 2 m_i; keep band entries with
+//      s~ >= theta.  They contain the exact top-k (see RowFilter).
+//   2. Dot2 (compensated FP32) for each candidate -> a 64-bit key interval
+//      [L, U] (units of 2^-60) that contains the exact score.
+//   3. Sort by U desc; sweep into groups of chained overlapping intervals.
+//      Groups are totally ordered (every member of a later group is strictly
+//      below every member of an earlier one), so only the order INSIDE a
+//      multi-member group is undecided.
+//   4. Members of multi-member groups within the first k positions get their
+//      exact value (fixed-point accumulator); sort those groups by
+//      (exact desc, j asc).  Scores: float32 rounding of the interval when
+//      both ends round alike, else of the exact value.
+// A row whose band list overflowed, or with more candidates than fit in
+// shared memory, is re-ranked from scratch against all of B (fallback).
+//
+// Threshold: per candidate, Dot2 decides s >= tau unless tau lies inside the
+// interval, where the exact value decides; accepted pairs are counted per row,
+// placed by an exclusive scan of the counts and sorted by j inside each row.
+#include <cfloat>
+
+#include "sj_device.cuh"
+#include "sj_internal.h"
+
+namespace sj {
+
+namespace {
+
+constexpr int kFinThreads = 128;
+constexpr int kCMax = 1024;
+constexpr int64_t kRowInSmemMax = 16384;  // left row cached in shared memory up to this width
+
+// Candidate arrays (shared memory in the normal path, global in the fallback).
+struct CandArrays {
+  long long *U, *L;
+  int32_t *j;
+  float *v;        // low-precision score (NaN when unknown)
+  int32_t *perm;   // sorted order (candidate ids), length n_pad
+  int32_t *perm2;  // final order (sorted positions), length n_pad
+  int32_t *grp;    // group id per sorted position
+  uint8_t *flag;   // per sorted position: 1 = exact computed
+  float *sc;       // score per sorted position
+  Exact *ex;       // exact value per sorted position
+};
+
+__device__ __forceinline__ int next_pow2(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+// Block-wide bitonic sort of idx[0, n_pad) (entries >= 0 are items, -1 pads
+// that sort last) with before(x, y) = "x goes first".
+template <typename Before>
+__device__ void block_bitonic(int32_t *idx, int n_pad, Before before) {
+  for (int size = 2; size <= n_pad; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < (n_pad >> 1); t += blockDim.x) {
+        int lo = 2 * stride * (t / stride) + (t % stride);
+        int hi = lo + stride;
+        bool asc = (lo & size) == 0;
+        int32_t x = idx[lo], y = idx[hi];
+        bool y_first = (x < 0) ? (y >= 0) : (y >= 0 && before(y, x));
+        bool x_first = (y < 0) ? (x >= 0) : (x >= 0 && before(x, y));
+        bool sw = asc ? y_first : x_first;
+        if (sw) {
+          idx[lo] = y;
+          idx[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Steps 3-4 above on n candidates whose U, L, j (and v) are filled in.
+// Writes k outputs.  a_row: the left row (shared or global memory).
+__device__ void rank_and_emit(CandArrays c, int n, int k, const float *a_row, const float *B,
+                              int64_t d, int64_t *out_idx, float *out_score, Counters *ctr) {
+  __shared__ int s_n_need;
+  __shared__ unsigned long long s_n_exact;
+  const int n_pad = next_pow2(n > 0 ? n : 1);
+  for (int t = threadIdx.x; t < n_pad; t += blockDim.x) c.perm[t] = t < n ? t : -1;
+  if (threadIdx.x == 0) s_n_exact = 0;
+  __syncthreads();
+  block_bitonic(c.perm, n_pad, [&](int32_t x, int32_t y) {
+    return c.U[x] > c.U[y] || (c.U[x] == c.U[y] && c.j[x] < c.j[y]);
+  });
+  // group sweep (sequential; n <= a few thousand in practice)
+  if (threadIdx.x == 0) {
+    int g = -1;
+    long long Lmin = 0;
+    int n_need = n;
+    for (int p = 0; p < n; ++p) {
+      int32_t x = c.perm[p];
+      if (g < 0 || c.U[x] < Lmin) {
+        if (p >= k) { n_need = p; break; }
+        ++g;
+        Lmin = c.L[x];
+      } else if (c.L[x] < Lmin) {
+        Lmin = c.L[x];
+      }
+      c.grp[p] = g;
+    }
+    s_n_need = n_need;
+  }
+  __syncthreads();
+  const int n_need = s_n_need;
+  // which positions need the exact value
+  for (int p = threadIdx.x; p < n_need; p += blockDim.x) {
+    bool multi = (p > 0 && c.grp[p - 1] == c.grp[p]) || (p + 1 < n_need && c.grp[p + 1] == c.grp[p]);
+    int32_t x = c.perm[p];
+    float s = 0.f;
+    bool need = multi;
+    if (!multi && p < k) need = !key_interval_round(c.L[x], c.U[x], s);
+    c.flag[p] = need ? 1 : 0;
+    c.sc[p] = s;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  for (int p = warp; p < n_need; p += nwarps) {
+    if (!c.flag[p]) continue;
+    int32_t x = c.perm[p];
+    Exact e = exact_dot_warp(a_row, B + (int64_t)c.j[x] * d, d);
+    if (lane == 0) {
+      c.ex[p] = e;
+      c.sc[p] = exact_to_float(e);
+      atomicAdd(&s_n_exact, 1ull);
+    }
+  }
+  __syncthreads();
+  const int n2_pad = next_pow2(n_need > 0 ? n_need : 1);
+  for (int t = threadIdx.x; t < n2_pad; t += blockDim.x) c.perm2[t] = t < n_need ? t : -1;
+  __syncthreads();
+  block_bitonic(c.perm2, n2_pad, [&](int32_t p, int32_t q) {
+    if (c.grp[p] != c.grp[q]) return c.grp[p] < c.grp[q];
+    int r = exact_cmp(c.ex[p], c.ex[q]);  // same multi-member group: both exact
+    if (r != 0) return r > 0;
+    return c.j[c.perm[p]] < c.j[c.perm[q]];
+  });
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    if (r < n_need && r < n) {
+      int32_t p = c.perm2[r];
+      out_idx[r] = c.j[c.perm[p]];
+      out_score[r] = c.sc[p];
+    } else {
+      out_idx[r] = -1;
+      out_score[r] = -INFINITY;
+    }
+  }
+  if (threadIdx.x == 0 && s_n_exact) atomicAdd(&ctr->n_exact, s_n_exact);
+  __syncthreads();
+}
+
+struct FinSmemLayout {
+  long long U[kCMax];
+  long long L[kCMax];
+  Exact ex[kCMax];
+  int32_t j[kCMax];
+  float v[kCMax];
+  int32_t perm[kCMax];
+  int32_t perm2[kCMax];
+  int32_t grp[kCMax];
+  float sc[kCMax];
+  uint8_t flag[kCMax];
+};
+
+__global__ void __launch_bounds__(kFinThreads) topk_finalize_kernel(TopkFinalArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FinSmemLayout &sm = *reinterpret_cast<FinSmemLayout *>(smem_raw);
+  float *a_row = reinterpret_cast<float *>(smem_raw + sizeof(FinSmemLayout));
+  __shared__ int s_n, s_overflow;
+  __shared__ float s_theta;
+  __shared__ unsigned int s_maxerr;
+  const int64_t i = blockIdx.x;
+  if (i >= a.nA) return;
+  const int S = a.n_splits, k = a.k;
+  if (threadIdx.x == 0) {
+    s_n = 0;
+    s_overflow = 0;
+    s_maxerr = 0;
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < S; s += blockDim.x)
+    if (a.band_cnt[i * S + s] < 0) s_overflow = 1;
+  __syncthreads();
+  // k-th best low-precision score over all splits
+  float kth;
+  if (S == 1) {
+    kth = a.heaps[i * k];  // root of the min-heap of the k best
+  } else {
+    float *buf = reinterpret_cast<float *>(sm.U);  // S*k <= 2*kCMax floats
+    const int m = S * k, m_pad = next_pow2(m);
+    int32_t *ord = sm.perm;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) buf[t] = a.heaps[i * (int64_t)m + t];
+    for (int t = threadIdx.x; t < m_pad; t += blockDim.x) ord[t] = t < m ? t : -1;
+    __syncthreads();
+    block_bitonic(ord, m_pad, [&](int32_t x, int32_t y) { return buf[x] > buf[y]; });
+    kth = buf[ord[k - 1]];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    RowMeta mi = a.metaA[i];
+    float t1 = __fmul_ru(mi.qerr, a.gmaxB[0]);
+    float t2 = __fmul_ru(mi.qnrm, a.gmaxB[2]);
+    float t3 = __fmul_ru(__fmul_ru(a.acc_coef, mi.qnrm), a.gmaxB[1]);
+    float m = __fadd_ru(__fadd_ru(t1, t2), t3);
+    s_theta = __fsub_rd(kth, __fmul_ru(2.f, m));
+  }
+  __syncthreads();
+  const float theta = s_theta;
+  if (!s_overflow) {
+    for (int s = 0; s < S; ++s) {
+      const int cnt = a.band_cnt[i * S + s];
+      const Cand *bl = a.band + (i * S + s) * (int64_t)a.cap;
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        Cand cd = bl[t];
+        if (cd.v >= theta) {
+          int p = atomicAdd(&s_n, 1);
+          if (p < kCMax) {
+            sm.j[p] = cd.j;
+            sm.v[p] = cd.v;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_overflow || s_n > kCMax) {
+    if (threadIdx.x == 0) {
+      unsigned slot = atomicAdd(&a.ctr->overflow_rows, 1u);
+      a.overflow_rows[slot] = (int)i;
+    }
+    return;
+  }
+  const int n = s_n;
+  const float *a_src = a.A + i * a.d;
+  if (a.d <= kRowInSmemMax) {
+    for (int64_t t = threadIdx.x; t < a.d; t += blockDim.x) a_row[t] = a_src[t];
+    a_src = a_row;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const float nrm_a = a.metaA[i].nrm;
+  for (int p = warp; p < n; p += nwarps) {
+    float hi, lo;
+    const int32_t j = sm.j[p];
+    dot2_warp(a_src, a.B + (int64_t)j * a.d, a.d, hi, lo);
+    if (lane == 0) {
+      long long K = dot2_key(hi, lo);
+      long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, a.metaB[j].nrm);
+      sm.U[p] = K + D;
+      sm.L[p] = K - D;
+      float err = fabsf(__fsub_rn(__fsub_rn(sm.v[p], hi), lo));
+      atomicMax(&s_maxerr, __float_as_uint(err));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&a.ctr->n_candidates, (unsigned long long)n);
+    atomicAdd(&a.ctr->n_rescored, (unsigned long long)n);
+    atomicMax(&a.ctr->max_err_bits, s_maxerr);
+  }
+  CandArrays c{sm.U, sm.L, sm.j, sm.v, sm.perm, sm.perm2, sm.grp, sm.flag, sm.sc, sm.ex};
+  rank_and_emit(c, n, k, a_src, a.B, a.d, a.out_idx + i * k, a.out_score + i * k, a.ctr);
+}
+
+// Fallback: rank ALL of B for one left row (scratch in global memory).
+__global__ void __launch_bounds__(kFinThreads) topk_fallback_kernel(TopkFallbackArgs a) {
+  const int r = blockIdx.x;
+  if (r >= a.n_rows) return;
+  const int64_t i = a.rows[r];
+  const int64_t n = a.nB;
+  const int n_pad = next_pow2((int)(n > 0 ? n : 1));
+  unsigned char *base = static_cast<unsigned char *>(a.scratch) + (size_t)r * a.per_row_bytes;
+  CandArrays c;
+  c.U = reinterpret_cast<long long *>(base);
+  c.L = c.U + n_pad;
+  c.ex = reinterpret_cast<Exact *>(c.L + n_pad);
+  c.j = reinterpret_cast<int32_t *>(c.ex + n_pad);
+  c.v = reinterpret_cast<float *>(c.j + n_pad);
+  c.perm = reinterpret_cast<int32_t *>(c.v + n_pad);
+  c.perm2 = c.perm + n_pad;
+  c.grp = c.perm2 + n_pad;
+  c.sc = reinterpret_cast<float *>(c.grp + n_pad);
+  c.flag = reinterpret_cast<uint8_t *>(c.sc + n_pad);
+  const float *a_row = a.A + i * a.d;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const float nrm_a = a.metaA[i].nrm;
+  for (int64_t j = warp; j < n; j += nwarps) {
+    float hi, lo;
+    dot2_warp(a_row, a.B + j * a.d, a.d, hi, lo);
+    if (lane == 0) {
+      long long K = dot2_key(hi, lo);
+      long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, a.metaB[j].nrm);
+      c.U[j] = K + D;
+      c.L[j] = K - D;
+      c.j[j] = (int32_t)j;
+      c.v[j] = NAN;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(&a.ctr->n_rescored, (unsigned long long)n);
+  rank_and_emit(c, (int)n, a.k, a_row, a.B, a.d, a.out_idx + i * a.k, a.out_score + i * a.k,
+                a.ctr);
+}
+
+// ---------------------------------------------------------------------------
+// Threshold
+
+__global__ void thr_rescore_kernel(ThrFinalArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long n_exact = 0;
+  for (int64_t c = w0; c < a.n_cand; c += nw) {
+    ThrCand t = a.cand[c];
+    const float *ar = a.A + (int64_t)t.i * a.d;
+    const float *br = a.B + (int64_t)t.j * a.d;
+    float hi, lo;
+    dot2_warp(ar, br, a.d, hi, lo);
+    long long K = dot2_key(hi, lo);
+    long long D = dot2_halfwidth(a.dot2_coef_key, a.metaA[t.i].nrm, a.metaB[t.j].nrm);
+    int in;
+    bool have_ex = false;
+    Exact ex;
+    if (K - D >= a.tau_key) {
+      in = 1;
+    } else if (K + D < a.tau_key) {
+      in = 0;
+    } else {
+      ex = exact_dot_warp(ar, br, a.d);
+      have_ex = true;
+      ++n_exact;
+      in = exact_cmp(ex, a.tau_exact) >= 0;
+    }
+    if (!in) continue;
+    float s;
+    if (!key_interval_round(K - D, K + D, s)) {
+      if (!have_ex) {
+        ex = exact_dot_warp(ar, br, a.d);
+        ++n_exact;
+      }
+      s = exact_to_float(ex);
+    }
+    if (lane == 0) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(a.row_count + t.i), 1ull);
+      unsigned long long slot = atomicAdd(&a.ctr->n_pairs, 1ull);
+      a.accepted[slot] = ThrCand{t.i, t.j, s, 0};
+    }
+  }
+  if (lane == 0 && n_exact) atomicAdd(&a.ctr->n_exact, n_exact);
+}
+
+// Exclusive scan helpers (3 phases).
+constexpr int kScanThreads = 1024, kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ long long block_exclusive_scan(long long v, long long *sh, long long &total) {
+  // sh: blockDim.x / 32 entries
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += y;
+    }
+    if (lane < nw) sh[lane] = w;
+  }
+  __syncthreads();
+  long long before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+  total = sh[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void scan_reduce_kernel(const int64_t *in, int64_t n, long long *block_sums) {
+  __shared__ long long sh[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  long long s = 0;
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t idx = base + (int64_t)threadIdx.x * kScanItems + q;
+    if (idx < n) s += in[idx];
+  }
+  long long total;
+  block_exclusive_scan(s, sh, total);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void scan_top_kernel(long long *block_sums, int64_t nb, int64_t *total_out) {
+  __shared__ long long sh[32];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    int64_t idx = b0 + threadIdx.x;
+    long long v = idx < nb ? block_sums[idx] : 0;
+    long long total;
+    long long ex = block_exclusive_scan(v, sh, total);
+    if (idx < nb) block_sums[idx] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void scan_apply_kernel(const int64_t *in, int64_t *out, int64_t n,
+                                  const long long *block_sums) {
+  __shared__ long long sh[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  long long vals[kScanItems];
+  long long s = 0;
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t idx = base + (int64_t)threadIdx.x * kScanItems + q;
+    vals[q] = idx < n ? in[idx] : 0;
+    s += vals[q];
+  }
+  long long total;
+  long long ex = block_exclusive_scan(s, sh, total) + block_sums[blockIdx.x];
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t idx = base + (int64_t)threadIdx.x * kScanItems + q;
+    if (idx < n) out[idx] = ex;
+    ex += vals[q];
+  }
+}
+
+__global__ void thr_scatter_kernel(const ThrCand *acc, const int64_t *n_acc_dev, int64_t cap,
+                                   const int64_t *row_off, int64_t *row_fill, PairOut *out) {
+  const int64_t n = min64(*n_acc_dev, cap);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    ThrCand c = acc[t];
+    unsigned long long r =
+        atomicAdd(reinterpret_cast<unsigned long long *>(row_fill + c.i), 1ull);
+    out[row_off[c.i] + (int64_t)r] = PairOut{c.i, c.j, c.v, 0};
+  }
+}
+
+// Sort each row's pairs by j: rows of <= 32 pairs inside one warp, larger
+// rows are listed for the block kernel.
+__global__ void thr_sort_small_kernel(PairOut *out, const int64_t *row_off,
+                                      const int64_t *row_count, int64_t nA, int *big_rows,
+                                      int *n_big, int big_cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= nA) return;
+  const int64_t cnt = row_count[row];
+  if (cnt <= 1) return;
+  if (cnt > 32) {
+    if (lane == 0) {
+      int s = atomicAdd(n_big, 1);
+      if (s < big_cap) big_rows[s] = (int)row;
+    }
+    return;
+  }
+  PairOut *seg = out + row_off[row];
+  PairOut p = lane < cnt ? seg[lane] : PairOut{0, INT64_MAX, 0.f, 0};
+  // bitonic over 32 lanes by j
+  for (int size = 2; size <= 32; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      long long oj = __shfl_xor_sync(0xffffffffu, (long long)p.j, stride);
+      float os = __shfl_xor_sync(0xffffffffu, p.score, stride);
+      const bool lower = (lane & stride) == 0;
+      const bool asc = (lane & size) == 0;
+      const bool keep_min = (lower == asc);
+      const bool take_other = keep_min ? (oj < p.j) : (oj > p.j);
+      if (take_other) {
+        p.j = oj;
+        p.score = os;
+      }
+    }
+  }
+  if (lane < cnt) seg[lane] = p;
+}
+
+// Rank-based merge sort of one large row in global memory (distinct j keys).
+__global__ void thr_sort_big_kernel(PairOut *out, PairOut *tmp, const int64_t *row_off,
+                                    const int64_t *row_count, const int *big_rows,
+                                    const int *n_big) {
+  const int b = blockIdx.x;
+  if (b >= *n_big) return;
+  const int64_t row = big_rows[b];
+  const int64_t n = row_count[row];
+  PairOut *src = out + row_off[row];
+  PairOut *dst = tmp + row_off[row];
+  for (int64_t width = 1; width < n; width <<= 1) {
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+      int64_t run = t / width;
+      int64_t run_start = run * width;
+      int64_t pair_start = (run & ~1ll) * width;
+      bool left = (run & 1) == 0;
+      int64_t other_start = left ? run_start + width : run_start - width;
+      int64_t other_len = left ? max64(0, min64(width, n - other_start)) : width;
+      long long key = src[t].j;
+      // number of elements in the other run with a smaller key
+      int64_t lo = 0, hi = other_len;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (src[other_start + mid].j < key) lo = mid + 1;
+        else hi = mid;
+      }
+      dst[pair_start + (t - run_start) + lo] = src[t];
+    }
+    __syncthreads();
+    PairOut *sw = src;
+    src = dst;
+    dst = sw;
+  }
+  if (src != out + row_off[row]) {
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) out[row_off[row] + t] = src[t];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_topk_finalize(const TopkFinalArgs &a, cudaStream_t st) {
+  if (a.nA == 0) return cudaSuccess;
+  const size_t smem =
+      sizeof(FinSmemLayout) + (a.d <= kRowInSmemMax ? (size_t)a.d * sizeof(float) : 0);
+  cudaError_t e = cudaFuncSetAttribute(topk_finalize_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  topk_finalize_kernel<<<(unsigned)a.nA, kFinThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+size_t topk_fallback_row_bytes(int64_t nB) {
+  int64_t n_pad = 1;
+  while (n_pad < nB) n_pad <<= 1;
+  // U, L, ex, j, v, perm, perm2, grp, sc, flag
+  return (size_t)n_pad * (8 + 8 + sizeof(Exact) + 4 + 4 + 4 + 4 + 4 + 4 + 1) + 256;
+}
+
+cudaError_t launch_topk_fallback(const TopkFallbackArgs &a, cudaStream_t st) {
+  if (a.n_rows == 0) return cudaSuccess;
+  topk_fallback_kernel<<<a.n_rows, kFinThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thr_rescore(const ThrFinalArgs &a, cudaStream_t st) {
+  if (a.n_cand == 0) return cudaSuccess;
+  int64_t warps = a.n_cand;
+  int64_t blocks = (warps + 7) / 8;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  thr_rescore_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+size_t scan_scratch_bytes(int64_t n) {
+  int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  return (size_t)(nb + 1) * sizeof(long long);
+}
+
+cudaError_t launch_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
+                                  void *scratch, cudaStream_t st) {
+  int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  long long *bs = static_cast<long long *>(scratch);
+  if (nb == 0) {
+    return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
+  }
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, bs);
+  scan_top_kernel<<<1, kScanThreads, 0, st>>>(bs, nb, total);
+  scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, bs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thr_scatter(const ThrCand *accepted, const int64_t *n_acc_dev,
+                               int64_t n_acc_cap, const int64_t *row_off, int64_t *row_fill,
+                               PairOut *out, cudaStream_t st) {
+  if (n_acc_cap == 0) return cudaSuccess;
+  int64_t blocks = (n_acc_cap + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  thr_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(accepted, n_acc_dev, n_acc_cap, row_off,
+                                                       row_fill, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thr_sort_rows(PairOut *out, const int64_t *row_off, const int64_t *row_count,
+                                 int64_t nA, int *big_rows, int *n_big, int big_cap,
+                                 cudaStream_t st) {
+  (void)out;
+  if (nA == 0) return cudaSuccess;
+  int64_t blocks = (nA * 32 + 255) / 256;
+  thr_sort_small_kernel<<<(unsigned)blocks, 256, 0, st>>>(out, row_off, row_count, nA, big_rows,
+                                                          n_big, big_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thr_sort_big(PairOut *out, PairOut *tmp, const int64_t *row_off,
+                                const int64_t *row_count, const int *big_rows, const int *n_big,
+                                int n_big_host, cudaStream_t st) {
+  if (n_big_host == 0) return cudaSuccess;
+  thr_sort_big_kernel<<<n_big_host, 512, 0, st>>>(out, tmp, row_off, row_count, big_rows, n_big);
+  return cudaGetLastError();
+}
+
+}  // namespace sj

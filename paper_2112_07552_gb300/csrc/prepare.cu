@@ -1,0 +1,127 @@
+// prepare.cu -- validation and operand packing for the scoring pass.
+//
+// One warp per row.  Every input row is checked (finite entries,
+// | ||x||^2 - 1 | <= 1e-5 with a compensated norm) and rewritten in the
+// layout the scoring kernel consumes: a zero-padded copy in FP32 or BF16
+// (rounded to nearest-even), plus per-row bounds used by the error margins:
+// ||x||, ||x~|| and ||x~ - x||, all rounded up.  Zero padding of rows and
+// columns is exact for the products.  This is the analogue of the on-device
+// table -> matrix transformation of Sec. 4.2.2 ("data transformation" cost).
+#include <cuda_bf16.h>
+
+#include "sj_device.cuh"
+#include "sj_internal.h"
+
+namespace sj {
+
+namespace {
+
+// Compensated sum of squares across the warp: returns hi + lo (same on all lanes).
+__device__ __forceinline__ float warp_sumsq2(float s, float c) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    float s2 = __shfl_xor_sync(0xffffffffu, s, off);
+    float c2 = __shfl_xor_sync(0xffffffffu, c, off);
+    float t, q;
+    two_sum(s, s2, t, q);
+    s = t;
+    c = __fadd_rn(__fadd_rn(c, c2), q);
+  }
+  return __fadd_rn(s, c);
+}
+
+__device__ __forceinline__ void acc_sq(float x, float &s, float &c) {
+  float p = __fmul_rn(x, x);
+  float e = __fmaf_rn(x, x, -p);
+  float t, q;
+  two_sum(s, p, t, q);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
+__device__ __forceinline__ void atomic_max_pos(float *addr, float v) {
+  // non-negative floats order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned int *>(addr), __float_as_uint(v));
+}
+
+// Upper bound on sqrt(x) for a compensated sum of squares x (relative error of
+// x far below 2^-40): inflate by 2^-20 and take the square root rounded up.
+__device__ __forceinline__ float sqrt_up(float x) {
+  return __fsqrt_ru(__fmul_ru(fmaxf(x, 0.f), 1.0f + 0x1p-20f));
+}
+
+template <typename OutT>
+__global__ void prepare_kernel(const float *__restrict__ X, int64_t n, int64_t d,
+                               OutT *__restrict__ Xp, int64_t n_pad, int64_t dp,
+                               RowMeta *__restrict__ meta, float *__restrict__ gmax,
+                               Counters *ctr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n_pad) return;
+  OutT *dst = Xp ? Xp + row * dp : nullptr;
+  if (row >= n) {
+    if (dst)
+      for (int64_t k = lane; k < dp; k += 32) dst[k] = OutT(0.f);
+    if (lane == 0) meta[row] = RowMeta{0.f, 0.f, 0.f, 0};
+    return;
+  }
+  const float *src = X + row * d;
+  float ns = 0.f, nc = 0.f;   // ||x||^2
+  float qs = 0.f, qc = 0.f;   // ||x~||^2
+  float es = 0.f, ec = 0.f;   // ||x~ - x||^2
+  bool bad = false;
+  for (int64_t k = lane; k < dp; k += 32) {
+    float x = k < d ? src[k] : 0.f;
+    if (!isfinite(x)) { bad = true; x = 0.f; }
+    OutT q = OutT(x);
+    float qf = float(q);
+    if (dst) dst[k] = q;
+    acc_sq(x, ns, nc);
+    acc_sq(qf, qs, qc);
+    acc_sq(__fsub_rn(qf, x), es, ec);  // exact difference of x and its rounding
+  }
+  bool any_bad = __any_sync(0xffffffffu, bad);
+  float n2 = warp_sumsq2(ns, nc);
+  float q2 = warp_sumsq2(qs, qc);
+  float e2 = warp_sumsq2(es, ec);
+  if (lane == 0) {
+    unsigned flags = 0;
+    if (any_bad) flags |= kErrNonFinite;
+    else if (!(fabsf(n2 - 1.0f) <= 1e-5f)) flags |= kErrNotUnit;
+    if (flags) atomicOr(&ctr->err_flags, flags);
+    RowMeta m;
+    m.nrm = sqrt_up(n2);
+    m.qnrm = sqrt_up(q2);
+    m.qerr = e2 > 0.f ? sqrt_up(e2) : 0.f;
+    m.sexp = 0;
+    meta[row] = m;
+    if (gmax) {
+      atomic_max_pos(gmax + 0, m.nrm);
+      atomic_max_pos(gmax + 1, m.qnrm);
+      atomic_max_pos(gmax + 2, m.qerr);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_prepare(const float *X, int64_t n, int64_t d, PackFormat fmt, void *Xp,
+                           int64_t n_pad, int64_t dp, RowMeta *meta, float *gmax,
+                           Counters *ctr, cudaStream_t st) {
+  if (n_pad == 0) return cudaSuccess;
+  const int warps = 8;
+  dim3 grid((unsigned)((n_pad + warps - 1) / warps)), block(32 * warps);
+  switch (fmt) {
+    case PackFormat::kF32:
+      prepare_kernel<float><<<grid, block, 0, st>>>(X, n, d, static_cast<float *>(Xp), n_pad,
+                                                    dp, meta, gmax, ctr);
+      break;
+    case PackFormat::kBF16:
+      prepare_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(
+          X, n, d, static_cast<__nv_bfloat16 *>(Xp), n_pad, dp, meta, gmax, ctr);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sj

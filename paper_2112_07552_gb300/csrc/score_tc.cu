@@ -1,0 +1,435 @@
+// score_tc.cu -- tensor-core scoring pass for sm_103a (tcgen05 + TMA + TMEM).
+//
+// s~ = a~ . b~ for bfloat16 operands, products exact and accumulated in FP32
+// in tensor memory.  The score matrix is a dense contraction (Sec. 3.1:
+// C = mat(A) mat(B)^T), so it runs on the 5th-generation tensor cores; the
+// paper's own kernels (WMMA on Ampere/Turing) are prior art only.
+//
+// Persistent kernel, one CTA per SM, warp-specialised (192 threads):
+//   warp 0     TMA producer: 128x64 A tile + 256x64 B tile per k-block into a
+//              4-stage ring of 128B-swizzled shared memory buffers;
+//   warp 1     TMEM allocator + MMA issuer: tcgen05.mma kind::f16, M=128,
+//              N=256, K=16, into one of two 256-column TMEM accumulators;
+//   warps 2-5  epilogue: tcgen05.ld of their 32-lane quarter (one left row
+//              per thread), fused top-k / threshold filter (epilogue.cuh),
+//              then release the accumulator to the MMA warp.
+// Work unit = (128-row block of A, column split of B); CTAs take units
+// round-robin.  Every wait is bounded (globaltimer); a wait that gives up
+// flags SJ_ERR_TIMEOUT, the CTA drains its in-flight copies and MMAs,
+// frees its tensor memory and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "epilogue.cuh"
+#include "tc_host.h"
+
+namespace sj {
+
+namespace {
+
+constexpr int BM = kTcBM;       // 128 rows of A per tile (TMEM lanes)
+constexpr int BN = kTcBN;       // 256 columns of B per tile (TMEM columns)
+constexpr int BK = 64;          // k-block: 64 bf16 = 128 bytes = one swizzle row
+constexpr int STAGES = 4;
+constexpr int kThreads = 192;
+constexpr uint32_t kTileABytes = BM * BK * 2;
+constexpr uint32_t kTileBBytes = BN * BK * 2;
+constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators
+
+struct alignas(1024) TcSmem {
+  unsigned char a[STAGES][kTileABytes];  // each 1024-byte aligned
+  unsigned char b[STAGES][kTileBBytes];
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t tmem_full[2];
+  uint64_t tmem_empty[2];
+  uint64_t drain;
+  uint64_t never;  // debug-timeout hook: nothing ever arrives here
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity; false when it gave up (or
+// when another role already aborted the CTA).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                          volatile int *abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (now_ns() - t0 > limit_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile written by TMA with
+// 128-byte swizzling; 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused with SW128)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void flag_timeout(TcSmem &sm, Counters *ctr) {
+  *(volatile int *)&sm.abort = 1;
+  atomicOr(&ctr->err_flags, kErrTimeout);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    score_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                    const __grid_constant__ CUtensorMap tmB, ScoreArgs a, uint32_t flags) {
+  extern __shared__ unsigned char smem_raw[];
+  TcSmem &sm = *reinterpret_cast<TcSmem *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool debug_timeout = (flags & SJ_FLAG_DEBUG_TIMEOUT) != 0;
+  const uint64_t limit = 4000000000ull;  // 4 s per wait
+  volatile int *abort = &sm.abort;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&sm.tmem_full[q], 1);
+      mbar_init(&sm.tmem_empty[q], 4 * 32);
+    }
+    mbar_init(&sm.drain, 1);
+    mbar_init(&sm.never, 1);
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&sm.tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm.tmem_base;
+
+  const int64_t nkb = a.dp / BK;
+  const int64_t n_col_tiles = (a.nB + BN - 1) / BN;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint64_t it = 0;
+      bool ok = true;
+      for (int64_t unit = blockIdx.x; unit < a.n_units && ok; unit += gridDim.x) {
+        const int64_t rb = unit / a.n_splits;
+        const int split = (int)(unit % a.n_splits);
+        const int64_t ct0 = split * a.tiles_per_split;
+        const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
+        for (int64_t ct = ct0; ct < ct1 && ok; ++ct) {
+          for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
+            const int s = (int)(it % STAGES);
+            const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+            if (!mbar_wait(&sm.empty[s], ph ^ 1, limit, abort)) {
+              flag_timeout(sm, a.ctr);
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&sm.full[s], kTileABytes + kTileBBytes);
+            tma_load_2d(sm.a[s], &tmA, (int)(kb * BK), (int)(rb * BM), &sm.full[s]);
+            tma_load_2d(sm.b[s], &tmB, (int)(kb * BK), (int)(ct * BN), &sm.full[s]);
+          }
+        }
+      }
+      // Drain: the last load issued into each stage must have landed before the
+      // CTA may exit (normal exit: they were consumed long ago).
+      for (uint64_t q = (it > STAGES ? it - STAGES : 0); q < it; ++q) {
+        const int s = (int)(q % STAGES);
+        const uint32_t ph = (uint32_t)((q / STAGES) & 1);
+        uint64_t t0 = now_ns();
+        while (!mbar_try(&sm.full[s], ph) && now_ns() - t0 < limit) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint64_t it = 0, tile = 0;
+      bool ok = true;
+      for (int64_t unit = blockIdx.x; unit < a.n_units && ok; unit += gridDim.x) {
+        const int split = (int)(unit % a.n_splits);
+        const int64_t ct0 = split * a.tiles_per_split;
+        const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
+        for (int64_t ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
+          const int acc = (int)(tile & 1);
+          const uint32_t aph = (uint32_t)((tile >> 1) & 1);
+          if (!mbar_wait(&sm.tmem_empty[acc], aph ^ 1, limit, abort)) {
+            flag_timeout(sm, a.ctr);
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
+          for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
+            const int s = (int)(it % STAGES);
+            const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+            if (!mbar_wait(&sm.full[s], ph, limit, abort)) {
+              flag_timeout(sm, a.ctr);
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint32_t a0 = su32(sm.a[s]), b0 = su32(sm.b[s]);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              mma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32),
+                       (kb > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&sm.empty[s]);  // frees the smem stage once these MMAs finish
+          }
+          if (!ok) break;
+          mma_commit(&sm.tmem_full[acc]);  // accumulator ready for the epilogue
+        }
+      }
+      // Drain: every MMA issued so far completes before tensor memory is freed.
+      mma_commit(&sm.drain);
+      uint64_t t0 = now_ns();
+      while (!mbar_try(&sm.drain, 0) && now_ns() - t0 < limit) {
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;  // TMEM lanes this warp may access
+    const int r_in_tile = quarter * 32 + lane;
+    uint64_t tile = 0;
+    bool ok = true;
+    if (debug_timeout) {
+      // test hook: a wait on a barrier nothing arrives at must give up cleanly
+      const bool w = mbar_wait(&sm.never, 0, 1000000ull, abort);
+      if (!__all_sync(0xffffffffu, w)) {
+        flag_timeout(sm, a.ctr);
+        ok = false;
+      }
+    }
+    for (int64_t unit = blockIdx.x; unit < a.n_units && ok; unit += gridDim.x) {
+      const int64_t rb = unit / a.n_splits;
+      const int split = (int)(unit % a.n_splits);
+      const int64_t row = rb * BM + r_in_tile;
+      const bool owner = row < a.nA;
+      RowCtx rc;
+      if (owner) row_begin(rc, a, row, split);
+      const int64_t ct0 = split * a.tiles_per_split;
+      const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
+      for (int64_t ct = ct0; ct < ct1; ++ct, ++tile) {
+        const int acc = (int)(tile & 1);
+        const uint32_t aph = (uint32_t)((tile >> 1) & 1);
+        // warp-uniform outcome: the TMEM loads below are .sync.aligned
+        const bool w = mbar_wait(&sm.tmem_full[acc], aph, limit, abort);
+        if (!__all_sync(0xffffffffu, w)) {
+          flag_timeout(sm, a.ctr);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const int64_t col0 = ct * BN;
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          float v[32];
+          tmem_ld32(taddr + c0, v);
+          if (owner) {
+            float mx = v[0];
+#pragma unroll
+            for (int q = 1; q < 32; ++q) mx = fmaxf(mx, v[q]);
+            const float tmin = fminf(rc.f.theta, rc.f.tau_lo);
+            if (mx >= tmin) {
+              const int64_t jb = col0 + c0;
+#pragma unroll 1
+              for (int q = 0; q < 32; ++q) {
+                if (jb + q < a.nB) row_visit(rc, a, v[q], (int32_t)(jb + q));
+              }
+            }
+          }
+        }
+        fence_before();
+        mbar_arrive(&sm.tmem_empty[acc]);
+      }
+      if (owner) row_end(rc, a, split);
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+
+struct TcContext {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+};
+
+sj_status tc_create(TcContext **out) {
+  TcContext *c = new TcContext();
+  cudaDriverEntryPointQueryResult q;
+  void *fn = nullptr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                    cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    delete c;
+    return SJ_ERR_UNSUPPORTED;
+  }
+  c->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  *out = c;
+  return SJ_OK;
+}
+
+void tc_destroy(TcContext *ctx) { delete ctx; }
+
+static sj_status make_map(TcContext *ctx, const void *base, int64_t rows, int64_t dp,
+                          int box_rows, unsigned char *out) {
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof m);
+  cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(dp * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = ctx->encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base),
+                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return SJ_ERR_CUDA;
+  static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
+  std::memcpy(out, &m, sizeof m);
+  return SJ_OK;
+}
+
+sj_status tc_make_maps(TcContext *ctx, const void *Ap, int64_t nA_pad, const void *Bp,
+                       int64_t nB_pad, int64_t dp, TcMaps *out) {
+  if (!ctx || !ctx->encode) return SJ_ERR_UNSUPPORTED;
+  if (dp % BK != 0 || nA_pad % BM != 0 || nB_pad % BN != 0) return SJ_ERR_INTERNAL;
+  sj_status s = make_map(ctx, Ap, nA_pad, dp, BM, out->a);
+  if (s != SJ_OK) return s;
+  return make_map(ctx, Bp, nB_pad, dp, BN, out->b);
+}
+
+cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, uint32_t flags,
+                            cudaStream_t st) {
+  if (a.n_units == 0) return cudaSuccess;
+  const size_t smem = sizeof(TcSmem) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(score_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  CUtensorMap ma, mb;
+  std::memcpy(&ma, maps->a, sizeof ma);
+  std::memcpy(&mb, maps->b, sizeof mb);
+  score_tc_kernel<<<grid, kThreads, smem, st>>>(ma, mb, a, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace sj

@@ -1,0 +1,119 @@
+// sj_internal.h -- host-side declarations shared by the library's translation
+// units (launchers and plan structures).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sj_device.cuh"
+
+namespace sj {
+
+enum class PackFormat { kF32, kBF16 };
+
+cudaError_t launch_prepare(const float *X, int64_t n, int64_t d, PackFormat fmt, void *Xp,
+                           int64_t n_pad, int64_t dp, RowMeta *meta, float *gmax,
+                           Counters *ctr, cudaStream_t st);
+
+// Everything the scoring kernels need for one join.
+struct ScoreArgs {
+  const void *Ap;          // packed A rows (stride dp elements), rows padded
+  const void *Bp;          // packed B rows
+  int64_t nA, nB, dp;      // true row counts, padded width
+  const RowMeta *metaA;    // per-row bounds of A
+  const float *gmaxB;      // device: max over B of {nrm, qnrm, qerr}
+  float acc_coef;          // accumulation error allowance per unit norm product
+  int k;                   // top-k (0: no top-k)
+  float tau_f;             // float tau rounded down (+inf: no threshold)
+  int n_splits;            // column splits per row block
+  int64_t tiles_per_split; // column tiles per split
+  int64_t n_units;         // row blocks x splits
+  float *heaps;            // [nA][n_splits][k]
+  Cand *band;              // [nA][n_splits][cap]
+  int cap;
+  int *band_cnt;           // [nA][n_splits]; < 0 marks overflow
+  ThrCand *thr;            // threshold candidates
+  unsigned long long thr_cap;
+  Counters *ctr;
+};
+
+// Tile sizes of the scoring kernels (rows x columns of one score tile).
+constexpr int kSimtBM = 128, kSimtBN = 128, kSimtBK = 16;
+constexpr int kTcBM = 128, kTcBN = 256;
+
+cudaError_t launch_score_simt(const ScoreArgs &a, int grid, cudaStream_t st);
+
+// Finalisation.
+struct TopkFinalArgs {
+  const float *A;          // original float32 rows (stride d)
+  const float *B;
+  int64_t nA, nB, d;
+  const RowMeta *metaA, *metaB;
+  const float *gmaxB;
+  float acc_coef;
+  int k, n_splits, cap;
+  const float *heaps;
+  const Cand *band;
+  const int *band_cnt;
+  float dot2_coef_key;     // Dot2 error bound per unit norm product, key units
+  int64_t *out_idx;
+  float *out_score;
+  int *overflow_rows;      // rows sent to the fallback pass
+  Counters *ctr;
+};
+cudaError_t launch_topk_finalize(const TopkFinalArgs &a, cudaStream_t st);
+
+struct TopkFallbackArgs {
+  const float *A, *B;
+  int64_t nA, nB, d;
+  const RowMeta *metaA, *metaB;
+  int k;
+  float dot2_coef_key;
+  const int *rows;         // rows to process
+  int n_rows;
+  void *scratch;           // n_rows x per_row_bytes
+  size_t per_row_bytes;
+  int64_t *out_idx;
+  float *out_score;
+  Counters *ctr;
+};
+size_t topk_fallback_row_bytes(int64_t nB);
+cudaError_t launch_topk_fallback(const TopkFallbackArgs &a, cudaStream_t st);
+
+struct ThrFinalArgs {
+  const float *A, *B;
+  int64_t nA, nB, d;
+  const RowMeta *metaA, *metaB;
+  float dot2_coef_key;
+  long long tau_key;       // ceil(tau 2^60)
+  Exact tau_exact;         // ceil(tau 2^298) in the exact format
+  const ThrCand *cand;
+  int64_t n_cand;
+  int64_t *row_count;      // [nA], zeroed by the caller
+  ThrCand *accepted;       // accepted pairs (score in v), capacity n_cand
+  Counters *ctr;
+};
+cudaError_t launch_thr_rescore(const ThrFinalArgs &a, cudaStream_t st);
+
+// Exclusive scan of n int64 values (in place allowed); total written to *total.
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t launch_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
+                                  void *scratch, cudaStream_t st);
+
+struct PairOut {  // layout of sj_pair
+  int64_t i, j;
+  float score;
+  int32_t pad;
+};
+cudaError_t launch_thr_scatter(const ThrCand *accepted, const int64_t *n_acc_dev,
+                               int64_t n_acc_cap, const int64_t *row_off, int64_t *row_fill,
+                               PairOut *out, cudaStream_t st);
+cudaError_t launch_thr_sort_rows(PairOut *out, const int64_t *row_off, const int64_t *row_count,
+                                 int64_t nA, int *big_rows, int *n_big, int big_cap,
+                                 cudaStream_t st);
+cudaError_t launch_thr_sort_big(PairOut *out, PairOut *tmp, const int64_t *row_off,
+                                const int64_t *row_count, const int *big_rows, const int *n_big,
+                                int n_big_host, cudaStream_t st);
+
+}  // namespace sj

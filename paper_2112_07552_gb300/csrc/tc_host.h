@@ -1,0 +1,27 @@
+// tc_host.h -- host side of the tensor-core scoring pass: TMA descriptors.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/sj.h"
+#include "sj_internal.h"
+
+namespace sj {
+
+struct TcContext;
+
+// Two TMA tensor maps (opaque 128-byte CUtensorMap objects) for the packed
+// A and B operands.
+struct TcMaps {
+  alignas(64) unsigned char a[128];
+  alignas(64) unsigned char b[128];
+};
+
+sj_status tc_create(TcContext **out);
+void tc_destroy(TcContext *ctx);
+sj_status tc_make_maps(TcContext *ctx, const void *Ap, int64_t nA_pad, const void *Bp,
+                       int64_t nB_pad, int64_t dp, TcMaps *out);
+cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, uint32_t flags,
+                            cudaStream_t st);
+
+}  // namespace sj

@@ -1,0 +1,279 @@
+"""Python binding of libsj.so (include/sj.h): argument marshalling only.
+
+Every step of the join runs inside the CUDA library; this module only turns
+torch tensors / numpy arrays into pointers and sizes, allocates outputs and
+maps status codes to exceptions.  If the library cannot be loaded the calls
+raise -- there is no CPU fallback.
+
+The C entry points are exposed under their own names (``sj_create``,
+``sj_topk``, ``sj_threshold``, ``sj_batch``, ``sj_contrastive_fwd``,
+``sj_backward``, ...) through :func:`lib`; :class:`SimilarityJoin` wraps a
+handle for torch users.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+SJ_OK = 0
+SJ_ERR_INVALID_ARG = 1
+SJ_ERR_NONFINITE = 2
+SJ_ERR_NOT_UNIT_NORM = 3
+SJ_ERR_CAPACITY = 4
+SJ_ERR_OOM = 5
+SJ_ERR_CUDA = 6
+SJ_ERR_TIMEOUT = 7
+SJ_ERR_UNSUPPORTED = 8
+SJ_ERR_INTERNAL = 9
+
+SJ_FP32, SJ_BF16, SJ_FP8_E4M3 = 0, 1, 2
+PRECISIONS = {"fp32": SJ_FP32, "bf16": SJ_BF16, "fp8": SJ_FP8_E4M3}
+
+SJ_FLAG_SYM_INFONCE = 0x1
+SJ_FLAG_DEBUG_TIMEOUT = 0x100
+
+# every symbol include/sj.h declares
+EXPORTS = ("sj_create", "sj_destroy", "sj_topk", "sj_threshold", "sj_batch",
+           "sj_contrastive_fwd", "sj_backward", "sj_status_string", "sj_version")
+
+I64, P = ctypes.c_int64, ctypes.c_void_p
+
+
+class SjConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", P), ("prec", ctypes.c_int),
+                ("d", I64), ("flags", ctypes.c_uint32), ("workspace_limit", ctypes.c_size_t)]
+
+
+class SjStats(ctypes.Structure):
+    _fields_ = [("ms_prepare", ctypes.c_double), ("ms_score", ctypes.c_double),
+                ("ms_select", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("n_candidates", I64), ("n_rescored", I64), ("n_exact", I64),
+                ("n_overflow_rows", I64), ("n_pairs", I64),
+                ("margin_max", ctypes.c_double), ("max_abs_err_lowprec", ctypes.c_double),
+                ("n_launches", I64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class SjPair(ctypes.Structure):
+    _fields_ = [("i", I64), ("j", I64), ("score", ctypes.c_float), ("_pad", ctypes.c_int32)]
+
+
+class SjJob(ctypes.Structure):
+    _fields_ = [("A", P), ("nA", I64), ("B", P), ("nB", I64), ("k", ctypes.c_int32),
+                ("tau", ctypes.c_double), ("topk_idx", P), ("topk_score", P), ("pairs", P),
+                ("capacity", I64), ("n_out", P)]
+
+
+class SJError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s failed: %s (status %d)" % (where, status_string(code), code))
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsj.so (building it in-tree with nvcc if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            _build.build()
+        L = ctypes.CDLL(path)
+        st = ctypes.c_int
+        L.sj_create.restype = st
+        L.sj_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(SjConfig)]
+        L.sj_destroy.restype = st
+        L.sj_destroy.argtypes = [P]
+        L.sj_topk.restype = st
+        L.sj_topk.argtypes = [P, P, I64, P, I64, ctypes.c_int32, P, P, ctypes.POINTER(SjStats)]
+        L.sj_threshold.restype = st
+        L.sj_threshold.argtypes = [P, P, I64, P, I64, ctypes.c_double, P, I64,
+                                   ctypes.POINTER(I64), ctypes.POINTER(SjStats)]
+        L.sj_batch.restype = st
+        L.sj_batch.argtypes = [P, ctypes.POINTER(SjJob), ctypes.c_int32, ctypes.POINTER(SjStats)]
+        L.sj_contrastive_fwd.restype = st
+        L.sj_contrastive_fwd.argtypes = [P, P, P, I64, ctypes.c_float, P, P]
+        L.sj_backward.restype = st
+        L.sj_backward.argtypes = [P, P, P, I64, ctypes.c_float, P, P, P, P]
+        L.sj_status_string.restype = ctypes.c_char_p
+        L.sj_status_string.argtypes = [ctypes.c_int]
+        L.sj_version.restype = ctypes.c_int
+        L.sj_version.argtypes = []
+        _lib = L
+        return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().sj_status_string(int(code)).decode()
+    except Exception:  # pragma: no cover - library missing
+        return "status %d" % code
+
+
+def _check(code: int, where: str):
+    if code != SJ_OK:
+        raise SJError(code, where)
+
+
+def _ptr(x) -> int:
+    """Pointer of a contiguous torch tensor or numpy array (device or host)."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("expected a torch tensor or numpy array")
+
+
+def _rows(x, d):
+    if x.ndim != 2 or x.shape[1] != d:
+        raise ValueError("expected an (n, %d) matrix, got %s" % (d, tuple(x.shape)))
+    return int(x.shape[0])
+
+
+class SimilarityJoin:
+    """A handle of the similarity join library bound to one device and stream.
+
+    Inputs are float32 (n, d) matrices of unit-norm rows, as CUDA tensors (used
+    in place) or host tensors / numpy arrays (staged by the library).
+    """
+
+    def __init__(self, d: int, prec: str = "bf16", device: int = 0, stream=None,
+                 flags: int = 0, workspace_limit: int = 0):
+        import torch
+        self.d = int(d)
+        self.prec = prec
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        cfg = SjConfig(self.device, P(stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                      else int(stream)),
+                       PRECISIONS[prec], self.d, int(flags), int(workspace_limit))
+        h = P()
+        _check(lib().sj_create(ctypes.byref(h), ctypes.byref(cfg)), "sj_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _out_like(self, A, shape, dtype):
+        import torch
+        dev = A.device if hasattr(A, "device") else torch.device("cpu")
+        return torch.empty(shape, dtype=dtype, device=dev)
+
+    def topk(self, A, B, k: int, with_stats: bool = False):
+        """(idx int64 [nA, k], score float32 [nA, k]) ordered (score desc, j asc)."""
+        import torch
+        nA, nB = _rows(A, self.d), _rows(B, self.d)
+        idx = self._out_like(A, (nA, k), torch.int64)
+        sc = self._out_like(A, (nA, k), torch.float32)
+        st = SjStats()
+        _check(lib().sj_topk(self._h, _ptr(A), nA, _ptr(B), nB, int(k), _ptr(idx), _ptr(sc),
+                             ctypes.byref(st)), "sj_topk")
+        return (idx, sc, st.as_dict()) if with_stats else (idx, sc)
+
+    def threshold(self, A, B, tau: float, capacity: int | None = None,
+                  with_stats: bool = False):
+        """(i int64, j int64, score float32) of every pair with s_ij >= tau."""
+        import torch
+        nA, nB = _rows(A, self.d), _rows(B, self.d)
+        if capacity is None:
+            capacity = max(1024, 8 * nA)
+        for _ in range(2):
+            buf = self._out_like(A, (max(int(capacity), 1), 3), torch.int64)
+            n = I64(0)
+            st = SjStats()
+            code = lib().sj_threshold(self._h, _ptr(A), nA, _ptr(B), nB, float(tau), _ptr(buf),
+                                      int(capacity), ctypes.byref(n), ctypes.byref(st))
+            if code == SJ_ERR_CAPACITY:
+                capacity = int(n.value)
+                continue
+            _check(code, "sj_threshold")
+            m = int(n.value)
+            i = buf[:m, 0]
+            j = buf[:m, 1]
+            s = buf[:m, 2:3].view(torch.float32)[:, 0]
+            return (i, j, s, st.as_dict()) if with_stats else (i, j, s)
+        raise SJError(SJ_ERR_CAPACITY, "sj_threshold")
+
+    def batch(self, jobs, with_stats: bool = False):
+        """Run independent joins in one call.
+
+        jobs: list of dicts with A, B and any of k (top-k) / tau (threshold,
+        with optional capacity).  Returns per job a dict with 'idx', 'score'
+        and/or 'i', 'j', 'pair_score'.
+        """
+        import torch
+        arr = (SjJob * max(1, len(jobs)))()
+        outs = []
+        keep = []
+        for q, jb in enumerate(jobs):
+            A, B = jb["A"], jb["B"]
+            nA, nB = _rows(A, self.d), _rows(B, self.d)
+            o = {}
+            arr[q].A, arr[q].nA, arr[q].B, arr[q].nB = _ptr(A), nA, _ptr(B), nB
+            if jb.get("k"):
+                o["idx"] = self._out_like(A, (nA, int(jb["k"])), torch.int64)
+                o["score"] = self._out_like(A, (nA, int(jb["k"])), torch.float32)
+                arr[q].k = int(jb["k"])
+                arr[q].topk_idx, arr[q].topk_score = _ptr(o["idx"]), _ptr(o["score"])
+            if jb.get("tau") is not None:
+                cap = int(jb.get("capacity", max(1024, 8 * nA)))
+                o["_buf"] = self._out_like(A, (max(cap, 1), 3), torch.int64)
+                o["_n"] = I64(0)
+                arr[q].tau = float(jb["tau"])
+                arr[q].pairs = _ptr(o["_buf"])
+                arr[q].capacity = cap
+                arr[q].n_out = ctypes.cast(ctypes.byref(o["_n"]), P)
+            outs.append(o)
+            keep.append((A, B))
+        st = SjStats()
+        _check(lib().sj_batch(self._h, arr, len(jobs), ctypes.byref(st)), "sj_batch")
+        for o in outs:
+            if "_buf" in o:
+                m = int(o["_n"].value)
+                buf = o.pop("_buf")
+                o.pop("_n")
+                o["i"], o["j"] = buf[:m, 0], buf[:m, 1]
+                o["pair_score"] = buf[:m, 2:3].view(torch.float32)[:, 0]
+        return (outs, st.as_dict()) if with_stats else outs

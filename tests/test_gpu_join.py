@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA join through the C ABI against the oracle.
+
+The bar is exact: identical index sets and orders, and bit-identical float32
+scores (each the round-to-nearest-even of the exact dot product), for both the
+tensor-core (bf16) and the plain FP32 scoring pass.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_07552_gb300 import datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECS = ("bf16", "fp32")
+
+
+@pytest.fixture(scope="module")
+def sjmod():
+    from paper_2112_07552_gb300 import _build, sj
+    _build.build()
+    return sj
+
+
+_handles = {}
+
+
+def join(sjmod, d, prec):
+    key = (d, prec)
+    if key not in _handles:
+        _handles[key] = sjmod.SimilarityJoin(d, prec=prec, device=0)
+    return _handles[key]
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def assert_topk(got_idx, got_s, A, B, k, rows=None):
+    idx, s32, _ = oracle.topk(A, B, k, rows=rows)
+    gi = got_idx.cpu().numpy() if hasattr(got_idx, "cpu") else got_idx
+    gs = got_s.cpu().numpy() if hasattr(got_s, "cpu") else got_s
+    if rows is not None:
+        gi, gs = gi[rows], gs[rows]
+    bad = np.nonzero((gi != idx).any(axis=1) | (gs.view(np.uint32) != s32.view(np.uint32)).any(axis=1))[0]
+    assert bad.size == 0, "rows %s differ: got %s %s want %s %s" % (
+        bad[:5], gi[bad[:1]], gs[bad[:1]], idx[bad[:1]], s32[bad[:1]])
+
+
+def assert_thr(got, A, B, tau):
+    gi, gj, gs = [t.cpu().numpy() for t in got]
+    wi, wj, ws, _ = oracle.threshold(A, B, tau, want_s64=False)
+    assert gi.shape == wi.shape, (gi.shape, wi.shape)
+    assert np.array_equal(gi, wi) and np.array_equal(gj, wj)
+    assert np.array_equal(gs.view(np.uint32), ws.view(np.uint32))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fp32_config_full(sjmod, prec):
+    # 2,000 x 2,000, d = 256, 200 clusters, sigma = 0.1, k = 10, tau = 0.8, seed 0
+    A = datagen.clustered(2000, 256, 200, 0.1, seed=0, stream=0)
+    B = datagen.clustered(2000, 256, 200, 0.1, seed=0, stream=1)
+    J = join(sjmod, 256, prec)
+    idx, sc = J.topk(dev(A), dev(B), 10)
+    assert_topk(idx, sc, A, B, 10)
+    assert_thr(J.threshold(dev(A), dev(B), 0.8), A, B, 0.8)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nA,nB,d", [(1, 1, 1), (1, 300, 3), (127, 129, 100), (129, 257, 64),
+                                     (255, 511, 257), (300, 1000, 33), (513, 700, 128)])
+def test_ragged_sizes(sjmod, prec, nA, nB, d):
+    A = datagen.clustered(nA, d, max(1, nA // 10), 0.2, seed=3, stream=0)
+    B = datagen.clustered(nB, d, max(1, nA // 10), 0.2, seed=3, stream=1)
+    J = join(sjmod, d, prec)
+    for k in (1, 5, 37):
+        idx, sc = J.topk(dev(A), dev(B), k)
+        assert_topk(idx, sc, A, B, k)
+    for tau in (0.0, 0.5, 0.9):
+        assert_thr(J.threshold(dev(A), dev(B), tau), A, B, tau)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_k_larger_than_B_pads(sjmod, prec):
+    A = datagen.unit_rows(40, 16, 1, 0)
+    B = datagen.unit_rows(6, 16, 1, 1)
+    J = join(sjmod, 16, prec)
+    idx, sc = J.topk(dev(A), dev(B), 9)
+    assert_topk(idx, sc, A, B, 9)
+    assert (idx[:, 6:] == -1).all() and torch.isinf(sc[:, 6:]).all()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_self_join_invariants(sjmod, prec):
+    X = datagen.clustered(700, 64, 30, 0.1, seed=4)
+    J = join(sjmod, 64, prec)
+    dX = dev(X)
+    idx, sc = J.topk(dX, dX, 12)
+    assert_topk(idx, sc, X, X, 12)
+    # own top-1
+    top1 = idx[:, 0].cpu().numpy()
+    assert np.all(top1 <= np.arange(700))
+    i, j, s = J.threshold(dX, dX, 0.9)
+    assert_thr((i, j, s), X, X, 0.9)
+    # symmetry of the pair set
+    pairs = set(zip(i.cpu().tolist(), j.cpu().tolist()))
+    assert all((b, a) in pairs for a, b in pairs)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_exact_ties_duplicates_and_onehot(sjmod, prec):
+    # one-hot rows (Sec. 3.1): scores exactly 0/1, massive exact ties
+    ka = datagen.keys(300, 12, 0, 0)
+    kb = datagen.keys(900, 12, 0, 1)
+    A, B = datagen.one_hot(ka, 12), datagen.one_hot(kb, 12)
+    J = join(sjmod, 12, prec)
+    idx, sc = J.topk(dev(A), dev(B), 10)
+    assert_topk(idx, sc, A, B, 10)
+    assert_thr(J.threshold(dev(A), dev(B), 1.0), A, B, 1.0)
+    assert_thr(J.threshold(dev(A), dev(B), 2.0 ** -30), A, B, 2.0 ** -30)
+    # duplicated rows in B
+    X = datagen.unit_rows(64, 40, 5, 0)
+    Y = np.repeat(datagen.unit_rows(50, 40, 5, 1), 3, axis=0)
+    J2 = join(sjmod, 40, prec)
+    idx, sc = J2.topk(dev(X), dev(Y), 8)
+    assert_topk(idx, sc, X, Y, 8)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_hadamard_and_inclusive_tau(sjmod, prec):
+    H = np.array([[1.0]])
+    while H.shape[0] < 256:
+        H = np.block([[H, H], [H, -H]])
+    H = (H / 16.0).astype(np.float32)
+    A, B = H[:100], np.concatenate([H[50:200], -H[:30]])
+    J = join(sjmod, 256, prec)
+    idx, sc = J.topk(dev(A), dev(B), 4)
+    assert_topk(idx, sc, A, B, 4)
+    for tau in (1.0, 0.0, -1.0):
+        assert_thr(J.threshold(dev(A), dev(B), tau), A, B, tau)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_host_pointers(sjmod, prec):
+    A = datagen.clustered(333, 48, 20, 0.1, seed=6, stream=0)
+    B = datagen.clustered(444, 48, 20, 0.1, seed=6, stream=1)
+    J = join(sjmod, 48, prec)
+    idx, sc = J.topk(torch.from_numpy(A), torch.from_numpy(B), 6)
+    assert idx.device.type == "cpu"
+    assert_topk(idx, sc, A, B, 6)
+    assert_thr(J.threshold(torch.from_numpy(A), torch.from_numpy(B), 0.7), A, B, 0.7)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_validation_errors(sjmod, prec):
+    J = join(sjmod, 8, prec)
+    A = datagen.unit_rows(10, 8, 0, 0)
+    bad = A.copy()
+    bad[3, 2] = np.nan
+    with pytest.raises(sjmod.SJError) as e:
+        J.topk(dev(bad), dev(A), 2)
+    assert e.value.code == sjmod.SJ_ERR_NONFINITE
+    bad = A.copy()
+    bad[1] *= 1.01
+    with pytest.raises(sjmod.SJError) as e:
+        J.threshold(dev(A), dev(bad), 0.5)
+    assert e.value.code == sjmod.SJ_ERR_NOT_UNIT_NORM
+    # the handle stays usable
+    idx, sc = J.topk(dev(A), dev(A), 3)
+    assert_topk(idx, sc, A, A, 3)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_capacity_reports_required_count(sjmod, prec):
+    import ctypes
+    A = datagen.clustered(200, 32, 5, 0.1, seed=8, stream=0)
+    B = datagen.clustered(300, 32, 5, 0.1, seed=8, stream=1)
+    wi, _, _, _ = oracle.threshold(A, B, 0.5, want_s64=False)
+    assert len(wi) > 10
+    J = join(sjmod, 32, prec)
+    out = torch.empty((10, 3), dtype=torch.int64, device="cuda")
+    n = sjmod.I64(0)
+    code = sjmod.lib().sj_threshold(J.handle, dev(A).data_ptr(), 200, dev(B).data_ptr(), 300,
+                                    0.5, out.data_ptr(), 10, ctypes.byref(n), None)
+    assert code == sjmod.SJ_ERR_CAPACITY and n.value == len(wi)
+
+
+def test_empty_inputs(sjmod):
+    J = join(sjmod, 8, "bf16")
+    A = datagen.unit_rows(5, 8, 0, 0)
+    E = np.zeros((0, 8), np.float32)
+    idx, sc = J.topk(dev(A), dev(E), 3)
+    assert (idx == -1).all() and torch.isinf(sc).all()
+    idx, sc = J.topk(dev(E), dev(A), 3)
+    assert idx.shape == (0, 3)
+    i, j, s = J.threshold(dev(A), dev(E), 0.1)
+    assert i.numel() == 0
+
+
+def test_debug_timeout_returns_status_and_context_survives(sjmod):
+    J = sjmod.SimilarityJoin(64, prec="bf16", device=0, flags=sjmod.SJ_FLAG_DEBUG_TIMEOUT)
+    A = datagen.unit_rows(300, 64, 0, 0)
+    with pytest.raises(sjmod.SJError) as e:
+        J.topk(dev(A), dev(A), 4)
+    assert e.value.code == sjmod.SJ_ERR_TIMEOUT
+    J.close()
+    # the context is still usable afterwards
+    J2 = join(sjmod, 64, "bf16")
+    idx, sc = J2.topk(dev(A), dev(A), 4)
+    assert_topk(idx, sc, A, A, 4)
+
+
+def test_batch_matches_single_calls(sjmod):
+    J = join(sjmod, 64, "bf16")
+    jobs, data = [], []
+    for q, (na, nb) in enumerate([(100, 150), (1, 700), (300, 20), (257, 257)]):
+        A = datagen.clustered(na, 64, 10, 0.1, seed=20 + q, stream=0)
+        B = datagen.clustered(nb, 64, 10, 0.1, seed=20 + q, stream=1)
+        data.append((A, B))
+        jobs.append({"A": dev(A), "B": dev(B), "k": 5, "tau": 0.8})
+    outs = J.batch(jobs)
+    for (A, B), o in zip(data, outs):
+        assert_topk(o["idx"], o["score"], A, B, 5)
+        assert_thr((o["i"], o["j"], o["pair_score"]), A, B, 0.8)
