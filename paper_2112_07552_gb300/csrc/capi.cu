@@ -474,7 +474,8 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
         d_idx = static_cast<int64_t *>(ar.take((size_t)nA * k * 8));
         d_score = static_cast<float *>(ar.take((size_t)nA * k * 4));
       }
-      if (!heaps || !band || !band_cnt || !ovf || !d_idx || !d_score) return SJ_ERR_INTERNAL;
+      if (!heaps || !band || !band_cnt || !ovf || (nA > 0 && (!d_idx || !d_score)))
+        return SJ_ERR_INTERNAL;
     }
     ThrCand *cand = nullptr, *accd = nullptr;
     int64_t *row_count = nullptr, *row_off = nullptr, *row_fill = nullptr, *total = nullptr;

@@ -241,39 +241,62 @@ class SimilarityJoin:
 
         jobs: list of dicts with A, B and any of k (top-k) / tau (threshold,
         with optional capacity).  Returns per job a dict with 'idx', 'score'
-        and/or 'i', 'j', 'pair_score'.
+        and/or 'i', 'j', 'pair_score'.  Jobs whose pairs exceed their capacity
+        are issued once more with the required capacity.
         """
         import torch
-        arr = (SjJob * max(1, len(jobs)))()
-        outs = []
-        keep = []
+        caps = {}
         for q, jb in enumerate(jobs):
-            A, B = jb["A"], jb["B"]
-            nA, nB = _rows(A, self.d), _rows(B, self.d)
-            o = {}
-            arr[q].A, arr[q].nA, arr[q].B, arr[q].nB = _ptr(A), nA, _ptr(B), nB
-            if jb.get("k"):
-                o["idx"] = self._out_like(A, (nA, int(jb["k"])), torch.int64)
-                o["score"] = self._out_like(A, (nA, int(jb["k"])), torch.float32)
-                arr[q].k = int(jb["k"])
-                arr[q].topk_idx, arr[q].topk_score = _ptr(o["idx"]), _ptr(o["score"])
             if jb.get("tau") is not None:
-                cap = int(jb.get("capacity", max(1024, 8 * nA)))
-                o["_buf"] = self._out_like(A, (max(cap, 1), 3), torch.int64)
-                o["_n"] = I64(0)
-                arr[q].tau = float(jb["tau"])
-                arr[q].pairs = _ptr(o["_buf"])
-                arr[q].capacity = cap
-                arr[q].n_out = ctypes.cast(ctypes.byref(o["_n"]), P)
-            outs.append(o)
-            keep.append((A, B))
-        st = SjStats()
-        _check(lib().sj_batch(self._h, arr, len(jobs), ctypes.byref(st)), "sj_batch")
-        for o in outs:
-            if "_buf" in o:
-                m = int(o["_n"].value)
-                buf = o.pop("_buf")
-                o.pop("_n")
-                o["i"], o["j"] = buf[:m, 0], buf[:m, 1]
-                o["pair_score"] = buf[:m, 2:3].view(torch.float32)[:, 0]
-        return (outs, st.as_dict()) if with_stats else outs
+                nA, nB = _rows(jb["A"], self.d), _rows(jb["B"], self.d)
+                caps[q] = int(jb.get("capacity", min(nA * nB, max(1024, 8 * nA))))
+        todo = list(range(len(jobs)))
+        outs = [None] * len(jobs)
+        total = SjStats()
+        for _ in range(2):
+            arr = (SjJob * max(1, len(todo)))()
+            cur = []
+            for slot, q in enumerate(todo):
+                jb = jobs[q]
+                A, B = jb["A"], jb["B"]
+                nA, nB = _rows(A, self.d), _rows(B, self.d)
+                o = {}
+                arr[slot].A, arr[slot].nA, arr[slot].B, arr[slot].nB = _ptr(A), nA, _ptr(B), nB
+                if jb.get("k"):
+                    o["idx"] = self._out_like(A, (nA, int(jb["k"])), torch.int64)
+                    o["score"] = self._out_like(A, (nA, int(jb["k"])), torch.float32)
+                    arr[slot].k = int(jb["k"])
+                    arr[slot].topk_idx, arr[slot].topk_score = _ptr(o["idx"]), _ptr(o["score"])
+                if q in caps:
+                    o["_buf"] = self._out_like(A, (max(caps[q], 1), 3), torch.int64)
+                    o["_n"] = I64(0)
+                    arr[slot].tau = float(jobs[q]["tau"])
+                    arr[slot].pairs = _ptr(o["_buf"])
+                    arr[slot].capacity = caps[q]
+                    arr[slot].n_out = ctypes.cast(ctypes.byref(o["_n"]), P)
+                cur.append((q, o))
+            st = SjStats()
+            code = lib().sj_batch(self._h, arr, len(todo), ctypes.byref(st))
+            for name, _t in SjStats._fields_:
+                setattr(total, name, getattr(total, name) + getattr(st, name))
+            if code not in (SJ_OK, SJ_ERR_CAPACITY):
+                _check(code, "sj_batch")
+            retry = []
+            for q, o in cur:
+                if "_buf" in o and int(o["_n"].value) > caps[q]:
+                    caps[q] = int(o["_n"].value)
+                    retry.append(q)
+                    continue
+                if "_buf" in o:
+                    m = int(o["_n"].value)
+                    buf = o.pop("_buf")
+                    o.pop("_n")
+                    o["i"], o["j"] = buf[:m, 0], buf[:m, 1]
+                    o["pair_score"] = buf[:m, 2:3].view(torch.float32)[:, 0]
+                outs[q] = o
+            if not retry:
+                break
+            todo = retry
+        if any(o is None for o in outs):
+            raise SJError(SJ_ERR_CAPACITY, "sj_batch")
+        return (outs, total.as_dict()) if with_stats else outs

@@ -181,7 +181,8 @@ def test_capacity_reports_required_count(sjmod, prec):
     J = join(sjmod, 32, prec)
     out = torch.empty((10, 3), dtype=torch.int64, device="cuda")
     n = sjmod.I64(0)
-    code = sjmod.lib().sj_threshold(J.handle, dev(A).data_ptr(), 200, dev(B).data_ptr(), 300,
+    dA, dB = dev(A), dev(B)  # keep both alive for the duration of the call
+    code = sjmod.lib().sj_threshold(J.handle, dA.data_ptr(), 200, dB.data_ptr(), 300,
                                     0.5, out.data_ptr(), 10, ctypes.byref(n), None)
     assert code == sjmod.SJ_ERR_CAPACITY and n.value == len(wi)
 
