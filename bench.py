@@ -330,6 +330,9 @@ def main():
         "n_pairs": n_pairs,
         "n_candidates": int(stats[-1].n_candidates),
         "n_exact": int(stats[-1].n_exact),
+        "n_rescored": int(stats[-1].n_rescored),
+        "n_tier2_rows": int(stats[-1].n_tier2_rows),
+        "n_overflow_rows": int(stats[-1].n_overflow_rows),
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,

@@ -68,6 +68,9 @@ typedef enum {
 
 /* cfg.flags */
 #define SJ_FLAG_SYM_INFONCE 0x1u   /* contrastive: add the column (B->A) term */
+#define SJ_FLAG_SINGLE_SPLIT 0x2u  /* one column split per row block (each row's
+                                      candidates collected in one list; lowers
+                                      parallelism when nA is small) */
 #define SJ_FLAG_DEBUG_TIMEOUT 0x100u /* test hook: device waits give up at once */
 
 typedef struct {
@@ -97,11 +100,12 @@ typedef struct {
   int64_t n_candidates;      /* pairs that passed the low-precision filter */
   int64_t n_rescored;        /* pairs rescored with the compensated FP32 dot */
   int64_t n_exact;           /* pairs evaluated with the exact accumulator */
-  int64_t n_overflow_rows;   /* rows whose candidate list needed a second pass */
+  int64_t n_overflow_rows;   /* rows re-ranked against all of B (fallback) */
   int64_t n_pairs;           /* threshold: pairs emitted */
   double margin_max;         /* reserved (0) */
   double max_abs_err_lowprec;/* max |s~ - s| seen over rescored top-k candidates */
   int64_t n_launches;        /* kernels this call launched */
+  int64_t n_tier2_rows;      /* rows finalised with the large candidate tier */
 } sj_stats;
 
 typedef struct sj_handle sj_handle;

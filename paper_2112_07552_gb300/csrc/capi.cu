@@ -224,13 +224,16 @@ JoinPlan make_plan(const sj_handle *h, int64_t nA, int64_t nB, int k) {
   int64_t ct = (std::max<int64_t>(nB, 1) + p.pp.BN - 1) / p.pp.BN;
   int64_t want_units = 2 * (int64_t)h->sm_count;
   int64_t S = (want_units + rb - 1) / rb;
-  if (S < 1) S = 1;
+  if (S < 1 || (h->cfg.flags & SJ_FLAG_SINGLE_SPLIT)) S = 1;
   if (S > ct) S = ct;
-  if (k > 0 && S * k > 1024) S = std::max<int64_t>(1, 1024 / k);
+  // the finaliser merges S*k heap values in shared memory: S*k <= 512
+  if (k > 0 && S * k > 512) S = std::max<int64_t>(1, 512 / k);
   p.tiles_per_split = (ct + S - 1) / S;
   p.S = (int)((ct + p.tiles_per_split - 1) / p.tiles_per_split);
   p.n_units = rb * p.S;
-  p.cap = (int)round_up(2 * (int64_t)k + 128, 32);
+  // band list per row: the k best plus the margin band (often ~60-150 rows
+  // for BF16 scores of d = 768 embeddings near the k-th score)
+  p.cap = (int)round_up(4 * (int64_t)k + 256, 32);
   return p;
 }
 
@@ -367,6 +370,7 @@ void fill_common_stats(sj_stats *st, const Counters &c) {
   st->n_rescored = (int64_t)c.n_rescored;
   st->n_exact = (int64_t)c.n_exact;
   st->n_overflow_rows = (int64_t)c.overflow_rows;
+  st->n_tier2_rows = (int64_t)c.tier2_rows;
   float me;
   std::memcpy(&me, &c.max_err_bits, sizeof me);
   st->max_abs_err_lowprec = me;
@@ -377,6 +381,116 @@ sj_status check_join_args(sj_handle *h, const float *A, int64_t nA, const float 
   if (nA < 0 || nB < 0) return SJ_ERR_INVALID_ARG;
   if ((nA > 0 && !A) || (nB > 0 && !B)) return SJ_ERR_INVALID_ARG;
   if (nA >= (1ll << 31) - 1024 || nB >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
+  return SJ_OK;
+}
+
+// Scratch that the fallback takes from the workspace if it fits, else from a
+// temporary allocation released before the call returns.
+struct Scratch {
+  void *p = nullptr;
+  bool own = false;
+  ~Scratch() {
+    if (own) cudaFree(p);
+  }
+  cudaError_t get(Arena &ar, size_t bytes) {
+    p = ar.take(bytes);
+    if (p) return cudaSuccess;
+    own = true;
+    return cudaMalloc(&p, bytes);
+  }
+};
+
+// Rows whose candidates did not fit: rescan all of B with Dot2 against the
+// row's key bound, then rank the lists (shared memory, or global memory for
+// very long ones).  Lists cut off at their capacity are rescanned once more
+// with the capacity they need.
+sj_status topk_fallback(sj_handle *h, const Prepared &P, const JoinPlan &pl, const int *rows,
+                        const long long *keys, int n_rows, int k, int64_t *d_idx, float *d_score,
+                        Arena &ar, int64_t &launches) {
+  cudaStream_t stm = h->stream;
+  const int64_t nB = pl.nB;
+  int cap = (int)std::min<int64_t>(nB, 4096);
+  Scratch lists_s, count_s, redo_s, big_s, rows2_s, keys2_s;
+  SJ_CUDA(count_s.get(ar, (size_t)n_rows * 4 + 256));
+  SJ_CUDA(redo_s.get(ar, (size_t)n_rows * 4 + 256));
+  SJ_CUDA(big_s.get(ar, (size_t)n_rows * 4 + 256));
+  SJ_CUDA(rows2_s.get(ar, (size_t)n_rows * 4 + 256));
+  SJ_CUDA(keys2_s.get(ar, (size_t)n_rows * 8 + 256));
+  const int *cur_rows = rows;
+  const long long *cur_keys = keys;
+  int n_cur = n_rows;
+  for (int pass = 0; pass < 2 && n_cur > 0; ++pass) {
+    Scratch lists;
+    SJ_CUDA(lists.get(ar, (size_t)n_cur * cap * sizeof(KeyCand)));
+    int *count = static_cast<int *>(count_s.p);
+    SJ_CUDA(cudaMemsetAsync(count, 0, (size_t)n_cur * 4, stm));
+    SJ_CUDA(cudaMemsetAsync(&P.ctr->redo_rows, 0, 4 * sizeof(unsigned), stm));
+    RescanArgs ra{};
+    ra.A = P.A;
+    ra.B = P.B;
+    ra.nB = nB;
+    ra.d = pl.d;
+    ra.metaA = P.metaA;
+    ra.metaB = P.metaB;
+    ra.dot2_coef_key = dot2_coef_key(pl.d);
+    ra.rows = cur_rows;
+    ra.keys = cur_keys;
+    ra.n_rows = n_cur;
+    ra.lists = static_cast<KeyCand *>(lists.p);
+    ra.count = count;
+    ra.cap = cap;
+    ra.ctr = P.ctr;
+    SJ_CUDA(launch_topk_rescan(ra, stm));
+    RankListArgs la{};
+    la.A = P.A;
+    la.B = P.B;
+    la.d = pl.d;
+    la.k = k;
+    la.rows = cur_rows;
+    la.n_rows = n_cur;
+    la.lists = ra.lists;
+    la.count = count;
+    la.cap = cap;
+    la.redo = static_cast<int *>(redo_s.p);
+    la.big = static_cast<int *>(big_s.p);
+    la.out_idx = d_idx;
+    la.out_score = d_score;
+    la.ctr = P.ctr;
+    SJ_CUDA(launch_topk_rank_lists(la, stm));
+    launches += 2;
+    sj_status s = read_counters(h, P.ctr);
+    if (s != SJ_OK) return s;
+    const unsigned n_big = h->h_ctr->big_rows;
+    if (n_big > 0) {
+      const size_t per_row = topk_rank_global_row_bytes(cap);
+      Scratch g;
+      SJ_CUDA(g.get(ar, (size_t)n_big * per_row));
+      SJ_CUDA(launch_topk_rank_global(la, la.big, (int)n_big, g.p, per_row, stm));
+      launches += 1;
+      SJ_CUDA(cudaStreamSynchronize(stm));
+    }
+    const unsigned n_redo = h->h_ctr->redo_rows;
+    if (n_redo == 0) break;
+    if (pass == 1) return SJ_ERR_INTERNAL;  // a full-capacity rescan cannot be cut off
+    // gather the rows (and keys) to redo, with the capacity they need
+    std::vector<int> slots(n_redo), hrows(n_redo), all_rows(n_cur);
+    std::vector<long long> hkeys(n_redo), all_keys(n_cur);
+    SJ_CUDA(cudaMemcpyAsync(slots.data(), la.redo, n_redo * 4, cudaMemcpyDeviceToHost, stm));
+    SJ_CUDA(cudaMemcpyAsync(all_rows.data(), cur_rows, (size_t)n_cur * 4, cudaMemcpyDeviceToHost, stm));
+    SJ_CUDA(cudaMemcpyAsync(all_keys.data(), cur_keys, (size_t)n_cur * 8, cudaMemcpyDeviceToHost, stm));
+    SJ_CUDA(cudaStreamSynchronize(stm));
+    for (unsigned q = 0; q < n_redo; ++q) {
+      hrows[q] = all_rows[slots[q]];
+      hkeys[q] = all_keys[slots[q]];
+    }
+    SJ_CUDA(cudaMemcpyAsync(rows2_s.p, hrows.data(), n_redo * 4, cudaMemcpyHostToDevice, stm));
+    SJ_CUDA(cudaMemcpyAsync(keys2_s.p, hkeys.data(), n_redo * 8, cudaMemcpyHostToDevice, stm));
+    SJ_CUDA(cudaStreamSynchronize(stm));
+    cur_rows = static_cast<int *>(rows2_s.p);
+    cur_keys = static_cast<long long *>(keys2_s.p);
+    n_cur = (int)n_redo;
+    cap = (int)std::min<int64_t>(nB, (int64_t)h->h_ctr->redo_cap);
+  }
   return SJ_OK;
 }
 
@@ -445,7 +559,7 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
       bytes += slots * k * 4 + 256;                          // heaps
       bytes += slots * (size_t)pl.cap * sizeof(Cand) + 256;  // band lists
       bytes += slots * 4 + 256;                              // band counts
-      bytes += rows1 * 4 + 256;                              // overflow rows
+      bytes += rows1 * 16 + 768;                             // tier-2/overflow rows, keys
       if (ot_host) bytes += (size_t)nA * k * 12 + 512;
     }
     if (r.thr) {
@@ -462,7 +576,8 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
     launches += (P.Bp == P.Ap) ? 1 : 2;
     float *heaps = nullptr;
     Cand *band = nullptr;
-    int *band_cnt = nullptr, *ovf = nullptr;
+    int *band_cnt = nullptr, *ovf = nullptr, *tier2 = nullptr;
+    long long *ovf_key = nullptr;
     int64_t *d_idx = r.out_idx;
     float *d_score = r.out_score;
     if (k > 0) {
@@ -470,11 +585,14 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
       band = static_cast<Cand *>(ar.take(slots * (size_t)pl.cap * sizeof(Cand)));
       band_cnt = static_cast<int *>(ar.take(slots * 4));
       ovf = static_cast<int *>(ar.take(rows1 * 4));
+      tier2 = static_cast<int *>(ar.take(rows1 * 4));
+      ovf_key = static_cast<long long *>(ar.take(rows1 * 8));
       if (ot_host) {
         d_idx = static_cast<int64_t *>(ar.take((size_t)nA * k * 8));
         d_score = static_cast<float *>(ar.take((size_t)nA * k * 4));
       }
-      if (!heaps || !band || !band_cnt || !ovf || (nA > 0 && (!d_idx || !d_score)))
+      if (!heaps || !band || !band_cnt || !ovf || !tier2 || !ovf_key ||
+          (nA > 0 && (!d_idx || !d_score)))
         return SJ_ERR_INTERNAL;
     }
     ThrCand *cand = nullptr, *accd = nullptr;
@@ -557,7 +675,9 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
       fa.dot2_coef_key = dot2_coef_key(pl.d);
       fa.out_idx = d_idx;
       fa.out_score = d_score;
+      fa.tier2_rows = tier2;
       fa.overflow_rows = ovf;
+      fa.overflow_key = ovf_key;
       fa.ctr = P.ctr;
       SJ_CUDA(launch_topk_finalize(fa, stm));
       launches += 1;
@@ -565,47 +685,17 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
       if (s != SJ_OK) return s;
       s = flags_status(h->h_ctr->err_flags);
       if (s != SJ_OK) return s;
+      const unsigned n_t2 = h->h_ctr->tier2_rows;
+      if (n_t2 > 0) {
+        SJ_CUDA(launch_topk_finalize_tier2(fa, (int)n_t2, stm));
+        launches += 1;
+        s = read_counters(h, P.ctr);
+        if (s != SJ_OK) return s;
+      }
       const unsigned n_ovf = h->h_ctr->overflow_rows;
       if (n_ovf > 0) {
-        // rank all of B for each overflowing row, in chunks that fit
-        const size_t per_row = topk_fallback_row_bytes(nB);
-        const size_t avail = h->ws_size > ar.used ? h->ws_size - ar.used - 256 : 0;
-        int chunk = (int)std::min<size_t>(n_ovf, std::max<size_t>(1, avail / per_row));
-        void *scratch = (size_t)chunk * per_row <= avail ? ar.take((size_t)chunk * per_row) : nullptr;
-        bool own = false;
-        if (!scratch) {
-          chunk = (int)std::min<unsigned>(n_ovf, 64);
-          if (cudaMalloc(&scratch, (size_t)chunk * per_row) != cudaSuccess) {
-            cudaGetLastError();
-            return SJ_ERR_OOM;
-          }
-          own = true;
-        }
-        cudaError_t e = cudaSuccess;
-        for (unsigned r0 = 0; r0 < n_ovf && e == cudaSuccess; r0 += chunk) {
-          TopkFallbackArgs fb{};
-          fb.A = P.A;
-          fb.B = P.B;
-          fb.nA = nA;
-          fb.nB = nB;
-          fb.d = pl.d;
-          fb.metaA = P.metaA;
-          fb.metaB = P.metaB;
-          fb.k = k;
-          fb.dot2_coef_key = fa.dot2_coef_key;
-          fb.rows = ovf + r0;
-          fb.n_rows = (int)std::min<unsigned>(chunk, n_ovf - r0);
-          fb.scratch = scratch;
-          fb.per_row_bytes = per_row;
-          fb.out_idx = d_idx;
-          fb.out_score = d_score;
-          fb.ctr = P.ctr;
-          e = launch_topk_fallback(fb, stm);
-          launches += 1;
-        }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
-        if (own) cudaFree(scratch);
-        if (e != cudaSuccess) return cuda_status(e);
+        s = topk_fallback(h, P, pl, ovf, ovf_key, (int)n_ovf, k, d_idx, d_score, ar, launches);
+        if (s != SJ_OK) return s;
       }
       if (ot_host) {
         SJ_CUDA(cudaMemcpyAsync(r.out_idx, d_idx, (size_t)nA * k * 8, cudaMemcpyDeviceToHost, stm));

@@ -48,6 +48,7 @@ struct alignas(1024) TcSmem {
   uint64_t tmem_empty[2];
   uint64_t drain;
   uint64_t never;  // debug-timeout hook: nothing ever arrives here
+  float stage[BM][33];  // epilogue slow-path staging, one row per thread
   uint32_t tmem_base;
   int abort;
 };
@@ -335,15 +336,34 @@ __global__ void __launch_bounds__(kThreads, 1)
           float v[32];
           tmem_ld32(taddr + c0, v);
           if (owner) {
-            float mx = v[0];
+            // fast path: one compare per 32 scores (balanced max tree)
+            float m16[16];
 #pragma unroll
-            for (int q = 1; q < 32; ++q) mx = fmaxf(mx, v[q]);
+            for (int q = 0; q < 16; ++q) m16[q] = fmaxf(v[2 * q], v[2 * q + 1]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) m16[q] = fmaxf(m16[2 * q], m16[2 * q + 1]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) m16[q] = fmaxf(m16[2 * q], m16[2 * q + 1]);
+            const float mx = fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3]));
             const float tmin = fminf(rc.f.theta, rc.f.tau_lo);
             if (mx >= tmin) {
-              const int64_t jb = col0 + c0;
-#pragma unroll 1
+              // slow path: visit only the passing columns; the values go
+              // through shared memory so the register array is never indexed
+              // dynamically (which would put it in local memory)
+              uint32_t mask = 0;
+              float *stg = sm.stage[r_in_tile];
+#pragma unroll
               for (int q = 0; q < 32; ++q) {
-                if (jb + q < a.nB) row_visit(rc, a, v[q], (int32_t)(jb + q));
+                mask |= (v[q] >= tmin ? 1u : 0u) << q;
+                stg[q] = v[q];
+              }
+              const int64_t jb = col0 + c0;
+              const int64_t rem = a.nB - jb;  // valid columns in this chunk
+              if (rem < 32) mask &= rem <= 0 ? 0u : ((1u << (uint32_t)rem) - 1u);
+              while (mask) {
+                const int q = __ffs(mask) - 1;
+                mask &= mask - 1;
+                row_visit(rc, a, stg[q], (int32_t)(jb + q));
               }
             }
           }

@@ -61,6 +61,10 @@ struct Counters {
   unsigned int err_flags;           // kErr* bits
   unsigned int overflow_rows;       // rows needing the fallback pass
   unsigned int max_err_bits;        // max |s~ - s| as float bits (>= 0)
+  unsigned int tier2_rows;          // rows for the second finalisation tier
+  unsigned int redo_rows;           // rescan lists cut off at their capacity
+  unsigned int redo_cap;            // capacity they need
+  unsigned int big_rows;            // rescan lists for the global-memory ranker
   unsigned int pad;
 };
 
@@ -89,19 +93,31 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // Warp-cooperative Dot2 over d entries (lane l takes k = l, l+32, ...).
 // Returns the unevaluated sum hi + lo, identical on every lane.  a may point
 // to shared or global memory.
+__device__ __forceinline__ void dot2_step(float x, float y, float &s, float &c) {
+  float p = __fmul_rn(x, y);
+  float e = __fmaf_rn(x, y, -p);
+  float t, q;
+  two_sum(s, p, t, q);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
 __device__ __forceinline__ void dot2_warp(const float *a, const float *b, int64_t d,
                                           float &hi, float &lo) {
   const int lane = threadIdx.x & 31;
   float s = 0.f, c = 0.f;
-  for (int64_t k = lane; k < d; k += 32) {
-    float x = a[k], y = __ldg(b + k);
-    float p = __fmul_rn(x, y);
-    float e = __fmaf_rn(x, y, -p);
-    float t, q;
-    two_sum(s, p, t, q);
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(q, e));
+  int64_t k = lane;
+  // four independent gathers in flight per lane; the arithmetic stays in
+  // index order k, k+32, k+64, ... of this lane's chain
+  for (; k + 96 < d; k += 128) {
+    float x0 = a[k], x1 = a[k + 32], x2 = a[k + 64], x3 = a[k + 96];
+    float y0 = __ldg(b + k), y1 = __ldg(b + k + 32), y2 = __ldg(b + k + 64), y3 = __ldg(b + k + 96);
+    dot2_step(x0, y0, s, c);
+    dot2_step(x1, y1, s, c);
+    dot2_step(x2, y2, s, c);
+    dot2_step(x3, y3, s, c);
   }
+  for (; k < d; k += 32) dot2_step(a[k], __ldg(b + k), s, c);
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) {
     float s2 = __shfl_xor_sync(0xffffffffu, s, off);

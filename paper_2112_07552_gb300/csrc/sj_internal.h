@@ -59,27 +59,54 @@ struct TopkFinalArgs {
   float dot2_coef_key;     // Dot2 error bound per unit norm product, key units
   int64_t *out_idx;
   float *out_score;
+  int *tier2_rows;         // rows with more candidates than the first tier holds
   int *overflow_rows;      // rows sent to the fallback pass
+  long long *overflow_key; // their rescan key bounds
   Counters *ctr;
 };
 cudaError_t launch_topk_finalize(const TopkFinalArgs &a, cudaStream_t st);
+cudaError_t launch_topk_finalize_tier2(const TopkFinalArgs &a, int n_rows, cudaStream_t st);
 
-struct TopkFallbackArgs {
+// Fallback of the top-k finalisation: rescan B for rows whose candidates did
+// not fit, then rank the resulting short lists.
+struct KeyCand {
+  long long U, L;  // key interval of the exact score
+  int32_t j, pad;
+};
+struct RescanArgs {
   const float *A, *B;
-  int64_t nA, nB, d;
+  int64_t nB, d;
   const RowMeta *metaA, *metaB;
-  int k;
   float dot2_coef_key;
-  const int *rows;         // rows to process
+  const int *rows;         // left rows to rescan
+  const long long *keys;   // per row: keep j when its upper key >= keys[r]
   int n_rows;
-  void *scratch;           // n_rows x per_row_bytes
-  size_t per_row_bytes;
+  KeyCand *lists;          // n_rows x cap
+  int *count;              // n_rows (zeroed by the caller)
+  int cap;
+  Counters *ctr;
+};
+cudaError_t launch_topk_rescan(const RescanArgs &a, cudaStream_t st);
+
+struct RankListArgs {
+  const float *A, *B;
+  int64_t d;
+  int k;
+  const int *rows;
+  int n_rows;
+  const KeyCand *lists;
+  const int *count;
+  int cap;
+  int *redo;               // list slots cut off at cap
+  int *big;                // list slots longer than the shared-memory ranker takes
   int64_t *out_idx;
   float *out_score;
   Counters *ctr;
 };
-size_t topk_fallback_row_bytes(int64_t nB);
-cudaError_t launch_topk_fallback(const TopkFallbackArgs &a, cudaStream_t st);
+cudaError_t launch_topk_rank_lists(const RankListArgs &a, cudaStream_t st);
+size_t topk_rank_global_row_bytes(int64_t n);
+cudaError_t launch_topk_rank_global(const RankListArgs &a, const int *big, int n_big,
+                                    void *scratch, size_t per_row, cudaStream_t st);
 
 struct ThrFinalArgs {
   const float *A, *B;

@@ -35,6 +35,7 @@ SJ_FP32, SJ_BF16, SJ_FP8_E4M3 = 0, 1, 2
 PRECISIONS = {"fp32": SJ_FP32, "bf16": SJ_BF16, "fp8": SJ_FP8_E4M3}
 
 SJ_FLAG_SYM_INFONCE = 0x1
+SJ_FLAG_SINGLE_SPLIT = 0x2
 SJ_FLAG_DEBUG_TIMEOUT = 0x100
 
 # every symbol include/sj.h declares
@@ -55,7 +56,7 @@ class SjStats(ctypes.Structure):
                 ("n_candidates", I64), ("n_rescored", I64), ("n_exact", I64),
                 ("n_overflow_rows", I64), ("n_pairs", I64),
                 ("margin_max", ctypes.c_double), ("max_abs_err_lowprec", ctypes.c_double),
-                ("n_launches", I64)]
+                ("n_launches", I64), ("n_tier2_rows", I64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -224,3 +224,21 @@ def test_batch_matches_single_calls(sjmod):
     for (A, B), o in zip(data, outs):
         assert_topk(o["idx"], o["score"], A, B, 5)
         assert_thr((o["i"], o["j"], o["pair_score"]), A, B, 0.8)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nA,nB,keys,k", [
+    (50, 900, 2, 10),    # ~450 exact ties per row: band overflow -> rescan -> shared-memory rank
+    (20, 3000, 2, 10),   # ~1500 ties: global-memory ranker
+    (8, 9000, 1, 5),     # 9000 ties: rescan list cut at 4096 -> redo with full capacity
+])
+def test_fallback_paths_massive_ties(sjmod, prec, nA, nB, keys, k):
+    ka = datagen.keys(nA, keys, 9, 0)
+    kb = datagen.keys(nB, keys, 9, 1)
+    A, B = datagen.one_hot(ka, keys), datagen.one_hot(kb, keys)
+    # one column split: each row's candidates go through one band list
+    J = sjmod.SimilarityJoin(keys, prec=prec, device=0, flags=sjmod.SJ_FLAG_SINGLE_SPLIT)
+    idx, sc, st = J.topk(dev(A), dev(B), k, with_stats=True)
+    J.close()
+    assert_topk(idx, sc, A, B, k)
+    assert st["n_overflow_rows"] > 0
