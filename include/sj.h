@@ -175,6 +175,29 @@ sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t
 sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, float T,
                       const float *lse, const float *grad_loss, float *dA, float *dB);
 
+/* Exact top-k join that allocates nothing, for callers that cannot allocate
+ * device memory at call time (their HBM is reserved in full by another
+ * allocator's pool, or they must not call cudaMalloc/cudaFree, which can
+ * synchronise the device).  The paper has no counterpart: this is a
+ * deployment variant of sj_topk.  No handle is needed; the work runs on
+ * `stream` (cudaStream_t, NULL = legacy default stream) of the current device
+ * and the call returns after that stream drains it.  Results equal sj_topk's.
+ *
+ * A, B: nA x d and nB x d float32 rows, out_idx/out_score: nA x k, all DEVICE
+ * memory owned by the caller.  Limits: nB <= 2048 (larger nB returns
+ * SJ_ERR_UNSUPPORTED), 1 <= k <= 1024 (k > nB pads with (-1, -inf)).
+ * Scratch: one fixed device array of about 5.2 MB inside the library, held by
+ * every GPU that loads it until the process exits.  The first call on each
+ * device resolves that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls on a device share the
+ * array and it keeps the previous call's contents: calls that overlap on the
+ * GPU (other threads or streams) race and must be serialised by the caller.
+ * Errors: SJ_ERR_INVALID_ARG (null or host pointers, bad sizes),
+ * SJ_ERR_UNSUPPORTED, SJ_ERR_NONFINITE, SJ_ERR_NOT_UNIT_NORM, SJ_ERR_CUDA. */
+sj_status sj_topk_noalloc(const float *A, int64_t nA, const float *B, int64_t nB,
+                          int64_t d, int32_t k, int64_t *out_idx, float *out_score,
+                          void *stream);
+
 /* Static description of a status code. */
 const char *sj_status_string(sj_status s);
 
