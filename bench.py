@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--small", action="store_true", help="65,536 x 65,536 variant (debug)")
+    p.add_argument("--shape", default=None,
+                   help="nA,nB override of the workload sizes (profiling runs)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -187,7 +189,11 @@ def run_reference(args, w):
 
 def main():
     args = parse()
-    w = SMALL if args.small else WORKLOAD
+    w = dict(SMALL if args.small else WORKLOAD)
+    if args.shape:
+        nA, nB = (int(x) for x in args.shape.split(","))
+        w.update(nA=nA, nB=nB, clusters=max(1, min(nA, nB) // 10),
+                 workload="bf16_similarity_join_%dx%d_d768_k20_tau0.85" % (nA, nB))
     if args.impl == "reference":
         return run_reference(args, w)
 
