@@ -192,7 +192,7 @@ def main():
     w = dict(SMALL if args.small else WORKLOAD)
     if args.shape:
         nA, nB = (int(x) for x in args.shape.split(","))
-        w.update(nA=nA, nB=nB, clusters=max(1, min(nA, nB) // 10),
+        w.update(nA=nA, nB=nB, clusters=max(1, nB // 10),
                  workload="bf16_similarity_join_%dx%d_d768_k20_tau0.85" % (nA, nB))
     if args.impl == "reference":
         return run_reference(args, w)

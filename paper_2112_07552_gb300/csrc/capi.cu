@@ -226,8 +226,7 @@ JoinPlan make_plan(const sj_handle *h, int64_t nA, int64_t nB, int k) {
   int64_t S = (want_units + rb - 1) / rb;
   if (S < 1 || (h->cfg.flags & SJ_FLAG_SINGLE_SPLIT)) S = 1;
   if (S > ct) S = ct;
-  // the finaliser merges S*k heap values in shared memory: S*k <= 512
-  if (k > 0 && S * k > 512) S = std::max<int64_t>(1, 512 / k);
+  if (S > 256) S = 256;  // bounds the per-(row, split) band lists
   p.tiles_per_split = (ct + S - 1) / S;
   p.S = (int)((ct + p.tiles_per_split - 1) / p.tiles_per_split);
   p.n_units = rb * p.S;
@@ -556,7 +555,6 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
     ev.rec(0);
     size_t bytes = prepare_bytes(pl, a_host, b_host, self);
     if (k > 0) {
-      bytes += slots * k * 4 + 256;                          // heaps
       bytes += slots * (size_t)pl.cap * sizeof(Cand) + 256;  // band lists
       bytes += slots * 4 + 256;                              // band counts
       bytes += rows1 * 16 + 768;                             // tier-2/overflow rows, keys
@@ -574,14 +572,12 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
     s = prepare_join(h, ar, A, nA, B, nB, k, P);
     if (s != SJ_OK) return s;
     launches += (P.Bp == P.Ap) ? 1 : 2;
-    float *heaps = nullptr;
     Cand *band = nullptr;
     int *band_cnt = nullptr, *ovf = nullptr, *tier2 = nullptr;
     long long *ovf_key = nullptr;
     int64_t *d_idx = r.out_idx;
     float *d_score = r.out_score;
     if (k > 0) {
-      heaps = static_cast<float *>(ar.take(slots * k * 4));
       band = static_cast<Cand *>(ar.take(slots * (size_t)pl.cap * sizeof(Cand)));
       band_cnt = static_cast<int *>(ar.take(slots * 4));
       ovf = static_cast<int *>(ar.take(rows1 * 4));
@@ -591,7 +587,7 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
         d_idx = static_cast<int64_t *>(ar.take((size_t)nA * k * 8));
         d_score = static_cast<float *>(ar.take((size_t)nA * k * 4));
       }
-      if (!heaps || !band || !band_cnt || !ovf || !tier2 || !ovf_key ||
+      if (!band || !band_cnt || !ovf || !tier2 || !ovf_key ||
           (nA > 0 && (!d_idx || !d_score)))
         return SJ_ERR_INTERNAL;
     }
@@ -632,7 +628,6 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
     ScoreArgs sa{};
     sa.k = k;
     sa.tau_f = tau_f;
-    sa.heaps = heaps;
     sa.band = band;
     sa.cap = k > 0 ? pl.cap : 0;
     sa.band_cnt = band_cnt;
@@ -669,7 +664,6 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
       fa.k = k;
       fa.n_splits = pl.S;
       fa.cap = pl.cap;
-      fa.heaps = heaps;
       fa.band = band;
       fa.band_cnt = band_cnt;
       fa.dot2_coef_key = dot2_coef_key(pl.d);

@@ -1,11 +1,21 @@
 // epilogue.cuh -- the fused filter every scoring kernel applies to its tile.
 //
 // The thread that owns left row i sees the low-precision scores s~_ij of one
-// tile, column by column in increasing j, and keeps
-//   * j in the row's band list when s~_ij >= theta_i (running top-k bound),
-//   * (i, j) in the threshold candidate list when s~_ij >= tau - m_i,
+// tile, in increasing j, and keeps
+//   * (s~, j) in the row's band list when s~ >= theta_i,
+//   * (i, j, s~) in the threshold candidate list when s~ >= tau - m_i,
 // so the |A| x |B| score matrix never reaches HBM (the analogue of fusing
 // nonzero() of Sec. 3.2 into the product).
+//
+// Top-k filter.  |s~_ij - s_ij| <= m_i for every j.  With s~_(k) the k-th
+// largest s~ of the row, every exact top-k member has s~ >= s~_(k) - 2 m_i
+// (k rows have s >= s~_(k) - m_i).  theta_i is s~_(k) - 2 m_i over the
+// columns seen so far, which never exceeds the final value, so the band list
+// is a superset of the final candidates.  theta_i is refreshed only when the
+// list is nearly full: the warp then finds the exact k-th largest banded score
+// (bisection on order-preserving integer keys) and compacts the list.  The
+// row's k best scores always pass and are never compacted away, so the final
+// list holds them and the finaliser recomputes s~_(k) from it.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -16,10 +26,13 @@
 namespace sj {
 
 struct RowCtx {
-  RowFilter f;
-  float *heap;  // k floats (min-heap of the k best s~ of this row and split)
-  Cand *band;   // cap entries
-  int32_t i;    // global left row
+  float theta;    // top-k filter (+inf: no top-k part)
+  float tau_lo;   // threshold filter: keep if s~ >= tau - m_i (+inf: off)
+  float two_m;    // 2 m_i, rounded up
+  int cnt;        // band list fill
+  int overflow;   // band list could not be compacted below the limit
+  Cand *band;     // cap entries
+  int32_t i;      // global left row
 };
 
 // Append a threshold candidate (warp-aggregated atomic on the global count).
@@ -44,51 +57,85 @@ __device__ __forceinline__ float row_margin(const RowMeta &m, const float *gmaxB
   return __fadd_ru(__fadd_ru(t1, t2), t3);
 }
 
-__device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, int64_t row,
-                                          int split) {
+__device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, int64_t row, int split) {
   r.i = (int32_t)row;
-  float m = row_margin(a.metaA[row], a.gmaxB, a.acc_coef);
-  r.f.two_m = __fmul_ru(2.f, m);
-  r.f.tau_lo = __fsub_rd(a.tau_f, m);
-  r.f.cnt = 0;
-  r.f.overflow = 0;
-  size_t slot = (size_t)row * a.n_splits + split;
-  r.heap = a.heaps + slot * a.k;
-  r.band = a.band + slot * a.cap;
-  if (a.k > 0) {
-    for (int t = 0; t < a.k; ++t) r.heap[t] = -INFINITY;
-    r.f.theta = -INFINITY;
-  } else {
-    r.f.theta = INFINITY;
-  }
+  const float m = row_margin(a.metaA[row], a.gmaxB, a.acc_coef);
+  r.two_m = __fmul_ru(2.f, m);
+  r.tau_lo = __fsub_rd(a.tau_f, m);
+  r.cnt = 0;
+  r.overflow = 0;
+  r.band = a.band + ((size_t)row * a.n_splits + split) * a.cap;
+  r.theta = a.k > 0 ? -INFINITY : INFINITY;
 }
 
+// Band count of the (row, split); an overflowed list stores -(cnt + 1), its
+// entries up to the overflow staying valid.
 __device__ __forceinline__ void row_end(const RowCtx &r, const ScoreArgs &a, int split) {
-  if (a.k > 0) a.band_cnt[(size_t)r.i * a.n_splits + split] = r.f.overflow ? -1 : r.f.cnt;
+  if (a.k > 0) a.band_cnt[(size_t)r.i * a.n_splits + split] = r.overflow ? -r.cnt - 1 : r.cnt;
 }
 
-__device__ __forceinline__ void row_visit_topk(RowCtx &r, const ScoreArgs &a, float v, int32_t j) {
-  if (r.f.overflow == 0) {
-    if (r.f.cnt == a.cap) {
-      int w = 0;
-      for (int t = 0; t < a.cap; ++t) {
-        Cand c = r.band[t];
-        if (c.v >= r.f.theta) r.band[w++] = c;
-      }
-      r.f.cnt = w;
-      if (w > a.cap - 32) r.f.overflow = 1;
+// Visit one score that passed min(theta, tau_lo).  The band list always has
+// room for a chunk of 32 visits (the owner compacts before each chunk).
+__device__ __forceinline__ void row_push(RowCtx &r, const ScoreArgs &a, float v, int32_t j) {
+  if (v >= r.theta && !r.overflow) {
+    r.band[r.cnt] = Cand{v, j};
+    r.cnt += 1;
+  }
+  if (v >= r.tau_lo) push_thr(a, r.i, j, v);
+}
+
+// Order-preserving map of non-NaN floats to unsigned integers.
+__device__ __forceinline__ uint32_t fkey(float v) {
+  uint32_t u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Warp-cooperative refresh of theta and compaction of every row of this warp
+// whose band list holds more than `limit` entries.  Must be called by all 32
+// lanes (each lane owning at most one row; non-owners pass has_row = false).
+__device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int limit) {
+  const int lane = threadIdx.x & 31;
+  unsigned need = __ballot_sync(0xffffffffu, has_row && !r.overflow && r.cnt > limit);
+  while (need) {
+    const int src = __ffs(need) - 1;
+    need &= need - 1;
+    const int n = __shfl_sync(0xffffffffu, r.cnt, src);
+    const unsigned long long bp =
+        __shfl_sync(0xffffffffu, (unsigned long long)reinterpret_cast<uintptr_t>(r.band), src);
+    Cand *band = reinterpret_cast<Cand *>((uintptr_t)bp);
+    const float two_m = __shfl_sync(0xffffffffu, r.two_m, src);
+    const float theta_old = __shfl_sync(0xffffffffu, r.theta, src);
+    // k-th largest banded score: the largest key T with #{key >= T} >= k
+    uint32_t T = 0;
+    for (int b = 31; b >= 0; --b) {
+      const uint32_t t = T | (1u << b);
+      unsigned c = 0;
+      for (int q = lane; q < n; q += 32) c += fkey(band[q].v) >= t;
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (c >= (unsigned)k) T = t;
     }
-    if (r.f.overflow == 0) r.band[r.f.cnt++] = Cand{v, j};
+    const float theta = fmaxf(theta_old, __fsub_rd(fkey_inv(T), two_m));
+    // stable in-place compaction: a chunk is read fully before it is written
+    int w = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int q = base + lane;
+      Cand cd = q < n ? band[q] : Cand{-INFINITY, 0};
+      const bool keep = q < n && cd.v >= theta;
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) band[w + __popc(bal & ((1u << lane) - 1u))] = cd;
+      w += __popc(bal);
+    }
+    __syncwarp();
+    if (lane == src) {
+      r.theta = theta;
+      r.cnt = w;
+      if (w > limit) r.overflow = 1;  // the band near the k-th score is too dense
+    }
   }
-  if (v > r.heap[0]) {
-    heap_replace_min(r.heap, a.k, v);
-    r.f.theta = __fsub_rd(r.heap[0], r.f.two_m);
-  }
-}
-
-__device__ __forceinline__ void row_visit(RowCtx &r, const ScoreArgs &a, float v, int32_t j) {
-  if (v >= r.f.theta) row_visit_topk(r, a, v, j);
-  if (v >= r.f.tau_lo) push_thr(a, r.i, j, v);
 }
 
 }  // namespace sj

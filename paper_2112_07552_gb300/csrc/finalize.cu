@@ -20,6 +20,9 @@
 // interval, where the exact value decides; accepted pairs are counted per row,
 // placed by an exclusive scan of the counts and sorted by j inside each row.
 #include <cfloat>
+#include <climits>
+
+#include "epilogue.cuh"
 
 #include "rank.cuh"
 #include "sj_device.cuh"
@@ -31,7 +34,7 @@ namespace {
 
 constexpr int kFinThreads = 128;
 constexpr int kCMax = 1024;   // candidates per row, second tier
-constexpr int kCSmall = 256;  // candidates per row, first tier (higher occupancy)
+constexpr int kCSmall = 384;  // candidates per row, first tier (higher occupancy)
 constexpr int64_t kRowInSmemMax = 16384;  // left row cached in shared memory up to this width
 
 template <int CMAX>
@@ -48,9 +51,10 @@ struct FinSmemLayout {
   uint8_t flag[CMAX];
 };
 
-// rows == nullptr: the row is blockIdx.x; otherwise rows[blockIdx.x].  A row
-// with more than CMAX candidates (or an overflowed band list) is appended to
-// `defer` (count in *n_defer) for the next tier.
+// rows == nullptr: the row is blockIdx.x; otherwise rows[blockIdx.x].
+// A row whose band list overflowed goes to the rescan list with its key
+// bound; a row with more than CMAX candidates goes to `defer` (with its key
+// bound in defer_key when given: the last tier defers to the rescan list).
 template <int CMAX>
 __global__ void __launch_bounds__(kFinThreads)
     topk_finalize_kernel(TopkFinalArgs a, const int *rows, int *defer, long long *defer_key,
@@ -60,8 +64,8 @@ __global__ void __launch_bounds__(kFinThreads)
   float *a_row = reinterpret_cast<float *>(smem_raw + sizeof(FinSmemLayout<CMAX>));
   __shared__ int s_n, s_overflow;
   __shared__ float s_theta;
-  __shared__ long long s_key;
   __shared__ unsigned int s_maxerr;
+  __shared__ unsigned s_cnt[kFinThreads / 32];
   const int64_t i = rows ? rows[blockIdx.x] : (int64_t)blockIdx.x;
   if (i >= a.nA) return;
   const int S = a.n_splits, k = a.k;
@@ -73,59 +77,77 @@ __global__ void __launch_bounds__(kFinThreads)
   __syncthreads();
   for (int s = threadIdx.x; s < S; s += blockDim.x)
     if (a.band_cnt[i * S + s] < 0) s_overflow = 1;
-  __syncthreads();
-  // k-th best low-precision score over all splits
-  float kth;
-  if (S == 1) {
-    kth = a.heaps[i * k];  // root of the min-heap of the k best
-  } else {
-    // S * k <= 512 (planner); U (CMAX long longs) holds 2*CMAX floats,
-    // perm2 + grp hold the 2*CMAX order slots
-    float *buf = reinterpret_cast<float *>(sm.U);
-    const int m = S * k, m_pad = next_pow2(m);
-    int32_t *ord = sm.perm2;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) buf[t] = a.heaps[i * (int64_t)m + t];
-    for (int t = threadIdx.x; t < m_pad; t += blockDim.x) ord[t] = t < m ? t : -1;
-    __syncthreads();
-    block_bitonic(ord, m_pad, [&](int32_t x, int32_t y) { return buf[x] > buf[y]; });
-    kth = buf[ord[k - 1]];
-    __syncthreads();
+  // k-th largest banded score over all splits (an overflowed list holds the
+  // entries up to its overflow, which still bound the final value from below):
+  // bisection on order-preserving keys, reading the lists in place
+  uint32_t T = 0;
+  int n_all = 0;
+  for (int s = 0; s < S; ++s) {
+    const int c = a.band_cnt[i * S + s];
+    n_all += c < 0 ? -c - 1 : c;
   }
-  if (threadIdx.x == 0) {
+  for (int b = 31; b >= 0; --b) {
+    const uint32_t t = T | (1u << b);
+    unsigned c = 0;
+    for (int s = 0; s < S; ++s) {
+      const int cs = a.band_cnt[i * S + s];
+      const int cnt = cs < 0 ? -cs - 1 : cs;
+      const Cand *bl = a.band + (i * S + s) * (int64_t)a.cap;
+      for (int q = threadIdx.x; q < cnt; q += blockDim.x) c += fkey(bl[q].v) >= t;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = c;
+    __syncthreads();
+    unsigned tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_cnt[w];
+    __syncthreads();
+    if (tot >= (unsigned)k) T = t;
+  }
+  const float kth = n_all >= k ? fkey_inv(T) : -INFINITY;
+  float m;
+  {
     RowMeta mi = a.metaA[i];
     float t1 = __fmul_ru(mi.qerr, a.gmaxB[0]);
     float t2 = __fmul_ru(mi.qnrm, a.gmaxB[2]);
     float t3 = __fmul_ru(__fmul_ru(a.acc_coef, mi.qnrm), a.gmaxB[1]);
-    float m = __fadd_ru(__fadd_ru(t1, t2), t3);
-    s_theta = __fsub_rd(kth, __fmul_ru(2.f, m));
-    // At least k rows have s~ >= kth, hence s >= kth - m: every exact top-k
-    // member has s >= kth - m.  Key of that bound, rounded down (rescan).
-    s_key = __float2ll_rd(__fmul_rd(__fsub_rd(kth, m), 0x1p60f));
+    m = __fadd_ru(__fadd_ru(t1, t2), t3);
   }
-  __syncthreads();
-  const float theta = s_theta;
-  if (!s_overflow) {
-    for (int s = 0; s < S; ++s) {
-      const int cnt = a.band_cnt[i * S + s];
-      const Cand *bl = a.band + (i * S + s) * (int64_t)a.cap;
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        Cand cd = bl[t];
-        if (cd.v >= theta) {
-          int p = atomicAdd(&s_n, 1);
-          if (p < CMAX) {
-            sm.j[p] = cd.j;
-            sm.v[p] = cd.v;
-          }
+  if (s_overflow) {
+    if (threadIdx.x == 0) {
+      // At least k rows have s~ >= kth, hence s >= kth - m: every exact top-k
+      // member has s >= kth - m.  Key of that bound, rounded down.
+      unsigned slot = atomicAdd(&a.ctr->overflow_rows, 1u);
+      a.overflow_rows[slot] = (int)i;
+      a.overflow_key[slot] = kth == -INFINITY
+                                 ? LLONG_MIN
+                                 : __float2ll_rd(__fmul_rd(__fsub_rd(kth, m), 0x1p60f));
+    }
+    return;
+  }
+  const float theta = __fsub_rd(kth, __fmul_ru(2.f, m));
+  for (int s = 0; s < S; ++s) {
+    const int cnt = a.band_cnt[i * S + s];
+    const Cand *bl = a.band + (i * S + s) * (int64_t)a.cap;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const Cand cd = bl[t];
+      if (cd.v >= theta) {
+        const int p = atomicAdd(&s_n, 1);
+        if (p < CMAX) {
+          sm.j[p] = cd.j;
+          sm.v[p] = cd.v;
         }
       }
     }
   }
   __syncthreads();
-  if (s_overflow || s_n > CMAX) {
+  if (s_n > CMAX) {
     if (threadIdx.x == 0) {
       unsigned slot = atomicAdd(n_defer, 1u);
       defer[slot] = (int)i;
-      if (defer_key) defer_key[slot] = s_key;
+      if (defer_key)
+        defer_key[slot] = kth == -INFINITY
+                              ? LLONG_MIN
+                              : __float2ll_rd(__fmul_rd(__fsub_rd(kth, m), 0x1p60f));
     }
     return;
   }
@@ -539,6 +561,7 @@ cudaError_t launch_topk_finalize(const TopkFinalArgs &a, cudaStream_t st) {
 
 cudaError_t launch_topk_finalize_tier2(const TopkFinalArgs &a, int n_rows, cudaStream_t st) {
   if (n_rows == 0) return cudaSuccess;
+  // rows with more than kCMax candidates join the rescan list
   return launch_fin<kCMax>(a, a.tier2_rows, n_rows, a.overflow_rows, a.overflow_key,
                            &a.ctr->overflow_rows, st);
 }

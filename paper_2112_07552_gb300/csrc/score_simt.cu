@@ -38,6 +38,10 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
     const int split = (int)(unit % a.n_splits);
     const int64_t row0 = rb * BM;
     RowCtx rc;
+    rc.cnt = 0;
+    rc.overflow = 0;
+    rc.theta = INFINITY;
+    rc.tau_lo = INFINITY;
     const bool owner = tid < BM && row0 + tid < a.nA;
     if (owner) row_begin(rc, a, row0 + tid, split);
 
@@ -108,9 +112,17 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
         }
       }
       __syncthreads();
-      if (owner) {
-        const int ncol = (int)min64(BN, a.nB - col0);
-        for (int c = 0; c < ncol; ++c) row_visit(rc, a, sm.S[tid][c], (int32_t)(col0 + c));
+      if (tid < BM) {
+        // the whole of warps 0-3 (the row owners) refreshes and compacts
+        if (a.k > 0) warp_compact(rc, owner, a.k, a.cap - BN);
+        if (owner) {
+          const int ncol = (int)min64(BN, a.nB - col0);
+          const float tmin = fminf(rc.theta, rc.tau_lo);
+          for (int c = 0; c < ncol; ++c) {
+            const float v = sm.S[tid][c];
+            if (v >= tmin) row_push(rc, a, v, (int32_t)(col0 + c));
+          }
+        }
       }
       __syncthreads();
     }

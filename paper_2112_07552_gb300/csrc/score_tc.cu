@@ -48,7 +48,6 @@ struct alignas(1024) TcSmem {
   uint64_t tmem_empty[2];
   uint64_t drain;
   uint64_t never;  // debug-timeout hook: nothing ever arrives here
-  float stage[BM][33];  // epilogue slow-path staging, one row per thread
   uint32_t tmem_base;
   int abort;
 };
@@ -183,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool debug_timeout = (flags & SJ_FLAG_DEBUG_TIMEOUT) != 0;
-  const uint64_t limit = 4000000000ull;  // 4 s per wait
+  const uint64_t limit_ns = 4000000000ull;  // 4 s per wait
   volatile int *abort = &sm.abort;
 
   if (threadIdx.x == 0) {
@@ -228,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
             const int s = (int)(it % STAGES);
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-            if (!mbar_wait(&sm.empty[s], ph ^ 1, limit, abort)) {
+            if (!mbar_wait(&sm.empty[s], ph ^ 1, limit_ns, abort)) {
               flag_timeout(sm, a.ctr);
               ok = false;
               break;
@@ -245,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = (int)(q % STAGES);
         const uint32_t ph = (uint32_t)((q / STAGES) & 1);
         uint64_t t0 = now_ns();
-        while (!mbar_try(&sm.full[s], ph) && now_ns() - t0 < limit) {
+        while (!mbar_try(&sm.full[s], ph) && now_ns() - t0 < limit_ns) {
         }
       }
     }
@@ -261,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
           const int acc = (int)(tile & 1);
           const uint32_t aph = (uint32_t)((tile >> 1) & 1);
-          if (!mbar_wait(&sm.tmem_empty[acc], aph ^ 1, limit, abort)) {
+          if (!mbar_wait(&sm.tmem_empty[acc], aph ^ 1, limit_ns, abort)) {
             flag_timeout(sm, a.ctr);
             ok = false;
             break;
@@ -271,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
             const int s = (int)(it % STAGES);
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-            if (!mbar_wait(&sm.full[s], ph, limit, abort)) {
+            if (!mbar_wait(&sm.full[s], ph, limit_ns, abort)) {
               flag_timeout(sm, a.ctr);
               ok = false;
               break;
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Drain: every MMA issued so far completes before tensor memory is freed.
       mma_commit(&sm.drain);
       uint64_t t0 = now_ns();
-      while (!mbar_try(&sm.drain, 0) && now_ns() - t0 < limit) {
+      while (!mbar_try(&sm.drain, 0) && now_ns() - t0 < limit_ns) {
       }
     }
   } else {
@@ -309,12 +308,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
       }
     }
+    const int limit = a.cap - 32;  // room for one chunk of visits
     for (int64_t unit = blockIdx.x; unit < a.n_units && ok; unit += gridDim.x) {
       const int64_t rb = unit / a.n_splits;
       const int split = (int)(unit % a.n_splits);
       const int64_t row = rb * BM + r_in_tile;
       const bool owner = row < a.nA;
       RowCtx rc;
+      rc.cnt = 0;
+      rc.overflow = 0;
+      rc.theta = INFINITY;
+      rc.tau_lo = INFINITY;
       if (owner) row_begin(rc, a, row, split);
       const int64_t ct0 = split * a.tiles_per_split;
       const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int acc = (int)(tile & 1);
         const uint32_t aph = (uint32_t)((tile >> 1) & 1);
         // warp-uniform outcome: the TMEM loads below are .sync.aligned
-        const bool w = mbar_wait(&sm.tmem_full[acc], aph, limit, abort);
+        const bool w = mbar_wait(&sm.tmem_full[acc], aph, limit_ns, abort);
         if (!__all_sync(0xffffffffu, w)) {
           flag_timeout(sm, a.ctr);
           ok = false;
@@ -333,37 +337,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
+          if (a.k > 0) warp_compact(rc, owner, a.k, limit);
           float v[32];
           tmem_ld32(taddr + c0, v);
           if (owner) {
             // fast path: one compare per 32 scores (balanced max tree)
-            float m16[16];
+            float p16[16], q8[8];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) m16[q] = fmaxf(v[2 * q], v[2 * q + 1]);
+            for (int q = 0; q < 16; ++q) p16[q] = fmaxf(v[2 * q], v[2 * q + 1]);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) m16[q] = fmaxf(m16[2 * q], m16[2 * q + 1]);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) m16[q] = fmaxf(m16[2 * q], m16[2 * q + 1]);
-            const float mx = fmaxf(fmaxf(m16[0], m16[1]), fmaxf(m16[2], m16[3]));
-            const float tmin = fminf(rc.f.theta, rc.f.tau_lo);
+            for (int q = 0; q < 8; ++q) q8[q] = fmaxf(p16[2 * q], p16[2 * q + 1]);
+            const float mx = fmaxf(fmaxf(fmaxf(q8[0], q8[1]), fmaxf(q8[2], q8[3])),
+                                   fmaxf(fmaxf(q8[4], q8[5]), fmaxf(q8[6], q8[7])));
+            const float tmin = fminf(rc.theta, rc.tau_lo);
             if (mx >= tmin) {
-              // slow path: visit only the passing columns; the values go
-              // through shared memory so the register array is never indexed
-              // dynamically (which would put it in local memory)
-              uint32_t mask = 0;
-              float *stg = sm.stage[r_in_tile];
-#pragma unroll
-              for (int q = 0; q < 32; ++q) {
-                mask |= (v[q] >= tmin ? 1u : 0u) << q;
-                stg[q] = v[q];
-              }
+              // slow path, fully unrolled (no dynamic register indexing)
               const int64_t jb = col0 + c0;
-              const int64_t rem = a.nB - jb;  // valid columns in this chunk
-              if (rem < 32) mask &= rem <= 0 ? 0u : ((1u << (uint32_t)rem) - 1u);
-              while (mask) {
-                const int q = __ffs(mask) - 1;
-                mask &= mask - 1;
-                row_visit(rc, a, stg[q], (int32_t)(jb + q));
+#pragma unroll
+              for (int g = 0; g < 8; ++g) {
+                if (q8[g] >= tmin) {
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    const int q = 4 * g + e;
+                    if (v[q] >= tmin && jb + q < a.nB) row_push(rc, a, v[q], (int32_t)(jb + q));
+                  }
+                }
               }
             }
           }

@@ -8,8 +8,6 @@
 //    entries are below 2 in magnitude (Kulisch's long accumulator, restricted
 //    to the exponent range such rows can produce), its comparison, and its
 //    correctly rounded conversion to float32.
-//  * The per-row candidate filter applied to every low-precision score in the
-//    scoring epilogue (running top-k threshold + threshold test).
 #pragma once
 
 #include <cstdint>
@@ -263,37 +261,6 @@ __device__ __forceinline__ float exact_to_float(const Exact &x) {
   }
   if (neg) bits |= 0x80000000u;
   return __uint_as_float(bits);
-}
-
-// ---------------------------------------------------------------------------
-// Per-row candidate filter of the scoring epilogue.
-//
-// For left row i the scoring pass sees s~_ij with |s~_ij - s_ij| <= m_i for
-// every j.  With L_(k) the k-th largest s~_ij - m_i, a right row j can be in
-// the exact top-k only if s~_ij + m_i >= L_(k), i.e. s~_ij >= s~_(k) - 2 m_i.
-// The running k-th largest seen so far never exceeds the final one, so
-// filtering with it keeps a superset.  The band list keeps every s~ that
-// passed at its time; when full it is compacted with the current threshold.
-struct RowFilter {
-  float theta;    // running top-k threshold  (k-th best s~ so far) - 2 m_i
-  float tau_lo;   // threshold test: keep if s~ >= tau_lo = tau - m_i (+inf: off)
-  float two_m;    // 2 m_i
-  int cnt;        // band list fill
-  int overflow;   // band list could not be compacted
-};
-
-// min-heap of the k best low-precision scores (global memory, k floats)
-__device__ __forceinline__ void heap_replace_min(float *h, int k, float v) {
-  int p = 0;
-  while (true) {
-    int c = 2 * p + 1;
-    if (c >= k) break;
-    if (c + 1 < k && h[c + 1] < h[c]) c += 1;
-    if (h[c] >= v) break;
-    h[p] = h[c];
-    p = c;
-  }
-  h[p] = v;
 }
 
 }  // namespace sj

@@ -29,10 +29,9 @@ struct ScoreArgs {
   int n_splits;            // column splits per row block
   int64_t tiles_per_split; // column tiles per split
   int64_t n_units;         // row blocks x splits
-  float *heaps;            // [nA][n_splits][k]
   Cand *band;              // [nA][n_splits][cap]
   int cap;
-  int *band_cnt;           // [nA][n_splits]; < 0 marks overflow
+  int *band_cnt;           // [nA][n_splits]; -(cnt + 1) marks an overflowed list
   ThrCand *thr;            // threshold candidates
   unsigned long long thr_cap;
   Counters *ctr;
@@ -53,14 +52,13 @@ struct TopkFinalArgs {
   const float *gmaxB;
   float acc_coef;
   int k, n_splits, cap;
-  const float *heaps;
   const Cand *band;
   const int *band_cnt;
   float dot2_coef_key;     // Dot2 error bound per unit norm product, key units
   int64_t *out_idx;
   float *out_score;
   int *tier2_rows;         // rows with more candidates than the first tier holds
-  int *overflow_rows;      // rows sent to the fallback pass
+  int *overflow_rows;      // rows whose band list overflowed (rescan fallback)
   long long *overflow_key; // their rescan key bounds
   Counters *ctr;
 };
