@@ -30,10 +30,41 @@ struct RowCtx {
   float tau_lo;   // threshold filter: keep if s~ >= tau - m_i (+inf: off)
   float two_m;    // 2 m_i, rounded up
   int cnt;        // band list fill
+  int last;       // fill right after the last refresh of theta
   int overflow;   // band list could not be compacted below the limit
   Cand *band;     // cap entries
+  float *heap;    // shared-memory min-heap of the k best s~ (stride kHeapStride), or null
   int32_t i;      // global left row
 };
+
+// Shared-memory heaps are stored transposed (element t of row r at
+// heap[t * kHeapStride + r]) so a warp's rows fall in distinct banks.
+constexpr int kHeapStride = 128;
+
+__device__ __forceinline__ void heap_init(float *h, int k) {
+  for (int t = 0; t < k; ++t) h[t * kHeapStride] = -INFINITY;
+}
+
+// Replace the minimum (root) of a k-element min-heap by v and sift down.
+__device__ __forceinline__ void heap_replace_min(float *h, int k, float v) {
+  int p = 0;
+  while (true) {
+    int c = 2 * p + 1;
+    if (c >= k) break;
+    float hc = h[c * kHeapStride];
+    if (c + 1 < k) {
+      const float h2 = h[(c + 1) * kHeapStride];
+      if (h2 < hc) {
+        hc = h2;
+        c += 1;
+      }
+    }
+    if (hc >= v) break;
+    h[p * kHeapStride] = hc;
+    p = c;
+  }
+  h[p * kHeapStride] = v;
+}
 
 // Append a threshold candidate (warp-aggregated atomic on the global count).
 __device__ __forceinline__ void push_thr(const ScoreArgs &a, int32_t i, int32_t j, float v) {
@@ -63,9 +94,11 @@ __device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, int64_t
   r.two_m = __fmul_ru(2.f, m);
   r.tau_lo = __fsub_rd(a.tau_f, m);
   r.cnt = 0;
+  r.last = 0;
   r.overflow = 0;
   r.band = a.band + ((size_t)row * a.n_splits + split) * a.cap;
   r.theta = a.k > 0 ? -INFINITY : INFINITY;
+  if (r.heap) heap_init(r.heap, a.k);
 }
 
 // Band count of the (row, split); an overflowed list stores -(cnt + 1), its
@@ -75,11 +108,18 @@ __device__ __forceinline__ void row_end(const RowCtx &r, const ScoreArgs &a, int
 }
 
 // Visit one score that passed min(theta, tau_lo).  The band list always has
-// room for a chunk of 32 visits (the owner compacts before each chunk).
+// room for a chunk of 32 visits (the owner compacts before each chunk).  With
+// a heap, theta tracks the running k-th best exactly.
 __device__ __forceinline__ void row_push(RowCtx &r, const ScoreArgs &a, float v, int32_t j) {
-  if (v >= r.theta && !r.overflow) {
-    r.band[r.cnt] = Cand{v, j};
-    r.cnt += 1;
+  if (v >= r.theta) {
+    if (!r.overflow) {
+      r.band[r.cnt] = Cand{v, j};
+      r.cnt += 1;
+    }
+    if (r.heap && v > r.heap[0]) {
+      heap_replace_min(r.heap, a.k, v);
+      r.theta = __fsub_rd(r.heap[0], r.two_m);
+    }
   }
   if (v >= r.tau_lo) push_thr(a, r.i, j, v);
 }
@@ -94,11 +134,17 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 }
 
 // Warp-cooperative refresh of theta and compaction of every row of this warp
-// whose band list holds more than `limit` entries.  Must be called by all 32
+// whose band list holds more than `limit` entries, or at least k entries and
+// kRefresh more than after its last refresh (keeps theta close to the running
+// k-th best, so few scores reach the slow path).  Must be called by all 32
 // lanes (each lane owning at most one row; non-owners pass has_row = false).
+constexpr int kRefresh = 32;
 __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int limit) {
   const int lane = threadIdx.x & 31;
-  unsigned need = __ballot_sync(0xffffffffu, has_row && !r.overflow && r.cnt > limit);
+  // with a heap theta is always exact: compact only when the list is full
+  const bool due = r.heap ? r.cnt > limit
+                          : (r.cnt > limit || (r.cnt >= k && r.cnt >= r.last + kRefresh));
+  unsigned need = __ballot_sync(0xffffffffu, has_row && !r.overflow && due);
   while (need) {
     const int src = __ffs(need) - 1;
     need &= need - 1;
@@ -108,16 +154,20 @@ __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int
     Cand *band = reinterpret_cast<Cand *>((uintptr_t)bp);
     const float two_m = __shfl_sync(0xffffffffu, r.two_m, src);
     const float theta_old = __shfl_sync(0xffffffffu, r.theta, src);
-    // k-th largest banded score: the largest key T with #{key >= T} >= k
-    uint32_t T = 0;
-    for (int b = 31; b >= 0; --b) {
-      const uint32_t t = T | (1u << b);
-      unsigned c = 0;
-      for (int q = lane; q < n; q += 32) c += fkey(band[q].v) >= t;
-      c = __reduce_add_sync(0xffffffffu, c);
-      if (c >= (unsigned)k) T = t;
+    const bool exact = __shfl_sync(0xffffffffu, r.heap != nullptr ? 1 : 0, src) != 0;
+    float theta = theta_old;
+    if (!exact) {
+      // k-th largest banded score: the largest key T with #{key >= T} >= k
+      uint32_t T = 0;
+      for (int b = 31; b >= 0; --b) {
+        const uint32_t t = T | (1u << b);
+        unsigned c = 0;
+        for (int q = lane; q < n; q += 32) c += fkey(band[q].v) >= t;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (c >= (unsigned)k) T = t;
+      }
+      theta = fmaxf(theta_old, __fsub_rd(fkey_inv(T), two_m));
     }
-    const float theta = fmaxf(theta_old, __fsub_rd(fkey_inv(T), two_m));
     // stable in-place compaction: a chunk is read fully before it is written
     int w = 0;
     for (int base = 0; base < n; base += 32) {
@@ -133,6 +183,7 @@ __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int
     if (lane == src) {
       r.theta = theta;
       r.cnt = w;
+      r.last = w;
       if (w > limit) r.overflow = 1;  // the band near the k-th score is too dense
     }
   }

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
     rc.overflow = 0;
     rc.theta = INFINITY;
     rc.tau_lo = INFINITY;
+    rc.heap = nullptr;  // theta refreshed lazily from the band list
     const bool owner = tid < BM && row0 + tid < a.nA;
     if (owner) row_begin(rc, a, row0 + tid, split);
 

@@ -34,6 +34,8 @@ constexpr int BM = kTcBM;       // 128 rows of A per tile (TMEM lanes)
 constexpr int BN = kTcBN;       // 256 columns of B per tile (TMEM columns)
 constexpr int BK = 64;          // k-block: 64 bf16 = 128 bytes = one swizzle row
 constexpr int STAGES = 4;
+constexpr int kEpiChunks = 2;  // 32-column chunks per TMEM round trip
+constexpr int kHeapMaxK = 64;  // top-k sizes tracked by shared-memory heaps
 constexpr int kThreads = 192;
 constexpr uint32_t kTileABytes = BM * BK * 2;
 constexpr uint32_t kTileBBytes = BN * BK * 2;
@@ -48,6 +50,7 @@ struct alignas(1024) TcSmem {
   uint64_t tmem_empty[2];
   uint64_t drain;
   uint64_t never;  // debug-timeout hook: nothing ever arrives here
+  float heap[kHeapMaxK * kHeapStride];  // per-row top-k min-heaps (k <= kHeapMaxK)
   uint32_t tmem_base;
   int abort;
 };
@@ -150,9 +153,10 @@ __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 consecutive TMEM columns of this warp's 32 lanes (one row per thread).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// 32 consecutive TMEM columns of this warp's 32 lanes (one row per thread);
+// the registers are valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, float (&v)[32]) {
+  uint32_t *r = reinterpret_cast<uint32_t *>(v);
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -164,9 +168,63 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
         "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Orders every later use of v after the wait: the registers are in/out
+// operands of the (volatile) wait, so no use can be scheduled above it.
+#define SJ_F32x32(v)                                                                      \
+  "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]),      \
+      "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]),          \
+      "+f"(v[13]), "+f"(v[14]), "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]),       \
+      "+f"(v[19]), "+f"(v[20]), "+f"(v[21]), "+f"(v[22]), "+f"(v[23]), "+f"(v[24]),       \
+      "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]), "+f"(v[29]), "+f"(v[30]), "+f"(v[31])
+__device__ __forceinline__ void tmem_wait_ld(float (&v0)[32], float (&v1)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : SJ_F32x32(v0) : : "memory");
+  asm volatile("" : SJ_F32x32(v1) : : "memory");
+}
+
+// Fused filter over 32 scores of the thread's row, columns jb .. jb+31.
+__device__ __forceinline__ void epilogue_chunk(RowCtx &rc, const ScoreArgs &a, const float (&v)[32],
+                                               int64_t jb) {
+  // fast path: one compare per 32 scores (balanced max tree)
+  float p16[16], q8[8];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+  for (int q = 0; q < 16; ++q) p16[q] = fmaxf(v[2 * q], v[2 * q + 1]);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) q8[q] = fmaxf(p16[2 * q], p16[2 * q + 1]);
+  const float mx = fmaxf(fmaxf(fmaxf(q8[0], q8[1]), fmaxf(q8[2], q8[3])),
+                         fmaxf(fmaxf(q8[4], q8[5]), fmaxf(q8[6], q8[7])));
+  const float tmin = fminf(rc.theta, rc.tau_lo);
+  if (mx >= tmin) {
+    // slow path: loop over the passing quads; a switch picks the quad's
+    // registers by static index (no local memory) and one copy of the push
+    // code serves every value
+    uint32_t qm = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) qm |= (q8[g] >= tmin ? 1u : 0u) << g;
+    while (qm) {
+      const int g = __ffs(qm) - 1;
+      qm &= qm - 1;
+      float x0, x1, x2, x3;
+      switch (g) {
+#define SJ_QUAD(G)     \
+  case G:              \
+    x0 = v[4 * G];     \
+    x1 = v[4 * G + 1]; \
+    x2 = v[4 * G + 2]; \
+    x3 = v[4 * G + 3]; \
+    break;
+        SJ_QUAD(0) SJ_QUAD(1) SJ_QUAD(2) SJ_QUAD(3) SJ_QUAD(4) SJ_QUAD(5) SJ_QUAD(6)
+        default: SJ_QUAD(7)
+#undef SJ_QUAD
+      }
+      const int64_t jq = jb + 4 * g;
+#pragma unroll 1
+      for (int e = 0; e < 4; ++e) {
+        const float x = e == 0 ? x0 : e == 1 ? x1 : e == 2 ? x2 : x3;
+        if (x >= fminf(rc.theta, rc.tau_lo) && jq + e < a.nB) row_push(rc, a, x, (int32_t)(jq + e));
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ void flag_timeout(TcSmem &sm, Counters *ctr) {
@@ -308,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
       }
     }
-    const int limit = a.cap - 32;  // room for one chunk of visits
+    const int limit = a.cap - 32 * kEpiChunks;  // room for one round of visits
     for (int64_t unit = blockIdx.x; unit < a.n_units && ok; unit += gridDim.x) {
       const int64_t rb = unit / a.n_splits;
       const int split = (int)(unit % a.n_splits);
@@ -319,6 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       rc.overflow = 0;
       rc.theta = INFINITY;
       rc.tau_lo = INFINITY;
+      rc.heap = (a.k > 0 && a.k <= kHeapMaxK) ? sm.heap + r_in_tile : nullptr;
       if (owner) row_begin(rc, a, row, split);
       const int64_t ct0 = split * a.tiles_per_split;
       const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
@@ -335,35 +394,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_after();
         const int64_t col0 = ct * BN;
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+        // two 32-column chunks per TMEM round trip
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 < BN; c0 += 64) {
           if (a.k > 0) warp_compact(rc, owner, a.k, limit);
-          float v[32];
-          tmem_ld32(taddr + c0, v);
+          float v0[32], v1[32];
+          tmem_ld32_nowait(taddr + c0, v0);
+          tmem_ld32_nowait(taddr + c0 + 32, v1);
+          tmem_wait_ld(v0, v1);
           if (owner) {
-            // fast path: one compare per 32 scores (balanced max tree)
-            float p16[16], q8[8];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) p16[q] = fmaxf(v[2 * q], v[2 * q + 1]);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) q8[q] = fmaxf(p16[2 * q], p16[2 * q + 1]);
-            const float mx = fmaxf(fmaxf(fmaxf(q8[0], q8[1]), fmaxf(q8[2], q8[3])),
-                                   fmaxf(fmaxf(q8[4], q8[5]), fmaxf(q8[6], q8[7])));
-            const float tmin = fminf(rc.theta, rc.tau_lo);
-            if (mx >= tmin) {
-              // slow path, fully unrolled (no dynamic register indexing)
-              const int64_t jb = col0 + c0;
-#pragma unroll
-              for (int g = 0; g < 8; ++g) {
-                if (q8[g] >= tmin) {
-#pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    const int q = 4 * g + e;
-                    if (v[q] >= tmin && jb + q < a.nB) row_push(rc, a, v[q], (int32_t)(jb + q));
-                  }
-                }
-              }
-            }
+            epilogue_chunk(rc, a, v0, col0 + c0);
+            epilogue_chunk(rc, a, v1, col0 + c0 + 32);
           }
         }
         fence_before();
