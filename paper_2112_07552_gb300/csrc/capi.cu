@@ -205,6 +205,7 @@ struct JoinPlan {
   PrecPlan pp;
   int64_t nA, nB, d, nA_pad, nB_pad;
   int S;
+  int bands;  // band lists per (row, split): epilogue column groups of the kernel
   int64_t tiles_per_split, n_units;
   int cap;
 };
@@ -230,6 +231,7 @@ JoinPlan make_plan(const sj_handle *h, int64_t nA, int64_t nB, int k) {
   p.tiles_per_split = (ct + S - 1) / S;
   p.S = (int)((ct + p.tiles_per_split - 1) / p.tiles_per_split);
   p.n_units = rb * p.S;
+  p.bands = h->cfg.prec == SJ_FP32 ? 1 : 2;
   // band list per row: the k best plus the margin band (often ~60-150 rows
   // for BF16 scores of d = 768 embeddings near the k-th score)
   p.cap = (int)round_up(4 * (int64_t)k + 256, 32);
@@ -350,6 +352,7 @@ sj_status run_score(sj_handle *h, const Prepared &P, ScoreArgs &sa) {
   sa.gmaxB = P.gmaxB;
   sa.acc_coef = (float)pl.pp.acc_coef;
   sa.n_splits = pl.S;
+  sa.bands_per_split = pl.bands;
   sa.tiles_per_split = pl.tiles_per_split;
   sa.n_units = pl.n_units;
   sa.ctr = P.ctr;
@@ -544,7 +547,7 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
   const bool op_host = r.thr && r.capacity > 0 && !is_device_ptr(r.out);
   const JoinPlan pl = make_plan(h, nA, nB, k);
   const bool self = (A == B && nA == nB);
-  const size_t slots = (size_t)std::max<int64_t>(nA, 1) * pl.S;
+  const size_t slots = (size_t)std::max<int64_t>(nA, 1) * pl.S * pl.bands;
   const size_t rows1 = (size_t)std::max<int64_t>(nA, 1);
   unsigned long long thr_cap = 0;
   if (r.thr)
@@ -662,7 +665,7 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
       fa.gmaxB = P.gmaxB;
       fa.acc_coef = (float)pl.pp.acc_coef;
       fa.k = k;
-      fa.n_splits = pl.S;
+      fa.n_splits = pl.S * pl.bands;
       fa.cap = pl.cap;
       fa.band = band;
       fa.band_cnt = band_cnt;

@@ -37,9 +37,10 @@ struct RowCtx {
   int32_t i;      // global left row
 };
 
-// Shared-memory heaps are stored transposed (element t of row r at
-// heap[t * kHeapStride + r]) so a warp's rows fall in distinct banks.
-constexpr int kHeapStride = 128;
+// Shared-memory heaps are stored transposed (element t of heap h at
+// heap[t * kHeapStride + h]) so the heaps of a warp's rows fall in distinct
+// banks; a CTA holds up to kHeapStride heaps.
+constexpr int kHeapStride = 256;
 
 __device__ __forceinline__ void heap_init(float *h, int k) {
   for (int t = 0; t < k; ++t) h[t * kHeapStride] = -INFINITY;
@@ -88,7 +89,8 @@ __device__ __forceinline__ float row_margin(const RowMeta &m, const float *gmaxB
   return __fadd_ru(__fadd_ru(t1, t2), t3);
 }
 
-__device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, int64_t row, int split) {
+// `list` numbers the row's band lists: split * bands_per_split + group.
+__device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, int64_t row, int list) {
   r.i = (int32_t)row;
   const float m = row_margin(a.metaA[row], a.gmaxB, a.acc_coef);
   r.two_m = __fmul_ru(2.f, m);
@@ -96,15 +98,17 @@ __device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, int64_t
   r.cnt = 0;
   r.last = 0;
   r.overflow = 0;
-  r.band = a.band + ((size_t)row * a.n_splits + split) * a.cap;
+  r.band = a.band + ((size_t)row * a.n_splits * a.bands_per_split + list) * a.cap;
   r.theta = a.k > 0 ? -INFINITY : INFINITY;
   if (r.heap) heap_init(r.heap, a.k);
 }
 
 // Band count of the (row, split); an overflowed list stores -(cnt + 1), its
 // entries up to the overflow staying valid.
-__device__ __forceinline__ void row_end(const RowCtx &r, const ScoreArgs &a, int split) {
-  if (a.k > 0) a.band_cnt[(size_t)r.i * a.n_splits + split] = r.overflow ? -r.cnt - 1 : r.cnt;
+__device__ __forceinline__ void row_end(const RowCtx &r, const ScoreArgs &a, int list) {
+  if (a.k > 0)
+    a.band_cnt[(size_t)r.i * a.n_splits * a.bands_per_split + list] =
+        r.overflow ? -r.cnt - 1 : r.cnt;
 }
 
 // Visit one score that passed min(theta, tau_lo).  The band list always has

@@ -5,14 +5,17 @@
 // C = mat(A) mat(B)^T), so it runs on the 5th-generation tensor cores; the
 // paper's own kernels (WMMA on Ampere/Turing) are prior art only.
 //
-// Persistent kernel, one CTA per SM, warp-specialised (192 threads):
+// Persistent kernel, one CTA per SM, warp-specialised (320 threads):
 //   warp 0     TMA producer: 128x64 A tile + 256x64 B tile per k-block into a
 //              4-stage ring of 128B-swizzled shared memory buffers;
 //   warp 1     TMEM allocator + MMA issuer: tcgen05.mma kind::f16, M=128,
 //              N=256, K=16, into one of two 256-column TMEM accumulators;
-//   warps 2-5  epilogue: tcgen05.ld of their 32-lane quarter (one left row
-//              per thread), fused top-k / threshold filter (epilogue.cuh),
-//              then release the accumulator to the MMA warp.
+//   warps 2-9  epilogue: two warps per 32-lane TMEM quarter (the quarter a
+//              warp may access is its index mod 4), each taking one half of
+//              the tile's columns; tcgen05.ld (one left row per thread),
+//              fused top-k / threshold filter (epilogue.cuh) with one band
+//              list and heap per (row, column half), then release the
+//              accumulator to the MMA warp.
 // Work unit = (128-row block of A, column split of B); CTAs take units
 // round-robin.  Every wait is bounded (globaltimer); a wait that gives up
 // flags SJ_ERR_TIMEOUT, the CTA drains its in-flight copies and MMAs,
@@ -35,8 +38,9 @@ constexpr int BN = kTcBN;       // 256 columns of B per tile (TMEM columns)
 constexpr int BK = 64;          // k-block: 64 bf16 = 128 bytes = one swizzle row
 constexpr int STAGES = 4;
 constexpr int kEpiChunks = 2;  // 32-column chunks per TMEM round trip
-constexpr int kHeapMaxK = 64;  // top-k sizes tracked by shared-memory heaps
-constexpr int kThreads = 192;
+constexpr int kHeapMaxK = 32;  // top-k sizes tracked by shared-memory heaps
+constexpr int kEpiWarps = 8;    // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTileABytes = BM * BK * 2;
 constexpr uint32_t kTileBBytes = BN * BK * 2;
 constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(&sm.tmem_full[q], 1);
-      mbar_init(&sm.tmem_empty[q], 4 * 32);
+      mbar_init(&sm.tmem_empty[q], kEpiWarps * 32);
     }
     mbar_init(&sm.drain, 1);
     mbar_init(&sm.never, 1);
@@ -354,7 +358,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
-    const int quarter = warp & 3;  // TMEM lanes this warp may access
+    const int quarter = warp & 3;        // TMEM lanes this warp may access
+    const int half = (warp - 2) >> 2;    // column half of each tile
     const int r_in_tile = quarter * 32 + lane;
     uint64_t tile = 0;
     bool ok = true;
@@ -377,8 +382,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       rc.overflow = 0;
       rc.theta = INFINITY;
       rc.tau_lo = INFINITY;
-      rc.heap = (a.k > 0 && a.k <= kHeapMaxK) ? sm.heap + r_in_tile : nullptr;
-      if (owner) row_begin(rc, a, row, split);
+      rc.heap = (a.k > 0 && a.k <= kHeapMaxK) ? sm.heap + half * BM + r_in_tile : nullptr;
+      const int list = split * a.bands_per_split + half;
+      if (owner) row_begin(rc, a, row, list);
       const int64_t ct0 = split * a.tiles_per_split;
       const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
       for (int64_t ct = ct0; ct < ct1; ++ct, ++tile) {
@@ -396,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
         // two 32-column chunks per TMEM round trip
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 64) {
+        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 64) {
           if (a.k > 0) warp_compact(rc, owner, a.k, limit);
           float v0[32], v1[32];
           tmem_ld32_nowait(taddr + c0, v0);
@@ -410,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before();
         mbar_arrive(&sm.tmem_empty[acc]);
       }
-      if (owner) row_end(rc, a, split);
+      if (owner) row_end(rc, a, list);
     }
   }
 
@@ -480,6 +486,7 @@ sj_status tc_make_maps(TcContext *ctx, const void *Ap, int64_t nA_pad, const voi
 cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, uint32_t flags,
                             cudaStream_t st) {
   if (a.n_units == 0) return cudaSuccess;
+  if (a.bands_per_split != 2) return cudaErrorInvalidValue;  // one list per column half
   const size_t smem = sizeof(TcSmem) + 1024;
   cudaError_t e = cudaFuncSetAttribute(score_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -27,11 +27,12 @@ struct ScoreArgs {
   int k;                   // top-k (0: no top-k)
   float tau_f;             // float tau rounded down (+inf: no threshold)
   int n_splits;            // column splits per row block
+  int bands_per_split;     // band lists per (row, split): one per epilogue column group
   int64_t tiles_per_split; // column tiles per split
   int64_t n_units;         // row blocks x splits
-  Cand *band;              // [nA][n_splits][cap]
+  Cand *band;              // [nA][n_splits * bands_per_split][cap]
   int cap;
-  int *band_cnt;           // [nA][n_splits]; -(cnt + 1) marks an overflowed list
+  int *band_cnt;           // [nA][n_splits * bands_per_split]; -(cnt + 1): overflowed
   ThrCand *thr;            // threshold candidates
   unsigned long long thr_cap;
   Counters *ctr;
@@ -51,7 +52,7 @@ struct TopkFinalArgs {
   const RowMeta *metaA, *metaB;
   const float *gmaxB;
   float acc_coef;
-  int k, n_splits, cap;
+  int k, n_splits, cap;    // n_splits here counts band lists per row
   const Cand *band;
   const int *band_cnt;
   float dot2_coef_key;     // Dot2 error bound per unit norm product, key units

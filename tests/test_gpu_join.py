@@ -228,7 +228,7 @@ def test_batch_matches_single_calls(sjmod):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("nA,nB,keys,k", [
-    (50, 900, 2, 10),    # ~450 exact ties per row: band overflow -> rescan -> shared-memory rank
+    (50, 1300, 2, 10),   # ~650 exact ties per row: band overflow -> rescan -> shared-memory rank
     (20, 3000, 2, 10),   # ~1500 ties: global-memory ranker
     (8, 9000, 1, 5),     # 9000 ties: rescan list cut at 4096 -> redo with full capacity
 ])
