@@ -41,6 +41,12 @@ SMALL = dict(WORKLOAD, workload="bf16_similarity_join_65536x65536_d768_k20_tau0.
              nA=65536, nB=65536, clusters=6554)
 METRIC = "pair-scores/s"
 
+# DRAM bytes of one headline score_tc_kernel launch: an ncu capture of the
+# current kernel on a one-wave case scaled by pair-scores
+# (profiles/score_tc_kernel_bf16_19456x262144_d768.md).  Must be re-taken
+# whenever the kernel changes.
+SCORE_TC_TRAFFIC_BYTES_PER_PAIR = 1.178853e9 / (19456 * 262144)
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -328,7 +334,10 @@ def main():
                    "l2": "inputs 6.1 GB > L2, no flush", "parallelism": "dp%d" % world},
         "roofline": {"bound": "tensor", "kernel": "score_tc_kernel", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": src + " bf16_tflops_sustained", "traffic": None,
+                     "peak_source": src + " bf16_tflops_sustained",
+                     "traffic": SCORE_TC_TRAFFIC_BYTES_PER_PAIR * nA * nB,
+                     "traffic_source": "ncu capture of a 19,456 x 262,144 launch scaled by "
+                                       "pair-scores (profiles/)",
                      "ms_kernel": ms_score},
         "stages_ms": {"prepare": statistics.mean(s.ms_prepare for s in stats),
                       "score": ms_score,
