@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/sj.h"
+#include "contrastive.h"
 #include "sj_internal.h"
 #include "tc_host.h"
 
@@ -923,17 +924,141 @@ sj_status sj_batch(sj_handle *h, const sj_job *jobs, int32_t n_jobs, sj_stats *s
   return first;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Shared set-up of the contrastive calls: BF16 packing (and transposes for the
+// backward) of A and B into the workspace, and their tensor maps.
+struct ContrastivePlan {
+  int64_t n, d, np, dp;
+  void *Ap, *Bp, *AT, *BT;
+  Counters *ctr;
+  float *scratch;  // 2n floats (per-row loss terms)
+  unsigned char mA[128], mB[128], mAT[128], mBT[128];
+};
+
+sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t N, bool bwd,
+                            ContrastivePlan &cp) {
+  if (!h || !A || !B || N < 1) return SJ_ERR_INVALID_ARG;
+  if (N >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
+  if (!is_device_ptr(A) || !is_device_ptr(B)) return SJ_ERR_INVALID_ARG;
+  SJ_CUDA(cudaSetDevice(h->cfg.device));
+  if (h->cc != 103) return SJ_ERR_UNSUPPORTED;
+  if (!h->tc) {
+    sj_status s = tc_create(&h->tc);
+    if (s != SJ_OK) return s;
+  }
+  cp.n = N;
+  cp.d = h->cfg.d;
+  cp.np = round_up(N, 128);
+  cp.dp = round_up(cp.d, 64);
+  const size_t op = (size_t)cp.np * cp.dp * 2;
+  size_t bytes = 2 * op + (bwd ? 2 * op : 0) + sizeof(Counters) + (size_t)2 * N * 4 + 8 * 256;
+  sj_status s = ensure_ws(h, bytes);
+  if (s != SJ_OK) return s;
+  Arena ar{static_cast<unsigned char *>(h->ws), h->ws_size, 0};
+  cp.ctr = static_cast<Counters *>(ar.take(sizeof(Counters)));
+  cp.scratch = static_cast<float *>(ar.take((size_t)2 * N * 4));
+  cp.Ap = ar.take(op);
+  cp.Bp = ar.take(op);
+  cp.AT = bwd ? ar.take(op) : nullptr;
+  cp.BT = bwd ? ar.take(op) : nullptr;
+  if (!cp.ctr || !cp.scratch || !cp.Ap || !cp.Bp || (bwd && (!cp.AT || !cp.BT))) return SJ_ERR_INTERNAL;
+  cudaStream_t st = h->stream;
+  SJ_CUDA(cudaMemsetAsync(cp.ctr, 0, sizeof(Counters), st));
+  SJ_CUDA(launch_contrastive_pack(static_cast<const float *>(A), N, cp.d, cp.Ap, cp.AT, cp.np, cp.dp,
+                                  &cp.ctr->err_flags, st));
+  SJ_CUDA(launch_contrastive_pack(static_cast<const float *>(B), N, cp.d, cp.Bp, cp.BT, cp.np, cp.dp,
+                                  &cp.ctr->err_flags, st));
+  s = tc_encode_2d(h->tc, cp.Ap, cp.dp, cp.np, 64, 128, cp.mA);
+  if (s == SJ_OK) s = tc_encode_2d(h->tc, cp.Bp, cp.dp, cp.np, 64, 128, cp.mB);
+  if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.AT, cp.np, cp.dp, 64, 64, cp.mAT);
+  if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.BT, cp.np, cp.dp, 64, 64, cp.mBT);
+  return s;
+}
+
+sj_status contrastive_finish(sj_handle *h, const ContrastivePlan &cp) {
+  sj_status s = read_counters(h, cp.ctr);
+  if (s != SJ_OK) return s;
+  const unsigned f = h->h_ctr->err_flags;
+  if (f & kErrNonFinite) return SJ_ERR_NONFINITE;
+  if (f & kErrTimeout) return SJ_ERR_TIMEOUT;
+  return SJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t N, float T,
                              float *loss, float *lse) {
   if (!h || !A || !B || N < 1 || !(T > 0.f) || !loss || !lse) return SJ_ERR_INVALID_ARG;
-  return SJ_ERR_UNSUPPORTED;
+  if (!is_device_ptr(loss) || !is_device_ptr(lse)) return SJ_ERR_INVALID_ARG;
+  ContrastivePlan cp;
+  sj_status s = contrastive_setup(h, A, B, N, false, cp);
+  if (s != SJ_OK) return s;
+  const bool sym = (h->cfg.flags & SJ_FLAG_SYM_INFONCE) != 0;
+  ContrastiveArgs a{};
+  a.n = N;
+  a.d = cp.d;
+  a.np = cp.np;
+  a.dp = cp.dp;
+  a.T = T;
+  a.n_chunks = 1;
+  a.ctr = cp.ctr;
+  a.debug_timeout = (h->cfg.flags & SJ_FLAG_DEBUG_TIMEOUT) ? 1 : 0;
+  const int grid = (int)std::min<int64_t>(cp.np / 128, h->sm_count);
+  a.lse_out = lse;
+  a.term_out = cp.scratch;
+  SJ_CUDA(launch_contrastive(false, cp.mA, cp.mB, nullptr, a, grid, h->stream));
+  if (sym) {
+    a.lse_out = lse + N;
+    a.term_out = cp.scratch + N;
+    SJ_CUDA(launch_contrastive(false, cp.mB, cp.mA, nullptr, a, grid, h->stream));
+  }
+  SJ_CUDA(launch_contrastive_loss(cp.scratch, sym ? cp.scratch + N : nullptr, N, sym ? 0.5f : 1.f,
+                                  0.5f, loss, h->stream));
+  return contrastive_finish(h, cp);
 }
 
 sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, float T,
                       const float *lse, const float *grad_loss, float *dA, float *dB) {
   if (!h || !A || !B || N < 1 || !(T > 0.f) || !lse || !grad_loss || !dA || !dB)
     return SJ_ERR_INVALID_ARG;
-  return SJ_ERR_UNSUPPORTED;
+  if (!is_device_ptr(lse) || !is_device_ptr(grad_loss) || !is_device_ptr(dA) || !is_device_ptr(dB))
+    return SJ_ERR_INVALID_ARG;
+  ContrastivePlan cp;
+  sj_status s = contrastive_setup(h, A, B, N, true, cp);
+  if (s != SJ_OK) return s;
+  const bool sym = (h->cfg.flags & SJ_FLAG_SYM_INFONCE) != 0;
+  ContrastiveArgs a{};
+  a.n = N;
+  a.d = cp.d;
+  a.np = cp.np;
+  a.dp = cp.dp;
+  a.T = T;
+  a.n_chunks = (int)((cp.dp + 383) / 384);
+  a.grad_loss = grad_loss;
+  a.ctr = cp.ctr;
+  a.debug_timeout = (h->cfg.flags & SJ_FLAG_DEBUG_TIMEOUT) ? 1 : 0;
+  const int grid = (int)std::min<int64_t>((cp.np / 128) * a.n_chunks, h->sm_count);
+  // dA: rows of A against columns (rows of B); row term = softmax over j
+  a.lse_r = lse;
+  a.wr = sym ? 0.5f : 1.f;
+  a.lse_c = sym ? lse + N : lse;
+  a.wc = sym ? 0.5f : 0.f;
+  a.dX = dA;
+  SJ_CUDA(launch_contrastive(true, cp.mA, cp.mB, cp.mBT, a, grid, h->stream));
+  // dB: rows of B against columns (rows of A); the row softmax term is indexed
+  // by the kernel's columns, the column softmax term by its rows
+  a.lse_r = sym ? lse + N : lse;
+  a.wr = sym ? 0.5f : 0.f;
+  a.lse_c = lse;
+  a.wc = sym ? 0.5f : 1.f;
+  a.dX = dB;
+  SJ_CUDA(launch_contrastive(true, cp.mB, cp.mA, cp.mAT, a, grid, h->stream));
+  return contrastive_finish(h, cp);
 }
 
 const char *sj_status_string(sj_status s) {

@@ -1,0 +1,518 @@
+// contrastive.cu -- InfoNCE-style contrastive join: forward and backward on
+// sm_103a tensor cores, recomputing score tiles instead of storing S.
+//
+// S = A B^T / T over N paired rows (positives on the diagonal), BF16 operands
+// (round-to-nearest-even of the float32 inputs), FP32 accumulation in TMEM.
+//   forward : l_i = logsumexp_j S_ij, loss = (1/N) sum_i (l_i - S_ii)
+//             (symmetric flag: also the column term, averaged)
+//   backward: G_ij = dloss/dS_ij = (g/N) (P_ij - [i == j]) (+ column term),
+//             dA = G B / T,  dB = G^T A / T.
+//
+// One persistent kernel template, one CTA per SM, warp-specialised:
+//   warp 0: TMA producer, warp 1: TMEM allocator + MMA issuer,
+//   warps 2-5: epilogue (one TMEM lane quarter each, one row per thread).
+// Tiles are 128 rows x 128 columns.
+//   FWD  : S tiles double-buffered in TMEM; epilogue keeps an online
+//          (max, sum) per row with exp2 and records the diagonal.
+//   BWD  : unit = (128-row block of X, chunk of <= 384 output dimensions).
+//          Per column tile t: S_t = X_blk Y_t^T (TMEM cols 0..127); the
+//          epilogue turns S_t into G'_t = w_r (P - I) + w_c (Q - I) in BF16,
+//          written 128B-swizzled into shared memory; the MMA warp then adds
+//          G'_t Z_t^T to the chunk accumulator (TMEM cols 128..511), Z^T being
+//          a transposed BF16 copy of the other side.  The same kernel gives dA
+//          (X = A, Y = B, Z^T = B^T) and dB (X = B, Y = A, Z^T = A^T, the
+//          softmax terms swapped between rows and columns).  A 128 x 768 FP32
+//          block would exceed tensor memory (512 columns), hence the chunks.
+// Every wait is bounded (globaltimer); a wait that gives up flags
+// SJ_ERR_TIMEOUT and the CTA drains its copies and MMAs before freeing TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "../../include/sj.h"
+#include "contrastive.h"
+#include "tc_common.cuh"
+
+namespace sj {
+namespace {
+
+using namespace tc;
+
+constexpr int TM = 128;             // rows per tile (TMEM lanes)
+constexpr int TN = 128;             // columns per tile
+constexpr int BK = 64;              // k-block (128 bytes of BF16)
+constexpr int kSStages = 2;         // S operand ring
+constexpr int kMaxChunk = 384;      // output dimensions per backward unit
+constexpr int kPiece = 192;         // N of one backward MMA
+constexpr int kZBox = 64;           // rows of one Z^T TMA box
+constexpr int kThreads = 192;       // producer, MMA, 4 epilogue warps
+constexpr uint32_t kOpBytes = TM * BK * 2;  // one operand k-block (16 KB)
+constexpr uint32_t kZBytes = kMaxChunk * BK * 2;  // one Z^T k-block (48 KB)
+constexpr uint32_t kGBytes = TM * TN * 2;         // one G tile (32 KB)
+constexpr float kLog2e = 1.4426950408889634f;
+
+struct alignas(1024) CSmem {
+  unsigned char x[kSStages][kOpBytes];
+  unsigned char y[kSStages][kOpBytes];
+  unsigned char z[2][kZBytes];      // the two 64-wide k-blocks of a column tile
+  unsigned char g[2][kGBytes];      // double-buffered G' tiles
+  uint64_t full[kSStages], empty[kSStages];
+  uint64_t zfull[2], zempty[2];
+  uint64_t s_full[2], s_empty[2];
+  uint64_t g_full[2], g_empty[2];
+  uint64_t acc_full, acc_empty;
+  uint64_t drain, never;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void flag_timeout(CSmem &sm, unsigned *err) {
+  *(volatile int *)&sm.abort = 1;
+  atomicOr(err, 4u);  // kErrTimeout
+}
+
+// fence the generic-proxy shared-memory writes before the tensor core reads them
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <bool BWD>
+__global__ void __launch_bounds__(kThreads, 1)
+    contrastive_kernel(const __grid_constant__ CUtensorMap tmX,
+                       const __grid_constant__ CUtensorMap tmY,
+                       const __grid_constant__ CUtensorMap tmZ, ContrastiveArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  CSmem &sm = *reinterpret_cast<CSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                         ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t limit_ns = 4000000000ull;
+  volatile int *abort = &sm.abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&sm.zfull[q], 1);
+      mbar_init(&sm.zempty[q], 1);
+      mbar_init(&sm.s_full[q], 1);
+      mbar_init(&sm.s_empty[q], 4 * 32);
+      mbar_init(&sm.g_full[q], 4 * 32);
+      mbar_init(&sm.g_empty[q], 1);
+    }
+    mbar_init(&sm.acc_full, 1);
+    mbar_init(&sm.acc_empty, 4 * 32);
+    mbar_init(&sm.drain, 1);
+    mbar_init(&sm.never, 1);
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&sm.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm.tmem_base;
+  const int nkb = (int)(a.dp / BK);
+  const int n_tiles = (int)(a.np / TN);
+  const int n_rb = (int)(a.np / TM);
+  const int n_chunks = BWD ? a.n_chunks : 1;
+  const int64_t n_units = (int64_t)n_rb * n_chunks;
+  const uint32_t idesc_s = idesc_bf16(TM, TN);
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint64_t it = 0, zt = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const int rb = (int)(u / n_chunks), ch = (int)(u % n_chunks);
+        const int c0 = ch * kMaxChunk;
+        const int cw = (int)min64(kMaxChunk, a.dp - c0);
+        for (int t = 0; t < n_tiles && ok; ++t) {
+          for (int kb = 0; kb < nkb; ++kb, ++it) {
+            const int s = (int)(it % kSStages);
+            const uint32_t ph = (uint32_t)((it / kSStages) & 1);
+            if (!mbar_wait(&sm.empty[s], ph ^ 1, limit_ns, abort)) {
+              flag_timeout(sm, &a.ctr->err_flags);
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&sm.full[s], 2 * kOpBytes);
+            tma_load_2d(sm.x[s], &tmX, kb * BK, rb * TM, &sm.full[s]);
+            tma_load_2d(sm.y[s], &tmY, kb * BK, t * TN, &sm.full[s]);
+          }
+          if (BWD && ok) {
+            for (int kz = 0; kz < 2; ++kz) {
+              const uint32_t ph = (uint32_t)(zt & 1);
+              if (!mbar_wait(&sm.zempty[kz], ph ^ 1, limit_ns, abort)) {
+                flag_timeout(sm, &a.ctr->err_flags);
+                ok = false;
+                break;
+              }
+              mbar_arrive_expect_tx(&sm.zfull[kz], (uint32_t)cw * BK * 2);
+              for (int p = 0; p < cw; p += kZBox)
+                tma_load_2d(sm.z[kz] + p * BK * 2, &tmZ, t * TN + kz * BK, c0 + p, &sm.zfull[kz]);
+            }
+            ++zt;
+          }
+        }
+      }
+      // drain: the last copy into each buffer must have landed
+      for (uint64_t q = (it > kSStages ? it - kSStages : 0); q < it; ++q) {
+        const uint64_t t0 = now_ns();
+        while (!mbar_try(&sm.full[q % kSStages], (uint32_t)((q / kSStages) & 1)) &&
+               now_ns() - t0 < limit_ns) {
+        }
+      }
+      if (BWD && zt > 0)
+        for (int kz = 0; kz < 2; ++kz) {
+          const uint64_t t0 = now_ns();
+          while (!mbar_try(&sm.zfull[kz], (uint32_t)((zt - 1) & 1)) && now_ns() - t0 < limit_ns) {
+          }
+        }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint64_t it = 0, tile = 0, zt = 0, unit_n = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++unit_n) {
+        const int ch = (int)(u % n_chunks);
+        const int cw = (int)min64(kMaxChunk, a.dp - ch * kMaxChunk);
+        // S tiles use TMEM buffer (tile & 1) in the forward, buffer 0 in the backward
+        auto issue_s = [&](uint64_t tl) -> bool {
+          const int buf = BWD ? 0 : (int)(tl & 1);
+          const uint32_t ph = BWD ? (uint32_t)(tl & 1) : (uint32_t)((tl >> 1) & 1);
+          if (!mbar_wait(&sm.s_empty[buf], ph ^ 1, limit_ns, abort)) return false;
+          fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * TN);
+          for (int kb = 0; kb < nkb; ++kb, ++it) {
+            const int s = (int)(it % kSStages);
+            const uint32_t sp = (uint32_t)((it / kSStages) & 1);
+            if (!mbar_wait(&sm.full[s], sp, limit_ns, abort)) return false;
+            fence_after();
+            const uint32_t x0 = su32(sm.x[s]), y0 = su32(sm.y[s]);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_bf16(d, sdesc(x0 + kk * 32), sdesc(y0 + kk * 32), idesc_s,
+                       (kb > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&sm.empty[s]);
+          }
+          mma_commit(&sm.s_full[buf]);
+          return true;
+        };
+        // backward product of tile tl: acc += G'_tl Z_tl^T
+        auto issue_g = [&](uint64_t tl, bool first) -> bool {
+          const int gb = (int)(tl & 1);
+          const uint32_t gph = (uint32_t)((tl >> 1) & 1);
+          if (!mbar_wait(&sm.g_full[gb], gph, limit_ns, abort)) return false;
+          if (first && unit_n > 0) {
+            if (!mbar_wait(&sm.acc_empty, (uint32_t)((unit_n - 1) & 1), limit_ns, abort))
+              return false;
+          }
+          fence_after();
+          for (int kz = 0; kz < 2; ++kz) {
+            if (!mbar_wait(&sm.zfull[kz], (uint32_t)(zt & 1), limit_ns, abort)) return false;
+            fence_after();
+            const uint32_t g0 = su32(sm.g[gb]) + kz * (TM * BK * 2);
+            const uint32_t z0 = su32(sm.z[kz]);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              for (int p = 0; p < cw; p += kPiece) {
+                const int pw = min(kPiece, cw - p);
+                mma_bf16(tmem + TN + (uint32_t)p, sdesc(g0 + kk * 32),
+                         sdesc(z0 + (uint32_t)p * BK * 2 + kk * 32), idesc_bf16(TM, pw),
+                         (first && kz == 0 && kk == 0) ? 0u : 1u);
+              }
+            }
+            mma_commit(&sm.zempty[kz]);
+          }
+          ++zt;
+          mma_commit(&sm.g_empty[gb]);
+          return true;
+        };
+        for (int t = 0; t < n_tiles && ok; ++t, ++tile) {
+          if (!issue_s(tile)) {
+            ok = false;
+            break;
+          }
+          if (BWD && t > 0 && !issue_g(tile - 1, t == 1)) {
+            ok = false;
+            break;
+          }
+        }
+        if (BWD && ok) {
+          if (!issue_g(tile - 1, n_tiles == 1)) ok = false;
+          else mma_commit(&sm.acc_full);
+        }
+        if (!ok) flag_timeout(sm, &a.ctr->err_flags);
+      }
+      mma_commit(&sm.drain);
+      const uint64_t t0 = now_ns();
+      while (!mbar_try(&sm.drain, 0) && now_ns() - t0 < limit_ns) {
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;  // row within the tile
+    uint64_t tile = 0, unit_n = 0;
+    bool ok = true;
+    if (a.debug_timeout) {
+      const bool w = mbar_wait(&sm.never, 0, 1000000ull, abort);
+      if (!__all_sync(0xffffffffu, w)) {
+        flag_timeout(sm, &a.ctr->err_flags);
+        ok = false;
+      }
+    }
+    const float c1 = kLog2e / a.T;
+    for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++unit_n) {
+      const int rb = (int)(u / n_chunks), ch = (int)(u % n_chunks);
+      const int64_t row = (int64_t)rb * TM + r;
+      const bool valid = row < a.n;
+      // forward state (log2 domain)
+      float m = -INFINITY, l = 0.f, diag = 0.f;
+      // backward: this row's own-term log-sum-exp (log2 domain)
+      const float lr2 = (BWD && valid && a.wr != 0.f) ? a.lse_r[row] * kLog2e : 0.f;
+      for (int t = 0; t < n_tiles; ++t, ++tile) {
+        const int buf = BWD ? 0 : (int)(tile & 1);
+        const uint32_t ph = BWD ? (uint32_t)(tile & 1) : (uint32_t)((tile >> 1) & 1);
+        const bool w = mbar_wait(&sm.s_full[buf], ph, limit_ns, abort);
+        if (!__all_sync(0xffffffffu, w)) {
+          flag_timeout(sm, &a.ctr->err_flags);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * TN);
+        float v[4][32];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld32_nowait(taddr + c * 32, v[c]);
+        tmem_wait_ld4(v);
+        fence_before();
+        mbar_arrive(&sm.s_empty[buf]);  // S buffer free for the next tile
+        const int64_t col0 = (int64_t)t * TN;
+        if (!BWD) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float x[32];
+            float cm = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              x[q] = (col0 + c * 32 + q < a.n) ? v[c][q] * c1 : -INFINITY;
+              cm = fmaxf(cm, x[q]);
+            }
+            if (cm > m) {
+              l = (m == -INFINITY) ? 0.f : l * ex2(m - cm);
+              m = cm;
+            }
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc += ex2(x[q] - m);
+            l += acc;
+            const int64_t jb = col0 + c * 32;
+            if (row >= jb && row < jb + 32) {
+#pragma unroll
+              for (int q = 0; q < 32; ++q)
+                if (jb + q == row) diag = v[c][q];
+            }
+          }
+        } else {
+          // G'_t, BF16, into the 128B-swizzled K-major layout the MMA reads
+          const int gb = (int)(tile & 1);
+          const uint32_t gph = (uint32_t)((tile >> 1) & 1);
+          const bool we = mbar_wait(&sm.g_empty[gb], gph ^ 1, limit_ns, abort);
+          if (!__all_sync(0xffffffffu, we)) {
+            flag_timeout(sm, &a.ctr->err_flags);
+            ok = false;
+            break;
+          }
+          unsigned char *gt = sm.g[gb];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float gq[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const int64_t j = col0 + c * 32 + q;
+              const float x = v[c][q] * c1;
+              float gv = 0.f;
+              if (j < a.n && valid) {
+                const float dlt = (j == row) ? 1.f : 0.f;
+                if (a.wr != 0.f) gv += a.wr * (ex2(x - lr2) - dlt);
+                if (a.wc != 0.f) gv += a.wc * (ex2(x - __ldg(a.lse_c + j) * kLog2e) - dlt);
+              }
+              gq[q] = gv;
+            }
+            // 32 columns = 4 chunks of 16 bytes in k-block (c >> 1)
+            unsigned char *kbase = gt + (c >> 1) * (TM * BK * 2) + r * 128;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int lc = (c & 1) * 4 + h;  // logical 16-byte chunk in the 128-byte row
+              __nv_bfloat162 p0 = __floats2bfloat162_rn(gq[h * 8 + 0], gq[h * 8 + 1]);
+              __nv_bfloat162 p1 = __floats2bfloat162_rn(gq[h * 8 + 2], gq[h * 8 + 3]);
+              __nv_bfloat162 p2 = __floats2bfloat162_rn(gq[h * 8 + 4], gq[h * 8 + 5]);
+              __nv_bfloat162 p3 = __floats2bfloat162_rn(gq[h * 8 + 6], gq[h * 8 + 7]);
+              uint4 pk;
+              pk.x = *reinterpret_cast<uint32_t *>(&p0);
+              pk.y = *reinterpret_cast<uint32_t *>(&p1);
+              pk.z = *reinterpret_cast<uint32_t *>(&p2);
+              pk.w = *reinterpret_cast<uint32_t *>(&p3);
+              *reinterpret_cast<uint4 *>(kbase + ((lc ^ (r & 7)) * 16)) = pk;
+            }
+          }
+          fence_proxy_async_smem();
+          mbar_arrive(&sm.g_full[gb]);
+        }
+      }
+      if (!ok) break;
+      if (!BWD) {
+        if (valid) {
+          const float lse = (m + __log2f(l)) * 0.69314718055994531f;  // natural log
+          a.lse_out[row] = lse;
+          a.term_out[row] = lse - diag / a.T;
+        }
+      } else {
+        // chunk accumulator -> dX[row, chunk] * (g / (N T))
+        const bool w = mbar_wait(&sm.acc_full, (uint32_t)(unit_n & 1), limit_ns, abort);
+        if (!__all_sync(0xffffffffu, w)) {
+          flag_timeout(sm, &a.ctr->err_flags);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const float scale = __ldg(a.grad_loss) / ((float)a.n * a.T);
+        const int c0 = ch * kMaxChunk;
+        const int cw = (int)min64(kMaxChunk, a.dp - c0);
+        for (int c = 0; c < cw; c += 32) {
+          float o[32];
+          tmem_ld32_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(TN + c), o);
+          tmem_wait_ld1(o);
+          if (valid) {
+            float *dst = a.dX + row * a.d + c0 + c;
+            const int64_t lim = a.d - (c0 + c);
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (q < lim) dst[q] = o[q] * scale;
+          }
+        }
+        fence_before();
+        mbar_arrive(&sm.acc_empty);
+      }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// Round float32 rows to BF16 (RNE) into a zero-padded row-major copy
+// (np x dp) and a transposed copy (dp x np); flags non-finite input.
+__global__ void contrastive_pack_kernel(const float *__restrict__ X, int64_t n, int64_t d,
+                                        __nv_bfloat16 *__restrict__ Xp,
+                                        __nv_bfloat16 *__restrict__ XT, int64_t np, int64_t dp,
+                                        unsigned *err) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int64_t r = r0 + yy, k = k0 + tx;
+    float x = (r < n && k < d) ? X[r * d + k] : 0.f;
+    if (!isfinite(x)) {
+      atomicOr(err, 1u);  // kErrNonFinite
+      x = 0.f;
+    }
+    const __nv_bfloat16 q = __float2bfloat16_rn(x);
+    Xp[r * dp + k] = q;
+    tile[yy][tx] = q;
+  }
+  __syncthreads();
+  if (XT) {
+    for (int yy = ty; yy < 32; yy += 8) XT[(k0 + yy) * np + r0 + tx] = tile[tx][yy];
+  }
+}
+
+// loss = (w1 sum term1 + w2 sum term2) / N, compensated summation, one block.
+__global__ void contrastive_loss_kernel(const float *t1, const float *t2, int64_t n, float w1,
+                                        float w2, float *loss) {
+  __shared__ float sh_s[32], sh_c[32];
+  float s = 0.f, c = 0.f;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    float v = w1 * t1[i] + (t2 ? w2 * t2[i] : 0.f);
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  s -= c;
+  for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sh_s[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float tot = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh_s[w];
+    *loss = tot / (float)n;
+  }
+  (void)sh_c;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+
+size_t contrastive_smem_bytes() { return sizeof(CSmem) + 1024; }
+
+cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *Xp, void *XT,
+                                    int64_t np, int64_t dp, unsigned *err, cudaStream_t st) {
+  dim3 grid((unsigned)(dp / 32), (unsigned)(np / 32)), block(32, 8);
+  contrastive_pack_kernel<<<grid, block, 0, st>>>(X, n, d, static_cast<__nv_bfloat16 *>(Xp),
+                                                  static_cast<__nv_bfloat16 *>(XT), np, dp, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n, float w1, float w2,
+                                    float *loss, cudaStream_t st) {
+  contrastive_loss_kernel<<<1, 1024, 0, st>>>(t1, t2, n, w1, w2, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contrastive(bool bwd, const void *tmX, const void *tmY, const void *tmZ,
+                               const ContrastiveArgs &a, int grid, cudaStream_t st) {
+  const size_t smem = contrastive_smem_bytes();
+  CUtensorMap mx, my, mz;
+  std::memcpy(&mx, tmX, sizeof mx);
+  std::memcpy(&my, tmY, sizeof my);
+  std::memcpy(&mz, tmZ ? tmZ : tmX, sizeof mz);
+  cudaError_t e;
+  if (bwd) {
+    e = cudaFuncSetAttribute(contrastive_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    contrastive_kernel<true><<<grid, kThreads, smem, st>>>(mx, my, mz, a);
+  } else {
+    e = cudaFuncSetAttribute(contrastive_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    contrastive_kernel<false><<<grid, kThreads, smem, st>>>(mx, my, mz, a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sj

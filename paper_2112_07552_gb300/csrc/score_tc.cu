@@ -27,11 +27,14 @@
 #include <cstring>
 
 #include "epilogue.cuh"
+#include "tc_common.cuh"
 #include "tc_host.h"
 
 namespace sj {
 
 namespace {
+
+using namespace tc;
 
 constexpr int BM = kTcBM;       // 128 rows of A per tile (TMEM lanes)
 constexpr int BN = kTcBN;       // 256 columns of B per tile (TMEM columns)
@@ -44,6 +47,7 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTileABytes = BM * BK * 2;
 constexpr uint32_t kTileBBytes = BN * BK * 2;
 constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators
+constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
 
 struct alignas(1024) TcSmem {
   unsigned char a[STAGES][kTileABytes];  // each 1024-byte aligned
@@ -58,133 +62,6 @@ struct alignas(1024) TcSmem {
   uint32_t tmem_base;
   int abort;
 };
-
-__device__ __forceinline__ uint32_t su32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t now_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(su32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase of the given parity; false when it gave up (or
-// when another role already aborted the CTA).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
-                                          volatile int *abort) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = now_ns();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort) return false;
-    if (now_ns() - t0 > limit_ns) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y,
-                                            uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(su32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand tile written by TMA with
-// 128-byte swizzling; 8-row core groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused with SW128)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          su32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// 32 consecutive TMEM columns of this warp's 32 lanes (one row per thread);
-// the registers are valid after tmem_wait_ld().
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, float (&v)[32]) {
-  uint32_t *r = reinterpret_cast<uint32_t *>(v);
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-}
-// Orders every later use of v after the wait: the registers are in/out
-// operands of the (volatile) wait, so no use can be scheduled above it.
-#define SJ_F32x32(v)                                                                      \
-  "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]),      \
-      "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]),          \
-      "+f"(v[13]), "+f"(v[14]), "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]),       \
-      "+f"(v[19]), "+f"(v[20]), "+f"(v[21]), "+f"(v[22]), "+f"(v[23]), "+f"(v[24]),       \
-      "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]), "+f"(v[29]), "+f"(v[30]), "+f"(v[31])
-__device__ __forceinline__ void tmem_wait_ld(float (&v0)[32], float (&v1)[32]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : SJ_F32x32(v0) : : "memory");
-  asm volatile("" : SJ_F32x32(v1) : : "memory");
-}
 
 // Fused filter over 32 scores of the thread's row, columns jb .. jb+31.
 __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, const ScoreArgs &a, const float (&v)[32],
@@ -341,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a0 = su32(sm.a[s]), b0 = su32(sm.b[s]);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-              mma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32),
+              mma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), kIdesc,
                        (kb > 0 || kk > 0) ? 1u : 0u);
             }
             mma_commit(&sm.empty[s]);  // frees the smem stage once these MMAs finish
@@ -456,13 +333,14 @@ sj_status tc_create(TcContext **out) {
 
 void tc_destroy(TcContext *ctx) { delete ctx; }
 
-static sj_status make_map(TcContext *ctx, const void *base, int64_t rows, int64_t dp,
-                          int box_rows, unsigned char *out) {
+sj_status tc_encode_2d(TcContext *ctx, const void *base, int64_t inner, int64_t rows,
+                       int box_inner, int box_rows, unsigned char out[128]) {
+  if (!ctx || !ctx->encode) return SJ_ERR_UNSUPPORTED;
   CUtensorMap m;
   std::memset(&m, 0, sizeof m);
-  cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(dp * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(inner * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = ctx->encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base),
                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -478,9 +356,9 @@ sj_status tc_make_maps(TcContext *ctx, const void *Ap, int64_t nA_pad, const voi
                        int64_t nB_pad, int64_t dp, TcMaps *out) {
   if (!ctx || !ctx->encode) return SJ_ERR_UNSUPPORTED;
   if (dp % BK != 0 || nA_pad % BM != 0 || nB_pad % BN != 0) return SJ_ERR_INTERNAL;
-  sj_status s = make_map(ctx, Ap, nA_pad, dp, BM, out->a);
+  sj_status s = tc_encode_2d(ctx, Ap, dp, nA_pad, BK, BM, out->a);
   if (s != SJ_OK) return s;
-  return make_map(ctx, Bp, nB_pad, dp, BN, out->b);
+  return tc_encode_2d(ctx, Bp, dp, nB_pad, BK, BN, out->b);
 }
 
 cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, uint32_t flags,

@@ -23,5 +23,9 @@ sj_status tc_make_maps(TcContext *ctx, const void *Ap, int64_t nA_pad, const voi
                        int64_t nB_pad, int64_t dp, TcMaps *out);
 cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, uint32_t flags,
                             cudaStream_t st);
+// Generic 2-D BF16 tensor map with 128-byte swizzle: `rows` rows of `inner`
+// elements (row stride = inner), box of box_inner x box_rows.
+sj_status tc_encode_2d(TcContext *ctx, const void *base, int64_t inner, int64_t rows,
+                       int box_inner, int box_rows, unsigned char out[128]);
 
 }  // namespace sj

@@ -168,6 +168,7 @@ class SimilarityJoin:
         import torch
         self.d = int(d)
         self.prec = prec
+        self.flags = int(flags)
         self.device = int(device)
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
@@ -240,6 +241,33 @@ class SimilarityJoin:
             return (i, j, s, st.as_dict()) if with_stats else (i, j, s)
         raise SJError(SJ_ERR_CAPACITY, "sj_threshold")
 
+    def contrastive_forward(self, A, B, T: float):
+        """(loss [1], lse [N] or [2N] with the symmetric flag) on CUDA tensors.
+
+        A, B: float32 (N, d) CUDA tensors (rounded to BF16 inside the library).
+        """
+        import torch
+        N = _rows(A, self.d)
+        if _rows(B, self.d) != N:
+            raise ValueError("A and B must have the same number of rows")
+        sym = bool(self.flags & SJ_FLAG_SYM_INFONCE)
+        loss = torch.empty(1, dtype=torch.float32, device=A.device)
+        lse = torch.empty(2 * N if sym else N, dtype=torch.float32, device=A.device)
+        _check(lib().sj_contrastive_fwd(self._h, _ptr(A), _ptr(B), N, float(T), _ptr(loss),
+                                        _ptr(lse)), "sj_contrastive_fwd")
+        return loss, lse
+
+    def contrastive_backward(self, A, B, T: float, lse, grad_loss):
+        """(dA, dB) float32 for the upstream gradient grad_loss [1] (CUDA)."""
+        import torch
+        N = _rows(A, self.d)
+        dA = torch.empty_like(A, dtype=torch.float32)
+        dB = torch.empty_like(B, dtype=torch.float32)
+        g = grad_loss.reshape(1).to(torch.float32).contiguous()
+        _check(lib().sj_backward(self._h, _ptr(A), _ptr(B), N, float(T), _ptr(lse), _ptr(g),
+                                 _ptr(dA), _ptr(dB)), "sj_backward")
+        return dA, dB
+
     def batch(self, jobs, with_stats: bool = False):
         """Run independent joins in one call.
 
@@ -304,3 +332,37 @@ class SimilarityJoin:
         if any(o is None for o in outs):
             raise SJError(SJ_ERR_CAPACITY, "sj_batch")
         return (outs, total.as_dict()) if with_stats else outs
+
+
+def _contrastive_function():
+    import torch
+
+    class ContrastiveJoin(torch.autograd.Function):
+        """InfoNCE over S = A B^T / T with the library's forward and backward.
+
+        The backward recomputes score tiles on the tensor cores; no N x N
+        matrix is stored.
+        """
+
+        @staticmethod
+        def forward(ctx, A, B, T, join):
+            A = A.contiguous()
+            B = B.contiguous()
+            loss, lse = join.contrastive_forward(A, B, T)
+            ctx.save_for_backward(A, B, lse)
+            ctx.T = T
+            ctx.join = join
+            return loss.reshape(())
+
+        @staticmethod
+        def backward(ctx, grad):
+            A, B, lse = ctx.saved_tensors
+            dA, dB = ctx.join.contrastive_backward(A, B, ctx.T, lse, grad.reshape(1))
+            return dA, dB, None, None
+
+    return ContrastiveJoin
+
+
+def contrastive_loss(A, B, T: float, join: "SimilarityJoin"):
+    """Differentiable InfoNCE loss of paired rows (positives on the diagonal)."""
+    return _contrastive_function().apply(A, B, T, join)
