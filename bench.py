@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--workload", choices=["join", "infonce"], default="join",
+                   help="join: the headline similarity join; infonce: the contrastive "
+                        "join (65,536 pairs, d = 768, T = 0.05) forward + backward")
     return p.parse_args()
 
 
@@ -193,8 +196,114 @@ def run_reference(args, w):
     return 0
 
 
+INFONCE = {"workload": "infonce_fwd_bwd_65536_d768_T0.05", "n": 65536, "d": 768,
+           "T": 0.05, "clusters": 100_000, "sigma_pair": 0.02, "seed": 0}
+
+
+def run_infonce(args):
+    """Contrastive join: one step = forward (loss, lse) + backward (dA, dB)."""
+    import torch
+
+    from paper_2112_07552_gb300 import _build, datagen, sj
+    w = dict(INFONCE)
+    if args.shape:
+        w["n"] = int(args.shape.split(",")[0])
+    n, d, T = w["n"], w["d"], w["T"]
+    _build.build()
+    A, B = datagen.paired(n, d, w["clusters"], 0.1, w["sigma_pair"], seed=w["seed"])
+    dev = torch.device("cuda", 0)
+    dA = torch.from_numpy(A).to(dev)
+    dB = torch.from_numpy(B).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    J = sj.SimilarityJoin(d, prec="bf16", device=0, stream=stream)
+    g = torch.ones(1, device=dev)
+
+    def step(Ain, Bin):
+        loss, lse = J.contrastive_forward(Ain, Bin, T)
+        gA, gB = J.contrastive_backward(Ain, Bin, T, lse, g)
+        return loss
+
+    for _ in range(args.warmup):
+        step(dA, dB)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J.contrastive_forward(dA, dB, T)
+    e1.record(stream)
+    loss, lse = J.contrastive_forward(dA, dB, T)
+    e1b = torch.cuda.Event(enable_timing=True)
+    e1b.record(stream)
+    for _ in range(args.steps):
+        J.contrastive_backward(dA, dB, T, lse, g)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms_fwd = e0.elapsed_time(e1) / args.steps
+    ms_bwd = e1b.elapsed_time(e2) / args.steps
+    ms = ms_fwd + ms_bwd
+    # e2e: pinned host inputs copied in, loss read back, every step
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xa = hA.to(dev, non_blocking=True)
+        xb = hB.to(dev, non_blocking=True)
+        float(step(xa, xb).item())
+    torch.cuda.synchronize()
+    e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    flops = 8.0 * n * n * d  # algorithmic: S (2N^2 d) + dA, dB, S-recompute (6N^2 d)
+    achieved = flops / (ms / 1e3) / 1e12
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        ab = torch.from_numpy(A).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        bb = torch.from_numpy(B).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        rows = np.arange(max(2, oracle.num_threads()))
+        t0 = time.perf_counter()
+        oracle.infonce_rows(ab, bb, T, rows)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(rows) * n / dt, "unit": METRIC, "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": "%d rows: row logsumexp + dA row over all %d columns, %.1f s"
+                         % (len(rows), n, dt)}
+    out = {
+        "metric": METRIC, "value": n * n / (ms / 1e3), "unit": METRIC, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": w["workload"], "n": n, "d": d, "T": T,
+                   "l2": "inputs 0.4 GB > L2, no flush"},
+        "stages_ms": {"forward": ms_fwd, "backward": ms_bwd},
+        "roofline": {"bound": "tensor", "kernel": "contrastive_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": src + " bf16_tflops_sustained", "traffic": None,
+                     "flops_per_step": flops},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clocks,
+        "e2e": {"value": n * n / (e_ms / 1e3), "unit": METRIC, "ms_per_step": e_ms,
+                "h2d_bytes_per_step": int(2 * n * d * 4), "d2h_bytes_per_step": 4},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+    J.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "infonce":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "workload": INFONCE["workload"],
+                              "unavailable": "the reference arm times the join workload"}))
+            return 0
+        return run_infonce(args)
     w = dict(SMALL if args.small else WORKLOAD)
     if args.shape:
         nA, nB = (int(x) for x in args.shape.split(","))

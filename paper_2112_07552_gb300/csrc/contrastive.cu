@@ -283,8 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int rb = (int)(u / n_chunks), ch = (int)(u % n_chunks);
       const int64_t row = (int64_t)rb * TM + r;
       const bool valid = row < a.n;
-      // forward state (log2 domain)
-      float m = -INFINITY, l = 0.f, diag = 0.f;
+      // forward state (log2 domain); the running sum is compensated (TwoSum),
+      // so its error does not grow with N
+      float m = -INFINITY, l = 0.f, lc = 0.f, diag = 0.f;
       // backward: this row's own-term log-sum-exp (log2 domain)
       const float lr2 = (BWD && valid && a.wr != 0.f) ? a.lse_r[row] * kLog2e : 0.f;
       for (int t = 0; t < n_tiles; ++t, ++tile) {
@@ -316,13 +317,25 @@ __global__ void __launch_bounds__(kThreads, 1)
               cm = fmaxf(cm, x[q]);
             }
             if (cm > m) {
-              l = (m == -INFINITY) ? 0.f : l * ex2(m - cm);
+              const float sc = (m == -INFINITY) ? 0.f : ex2(m - cm);
+              l *= sc;
+              lc *= sc;
               m = cm;
             }
-            float acc = 0.f;
+            // pairwise sum of the chunk, then a compensated add into l
+            float e[32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) acc += ex2(x[q] - m);
-            l += acc;
+            for (int q = 0; q < 32; ++q) e[q] = ex2(x[q] - m);
+#pragma unroll
+            for (int w2 = 16; w2 >= 1; w2 >>= 1)
+#pragma unroll
+              for (int q = 0; q < w2; ++q) e[q] += e[q + w2];
+            {
+              const float t = __fadd_rn(l, e[0]);
+              const float bp = __fsub_rn(t, l);
+              lc = __fadd_rn(lc, __fadd_rn(__fsub_rn(l, __fsub_rn(t, bp)), __fsub_rn(e[0], bp)));
+              l = t;
+            }
             const int64_t jb = col0 + c * 32;
             if (row >= jb && row < jb + 32) {
 #pragma unroll
@@ -380,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       if (!BWD) {
         if (valid) {
-          const float lse = (m + __log2f(l)) * 0.69314718055994531f;  // natural log
+          const float lse = (m + log2f(__fadd_rn(l, lc))) * 0.69314718055994531f;  // natural log
           a.lse_out[row] = lse;
           a.term_out[row] = lse - diag / a.T;
         }

@@ -7,9 +7,12 @@ approximate exp2 (relative ~1e-6 of |S| <= 1/T), so lse and loss agree to a
 few 1e-5 absolute.  The backward feeds dL/dS tiles rounded to BF16 (relative
 error <= 2^-8) to the tensor cores and accumulates N products in FP32, so each
 gradient entry is held to the bound derived from that arithmetic,
-  |dA_ik - ref| <= (2^-8 + (N + 64) 2^-22 + 1e-5) (g / (N T)) sum_j |G'_ij| |b_jk|,
-(G' = P - I, plus the column term when symmetric), and the gradient as a
-whole to a cosine of 0.999 with the reference.
+  |dA_ik - ref| <= (g / (N T)) sum_j [(2^-8 + (N + 64) 2^-22 + 1e-5) |G'_ij|
+                                       + P_ij (|dl_i| + 1e-6)] |b_jk|,
+(G' = P - I, plus the column term when symmetric), where dl_i is the
+measured error of the forward's logsumexp the backward consumes (it scales
+every P_ij of the row by exp(dl_i)), and the gradient as a whole to a cosine
+of 0.999 with the reference.
 """
 import numpy as np
 import pytest
@@ -40,8 +43,11 @@ def run(sjmod, A, B, T, sym=False, g=1.0):
     return float(loss.item()), lse.cpu().numpy(), gA.cpu().numpy(), gB.cpu().numpy()
 
 
-def grad_bounds(ab, bb, T, sym, g):
-    """Per-entry error bounds of dA and dB (see the module docstring)."""
+def grad_bounds(ab, bb, T, sym, g, dl_row=None, dl_col=None):
+    """Per-entry error bounds of dA and dB (see the module docstring).
+
+    dl_row / dl_col: measured |lse_gpu - lse_ref| per row / column (or None).
+    """
     A = oracle.bf16_bits_to_f64(ab) if ab.dtype == np.uint16 else ab.astype(np.float64)
     B = oracle.bf16_bits_to_f64(bb) if bb.dtype == np.uint16 else bb.astype(np.float64)
     N = A.shape[0]
@@ -51,13 +57,19 @@ def grad_bounds(ab, bb, T, sym, g):
     P = np.exp(S - lr)
     P /= P.sum(axis=1, keepdims=True)
     G = P - I
+    dlr = (np.zeros(N) if dl_row is None else np.asarray(dl_row)) + 1e-6
+    E = P * dlr[:, None]          # propagated lse error of the row softmax
     if sym:
         lc = S.max(axis=0, keepdims=True)
         Q = np.exp(S - lc)
         Q /= Q.sum(axis=0, keepdims=True)
         G = 0.5 * (G + Q - I)
-    c = (2.0 ** -8 + (N + 64) * 2.0 ** -22 + 1e-5) * abs(g) / (N * T)
-    return c * (np.abs(G) @ np.abs(B)), c * (np.abs(G).T @ np.abs(A))
+        dlc = (np.zeros(N) if dl_col is None else np.asarray(dl_col)) + 1e-6
+        E = 0.5 * (E + Q * dlc[None, :])
+    c = (2.0 ** -8 + (N + 64) * 2.0 ** -22 + 1e-5)
+    W = c * np.abs(G) + E
+    s = abs(g) / (N * T)
+    return s * (W @ np.abs(B)), s * (W.T @ np.abs(A))
 
 
 def check_grad(got, want, bound=None):
@@ -89,7 +101,8 @@ def test_contrastive_matches_oracle(sjmod, N, d, T, sym):
     assert np.max(np.abs(lse[:N] - lse_w)) <= 5e-5 * max(1.0, np.max(np.abs(lse_w)))
     if sym:
         assert np.max(np.abs(lse[N:] - lsec_w)) <= 5e-5 * max(1.0, np.max(np.abs(lsec_w)))
-    bA, bB = grad_bounds(ab, bb, T, sym, 0.7)
+    bA, bB = grad_bounds(ab, bb, T, sym, 0.7, np.abs(lse[:N] - lse_w),
+                         np.abs(lse[N:] - lsec_w) if sym else None)
     check_grad(gA, dA_w, bA)
     check_grad(gB, dB_w, bB)
 
@@ -163,4 +176,40 @@ def test_contrastive_debug_timeout(sjmod):
     J.close()
     # the context stays usable
     loss, _, _, _ = run(sjmod, A, B, 0.05)
+    assert np.isfinite(loss)
+
+
+def test_contrastive_8192_full(sjmod):
+    # every output against the oracle at N = 8,192, d = 768
+    N, d, T = 8192, 768, 0.05
+    A, B = datagen.paired(N, d, 1000, seed=45)
+    ab, bb = bf16_inputs(A, B)
+    loss_w, lse_w, _, dA_w, dB_w = oracle.infonce(ab, bb, T, g=1.0)
+    loss, lse, gA, gB = run(sjmod, A, B, T)
+    assert abs(loss - loss_w) <= 5e-5 * max(1.0, abs(loss_w))
+    assert np.max(np.abs(lse - lse_w)) <= 5e-5 * max(1.0, np.max(np.abs(lse_w)))
+    bA, bB = grad_bounds(ab, bb, T, False, 1.0, np.abs(lse - lse_w))
+    check_grad(gA, dA_w, bA)
+    check_grad(gB, dB_w, bB)
+
+
+def test_contrastive_65536_sampled_rows(sjmod):
+    # the full-size join: row logsumexp and dA on sampled rows (each needs one
+    # row of S only); dB needs every row's lse and is covered at N = 8,192
+    N, d, T = 65536, 768, 0.05
+    A, B = datagen.paired(N, d, 100_000, seed=0)
+    ab, bb = bf16_inputs(A, B)
+    loss, lse, gA, _ = run(sjmod, A, B, T)
+    rows = np.sort(np.random.default_rng(7).choice(N, size=24, replace=False))
+    lse_w, dA_w = oracle.infonce_rows(ab, bb, T, rows, g=1.0)
+    assert np.max(np.abs(lse[rows] - lse_w)) <= 5e-5 * max(1.0, np.max(np.abs(lse_w)))
+    # per-row bound as in grad_bounds, restricted to the sampled rows
+    A64, B64 = oracle.bf16_bits_to_f64(ab[rows]), oracle.bf16_bits_to_f64(bb)
+    S = A64 @ B64.T / T
+    P = np.exp(S - lse_w[:, None])
+    G = P.copy()
+    G[np.arange(len(rows)), rows] -= 1.0
+    c = 2.0 ** -8 + (N + 64) * 2.0 ** -22 + 1e-5
+    W = c * np.abs(G) + P * (np.abs(lse[rows] - lse_w) + 1e-6)[:, None]
+    check_grad(gA[rows], dA_w, (W @ np.abs(B64)) / (N * T))
     assert np.isfinite(loss)
