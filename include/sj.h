@@ -137,8 +137,10 @@ sj_status sj_threshold(sj_handle *h, const float *A, int64_t nA, const float *B,
                        int64_t *n_out, sj_stats *st);
 
 /* One job of a batch: an independent join with its own sizes and outputs.
- * topk_idx/topk_score may be NULL (no top-k); pairs may be NULL (no
- * threshold).  All pointers follow the same device/host rule. */
+ * k > 0 requests the top-k part (topk_idx/topk_score required when nA > 0);
+ * a non-NULL n_out requests the threshold part at tau (pairs required when
+ * capacity > 0).  A job requesting neither is skipped.  All pointers follow
+ * the same device/host rule as sj_topk. */
 typedef struct {
   const float *A;
   int64_t nA;
@@ -153,11 +155,16 @@ typedef struct {
   int64_t *n_out;
 } sj_job;
 
-/* Run n_jobs independent joins (same d and precision).  A job that asks for
- * both parts (top-k outputs and n_out) gets them from ONE scoring pass.
- * Results per job are exactly those of sj_topk / sj_threshold.  Returns the
- * first error; a job over capacity sets its *n_out and the call returns
- * SJ_ERR_CAPACITY after finishing the other jobs. */
+/* Run n_jobs independent joins of the same d and precision as ONE pipeline:
+ * one validation/packing launch over all rows, one persistent scoring launch
+ * over every job's (row block, column split) units, and one finalisation.
+ * Sec. 3.1 states one join as one matrix product; batching many uneven
+ * products into one launch is this library's own addition.  A job that asks for both parts gets them from
+ * the same scoring pass.  Results per job are exactly those of sj_topk /
+ * sj_threshold.  Input checks cover the whole batch: a non-finite or
+ * non-unit row in any job fails the call.  A job whose pairs exceed its
+ * capacity writes no pairs and sets *n_out to the required count; the other
+ * jobs complete and the call returns SJ_ERR_CAPACITY. */
 sj_status sj_batch(sj_handle *h, const sj_job *jobs, int32_t n_jobs, sj_stats *st);
 
 /* Contrastive (InfoNCE) join over N paired rows, positives on the diagonal:

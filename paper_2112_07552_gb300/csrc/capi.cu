@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -28,12 +29,18 @@ constexpr int kVersion = 100;  // 0.1.0
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// Bump allocator over the handle's workspace.
+// Bump allocator over the handle's workspace.  A measuring arena hands out
+// no memory and only counts the bytes a sequence of takes needs.
 struct Arena {
   unsigned char *base = nullptr;
   size_t size = 0, used = 0;
+  bool measure = false;
   void *take(size_t bytes) {
     size_t off = align_up(used, 256);
+    if (measure) {
+      used = off + bytes;
+      return reinterpret_cast<void *>((uintptr_t)(off + 256));
+    }
     if (off + bytes > size) return nullptr;
     used = off + bytes;
     return base + off;
@@ -202,43 +209,6 @@ Exact tau_to_exact(double tau) {
   return x;
 }
 
-struct JoinPlan {
-  PrecPlan pp;
-  int64_t nA, nB, d, nA_pad, nB_pad;
-  int S;
-  int bands;  // band lists per (row, split): epilogue column groups of the kernel
-  int64_t tiles_per_split, n_units;
-  int cap;
-};
-
-JoinPlan make_plan(const sj_handle *h, int64_t nA, int64_t nB, int k) {
-  JoinPlan p;
-  p.pp = plan_prec(h->cfg.prec, h->cfg.d);
-  p.nA = nA;
-  p.nB = nB;
-  p.d = h->cfg.d;
-  // Both operands are padded to the larger tile edge so that a self-join can
-  // share one packed copy; row blocks and column tiles cover the true sizes.
-  const int64_t edge = std::max(p.pp.BM, p.pp.BN);
-  p.nA_pad = round_up(std::max<int64_t>(nA, 1), edge);
-  p.nB_pad = round_up(std::max<int64_t>(nB, 1), edge);
-  int64_t rb = (std::max<int64_t>(nA, 1) + p.pp.BM - 1) / p.pp.BM;
-  int64_t ct = (std::max<int64_t>(nB, 1) + p.pp.BN - 1) / p.pp.BN;
-  int64_t want_units = 2 * (int64_t)h->sm_count;
-  int64_t S = (want_units + rb - 1) / rb;
-  if (S < 1 || (h->cfg.flags & SJ_FLAG_SINGLE_SPLIT)) S = 1;
-  if (S > ct) S = ct;
-  if (S > 256) S = 256;  // bounds the per-(row, split) band lists
-  p.tiles_per_split = (ct + S - 1) / S;
-  p.S = (int)((ct + p.tiles_per_split - 1) / p.tiles_per_split);
-  p.n_units = rb * p.S;
-  p.bands = h->cfg.prec == SJ_FP32 ? 1 : 2;
-  // band list per row: the k best plus the margin band (often ~60-150 rows
-  // for BF16 scores of d = 768 embeddings near the k-th score)
-  p.cap = (int)round_up(4 * (int64_t)k + 256, 32);
-  return p;
-}
-
 struct Events {
   sj_handle *h;
   void rec(int t) { cudaEventRecord(h->ev[t], h->stream); }
@@ -266,108 +236,6 @@ sj_status flags_status(unsigned f) {
   return SJ_OK;
 }
 
-// Inputs of one join, resolved to device memory.
-struct JoinIO {
-  const float *A, *B;
-  bool a_host, b_host;
-};
-
-// Shared front half: staging, validation, packing.  Fills the plan buffers.
-struct Prepared {
-  JoinPlan plan;
-  const float *A, *B;          // device float32 rows
-  void *Ap, *Bp;               // packed
-  RowMeta *metaA, *metaB;
-  float *gmaxB;
-  Counters *ctr;
-  TcMaps maps;
-};
-
-sj_status prepare_join(sj_handle *h, Arena &ar, const float *A, int64_t nA, const float *B,
-                       int64_t nB, int k, Prepared &P) {
-  cudaStream_t st = h->stream;
-  P.plan = make_plan(h, nA, nB, k);
-  const JoinPlan &pl = P.plan;
-  const int64_t d = pl.d;
-  P.ctr = static_cast<Counters *>(ar.take(sizeof(Counters)));
-  P.gmaxB = static_cast<float *>(ar.take(4 * sizeof(float)));
-  float *gmaxA = static_cast<float *>(ar.take(4 * sizeof(float)));
-  P.metaA = static_cast<RowMeta *>(ar.take(sizeof(RowMeta) * pl.nA_pad));
-  P.metaB = static_cast<RowMeta *>(ar.take(sizeof(RowMeta) * pl.nB_pad));
-  P.Ap = ar.take((size_t)pl.nA_pad * pl.pp.dp * pl.pp.elem);
-  P.Bp = (A == B && nA == nB)
-             ? P.Ap
-             : ar.take((size_t)pl.nB_pad * pl.pp.dp * pl.pp.elem);
-  P.A = A;
-  P.B = B;
-  if (!is_device_ptr(A) && nA > 0) {
-    float *dA = static_cast<float *>(ar.take((size_t)nA * d * sizeof(float)));
-    if (!dA) return SJ_ERR_INTERNAL;
-    SJ_CUDA(cudaMemcpyAsync(dA, A, (size_t)nA * d * sizeof(float), cudaMemcpyHostToDevice, st));
-    P.A = dA;
-  }
-  if (B == A) {
-    P.B = P.A;
-  } else if (!is_device_ptr(B) && nB > 0) {
-    float *dB = static_cast<float *>(ar.take((size_t)nB * d * sizeof(float)));
-    if (!dB) return SJ_ERR_INTERNAL;
-    SJ_CUDA(cudaMemcpyAsync(dB, B, (size_t)nB * d * sizeof(float), cudaMemcpyHostToDevice, st));
-    P.B = dB;
-  }
-  if (!P.ctr || !P.gmaxB || !P.metaA || !P.metaB || !P.Ap || !P.Bp) return SJ_ERR_INTERNAL;
-  SJ_CUDA(cudaMemsetAsync(P.ctr, 0, sizeof(Counters), st));
-  SJ_CUDA(cudaMemsetAsync(P.gmaxB, 0, 4 * sizeof(float), st));
-  SJ_CUDA(cudaMemsetAsync(gmaxA, 0, 4 * sizeof(float), st));
-  SJ_CUDA(launch_prepare(P.A, nA, d, pl.pp.fmt, P.Ap, pl.nA_pad, pl.pp.dp, P.metaA, gmaxA, P.ctr, st));
-  if (P.Bp != P.Ap)
-    SJ_CUDA(launch_prepare(P.B, nB, d, pl.pp.fmt, P.Bp, pl.nB_pad, pl.pp.dp, P.metaB, P.gmaxB, P.ctr, st));
-  else {
-    SJ_CUDA(cudaMemcpyAsync(P.metaB, P.metaA, sizeof(RowMeta) * pl.nB_pad, cudaMemcpyDeviceToDevice, st));
-    SJ_CUDA(cudaMemcpyAsync(P.gmaxB, gmaxA, 4 * sizeof(float), cudaMemcpyDeviceToDevice, st));
-  }
-  if (h->cfg.prec != SJ_FP32) {
-    sj_status s = tc_make_maps(h->tc, P.Ap, pl.nA_pad, P.Bp, pl.nB_pad, pl.pp.dp, &P.maps);
-    if (s != SJ_OK) return s;
-  }
-  return SJ_OK;
-}
-
-// Workspace estimate of the front half.
-size_t prepare_bytes(const JoinPlan &pl, bool a_host, bool b_host, bool self) {
-  size_t b = 4096 + sizeof(RowMeta) * (pl.nA_pad + pl.nB_pad) + 8 * 256;
-  b += (size_t)pl.nA_pad * pl.pp.dp * pl.pp.elem;
-  if (!self) b += (size_t)pl.nB_pad * pl.pp.dp * pl.pp.elem;
-  if (a_host) b += (size_t)pl.nA * pl.d * 4 + 256;
-  if (b_host && !self) b += (size_t)pl.nB * pl.d * 4 + 256;
-  return b;
-}
-
-sj_status run_score(sj_handle *h, const Prepared &P, ScoreArgs &sa) {
-  const JoinPlan &pl = P.plan;
-  sa.Ap = P.Ap;
-  sa.Bp = P.Bp;
-  sa.nA = pl.nA;
-  sa.nB = pl.nB;
-  sa.dp = pl.pp.dp;
-  sa.metaA = P.metaA;
-  sa.gmaxB = P.gmaxB;
-  sa.acc_coef = (float)pl.pp.acc_coef;
-  sa.n_splits = pl.S;
-  sa.bands_per_split = pl.bands;
-  sa.tiles_per_split = pl.tiles_per_split;
-  sa.n_units = pl.n_units;
-  sa.ctr = P.ctr;
-  if (pl.nA == 0 || pl.nB == 0) return SJ_OK;
-  int grid = (int)std::min<int64_t>(pl.n_units, (int64_t)h->sm_count * 2);
-  if (h->cfg.prec == SJ_FP32) {
-    SJ_CUDA(launch_score_simt(sa, grid, h->stream));
-  } else {
-    grid = (int)std::min<int64_t>(pl.n_units, (int64_t)h->sm_count);
-    SJ_CUDA(launch_score_tc(sa, grid, &P.maps, h->cfg.flags, h->stream));
-  }
-  return SJ_OK;
-}
-
 void fill_common_stats(sj_stats *st, const Counters &c) {
   st->n_candidates = (int64_t)c.n_candidates;
   st->n_rescored = (int64_t)c.n_rescored;
@@ -377,14 +245,6 @@ void fill_common_stats(sj_stats *st, const Counters &c) {
   float me;
   std::memcpy(&me, &c.max_err_bits, sizeof me);
   st->max_abs_err_lowprec = me;
-}
-
-sj_status check_join_args(sj_handle *h, const float *A, int64_t nA, const float *B, int64_t nB) {
-  if (!h) return SJ_ERR_INVALID_ARG;
-  if (nA < 0 || nB < 0) return SJ_ERR_INVALID_ARG;
-  if ((nA > 0 && !A) || (nB > 0 && !B)) return SJ_ERR_INVALID_ARG;
-  if (nA >= (1ll << 31) - 1024 || nB >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
-  return SJ_OK;
 }
 
 // Scratch that the fallback takes from the workspace if it fits, else from a
@@ -403,17 +263,234 @@ struct Scratch {
   }
 };
 
-// Rows whose candidates did not fit: rescan all of B with Dot2 against the
-// row's key bound, then rank the lists (shared memory, or global memory for
-// very long ones).  Lists cut off at their capacity are rescanned once more
-// with the capacity they need.
-sj_status topk_fallback(sj_handle *h, const Prepared &P, const JoinPlan &pl, const int *rows,
-                        const long long *keys, int n_rows, int k, int64_t *d_idx, float *d_score,
+// One join request: top-k part (k > 0) and/or threshold part (thr).
+struct JoinReq {
+  const float *A;
+  int64_t nA;
+  const float *B;
+  int64_t nB;
+  int k;                 // 0: no top-k
+  int64_t *out_idx;
+  float *out_score;
+  bool thr;              // threshold part requested
+  double tau;
+  sj_pair *out;
+  int64_t capacity;
+  int64_t *n_out;
+};
+
+sj_status check_req(const JoinReq &r) {
+  if (r.nA < 0 || r.nB < 0) return SJ_ERR_INVALID_ARG;
+  if ((r.nA > 0 && !r.A) || (r.nB > 0 && !r.B)) return SJ_ERR_INVALID_ARG;
+  if (r.k < 0 || r.k > 1024 || (r.k > 0 && r.nA > 0 && (!r.out_idx || !r.out_score)))
+    return SJ_ERR_INVALID_ARG;
+  if (r.thr && (!r.n_out || r.capacity < 0 || std::isnan(r.tau) || (r.capacity > 0 && !r.out)))
+    return SJ_ERR_INVALID_ARG;
+  if (r.k == 0 && !r.thr) return SJ_ERR_INVALID_ARG;
+  if (r.nA >= (1ll << 31) - 1024 || r.nB >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
+  return SJ_OK;
+}
+
+// Host side of one job: where its pointers live.
+struct JobHost {
+  bool a_host, b_host, self, ot_host, op_host, nout_dev;
+};
+
+// The batch as the kernels see it (device tables) plus host bookkeeping.
+struct BatchPlan {
+  PrecPlan pp;
+  int64_t d = 0;
+  int bands = 1;
+  std::vector<JobDev> jobs;
+  std::vector<JobHost> host;
+  std::vector<PackSeg> segs;
+  std::vector<UnitDev> units;
+  int64_t rows = 0, prows = 0, slots = 0, band_entries = 0;
+  int64_t rows_thr = 0, cap_sum = 0;
+  bool any_topk = false, any_thr = false, any_op_host = false;
+};
+
+// Column splits: a unit covers at most total_tiles / (2 SMs) column tiles, so
+// a small batch still yields about two units per SM and a large one keeps
+// units long (one band list per row and split).  At most 256 splits per job.
+sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchPlan &P) {
+  P.d = h->cfg.d;
+  P.pp = plan_prec(h->cfg.prec, P.d);
+  P.bands = h->cfg.prec == SJ_FP32 ? 1 : 2;
+  const int64_t BM = P.pp.BM, BN = P.pp.BN, edge = std::max(BM, BN);
+  int64_t total_tiles = 0;
+  for (int q = 0; q < n; ++q)
+    if (reqs[q].nA > 0 && reqs[q].nB > 0)
+      total_tiles += ((reqs[q].nA + BM - 1) / BM) * ((reqs[q].nB + BN - 1) / BN);
+  const int64_t tps_target = std::max<int64_t>(1, total_tiles / (2 * (int64_t)h->sm_count));
+  P.jobs.assign(n, JobDev{});
+  P.host.assign(n, JobHost{});
+  for (int q = 0; q < n; ++q) {
+    const JoinReq &r = reqs[q];
+    JobDev &jd = P.jobs[q];
+    JobHost &hh = P.host[q];
+    jd.nA = r.nA;
+    jd.nB = r.nB;
+    hh.self = r.A == r.B && r.nA == r.nB;
+    hh.a_host = r.nA > 0 && !is_device_ptr(r.A);
+    hh.b_host = !hh.self && r.nB > 0 && !is_device_ptr(r.B);
+    hh.ot_host = r.k > 0 && r.nA > 0 && (!is_device_ptr(r.out_idx) || !is_device_ptr(r.out_score));
+    hh.op_host = r.thr && r.capacity > 0 && !is_device_ptr(r.out);
+    hh.nout_dev = r.thr && is_device_ptr(r.n_out);
+    jd.row0 = P.rows;
+    P.rows += r.nA;
+    // packed segments (zero-row segments are left out)
+    if (hh.self) {
+      jd.a_prow0 = jd.b_prow0 = P.prows;
+      if (r.nA > 0) P.segs.push_back(PackSeg{nullptr, r.nA, P.prows, q, 2});
+      P.prows += round_up(r.nA, edge);
+    } else {
+      jd.a_prow0 = P.prows;
+      if (r.nA > 0) P.segs.push_back(PackSeg{nullptr, r.nA, P.prows, q, 0});
+      P.prows += round_up(r.nA, BM);
+      jd.b_prow0 = P.prows;
+      if (r.nB > 0) P.segs.push_back(PackSeg{nullptr, r.nB, P.prows, q, 1});
+      P.prows += round_up(r.nB, BN);
+    }
+    const int64_t rb = (r.nA + BM - 1) / BM, ct = (r.nB + BN - 1) / BN;
+    int64_t S = 0, tps = 1;
+    if (rb > 0 && ct > 0) {
+      tps = (h->cfg.flags & SJ_FLAG_SINGLE_SPLIT) ? ct : std::min(ct, tps_target);
+      if ((ct + tps - 1) / tps > 256) tps = (ct + 255) / 256;
+      S = (ct + tps - 1) / tps;
+    }
+    jd.n_col_tiles = (int32_t)ct;
+    jd.tiles_per_split = (int32_t)tps;
+    jd.n_splits = (int32_t)S;
+    jd.k = r.k;
+    // band list per row: the k best plus the margin band (often ~60-150 rows
+    // for BF16 scores of d = 768 embeddings near the k-th score)
+    jd.cap = r.k > 0 ? (int32_t)round_up(4 * (int64_t)r.k + 256, 32) : 0;
+    jd.lists = r.k > 0 ? (int32_t)(S * P.bands) : 0;
+    jd.slot0 = P.slots;
+    jd.band0 = P.band_entries;
+    P.slots += r.nA * jd.lists;
+    P.band_entries += r.nA * jd.lists * (int64_t)jd.cap;
+    for (int64_t b = 0; b < rb; ++b)
+      for (int64_t sp = 0; sp < S; ++sp) P.units.push_back(UnitDev{q, (int32_t)b, (int32_t)sp, 0});
+    // |s| <= ||a|| ||b|| < 1.00001 for validated rows: clamping tau to [-4, 4]
+    // changes no decision and keeps it inside the key and exact ranges.
+    jd.tau_f = INFINITY;
+    if (r.thr) {
+      const double tc = std::min(4.0, std::max(-4.0, r.tau));
+      float tf = (float)tc;
+      if ((double)tf > tc) tf = std::nextafter(tf, -INFINITY);
+      jd.tau_f = tf;
+      jd.tau_key = (long long)std::ceil(std::ldexp(tc, kKeyShift));
+      jd.tau_exact = tau_to_exact(tc);
+      P.rows_thr += r.nA;
+      P.cap_sum += r.capacity;
+      P.any_thr = true;
+      P.any_op_host |= hh.op_host;
+    }
+    P.any_topk |= r.k > 0;
+    jd.capacity = r.thr ? r.capacity : 0;
+  }
+  if (P.rows >= (1ll << 31) - 1024 || P.prows >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
+  // longest units first: the persistent grid takes them round-robin
+  auto tiles = [&](const UnitDev &u) {
+    const JobDev &jd = P.jobs[u.job];
+    const int64_t c0 = (int64_t)u.split * jd.tiles_per_split;
+    return std::min<int64_t>(jd.n_col_tiles, c0 + jd.tiles_per_split) - c0;
+  };
+  if (n > 1)
+    std::stable_sort(P.units.begin(), P.units.end(),
+                     [&](const UnitDev &x, const UnitDev &y) { return tiles(x) > tiles(y); });
+  return SJ_OK;
+}
+
+// Device buffers of one call, carved from the workspace.  The same sequence of
+// takes runs once on a measuring arena to size the workspace.
+struct Bufs {
+  Counters *ctr = nullptr;
+  JobDev *jobs = nullptr;
+  PackSeg *segs = nullptr;
+  UnitDev *units = nullptr;
+  RowMeta *meta = nullptr;
+  void *packed = nullptr;
+  std::vector<float *> stA, stB;
+  Cand *band = nullptr;
+  int *band_cnt = nullptr, *tier2 = nullptr, *ovf = nullptr;
+  long long *ovf_key = nullptr;
+  std::vector<int64_t *> st_idx;
+  std::vector<float *> st_score;
+  ThrCand *cand = nullptr, *acc = nullptr;
+  int64_t *row_count = nullptr, *row_off = nullptr, *row_fill = nullptr, *total = nullptr;
+  int *big_rows = nullptr, *n_big = nullptr;
+  void *scan = nullptr;
+  int64_t *job_info = nullptr;
+  PairOut *staging = nullptr, *tmp = nullptr;
+};
+
+bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long long thr_cap,
+            Bufs &B) {
+  const int n = (int)P.jobs.size();
+  const int64_t rows1 = std::max<int64_t>(P.rows, 1);
+  bool ok = true;
+  auto take = [&](size_t bytes) {
+    void *p = ar.take(bytes);
+    ok = ok && p;
+    return p;
+  };
+  B.ctr = static_cast<Counters *>(take(sizeof(Counters)));
+  B.jobs = static_cast<JobDev *>(take(sizeof(JobDev) * std::max(n, 1)));
+  B.segs = static_cast<PackSeg *>(take(sizeof(PackSeg) * std::max<size_t>(P.segs.size(), 1)));
+  B.units = static_cast<UnitDev *>(take(sizeof(UnitDev) * std::max<size_t>(P.units.size(), 1)));
+  B.meta = static_cast<RowMeta *>(take(sizeof(RowMeta) * std::max<int64_t>(P.prows, 1)));
+  B.packed = take((size_t)std::max<int64_t>(P.prows, 1) * P.pp.dp * P.pp.elem);
+  B.stA.assign(n, nullptr);
+  B.stB.assign(n, nullptr);
+  B.st_idx.assign(n, nullptr);
+  B.st_score.assign(n, nullptr);
+  for (int q = 0; q < n; ++q) {
+    if (P.host[q].a_host) B.stA[q] = static_cast<float *>(take((size_t)reqs[q].nA * P.d * 4));
+    if (P.host[q].b_host) B.stB[q] = static_cast<float *>(take((size_t)reqs[q].nB * P.d * 4));
+  }
+  if (P.any_topk) {
+    B.band = static_cast<Cand *>(take(sizeof(Cand) * std::max<int64_t>(P.band_entries, 1)));
+    B.band_cnt = static_cast<int *>(take(4 * (size_t)std::max<int64_t>(P.slots, 1)));
+    B.tier2 = static_cast<int *>(take(4 * (size_t)rows1));
+    B.ovf = static_cast<int *>(take(4 * (size_t)rows1));
+    B.ovf_key = static_cast<long long *>(take(8 * (size_t)rows1));
+    for (int q = 0; q < n; ++q)
+      if (P.host[q].ot_host) {
+        B.st_idx[q] = static_cast<int64_t *>(take((size_t)reqs[q].nA * reqs[q].k * 8));
+        B.st_score[q] = static_cast<float *>(take((size_t)reqs[q].nA * reqs[q].k * 4));
+      }
+  }
+  if (P.any_thr) {
+    B.cand = static_cast<ThrCand *>(take((size_t)thr_cap * sizeof(ThrCand)));
+    B.acc = static_cast<ThrCand *>(take((size_t)thr_cap * sizeof(ThrCand)));
+    B.row_count = static_cast<int64_t *>(take(8 * (size_t)rows1));
+    B.row_off = static_cast<int64_t *>(take(8 * (size_t)rows1));
+    B.row_fill = static_cast<int64_t *>(take(8 * (size_t)rows1));
+    B.total = static_cast<int64_t *>(take(64));
+    B.big_rows = static_cast<int *>(take(4 * (size_t)rows1));
+    B.n_big = static_cast<int *>(take(64));
+    B.scan = take(scan_scratch_bytes(rows1));
+    B.job_info = static_cast<int64_t *>(take(16 * (size_t)std::max(n, 1)));
+    if (P.any_op_host) B.staging = static_cast<PairOut *>(take((size_t)thr_cap * sizeof(PairOut)));
+    B.tmp = static_cast<PairOut *>(take((size_t)thr_cap * sizeof(PairOut)));
+  }
+  return ok;
+}
+
+// Rows whose candidates did not fit (one job): rescan all of B with Dot2
+// against the row's key bound, then rank the lists (shared memory, or global
+// memory for very long ones).  Lists cut off at their capacity are rescanned
+// once more with the capacity they need.  `rows` are local rows.
+sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const JobDev &jd,
+                        int64_t d, const int *rows, const long long *keys, int n_rows,
                         Arena &ar, int64_t &launches) {
   cudaStream_t stm = h->stream;
-  const int64_t nB = pl.nB;
+  const int64_t nB = jd.nB;
   int cap = (int)std::min<int64_t>(nB, 4096);
-  Scratch lists_s, count_s, redo_s, big_s, rows2_s, keys2_s;
+  Scratch count_s, redo_s, big_s, rows2_s, keys2_s;
   SJ_CUDA(count_s.get(ar, (size_t)n_rows * 4 + 256));
   SJ_CUDA(redo_s.get(ar, (size_t)n_rows * 4 + 256));
   SJ_CUDA(big_s.get(ar, (size_t)n_rows * 4 + 256));
@@ -427,28 +504,28 @@ sj_status topk_fallback(sj_handle *h, const Prepared &P, const JoinPlan &pl, con
     SJ_CUDA(lists.get(ar, (size_t)n_cur * cap * sizeof(KeyCand)));
     int *count = static_cast<int *>(count_s.p);
     SJ_CUDA(cudaMemsetAsync(count, 0, (size_t)n_cur * 4, stm));
-    SJ_CUDA(cudaMemsetAsync(&P.ctr->redo_rows, 0, 4 * sizeof(unsigned), stm));
+    SJ_CUDA(cudaMemsetAsync(&ctr->redo_rows, 0, 4 * sizeof(unsigned), stm));
     RescanArgs ra{};
-    ra.A = P.A;
-    ra.B = P.B;
+    ra.A = jd.A;
+    ra.B = jd.B;
     ra.nB = nB;
-    ra.d = pl.d;
-    ra.metaA = P.metaA;
-    ra.metaB = P.metaB;
-    ra.dot2_coef_key = dot2_coef_key(pl.d);
+    ra.d = d;
+    ra.metaA = meta + jd.a_prow0;
+    ra.metaB = meta + jd.b_prow0;
+    ra.dot2_coef_key = dot2_coef_key(d);
     ra.rows = cur_rows;
     ra.keys = cur_keys;
     ra.n_rows = n_cur;
     ra.lists = static_cast<KeyCand *>(lists.p);
     ra.count = count;
     ra.cap = cap;
-    ra.ctr = P.ctr;
+    ra.ctr = ctr;
     SJ_CUDA(launch_topk_rescan(ra, stm));
     RankListArgs la{};
-    la.A = P.A;
-    la.B = P.B;
-    la.d = pl.d;
-    la.k = k;
+    la.A = jd.A;
+    la.B = jd.B;
+    la.d = d;
+    la.k = jd.k;
     la.rows = cur_rows;
     la.n_rows = n_cur;
     la.lists = ra.lists;
@@ -456,12 +533,12 @@ sj_status topk_fallback(sj_handle *h, const Prepared &P, const JoinPlan &pl, con
     la.cap = cap;
     la.redo = static_cast<int *>(redo_s.p);
     la.big = static_cast<int *>(big_s.p);
-    la.out_idx = d_idx;
-    la.out_score = d_score;
-    la.ctr = P.ctr;
+    la.out_idx = jd.out_idx;
+    la.out_score = jd.out_score;
+    la.ctr = ctr;
     SJ_CUDA(launch_topk_rank_lists(la, stm));
     launches += 2;
-    sj_status s = read_counters(h, P.ctr);
+    sj_status s = read_counters(h, ctr);
     if (s != SJ_OK) return s;
     const unsigned n_big = h->h_ctr->big_rows;
     if (n_big > 0) {
@@ -497,156 +574,159 @@ sj_status topk_fallback(sj_handle *h, const Prepared &P, const JoinPlan &pl, con
   return SJ_OK;
 }
 
-// One join request: top-k part (k > 0) and/or threshold part (thr).
-struct JoinReq {
-  const float *A;
-  int64_t nA;
-  const float *B;
-  int64_t nB;
-  int k;                 // 0: no top-k
-  int64_t *out_idx;
-  float *out_score;
-  bool thr;              // threshold part requested
-  double tau;
-  sj_pair *out;
-  int64_t capacity;
-  int64_t *n_out;
-};
+// Fallback rows of the whole batch, grouped by job.
+sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, unsigned n_ovf,
+                            Arena &ar, int64_t &launches) {
+  cudaStream_t stm = h->stream;
+  std::vector<int> grow(n_ovf);
+  std::vector<long long> gkey(n_ovf);
+  SJ_CUDA(cudaMemcpyAsync(grow.data(), B.ovf, (size_t)n_ovf * 4, cudaMemcpyDeviceToHost, stm));
+  SJ_CUDA(cudaMemcpyAsync(gkey.data(), B.ovf_key, (size_t)n_ovf * 8, cudaMemcpyDeviceToHost, stm));
+  SJ_CUDA(cudaStreamSynchronize(stm));
+  std::vector<std::pair<int, int>> by_job(n_ovf);  // (job, index)
+  for (unsigned t = 0; t < n_ovf; ++t) {
+    auto it = std::upper_bound(P.jobs.begin(), P.jobs.end(), (int64_t)grow[t],
+                               [](int64_t x, const JobDev &jd) { return x < jd.row0; });
+    by_job[t] = {(int)(it - P.jobs.begin()) - 1, (int)t};
+  }
+  std::sort(by_job.begin(), by_job.end());
+  Scratch rows_s, keys_s;
+  SJ_CUDA(rows_s.get(ar, (size_t)n_ovf * 4 + 256));
+  SJ_CUDA(keys_s.get(ar, (size_t)n_ovf * 8 + 256));
+  std::vector<int> lrow(n_ovf);
+  std::vector<long long> lkey(n_ovf);
+  for (unsigned t = 0; t < n_ovf; ++t) {
+    const int q = by_job[t].first, src = by_job[t].second;
+    lrow[t] = (int)(grow[src] - P.jobs[q].row0);
+    lkey[t] = gkey[src];
+  }
+  SJ_CUDA(cudaMemcpyAsync(rows_s.p, lrow.data(), (size_t)n_ovf * 4, cudaMemcpyHostToDevice, stm));
+  SJ_CUDA(cudaMemcpyAsync(keys_s.p, lkey.data(), (size_t)n_ovf * 8, cudaMemcpyHostToDevice, stm));
+  SJ_CUDA(cudaStreamSynchronize(stm));
+  for (unsigned t0 = 0; t0 < n_ovf;) {
+    unsigned t1 = t0;
+    while (t1 < n_ovf && by_job[t1].first == by_job[t0].first) ++t1;
+    const JobDev &jd = P.jobs[by_job[t0].first];
+    sj_status s = topk_fallback(h, B.ctr, B.meta, jd, P.d, static_cast<int *>(rows_s.p) + t0,
+                                static_cast<long long *>(keys_s.p) + t0, (int)(t1 - t0), ar,
+                                launches);
+    if (s != SJ_OK) return s;
+    t0 = t1;
+  }
+  return SJ_OK;
+}
 
-// Both parts share one validation/packing pass and one scoring pass.
-sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
-  const float *A = r.A, *B = r.B;
-  const int64_t nA = r.nA, nB = r.nB;
-  const int k = r.k;
-  sj_status s = check_join_args(h, A, nA, B, nB);
-  if (s != SJ_OK) return s;
-  if (k < 0 || k > 1024 || (k > 0 && nA > 0 && (!r.out_idx || !r.out_score)))
-    return SJ_ERR_INVALID_ARG;
-  if (r.thr && (!r.n_out || r.capacity < 0 || std::isnan(r.tau) || (r.capacity > 0 && !r.out)))
-    return SJ_ERR_INVALID_ARG;
-  if (k == 0 && !r.thr) return SJ_ERR_INVALID_ARG;
+// All jobs of a batch share one validation/packing pass, one scoring launch
+// and one finalisation pipeline.
+sj_status join_batch(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
+  if (!h || n < 0 || (n > 0 && !reqs)) return SJ_ERR_INVALID_ARG;
+  for (int q = 0; q < n; ++q) {
+    sj_status s = check_req(reqs[q]);
+    if (s != SJ_OK) return s;
+  }
+  if (st) std::memset(st, 0, sizeof *st);
+  if (n == 0) return SJ_OK;
   SJ_CUDA(cudaSetDevice(h->cfg.device));
   cudaStream_t stm = h->stream;
   Events ev{h};
   int64_t launches = 0;
-  if (st) std::memset(st, 0, sizeof *st);
-
-  // |s| <= ||a|| ||b|| < 1.00001 for validated rows: clamping tau to [-4, 4]
-  // changes no decision and keeps it inside the key and exact ranges.
-  const double tau_c = std::min(4.0, std::max(-4.0, r.thr ? r.tau : 4.0));
-  float tau_f = INFINITY;
-  if (r.thr) {
-    tau_f = (float)tau_c;
-    if ((double)tau_f > tau_c) tau_f = std::nextafter(tau_f, -INFINITY);
-  }
-  const long long tau_key = (long long)std::ceil(std::ldexp(tau_c, kKeyShift));
-  const Exact tau_ex = tau_to_exact(tau_c);
-
-  const bool a_host = nA > 0 && !is_device_ptr(A);
-  const bool b_host = nB > 0 && !is_device_ptr(B) && B != A;
-  const bool ot_host = k > 0 && nA > 0 && (!is_device_ptr(r.out_idx) || !is_device_ptr(r.out_score));
-  const bool op_host = r.thr && r.capacity > 0 && !is_device_ptr(r.out);
-  const JoinPlan pl = make_plan(h, nA, nB, k);
-  const bool self = (A == B && nA == nB);
-  const size_t slots = (size_t)std::max<int64_t>(nA, 1) * pl.S * pl.bands;
-  const size_t rows1 = (size_t)std::max<int64_t>(nA, 1);
+  BatchPlan P;
+  sj_status s = make_batch_plan(h, reqs, n, P);
+  if (s != SJ_OK) return s;
   unsigned long long thr_cap = 0;
-  if (r.thr)
-    thr_cap = (unsigned long long)std::max<int64_t>({(int64_t)1 << 16, 2 * nA,
-                                                     r.capacity + r.capacity / 4});
+  if (P.any_thr)
+    thr_cap = (unsigned long long)std::max<int64_t>(
+        {(int64_t)1 << 16, 2 * P.rows_thr,
+         std::min<int64_t>(P.cap_sum + P.cap_sum / 4, 32 * P.rows_thr + (1 << 20))});
 
   for (int attempt = 0; attempt < 3; ++attempt) {
-    ev.rec(0);
-    size_t bytes = prepare_bytes(pl, a_host, b_host, self);
-    if (k > 0) {
-      bytes += slots * (size_t)pl.cap * sizeof(Cand) + 256;  // band lists
-      bytes += slots * 4 + 256;                              // band counts
-      bytes += rows1 * 16 + 768;                             // tier-2/overflow rows, keys
-      if (ot_host) bytes += (size_t)nA * k * 12 + 512;
+    Bufs B;
+    {
+      Arena meas;
+      meas.measure = true;
+      layout(meas, P, reqs, thr_cap, B);
+      s = ensure_ws(h, meas.used + 4096);
+      if (s != SJ_OK) return s;
     }
-    if (r.thr) {
-      bytes += (size_t)thr_cap * sizeof(ThrCand) * 2 + 512;  // candidates + accepted
-      bytes += rows1 * 8 * 3 + 768;                          // count, offset, fill
-      bytes += scan_scratch_bytes(nA) + 256 + 4096;
-    }
-    s = ensure_ws(h, bytes);
-    if (s != SJ_OK) return s;
     Arena ar{static_cast<unsigned char *>(h->ws), h->ws_size, 0};
-    Prepared P;
-    s = prepare_join(h, ar, A, nA, B, nB, k, P);
-    if (s != SJ_OK) return s;
-    launches += (P.Bp == P.Ap) ? 1 : 2;
-    Cand *band = nullptr;
-    int *band_cnt = nullptr, *ovf = nullptr, *tier2 = nullptr;
-    long long *ovf_key = nullptr;
-    int64_t *d_idx = r.out_idx;
-    float *d_score = r.out_score;
-    if (k > 0) {
-      band = static_cast<Cand *>(ar.take(slots * (size_t)pl.cap * sizeof(Cand)));
-      band_cnt = static_cast<int *>(ar.take(slots * 4));
-      ovf = static_cast<int *>(ar.take(rows1 * 4));
-      tier2 = static_cast<int *>(ar.take(rows1 * 4));
-      ovf_key = static_cast<long long *>(ar.take(rows1 * 8));
-      if (ot_host) {
-        d_idx = static_cast<int64_t *>(ar.take((size_t)nA * k * 8));
-        d_score = static_cast<float *>(ar.take((size_t)nA * k * 4));
-      }
-      if (!band || !band_cnt || !ovf || !tier2 || !ovf_key ||
-          (nA > 0 && (!d_idx || !d_score)))
-        return SJ_ERR_INTERNAL;
+    if (!layout(ar, P, reqs, thr_cap, B)) return SJ_ERR_INTERNAL;
+    ev.rec(0);
+    // device pointers of every job
+    for (int q = 0; q < n; ++q) {
+      const JoinReq &r = reqs[q];
+      JobDev &jd = P.jobs[q];
+      const JobHost &hh = P.host[q];
+      jd.A = hh.a_host ? B.stA[q] : r.A;
+      jd.B = hh.self ? jd.A : (hh.b_host ? B.stB[q] : r.B);
+      jd.out_idx = hh.ot_host ? B.st_idx[q] : r.out_idx;
+      jd.out_score = hh.ot_host ? B.st_score[q] : r.out_score;
+      jd.out_pairs = (r.thr && !hh.op_host && r.capacity > 0) ? reinterpret_cast<PairOut *>(r.out)
+                                                              : nullptr;
+      jd.gmaxB[0] = jd.gmaxB[1] = jd.gmaxB[2] = 0.f;
+      jd.n_pairs = 0;
+      if (hh.a_host)
+        SJ_CUDA(cudaMemcpyAsync(B.stA[q], r.A, (size_t)r.nA * P.d * 4, cudaMemcpyHostToDevice, stm));
+      if (hh.b_host)
+        SJ_CUDA(cudaMemcpyAsync(B.stB[q], r.B, (size_t)r.nB * P.d * 4, cudaMemcpyHostToDevice, stm));
     }
-    ThrCand *cand = nullptr, *accd = nullptr;
-    int64_t *row_count = nullptr, *row_off = nullptr, *row_fill = nullptr, *total = nullptr;
-    int *n_big = nullptr;
-    void *scan_scr = nullptr;
-    if (r.thr) {
-      cand = static_cast<ThrCand *>(ar.take((size_t)thr_cap * sizeof(ThrCand)));
-      accd = static_cast<ThrCand *>(ar.take((size_t)thr_cap * sizeof(ThrCand)));
-      row_count = static_cast<int64_t *>(ar.take(rows1 * 8));
-      row_off = static_cast<int64_t *>(ar.take(rows1 * 8));
-      row_fill = static_cast<int64_t *>(ar.take(rows1 * 8));
-      total = static_cast<int64_t *>(ar.take(64));
-      n_big = static_cast<int *>(ar.take(64));
-      scan_scr = ar.take(scan_scratch_bytes(nA));
-      if (!cand || !accd || !row_count || !row_off || !row_fill || !total || !n_big || !scan_scr)
-        return SJ_ERR_INTERNAL;
-    }
+    for (PackSeg &sg : P.segs) sg.src = sg.side == 1 ? P.jobs[sg.job].B : P.jobs[sg.job].A;
+    SJ_CUDA(cudaMemsetAsync(B.ctr, 0, sizeof(Counters), stm));
+    SJ_CUDA(cudaMemcpyAsync(B.jobs, P.jobs.data(), sizeof(JobDev) * n, cudaMemcpyHostToDevice, stm));
+    if (!P.segs.empty())
+      SJ_CUDA(cudaMemcpyAsync(B.segs, P.segs.data(), sizeof(PackSeg) * P.segs.size(),
+                              cudaMemcpyHostToDevice, stm));
+    if (!P.units.empty())
+      SJ_CUDA(cudaMemcpyAsync(B.units, P.units.data(), sizeof(UnitDev) * P.units.size(),
+                              cudaMemcpyHostToDevice, stm));
+    SJ_CUDA(launch_prepare(B.segs, (int)P.segs.size(), B.jobs, P.prows, P.d, P.pp.fmt, B.packed,
+                           P.pp.dp, B.meta, B.ctr, stm));
+    launches += P.prows > 0 ? 1 : 0;
     ev.rec(1);
-    s = read_counters(h, P.ctr);
+    s = read_counters(h, B.ctr);
     if (s != SJ_OK) return s;
     s = flags_status(h->h_ctr->err_flags);
     if (s != SJ_OK) return s;
 
-    if (nA == 0 || nB == 0) {
-      if (k > 0 && nA > 0) {
-        std::vector<int64_t> pad_i((size_t)nA * k, -1);
-        std::vector<float> pad_s((size_t)nA * k, -INFINITY);
-        SJ_CUDA(cudaMemcpyAsync(r.out_idx, pad_i.data(), pad_i.size() * 8, cudaMemcpyDefault, stm));
-        SJ_CUDA(cudaMemcpyAsync(r.out_score, pad_s.data(), pad_s.size() * 4, cudaMemcpyDefault, stm));
-        SJ_CUDA(cudaStreamSynchronize(stm));
+    // ---- scoring pass with the fused filter ----
+    if (P.any_topk && P.slots > 0)
+      SJ_CUDA(cudaMemsetAsync(B.band_cnt, 0, (size_t)P.slots * 4, stm));
+    if (!P.units.empty()) {
+      ScoreArgs sa{};
+      sa.jobs = B.jobs;
+      sa.n_jobs = n;
+      sa.units = B.units;
+      sa.n_units = (int64_t)P.units.size();
+      sa.Ap = B.packed;
+      sa.Bp = B.packed;
+      sa.dp = P.pp.dp;
+      sa.metaA = B.meta;
+      sa.acc_coef = (float)P.pp.acc_coef;
+      sa.bands_per_split = P.bands;
+      sa.band = B.band;
+      sa.band_cnt = B.band_cnt;
+      sa.thr = B.cand;
+      sa.thr_cap = thr_cap;
+      sa.ctr = B.ctr;
+      if (h->cfg.prec == SJ_FP32) {
+        const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count * 2);
+        SJ_CUDA(launch_score_simt(sa, grid, stm));
+      } else {
+        TcMaps maps;
+        s = tc_make_maps(h->tc, B.packed, P.prows, B.packed, P.prows, P.pp.dp, &maps);
+        if (s != SJ_OK) return s;
+        const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count);
+        SJ_CUDA(launch_score_tc(sa, grid, &maps, h->cfg.flags, stm));
       }
-      if (r.thr) *r.n_out = 0;
-      return SJ_OK;
+      launches += 1;
     }
-
-    ScoreArgs sa{};
-    sa.k = k;
-    sa.tau_f = tau_f;
-    sa.band = band;
-    sa.cap = k > 0 ? pl.cap : 0;
-    sa.band_cnt = band_cnt;
-    sa.thr = cand;
-    sa.thr_cap = thr_cap;
-    s = run_score(h, P, sa);
-    if (s != SJ_OK) return s;
-    launches += 1;
     ev.rec(2);
-    if (r.thr) {
-      s = read_counters(h, P.ctr);
+    unsigned long long n_cand = 0;
+    if (P.any_thr) {
+      s = read_counters(h, B.ctr);
       if (s != SJ_OK) return s;
       s = flags_status(h->h_ctr->err_flags);
       if (s != SJ_OK) return s;
-      const unsigned long long n_cand = h->h_ctr->thr_count;
+      n_cand = h->h_ctr->thr_count;
       if (n_cand > thr_cap) {
         thr_cap = n_cand + n_cand / 8 + 1024;  // rerun with room for every candidate
         continue;
@@ -654,32 +734,25 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
     }
 
     // ---- top-k finalisation (+ fallback rows) ----
-    if (k > 0) {
+    if (P.any_topk) {
       TopkFinalArgs fa{};
-      fa.A = P.A;
-      fa.B = P.B;
-      fa.nA = nA;
-      fa.nB = nB;
-      fa.d = pl.d;
-      fa.metaA = P.metaA;
-      fa.metaB = P.metaB;
-      fa.gmaxB = P.gmaxB;
-      fa.acc_coef = (float)pl.pp.acc_coef;
-      fa.k = k;
-      fa.n_splits = pl.S * pl.bands;
-      fa.cap = pl.cap;
-      fa.band = band;
-      fa.band_cnt = band_cnt;
-      fa.dot2_coef_key = dot2_coef_key(pl.d);
-      fa.out_idx = d_idx;
-      fa.out_score = d_score;
-      fa.tier2_rows = tier2;
-      fa.overflow_rows = ovf;
-      fa.overflow_key = ovf_key;
-      fa.ctr = P.ctr;
+      fa.jobs = B.jobs;
+      fa.n_jobs = n;
+      fa.rows = P.rows;
+      fa.d = P.d;
+      fa.metaA = B.meta;
+      fa.metaB = B.meta;
+      fa.acc_coef = (float)P.pp.acc_coef;
+      fa.band = B.band;
+      fa.band_cnt = B.band_cnt;
+      fa.dot2_coef_key = dot2_coef_key(P.d);
+      fa.tier2_rows = B.tier2;
+      fa.overflow_rows = B.ovf;
+      fa.overflow_key = B.ovf_key;
+      fa.ctr = B.ctr;
       SJ_CUDA(launch_topk_finalize(fa, stm));
-      launches += 1;
-      s = read_counters(h, P.ctr);
+      launches += P.rows > 0 ? 1 : 0;
+      s = read_counters(h, B.ctr);
       if (s != SJ_OK) return s;
       s = flags_status(h->h_ctr->err_flags);
       if (s != SJ_OK) return s;
@@ -687,139 +760,112 @@ sj_status join_impl(sj_handle *h, const JoinReq &r, sj_stats *st) {
       if (n_t2 > 0) {
         SJ_CUDA(launch_topk_finalize_tier2(fa, (int)n_t2, stm));
         launches += 1;
-        s = read_counters(h, P.ctr);
+        s = read_counters(h, B.ctr);
         if (s != SJ_OK) return s;
       }
       const unsigned n_ovf = h->h_ctr->overflow_rows;
       if (n_ovf > 0) {
-        s = topk_fallback(h, P, pl, ovf, ovf_key, (int)n_ovf, k, d_idx, d_score, ar, launches);
+        s = topk_fallback_all(h, P, B, n_ovf, ar, launches);
         if (s != SJ_OK) return s;
       }
-      if (ot_host) {
-        SJ_CUDA(cudaMemcpyAsync(r.out_idx, d_idx, (size_t)nA * k * 8, cudaMemcpyDeviceToHost, stm));
-        SJ_CUDA(cudaMemcpyAsync(r.out_score, d_score, (size_t)nA * k * 4, cudaMemcpyDeviceToHost, stm));
-      }
+      for (int q = 0; q < n; ++q)
+        if (P.host[q].ot_host) {
+          const size_t e = (size_t)reqs[q].nA * reqs[q].k;
+          SJ_CUDA(cudaMemcpyAsync(reqs[q].out_idx, B.st_idx[q], e * 8, cudaMemcpyDeviceToHost, stm));
+          SJ_CUDA(cudaMemcpyAsync(reqs[q].out_score, B.st_score[q], e * 4, cudaMemcpyDeviceToHost, stm));
+        }
     }
 
     // ---- threshold finalisation ----
-    int64_t n_pairs = 0;
-    if (r.thr) {
-      const unsigned long long n_cand = h->h_ctr->thr_count;
-      SJ_CUDA(cudaMemsetAsync(row_count, 0, (size_t)nA * 8, stm));
-      SJ_CUDA(cudaMemsetAsync(row_fill, 0, (size_t)nA * 8, stm));
-      ThrFinalArgs ta{};
-      ta.A = P.A;
-      ta.B = P.B;
-      ta.nA = nA;
-      ta.nB = nB;
-      ta.d = pl.d;
-      ta.metaA = P.metaA;
-      ta.metaB = P.metaB;
-      ta.dot2_coef_key = dot2_coef_key(pl.d);
-      ta.tau_key = tau_key;
-      ta.tau_exact = tau_ex;
-      ta.cand = cand;
-      ta.n_cand = (int64_t)n_cand;
-      ta.row_count = row_count;
-      ta.accepted = accd;
-      ta.ctr = P.ctr;
-      SJ_CUDA(launch_thr_rescore(ta, stm));
-      launches += n_cand ? 1 : 0;
-      s = read_counters(h, P.ctr);
-      if (s != SJ_OK) return s;
-      n_pairs = (int64_t)h->h_ctr->n_pairs;
-      *r.n_out = n_pairs;
-      if (n_pairs > r.capacity) {
-        if (st) {
-          fill_common_stats(st, *h->h_ctr);
-          st->n_pairs = n_pairs;
-        }
-        return SJ_ERR_CAPACITY;
+    int64_t n_pairs_all = 0;
+    bool over_cap = false;
+    if (P.any_thr) {
+      std::vector<int64_t> info(2 * (size_t)n, 0);
+      if (n_cand > 0) {
+        SJ_CUDA(cudaMemsetAsync(B.row_count, 0, (size_t)P.rows * 8, stm));
+        SJ_CUDA(cudaMemsetAsync(B.row_fill, 0, (size_t)P.rows * 8, stm));
+        SJ_CUDA(cudaMemsetAsync(B.n_big, 0, sizeof(int), stm));
+        ThrFinalArgs ta{};
+        ta.jobs = B.jobs;
+        ta.n_jobs = n;
+        ta.d = P.d;
+        ta.metaA = B.meta;
+        ta.metaB = B.meta;
+        ta.dot2_coef_key = dot2_coef_key(P.d);
+        ta.cand = B.cand;
+        ta.n_cand = &B.ctr->thr_count;
+        ta.cand_cap = (int64_t)thr_cap;
+        ta.row_count = B.row_count;
+        ta.accepted = B.acc;
+        ta.ctr = B.ctr;
+        const int g_res = (int)std::min<unsigned long long>((n_cand + 7) / 8, 152ull * 32);
+        SJ_CUDA(launch_thr_rescore(ta, g_res, stm));
+        SJ_CUDA(launch_exclusive_scan(B.row_count, B.row_off, P.rows, B.total, B.scan, stm));
+        SJ_CUDA(launch_job_pairs(B.jobs, n, P.rows, B.row_off, B.total, B.job_info, stm));
+        const int g_sc = (int)std::min<unsigned long long>((n_cand + 255) / 256, 152ull * 16);
+        SJ_CUDA(launch_thr_scatter(B.jobs, n, B.acc, &B.ctr->n_pairs, (int64_t)thr_cap,
+                                   B.row_off, B.row_fill, B.staging, g_sc, stm));
+        SJ_CUDA(launch_thr_sort_rows(B.jobs, n, P.rows, B.row_off, B.row_count, B.staging,
+                                     B.big_rows, B.n_big, stm));
+        SJ_CUDA(launch_thr_sort_big(B.jobs, n, B.staging, B.tmp, B.row_off, B.row_count,
+                                    B.big_rows, B.n_big, 2 * h->sm_count, stm));
+        launches += 9;
+        SJ_CUDA(cudaMemcpyAsync(info.data(), B.job_info, 16 * (size_t)n, cudaMemcpyDeviceToHost, stm));
+        SJ_CUDA(cudaStreamSynchronize(stm));
       }
-      if (n_pairs > 0) {
-        SJ_CUDA(launch_exclusive_scan(row_count, row_off, nA, total, scan_scr, stm));
-        launches += 3;
-        Arena ar2 = ar;
-        PairOut *d_out = op_host ? static_cast<PairOut *>(ar2.take((size_t)n_pairs * sizeof(PairOut)))
-                                 : reinterpret_cast<PairOut *>(r.out);
-        // the candidate list is free now: reuse it as merge-sort scratch when it fits
-        PairOut *tmp = ((size_t)thr_cap * sizeof(ThrCand) >= (size_t)n_pairs * sizeof(PairOut))
-                           ? reinterpret_cast<PairOut *>(cand)
-                           : static_cast<PairOut *>(ar2.take((size_t)n_pairs * sizeof(PairOut)));
-        bool own_out = false, own_tmp = false;
-        if (!d_out) {
-          if (cudaMalloc(&d_out, (size_t)n_pairs * sizeof(PairOut)) != cudaSuccess) {
-            cudaGetLastError();
-            return SJ_ERR_OOM;
-          }
-          own_out = true;
+      for (int q = 0; q < n; ++q) {
+        const JoinReq &r = reqs[q];
+        if (!r.thr) continue;
+        const int64_t np = info[2 * q], off = info[2 * q + 1];
+        n_pairs_all += np;
+        if (P.host[q].nout_dev) {
+          SJ_CUDA(cudaMemcpyAsync(r.n_out, &info[2 * q], 8, cudaMemcpyHostToDevice, stm));
+        } else {
+          *r.n_out = np;
         }
-        if (!tmp) {
-          if (cudaMalloc(&tmp, (size_t)n_pairs * sizeof(PairOut)) != cudaSuccess) {
-            cudaGetLastError();
-            if (own_out) cudaFree(d_out);
-            return SJ_ERR_OOM;
-          }
-          own_tmp = true;
+        if (np > r.capacity) {
+          over_cap = true;
+        } else if (np > 0 && P.host[q].op_host) {
+          SJ_CUDA(cudaMemcpyAsync(r.out, B.staging + off, (size_t)np * sizeof(PairOut),
+                                  cudaMemcpyDeviceToHost, stm));
         }
-        cudaError_t e = launch_thr_scatter(accd, total, n_pairs, row_off, row_fill, d_out, stm);
-        // rows of more than 32 pairs are listed in row_fill's memory, which the
-        // scatter (earlier on the same stream) no longer needs
-        int *big_rows = reinterpret_cast<int *>(row_fill);
-        if (e == cudaSuccess) e = cudaMemsetAsync(n_big, 0, sizeof(int), stm);
-        if (e == cudaSuccess)
-          e = launch_thr_sort_rows(d_out, row_off, row_count, nA, big_rows, n_big, (int)nA, stm);
-        launches += 2;
-        int hb = 0;
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(&h->h_i64[0], n_big, sizeof(int), cudaMemcpyDeviceToHost, stm);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
-        if (e == cudaSuccess) {
-          std::memcpy(&hb, &h->h_i64[0], sizeof(int));
-          e = launch_thr_sort_big(d_out, tmp, row_off, row_count, big_rows, n_big, hb, stm);
-          launches += hb ? 1 : 0;
-        }
-        if (e == cudaSuccess && op_host)
-          e = cudaMemcpyAsync(r.out, d_out, (size_t)n_pairs * sizeof(PairOut), cudaMemcpyDeviceToHost, stm);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
-        if (own_out) cudaFree(d_out);
-        if (own_tmp) cudaFree(tmp);
-        if (e != cudaSuccess) return cuda_status(e);
       }
     }
     ev.rec(3);
-    s = read_counters(h, P.ctr);  // also drains the stream
+    s = read_counters(h, B.ctr);  // also drains the stream
     if (s != SJ_OK) return s;
     if (st) {
       fill_common_stats(st, *h->h_ctr);
-      if (r.thr) st->n_candidates += (int64_t)h->h_ctr->thr_count;
-      st->n_pairs = n_pairs;
+      st->n_candidates += (int64_t)n_cand;
+      st->n_pairs = n_pairs_all;
       st->n_launches = launches;
       st->ms_prepare = ev.ms(0, 1);
       st->ms_score = ev.ms(1, 2);
       st->ms_select = ev.ms(2, 3);
       st->ms_total = ev.ms(0, 3);
-      float mB = 0.f;
       st->margin_max = 0.0;
-      (void)mB;
     }
-    return flags_status(h->h_ctr->err_flags);
+    s = flags_status(h->h_ctr->err_flags);
+    if (s != SJ_OK) return s;
+    return over_cap ? SJ_ERR_CAPACITY : SJ_OK;
   }
   return SJ_ERR_INTERNAL;
 }
 
 sj_status topk_impl(sj_handle *h, const float *A, int64_t nA, const float *B, int64_t nB,
                     int32_t k, int64_t *out_idx, float *out_score, sj_stats *st) {
+  if (!h) return SJ_ERR_INVALID_ARG;
   if (k < 1) return SJ_ERR_INVALID_ARG;
   JoinReq r{A, nA, B, nB, k, out_idx, out_score, false, 0.0, nullptr, 0, nullptr};
-  return join_impl(h, r, st);
+  return join_batch(h, &r, 1, st);
 }
 
 sj_status threshold_impl(sj_handle *h, const float *A, int64_t nA, const float *B, int64_t nB,
                          double tau, sj_pair *out, int64_t capacity, int64_t *n_out,
                          sj_stats *st) {
+  if (!h) return SJ_ERR_INVALID_ARG;
   JoinReq r{A, nA, B, nB, 0, nullptr, nullptr, true, tau, out, capacity, n_out};
-  return join_impl(h, r, st);
+  return join_batch(h, &r, 1, st);
 }
 
 }  // namespace
@@ -892,36 +938,20 @@ sj_status sj_threshold(sj_handle *h, const float *A, int64_t nA, const float *B,
 
 sj_status sj_batch(sj_handle *h, const sj_job *jobs, int32_t n_jobs, sj_stats *st) {
   if (!h || n_jobs < 0 || (n_jobs > 0 && !jobs)) return SJ_ERR_INVALID_ARG;
-  sj_status first = SJ_OK;
-  sj_stats acc{};
+  std::vector<JoinReq> reqs;
+  reqs.reserve((size_t)n_jobs);
   for (int32_t q = 0; q < n_jobs; ++q) {
     const sj_job &jb = jobs[q];
-    const bool want_topk = jb.topk_idx || jb.topk_score;
-    const bool want_thr = jb.pairs || jb.n_out;
-    JoinReq r{jb.A, jb.nA, jb.B, jb.nB, want_topk ? jb.k : 0, jb.topk_idx, jb.topk_score,
-              want_thr, jb.tau, jb.pairs, jb.capacity, jb.n_out};
-    if (want_topk && jb.k < 1) return SJ_ERR_INVALID_ARG;
-    sj_stats one{};
-    sj_status s = join_impl(h, r, &one);
-    acc.ms_prepare += one.ms_prepare;
-    acc.ms_score += one.ms_score;
-    acc.ms_select += one.ms_select;
-    acc.ms_total += one.ms_total;
-    acc.n_candidates += one.n_candidates;
-    acc.n_rescored += one.n_rescored;
-    acc.n_exact += one.n_exact;
-    acc.n_overflow_rows += one.n_overflow_rows;
-    acc.n_pairs += one.n_pairs;
-    acc.n_launches += one.n_launches;
-    acc.max_abs_err_lowprec = std::max(acc.max_abs_err_lowprec, one.max_abs_err_lowprec);
-    if (s != SJ_OK && first == SJ_OK) first = s;
-    if (s != SJ_OK && s != SJ_ERR_CAPACITY) {
-      if (st) *st = acc;
-      return s;
-    }
+    if (jb.k < 0) return SJ_ERR_INVALID_ARG;
+    const bool want_topk = jb.k > 0;
+    const bool want_thr = jb.n_out != nullptr;
+    if ((jb.topk_idx || jb.topk_score) && !want_topk) return SJ_ERR_INVALID_ARG;
+    if (jb.pairs && !want_thr) return SJ_ERR_INVALID_ARG;
+    if (!want_topk && !want_thr) continue;  // nothing requested
+    reqs.push_back(JoinReq{jb.A, jb.nA, jb.B, jb.nB, jb.k, jb.topk_idx, jb.topk_score, want_thr,
+                           jb.tau, jb.pairs, jb.capacity, jb.n_out});
   }
-  if (st) *st = acc;
-  return first;
+  return join_batch(h, reqs.data(), (int)reqs.size(), st);
 }
 
 }  // extern "C"

@@ -26,6 +26,8 @@
 namespace sj {
 
 struct RowCtx {
+  int64_t slot;   // band-list slot (band_cnt index)
+  int k;          // the job's k (0: no top-k part)
   float theta;    // top-k filter (+inf: no top-k part)
   float tau_lo;   // threshold filter: keep if s~ >= tau - m_i (+inf: off)
   float two_m;    // 2 m_i, rounded up
@@ -89,26 +91,28 @@ __device__ __forceinline__ float row_margin(const RowMeta &m, const float *gmaxB
   return __fadd_ru(__fadd_ru(t1, t2), t3);
 }
 
-// `list` numbers the row's band lists: split * bands_per_split + group.
-__device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, int64_t row, int list) {
-  r.i = (int32_t)row;
-  const float m = row_margin(a.metaA[row], a.gmaxB, a.acc_coef);
+// `local` is the row within its job; `list` numbers the row's band lists:
+// split * bands_per_split + column group.
+__device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, const JobDev &jb,
+                                          int64_t local, int list) {
+  r.i = (int32_t)(jb.row0 + local);
+  r.k = jb.k;
+  const float m = row_margin(a.metaA[jb.a_prow0 + local], jb.gmaxB, a.acc_coef);
   r.two_m = __fmul_ru(2.f, m);
-  r.tau_lo = __fsub_rd(a.tau_f, m);
+  r.tau_lo = __fsub_rd(jb.tau_f, m);
   r.cnt = 0;
   r.last = 0;
   r.overflow = 0;
-  r.band = a.band + ((size_t)row * a.n_splits * a.bands_per_split + list) * a.cap;
-  r.theta = a.k > 0 ? -INFINITY : INFINITY;
-  if (r.heap) heap_init(r.heap, a.k);
+  r.slot = jb.slot0 + local * jb.lists + list;
+  r.band = a.band + jb.band0 + (local * jb.lists + list) * (int64_t)jb.cap;
+  r.theta = jb.k > 0 ? -INFINITY : INFINITY;
+  if (r.heap) heap_init(r.heap, jb.k);
 }
 
 // Band count of the (row, split); an overflowed list stores -(cnt + 1), its
 // entries up to the overflow staying valid.
-__device__ __forceinline__ void row_end(const RowCtx &r, const ScoreArgs &a, int list) {
-  if (a.k > 0)
-    a.band_cnt[(size_t)r.i * a.n_splits * a.bands_per_split + list] =
-        r.overflow ? -r.cnt - 1 : r.cnt;
+__device__ __forceinline__ void row_end(const RowCtx &r, const ScoreArgs &a) {
+  if (r.k > 0) a.band_cnt[r.slot] = r.overflow ? -r.cnt - 1 : r.cnt;
 }
 
 // Visit one score that passed min(theta, tau_lo).  The band list always has
@@ -121,7 +125,7 @@ __device__ __forceinline__ void row_push(RowCtx &r, const ScoreArgs &a, float v,
       r.cnt += 1;
     }
     if (r.heap && v > r.heap[0]) {
-      heap_replace_min(r.heap, a.k, v);
+      heap_replace_min(r.heap, r.k, v);
       r.theta = __fsub_rd(r.heap[0], r.two_m);
     }
   }

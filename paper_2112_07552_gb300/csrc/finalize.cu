@@ -51,7 +51,7 @@ struct FinSmemLayout {
   uint8_t flag[CMAX];
 };
 
-// rows == nullptr: the row is blockIdx.x; otherwise rows[blockIdx.x].
+// rows == nullptr: the global row is blockIdx.x; otherwise rows[blockIdx.x].
 // A row whose band list overflowed goes to the rescan list with its key
 // bound; a row with more than CMAX candidates goes to `defer` (with its key
 // bound in defer_key when given: the last tier defers to the rescan list).
@@ -63,12 +63,18 @@ __global__ void __launch_bounds__(kFinThreads)
   FinSmemLayout<CMAX> &sm = *reinterpret_cast<FinSmemLayout<CMAX> *>(smem_raw);
   float *a_row = reinterpret_cast<float *>(smem_raw + sizeof(FinSmemLayout<CMAX>));
   __shared__ int s_n, s_overflow;
-  __shared__ float s_theta;
   __shared__ unsigned int s_maxerr;
   __shared__ unsigned s_cnt[kFinThreads / 32];
-  const int64_t i = rows ? rows[blockIdx.x] : (int64_t)blockIdx.x;
-  if (i >= a.nA) return;
-  const int S = a.n_splits, k = a.k;
+  const int64_t g = rows ? rows[blockIdx.x] : (int64_t)blockIdx.x;
+  if (g >= a.rows) return;
+  const JobDev &jb = a.jobs[find_job_row0(a.jobs, a.n_jobs, g)];
+  const int k = jb.k;
+  if (k == 0) return;
+  const int64_t i = g - jb.row0;  // row within the job
+  const int S = jb.lists;
+  const int *cnts = a.band_cnt + jb.slot0 + i * S;
+  const Cand *bands = a.band + jb.band0 + i * S * (int64_t)jb.cap;
+  const int64_t d = a.d;
   if (threadIdx.x == 0) {
     s_n = 0;
     s_overflow = 0;
@@ -76,23 +82,23 @@ __global__ void __launch_bounds__(kFinThreads)
   }
   __syncthreads();
   for (int s = threadIdx.x; s < S; s += blockDim.x)
-    if (a.band_cnt[i * S + s] < 0) s_overflow = 1;
-  // k-th largest banded score over all splits (an overflowed list holds the
+    if (cnts[s] < 0) s_overflow = 1;
+  // k-th largest banded score over all lists (an overflowed list holds the
   // entries up to its overflow, which still bound the final value from below):
   // bisection on order-preserving keys, reading the lists in place
   uint32_t T = 0;
   int n_all = 0;
   for (int s = 0; s < S; ++s) {
-    const int c = a.band_cnt[i * S + s];
+    const int c = cnts[s];
     n_all += c < 0 ? -c - 1 : c;
   }
   for (int b = 31; b >= 0; --b) {
     const uint32_t t = T | (1u << b);
     unsigned c = 0;
     for (int s = 0; s < S; ++s) {
-      const int cs = a.band_cnt[i * S + s];
+      const int cs = cnts[s];
       const int cnt = cs < 0 ? -cs - 1 : cs;
-      const Cand *bl = a.band + (i * S + s) * (int64_t)a.cap;
+      const Cand *bl = bands + s * (int64_t)jb.cap;
       for (int q = threadIdx.x; q < cnt; q += blockDim.x) c += fkey(bl[q].v) >= t;
     }
     c = __reduce_add_sync(0xffffffffu, c);
@@ -104,20 +110,13 @@ __global__ void __launch_bounds__(kFinThreads)
     if (tot >= (unsigned)k) T = t;
   }
   const float kth = n_all >= k ? fkey_inv(T) : -INFINITY;
-  float m;
-  {
-    RowMeta mi = a.metaA[i];
-    float t1 = __fmul_ru(mi.qerr, a.gmaxB[0]);
-    float t2 = __fmul_ru(mi.qnrm, a.gmaxB[2]);
-    float t3 = __fmul_ru(__fmul_ru(a.acc_coef, mi.qnrm), a.gmaxB[1]);
-    m = __fadd_ru(__fadd_ru(t1, t2), t3);
-  }
+  const float m = row_margin(a.metaA[jb.a_prow0 + i], jb.gmaxB, a.acc_coef);
   if (s_overflow) {
     if (threadIdx.x == 0) {
       // At least k rows have s~ >= kth, hence s >= kth - m: every exact top-k
       // member has s >= kth - m.  Key of that bound, rounded down.
       unsigned slot = atomicAdd(&a.ctr->overflow_rows, 1u);
-      a.overflow_rows[slot] = (int)i;
+      a.overflow_rows[slot] = (int)g;
       a.overflow_key[slot] = kth == -INFINITY
                                  ? LLONG_MIN
                                  : __float2ll_rd(__fmul_rd(__fsub_rd(kth, m), 0x1p60f));
@@ -126,8 +125,8 @@ __global__ void __launch_bounds__(kFinThreads)
   }
   const float theta = __fsub_rd(kth, __fmul_ru(2.f, m));
   for (int s = 0; s < S; ++s) {
-    const int cnt = a.band_cnt[i * S + s];
-    const Cand *bl = a.band + (i * S + s) * (int64_t)a.cap;
+    const int cnt = cnts[s];
+    const Cand *bl = bands + s * (int64_t)jb.cap;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
       const Cand cd = bl[t];
       if (cd.v >= theta) {
@@ -143,7 +142,7 @@ __global__ void __launch_bounds__(kFinThreads)
   if (s_n > CMAX) {
     if (threadIdx.x == 0) {
       unsigned slot = atomicAdd(n_defer, 1u);
-      defer[slot] = (int)i;
+      defer[slot] = (int)g;
       if (defer_key)
         defer_key[slot] = kth == -INFINITY
                               ? LLONG_MIN
@@ -152,21 +151,23 @@ __global__ void __launch_bounds__(kFinThreads)
     return;
   }
   const int n = s_n;
-  const float *a_src = a.A + i * a.d;
-  if (a.d <= kRowInSmemMax) {
-    for (int64_t t = threadIdx.x; t < a.d; t += blockDim.x) a_row[t] = a_src[t];
+  const float *a_src = jb.A + i * d;
+  const float *B = jb.B;
+  if (d <= kRowInSmemMax) {
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) a_row[t] = a_src[t];
     a_src = a_row;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
-  const float nrm_a = a.metaA[i].nrm;
+  const float nrm_a = a.metaA[jb.a_prow0 + i].nrm;
+  const RowMeta *metaB = a.metaB + jb.b_prow0;
   for (int p = warp; p < n; p += nwarps) {
     float hi, lo;
     const int32_t j = sm.j[p];
-    dot2_warp(a_src, a.B + (int64_t)j * a.d, a.d, hi, lo);
+    dot2_warp(a_src, B + (int64_t)j * d, d, hi, lo);
     if (lane == 0) {
       long long K = dot2_key(hi, lo);
-      long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, a.metaB[j].nrm);
+      long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, metaB[j].nrm);
       sm.U[p] = K + D;
       sm.L[p] = K - D;
       float err = fabsf(__fsub_rn(__fsub_rn(sm.v[p], hi), lo));
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kFinThreads)
     atomicMax(&a.ctr->max_err_bits, s_maxerr);
   }
   CandArrays c{sm.U, sm.L, sm.j, sm.v, sm.perm, sm.perm2, sm.grp, sm.flag, sm.sc, sm.ex};
-  rank_and_emit(c, n, k, a_src, a.B, a.d, a.out_idx + i * k, a.out_score + i * k, a.ctr);
+  rank_and_emit(c, n, k, a_src, B, d, jb.out_idx + i * k, jb.out_score + i * k, a.ctr);
 }
 
 // Fallback for rows whose candidates did not fit: rescan all of B with Dot2
@@ -328,33 +329,38 @@ __global__ void thr_rescore_kernel(ThrFinalArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n_cand = min64((int64_t)*a.n_cand, a.cand_cap);
+  const int64_t d = a.d;
   unsigned long long n_exact = 0;
-  for (int64_t c = w0; c < a.n_cand; c += nw) {
-    ThrCand t = a.cand[c];
-    const float *ar = a.A + (int64_t)t.i * a.d;
-    const float *br = a.B + (int64_t)t.j * a.d;
+  for (int64_t c = w0; c < n_cand; c += nw) {
+    const ThrCand t = a.cand[c];
+    const JobDev &jb = a.jobs[find_job_row0(a.jobs, a.n_jobs, t.i)];
+    const int64_t li = t.i - jb.row0;
+    const float *ar = jb.A + li * d;
+    const float *br = jb.B + (int64_t)t.j * d;
     float hi, lo;
-    dot2_warp(ar, br, a.d, hi, lo);
-    long long K = dot2_key(hi, lo);
-    long long D = dot2_halfwidth(a.dot2_coef_key, a.metaA[t.i].nrm, a.metaB[t.j].nrm);
+    dot2_warp(ar, br, d, hi, lo);
+    const long long K = dot2_key(hi, lo);
+    const long long D = dot2_halfwidth(a.dot2_coef_key, a.metaA[jb.a_prow0 + li].nrm,
+                                       a.metaB[jb.b_prow0 + t.j].nrm);
     int in;
     bool have_ex = false;
     Exact ex;
-    if (K - D >= a.tau_key) {
+    if (K - D >= jb.tau_key) {
       in = 1;
-    } else if (K + D < a.tau_key) {
+    } else if (K + D < jb.tau_key) {
       in = 0;
     } else {
-      ex = exact_dot_warp(ar, br, a.d);
+      ex = exact_dot_warp(ar, br, d);
       have_ex = true;
       ++n_exact;
-      in = exact_cmp(ex, a.tau_exact) >= 0;
+      in = exact_cmp(ex, jb.tau_exact) >= 0;
     }
     if (!in) continue;
     float s;
     if (!key_interval_round(K - D, K + D, s)) {
       if (!have_ex) {
-        ex = exact_dot_warp(ar, br, a.d);
+        ex = exact_dot_warp(ar, br, d);
         ++n_exact;
       }
       s = exact_to_float(ex);
@@ -450,36 +456,60 @@ __global__ void scan_apply_kernel(const int64_t *in, int64_t *out, int64_t n,
   }
 }
 
-__global__ void thr_scatter_kernel(const ThrCand *acc, const int64_t *n_acc_dev, int64_t cap,
-                                   const int64_t *row_off, int64_t *row_fill, PairOut *out) {
-  const int64_t n = min64(*n_acc_dev, cap);
+// Destination of global row i's pairs (see launch_thr_scatter).
+__device__ __forceinline__ PairOut *pair_seg(const JobDev &jb, PairOut *staging,
+                                             const int64_t *row_off, int64_t i) {
+  return jb.out_pairs ? jb.out_pairs + (row_off[i] - row_off[jb.row0]) : staging + row_off[i];
+}
+
+__global__ void job_pairs_kernel(JobDev *jobs, int n_jobs, int64_t rows, const int64_t *row_off,
+                                 const int64_t *total, int64_t *job_info) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_jobs) return;
+  JobDev &jb = jobs[q];
+  int64_t np = 0, off = 0;
+  if (jb.nA > 0) {
+    off = row_off[jb.row0];
+    const int64_t end = jb.row0 + jb.nA < rows ? row_off[jb.row0 + jb.nA] : *total;
+    np = end - off;
+  }
+  jb.n_pairs = np;
+  job_info[2 * q] = np;
+  job_info[2 * q + 1] = off;
+}
+
+__global__ void thr_scatter_kernel(const JobDev *jobs, int n_jobs, const ThrCand *acc,
+                                   const unsigned long long *n_acc_dev, int64_t cap,
+                                   const int64_t *row_off, int64_t *row_fill, PairOut *staging) {
+  const int64_t n = min64((int64_t)*n_acc_dev, cap);
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
-    ThrCand c = acc[t];
+    const ThrCand c = acc[t];
+    const JobDev &jb = jobs[find_job_row0(jobs, n_jobs, c.i)];
+    if (jb.n_pairs > jb.capacity) continue;
     unsigned long long r =
         atomicAdd(reinterpret_cast<unsigned long long *>(row_fill + c.i), 1ull);
-    out[row_off[c.i] + (int64_t)r] = PairOut{c.i, c.j, c.v, 0};
+    pair_seg(jb, staging, row_off, c.i)[r] = PairOut{c.i - jb.row0, c.j, c.v, 0};
   }
 }
 
 // Sort each row's pairs by j: rows of <= 32 pairs inside one warp, larger
 // rows are listed for the block kernel.
-__global__ void thr_sort_small_kernel(PairOut *out, const int64_t *row_off,
-                                      const int64_t *row_count, int64_t nA, int *big_rows,
-                                      int *n_big, int big_cap) {
+__global__ void thr_sort_small_kernel(const JobDev *jobs, int n_jobs, int64_t rows,
+                                      const int64_t *row_off, const int64_t *row_count,
+                                      PairOut *staging, int *big_rows, int *n_big) {
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= nA) return;
+  if (row >= rows) return;
   const int64_t cnt = row_count[row];
   if (cnt <= 1) return;
+  const JobDev &jb = jobs[find_job_row0(jobs, n_jobs, row)];
+  if (jb.n_pairs > jb.capacity) return;
   if (cnt > 32) {
-    if (lane == 0) {
-      int s = atomicAdd(n_big, 1);
-      if (s < big_cap) big_rows[s] = (int)row;
-    }
+    if (lane == 0) big_rows[atomicAdd(n_big, 1)] = (int)row;
     return;
   }
-  PairOut *seg = out + row_off[row];
+  PairOut *seg = pair_seg(jb, staging, row_off, row);
   PairOut p = lane < cnt ? seg[lane] : PairOut{0, INT64_MAX, 0.f, 0};
   // bitonic over 32 lanes by j
   for (int size = 2; size <= 32; size <<= 1) {
@@ -499,41 +529,47 @@ __global__ void thr_sort_small_kernel(PairOut *out, const int64_t *row_off,
   if (lane < cnt) seg[lane] = p;
 }
 
-// Rank-based merge sort of one large row in global memory (distinct j keys).
-__global__ void thr_sort_big_kernel(PairOut *out, PairOut *tmp, const int64_t *row_off,
+// Rank-based merge sort of one large row in global memory (distinct j keys),
+// ping-ponging with the row's range of `tmp` (concatenated order).
+__global__ void thr_sort_big_kernel(const JobDev *jobs, int n_jobs, PairOut *staging,
+                                    PairOut *tmp, const int64_t *row_off,
                                     const int64_t *row_count, const int *big_rows,
                                     const int *n_big) {
-  const int b = blockIdx.x;
-  if (b >= *n_big) return;
-  const int64_t row = big_rows[b];
-  const int64_t n = row_count[row];
-  PairOut *src = out + row_off[row];
-  PairOut *dst = tmp + row_off[row];
-  for (int64_t width = 1; width < n; width <<= 1) {
-    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
-      int64_t run = t / width;
-      int64_t run_start = run * width;
-      int64_t pair_start = (run & ~1ll) * width;
-      bool left = (run & 1) == 0;
-      int64_t other_start = left ? run_start + width : run_start - width;
-      int64_t other_len = left ? max64(0, min64(width, n - other_start)) : width;
-      long long key = src[t].j;
-      // number of elements in the other run with a smaller key
-      int64_t lo = 0, hi = other_len;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (src[other_start + mid].j < key) lo = mid + 1;
-        else hi = mid;
+  const int nb = *n_big;
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int64_t row = big_rows[b];
+    const int64_t n = row_count[row];
+    const JobDev &jb = jobs[find_job_row0(jobs, n_jobs, row)];
+    PairOut *const home = pair_seg(jb, staging, row_off, row);
+    PairOut *src = home;
+    PairOut *dst = tmp + row_off[row];
+    for (int64_t width = 1; width < n; width <<= 1) {
+      for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        int64_t run = t / width;
+        int64_t run_start = run * width;
+        int64_t pair_start = (run & ~1ll) * width;
+        bool left = (run & 1) == 0;
+        int64_t other_start = left ? run_start + width : run_start - width;
+        int64_t other_len = left ? max64(0, min64(width, n - other_start)) : width;
+        long long key = src[t].j;
+        // number of elements in the other run with a smaller key
+        int64_t lo = 0, hi = other_len;
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          if (src[other_start + mid].j < key) lo = mid + 1;
+          else hi = mid;
+        }
+        dst[pair_start + (t - run_start) + lo] = src[t];
       }
-      dst[pair_start + (t - run_start) + lo] = src[t];
+      __syncthreads();
+      PairOut *sw = src;
+      src = dst;
+      dst = sw;
+    }
+    if (src != home) {
+      for (int64_t t = threadIdx.x; t < n; t += blockDim.x) home[t] = src[t];
     }
     __syncthreads();
-    PairOut *sw = src;
-    src = dst;
-    dst = sw;
-  }
-  if (src != out + row_off[row]) {
-    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) out[row_off[row] + t] = src[t];
   }
 }
 
@@ -553,9 +589,9 @@ static cudaError_t launch_fin(const TopkFinalArgs &a, const int *rows, int n_row
 }
 
 cudaError_t launch_topk_finalize(const TopkFinalArgs &a, cudaStream_t st) {
-  if (a.nA == 0) return cudaSuccess;
+  if (a.rows == 0) return cudaSuccess;
   // every row: candidates up to kCSmall; rows beyond go to tier2_rows
-  return launch_fin<kCSmall>(a, nullptr, (int)a.nA, a.tier2_rows, nullptr, &a.ctr->tier2_rows,
+  return launch_fin<kCSmall>(a, nullptr, (int)a.rows, a.tier2_rows, nullptr, &a.ctr->tier2_rows,
                              st);
 }
 
@@ -604,12 +640,9 @@ cudaError_t launch_topk_rank_global(const RankListArgs &a, const int *big, int n
   return cudaGetLastError();
 }
 
-cudaError_t launch_thr_rescore(const ThrFinalArgs &a, cudaStream_t st) {
-  if (a.n_cand == 0) return cudaSuccess;
-  int64_t warps = a.n_cand;
-  int64_t blocks = (warps + 7) / 8;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  thr_rescore_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+cudaError_t launch_thr_rescore(const ThrFinalArgs &a, int grid, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  thr_rescore_kernel<<<(unsigned)grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -631,33 +664,40 @@ cudaError_t launch_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_thr_scatter(const ThrCand *accepted, const int64_t *n_acc_dev,
-                               int64_t n_acc_cap, const int64_t *row_off, int64_t *row_fill,
-                               PairOut *out, cudaStream_t st) {
-  if (n_acc_cap == 0) return cudaSuccess;
-  int64_t blocks = (n_acc_cap + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  thr_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(accepted, n_acc_dev, n_acc_cap, row_off,
-                                                       row_fill, out);
+cudaError_t launch_job_pairs(JobDev *jobs, int n_jobs, int64_t rows, const int64_t *row_off,
+                             const int64_t *total, int64_t *job_info, cudaStream_t st) {
+  if (n_jobs == 0) return cudaSuccess;
+  job_pairs_kernel<<<(n_jobs + 255) / 256, 256, 0, st>>>(jobs, n_jobs, rows, row_off, total,
+                                                         job_info);
   return cudaGetLastError();
 }
 
-cudaError_t launch_thr_sort_rows(PairOut *out, const int64_t *row_off, const int64_t *row_count,
-                                 int64_t nA, int *big_rows, int *n_big, int big_cap,
-                                 cudaStream_t st) {
-  (void)out;
-  if (nA == 0) return cudaSuccess;
-  int64_t blocks = (nA * 32 + 255) / 256;
-  thr_sort_small_kernel<<<(unsigned)blocks, 256, 0, st>>>(out, row_off, row_count, nA, big_rows,
-                                                          n_big, big_cap);
+cudaError_t launch_thr_scatter(const JobDev *jobs, int n_jobs, const ThrCand *accepted,
+                               const unsigned long long *n_acc, int64_t acc_cap,
+                               const int64_t *row_off, int64_t *row_fill, PairOut *staging,
+                               int grid, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  thr_scatter_kernel<<<(unsigned)grid, 256, 0, st>>>(jobs, n_jobs, accepted, n_acc, acc_cap,
+                                                     row_off, row_fill, staging);
   return cudaGetLastError();
 }
 
-cudaError_t launch_thr_sort_big(PairOut *out, PairOut *tmp, const int64_t *row_off,
-                                const int64_t *row_count, const int *big_rows, const int *n_big,
-                                int n_big_host, cudaStream_t st) {
-  if (n_big_host == 0) return cudaSuccess;
-  thr_sort_big_kernel<<<n_big_host, 512, 0, st>>>(out, tmp, row_off, row_count, big_rows, n_big);
+cudaError_t launch_thr_sort_rows(const JobDev *jobs, int n_jobs, int64_t rows,
+                                 const int64_t *row_off, const int64_t *row_count,
+                                 PairOut *staging, int *big_rows, int *n_big, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  const int64_t blocks = (rows * 32 + 255) / 256;
+  thr_sort_small_kernel<<<(unsigned)blocks, 256, 0, st>>>(jobs, n_jobs, rows, row_off, row_count,
+                                                          staging, big_rows, n_big);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thr_sort_big(const JobDev *jobs, int n_jobs, PairOut *staging, PairOut *tmp,
+                                const int64_t *row_off, const int64_t *row_count,
+                                const int *big_rows, const int *n_big, int grid, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  thr_sort_big_kernel<<<(unsigned)grid, 512, 0, st>>>(jobs, n_jobs, staging, tmp, row_off,
+                                                      row_count, big_rows, n_big);
   return cudaGetLastError();
 }
 

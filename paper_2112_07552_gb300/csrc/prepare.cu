@@ -50,22 +50,33 @@ __device__ __forceinline__ float sqrt_up(float x) {
   return __fsqrt_ru(__fmul_ru(fmaxf(x, 0.f), 1.0f + 0x1p-20f));
 }
 
+// Last segment starting at or before packed row p (prow0 ascending).
+__device__ __forceinline__ int find_seg(const PackSeg *segs, int n_segs, int64_t p) {
+  int lo = 0, hi = n_segs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].prow0 <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <typename OutT>
-__global__ void prepare_kernel(const float *__restrict__ X, int64_t n, int64_t d,
-                               OutT *__restrict__ Xp, int64_t n_pad, int64_t dp,
-                               RowMeta *__restrict__ meta, float *__restrict__ gmax,
-                               Counters *ctr) {
+__global__ void prepare_kernel(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows,
+                               int64_t d, OutT *__restrict__ Xp, int64_t dp,
+                               RowMeta *__restrict__ meta, Counters *ctr) {
   const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row >= n_pad) return;
-  OutT *dst = Xp ? Xp + row * dp : nullptr;
-  if (row >= n) {
-    if (dst)
-      for (int64_t k = lane; k < dp; k += 32) dst[k] = OutT(0.f);
-    if (lane == 0) meta[row] = RowMeta{0.f, 0.f, 0.f, 0};
+  const int64_t prow = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (prow >= prows) return;
+  const PackSeg sg = segs[find_seg(segs, n_segs, prow)];
+  const int64_t local = prow - sg.prow0;
+  OutT *dst = Xp + prow * dp;
+  if (local >= sg.n) {
+    for (int64_t k = lane; k < dp; k += 32) dst[k] = OutT(0.f);
+    if (lane == 0) meta[prow] = RowMeta{0.f, 0.f, 0.f, 0};
     return;
   }
-  const float *src = X + row * d;
+  const float *src = sg.src + local * d;
   float ns = 0.f, nc = 0.f;   // ||x||^2
   float qs = 0.f, qc = 0.f;   // ||x~||^2
   float es = 0.f, ec = 0.f;   // ||x~ - x||^2
@@ -73,9 +84,9 @@ __global__ void prepare_kernel(const float *__restrict__ X, int64_t n, int64_t d
   for (int64_t k = lane; k < dp; k += 32) {
     float x = k < d ? src[k] : 0.f;
     if (!isfinite(x)) { bad = true; x = 0.f; }
-    OutT q = OutT(x);
-    float qf = float(q);
-    if (dst) dst[k] = q;
+    OutT qv = OutT(x);
+    float qf = float(qv);
+    dst[k] = qv;
     acc_sq(x, ns, nc);
     acc_sq(qf, qs, qc);
     acc_sq(__fsub_rn(qf, x), es, ec);  // exact difference of x and its rounding
@@ -94,31 +105,32 @@ __global__ void prepare_kernel(const float *__restrict__ X, int64_t n, int64_t d
     m.qnrm = sqrt_up(q2);
     m.qerr = e2 > 0.f ? sqrt_up(e2) : 0.f;
     m.sexp = 0;
-    meta[row] = m;
-    if (gmax) {
-      atomic_max_pos(gmax + 0, m.nrm);
-      atomic_max_pos(gmax + 1, m.qnrm);
-      atomic_max_pos(gmax + 2, m.qerr);
+    meta[prow] = m;
+    if (sg.side != 0) {
+      float *g = jobs[sg.job].gmaxB;
+      atomic_max_pos(g + 0, m.nrm);
+      atomic_max_pos(g + 1, m.qnrm);
+      atomic_max_pos(g + 2, m.qerr);
     }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_prepare(const float *X, int64_t n, int64_t d, PackFormat fmt, void *Xp,
-                           int64_t n_pad, int64_t dp, RowMeta *meta, float *gmax,
+cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows,
+                           int64_t d, PackFormat fmt, void *Xp, int64_t dp, RowMeta *meta,
                            Counters *ctr, cudaStream_t st) {
-  if (n_pad == 0) return cudaSuccess;
+  if (prows == 0 || n_segs == 0) return cudaSuccess;
   const int warps = 8;
-  dim3 grid((unsigned)((n_pad + warps - 1) / warps)), block(32 * warps);
+  dim3 grid((unsigned)((prows + warps - 1) / warps)), block(32 * warps);
   switch (fmt) {
     case PackFormat::kF32:
-      prepare_kernel<float><<<grid, block, 0, st>>>(X, n, d, static_cast<float *>(Xp), n_pad,
-                                                    dp, meta, gmax, ctr);
+      prepare_kernel<float><<<grid, block, 0, st>>>(segs, n_segs, jobs, prows, d,
+                                                    static_cast<float *>(Xp), dp, meta, ctr);
       break;
     case PackFormat::kBF16:
       prepare_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(
-          X, n, d, static_cast<__nv_bfloat16 *>(Xp), n_pad, dp, meta, gmax, ctr);
+          segs, n_segs, jobs, prows, d, static_cast<__nv_bfloat16 *>(Xp), dp, meta, ctr);
       break;
   }
   return cudaGetLastError();

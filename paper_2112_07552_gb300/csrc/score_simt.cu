@@ -31,25 +31,27 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
   const float *Bp = static_cast<const float *>(a.Bp);
   const int64_t dp = a.dp;
   const int64_t nkt = dp / BK;
-  const int64_t n_col_tiles = (a.nB + BN - 1) / BN;
 
   for (int64_t unit = blockIdx.x; unit < a.n_units; unit += gridDim.x) {
-    const int64_t rb = unit / a.n_splits;
-    const int split = (int)(unit % a.n_splits);
-    const int64_t row0 = rb * BM;
+    const UnitDev un = a.units[unit];
+    const JobDev &jb = a.jobs[un.job];
+    const int64_t row0 = jb.a_prow0 + (int64_t)un.rb * BM;  // packed rows of A
+    const int64_t lrow = (int64_t)un.rb * BM + tid;         // local row of this thread
     RowCtx rc;
     rc.cnt = 0;
     rc.overflow = 0;
+    rc.k = jb.k;
     rc.theta = INFINITY;
     rc.tau_lo = INFINITY;
     rc.heap = nullptr;  // theta refreshed lazily from the band list
-    const bool owner = tid < BM && row0 + tid < a.nA;
-    if (owner) row_begin(rc, a, row0 + tid, split);
-
-    const int64_t ct0 = split * a.tiles_per_split;
-    const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
+    const bool owner = tid < BM && lrow < jb.nA;
+    if (owner) row_begin(rc, a, jb, lrow, un.split);
+    const int64_t nB = jb.nB;
+    const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
+    const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
     for (int64_t ct = ct0; ct < ct1; ++ct) {
-      const int64_t col0 = ct * BN;
+      const int64_t col0 = ct * BN;                  // local column
+      const int64_t bcol0 = jb.b_prow0 + col0;       // packed rows of B
       float acc[8][8];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           ra[h] = *reinterpret_cast<const float4 *>(Ap + (row0 + lr + 64 * h) * dp + k0);
-          rb4[h] = *reinterpret_cast<const float4 *>(Bp + (col0 + lr + 64 * h) * dp + k0);
+          rb4[h] = *reinterpret_cast<const float4 *>(Bp + (bcol0 + lr + 64 * h) * dp + k0);
         }
       };
       auto sstore = [&](int buf) {
@@ -115,9 +117,9 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
       __syncthreads();
       if (tid < BM) {
         // the whole of warps 0-3 (the row owners) refreshes and compacts
-        if (a.k > 0) warp_compact(rc, owner, a.k, a.cap - BN);
+        if (rc.k > 0) warp_compact(rc, owner, rc.k, jb.cap - BN);
         if (owner) {
-          const int ncol = (int)min64(BN, a.nB - col0);
+          const int ncol = (int)min64(BN, nB - col0);
           const float tmin = fminf(rc.theta, rc.tau_lo);
           for (int c = 0; c < ncol; ++c) {
             const float v = sm.S[tid][c];
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
       }
       __syncthreads();
     }
-    if (owner) row_end(rc, a, split);
+    if (owner) row_end(rc, a);
   }
 }
 

@@ -65,7 +65,7 @@ struct alignas(1024) TcSmem {
 
 // Fused filter over 32 scores of the thread's row, columns jb .. jb+31.
 __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, const ScoreArgs &a, const float (&v)[32],
-                                               int64_t jb) {
+                                               int64_t jb, int64_t nB) {
   // fast path: one compare per 32 scores (balanced max tree)
   float p16[16], q8[8];
 #pragma unroll
@@ -102,7 +102,7 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, const ScoreArgs &a, c
 #pragma unroll 1
       for (int e = 0; e < 4; ++e) {
         const float x = e == 0 ? x0 : e == 1 ? x1 : e == 2 ? x2 : x3;
-        if (x >= fminf(rc.theta, rc.tau_lo) && jq + e < a.nB) row_push(rc, a, x, (int32_t)(jq + e));
+        if (x >= fminf(rc.theta, rc.tau_lo) && jq + e < nB) row_push(rc, a, x, (int32_t)(jq + e));
       }
     }
   }
@@ -150,7 +150,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = sm.tmem_base;
 
   const int64_t nkb = a.dp / BK;
-  const int64_t n_col_tiles = (a.nB + BN - 1) / BN;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -158,11 +157,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint64_t it = 0;
       bool ok = true;
       for (int64_t unit = blockIdx.x; unit < a.n_units && ok; unit += gridDim.x) {
-        const int64_t rb = unit / a.n_splits;
-        const int split = (int)(unit % a.n_splits);
-        const int64_t ct0 = split * a.tiles_per_split;
-        const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
+        const UnitDev un = a.units[unit];
+        const JobDev &jb = a.jobs[un.job];
+        const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
+        const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
+        const int arow = (int)(jb.a_prow0 + (int64_t)un.rb * BM);
         for (int64_t ct = ct0; ct < ct1 && ok; ++ct) {
+          const int brow = (int)(jb.b_prow0 + ct * BN);
           for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
             const int s = (int)(it % STAGES);
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
@@ -172,8 +173,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             mbar_arrive_expect_tx(&sm.full[s], kTileABytes + kTileBBytes);
-            tma_load_2d(sm.a[s], &tmA, (int)(kb * BK), (int)(rb * BM), &sm.full[s]);
-            tma_load_2d(sm.b[s], &tmB, (int)(kb * BK), (int)(ct * BN), &sm.full[s]);
+            tma_load_2d(sm.a[s], &tmA, (int)(kb * BK), arow, &sm.full[s]);
+            tma_load_2d(sm.b[s], &tmB, (int)(kb * BK), brow, &sm.full[s]);
           }
         }
       }
@@ -193,9 +194,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint64_t it = 0, tile = 0;
       bool ok = true;
       for (int64_t unit = blockIdx.x; unit < a.n_units && ok; unit += gridDim.x) {
-        const int split = (int)(unit % a.n_splits);
-        const int64_t ct0 = split * a.tiles_per_split;
-        const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
+        const UnitDev un = a.units[unit];
+        const JobDev &jb = a.jobs[un.job];
+        const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
+        const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
         for (int64_t ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
           const int acc = (int)(tile & 1);
           const uint32_t aph = (uint32_t)((tile >> 1) & 1);
@@ -248,22 +250,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
       }
     }
-    const int limit = a.cap - 32 * kEpiChunks;  // room for one round of visits
     for (int64_t unit = blockIdx.x; unit < a.n_units && ok; unit += gridDim.x) {
-      const int64_t rb = unit / a.n_splits;
-      const int split = (int)(unit % a.n_splits);
-      const int64_t row = rb * BM + r_in_tile;
-      const bool owner = row < a.nA;
+      const UnitDev un = a.units[unit];
+      const JobDev &jb = a.jobs[un.job];
+      const int64_t row = (int64_t)un.rb * BM + r_in_tile;  // local row of the job
+      const bool owner = row < jb.nA;
+      const int kj = jb.k;
+      const int limit = jb.cap - 32 * kEpiChunks;  // room for one round of visits
+      const int64_t nB = jb.nB;
       RowCtx rc;
       rc.cnt = 0;
       rc.overflow = 0;
+      rc.k = kj;
       rc.theta = INFINITY;
       rc.tau_lo = INFINITY;
-      rc.heap = (a.k > 0 && a.k <= kHeapMaxK) ? sm.heap + half * BM + r_in_tile : nullptr;
-      const int list = split * a.bands_per_split + half;
-      if (owner) row_begin(rc, a, row, list);
-      const int64_t ct0 = split * a.tiles_per_split;
-      const int64_t ct1 = min64(n_col_tiles, ct0 + a.tiles_per_split);
+      rc.heap = (kj > 0 && kj <= kHeapMaxK) ? sm.heap + half * BM + r_in_tile : nullptr;
+      const int list = un.split * a.bands_per_split + half;
+      if (owner) row_begin(rc, a, jb, row, list);
+      const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
+      const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
       for (int64_t ct = ct0; ct < ct1; ++ct, ++tile) {
         const int acc = (int)(tile & 1);
         const uint32_t aph = (uint32_t)((tile >> 1) & 1);
@@ -280,20 +285,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         // two 32-column chunks per TMEM round trip
 #pragma unroll 1
         for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 64) {
-          if (a.k > 0) warp_compact(rc, owner, a.k, limit);
+          if (kj > 0) warp_compact(rc, owner, kj, limit);
           float v0[32], v1[32];
           tmem_ld32_nowait(taddr + c0, v0);
           tmem_ld32_nowait(taddr + c0 + 32, v1);
           tmem_wait_ld(v0, v1);
           if (owner) {
-            epilogue_chunk(rc, a, v0, col0 + c0);
-            epilogue_chunk(rc, a, v1, col0 + c0 + 32);
+            epilogue_chunk(rc, a, v0, col0 + c0, nB);
+            epilogue_chunk(rc, a, v1, col0 + c0 + 32, nB);
           }
         }
         fence_before();
         mbar_arrive(&sm.tmem_empty[acc]);
       }
-      if (owner) row_end(rc, a, list);
+      if (owner) row_end(rc, a);
     }
   }
 
@@ -355,7 +360,8 @@ sj_status tc_encode_2d(TcContext *ctx, const void *base, int64_t inner, int64_t 
 sj_status tc_make_maps(TcContext *ctx, const void *Ap, int64_t nA_pad, const void *Bp,
                        int64_t nB_pad, int64_t dp, TcMaps *out) {
   if (!ctx || !ctx->encode) return SJ_ERR_UNSUPPORTED;
-  if (dp % BK != 0 || nA_pad % BM != 0 || nB_pad % BN != 0) return SJ_ERR_INTERNAL;
+  // B tiles never cross a segment end (segments are padded to BN rows)
+  if (dp % BK != 0 || nA_pad % BM != 0 || nB_pad < BN) return SJ_ERR_INTERNAL;
   sj_status s = tc_encode_2d(ctx, Ap, dp, nA_pad, BK, BM, out->a);
   if (s != SJ_OK) return s;
   return tc_encode_2d(ctx, Bp, dp, nB_pad, BK, BN, out->b);

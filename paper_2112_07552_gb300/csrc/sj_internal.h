@@ -1,5 +1,11 @@
 // sj_internal.h -- host-side declarations shared by the library's translation
 // units (launchers and plan structures).  Not part of the public ABI.
+//
+// Every join kernel works on a batch of independent joins described by a job
+// table in device memory; a single join is a batch of one.  Rows are numbered
+// three ways: local (within a job), global (A rows of all jobs in job order,
+// unpadded) and packed (rows of the packed operand buffers, each job padded
+// to the tile edge).
 #pragma once
 
 #include <cstddef>
@@ -12,28 +18,82 @@ namespace sj {
 
 enum class PackFormat { kF32, kBF16 };
 
-cudaError_t launch_prepare(const float *X, int64_t n, int64_t d, PackFormat fmt, void *Xp,
-                           int64_t n_pad, int64_t dp, RowMeta *meta, float *gmax,
+struct PairOut {  // layout of sj_pair
+  int64_t i, j;
+  float score;
+  int32_t pad;
+};
+
+// One join of a batch as the kernels see it.
+struct JobDev {
+  const float *A, *B;        // float32 rows on the device (staged copies of host inputs)
+  int64_t nA, nB;
+  int64_t a_prow0, b_prow0;  // first packed row of A / B (multiples of the tile edges)
+  int64_t row0;              // first global row
+  int64_t slot0;             // first band-list slot (row-major: local row * lists + list)
+  int64_t band0;             // first band-list entry (slots of this job hold cap entries)
+  int32_t k;                 // 0: no top-k part
+  int32_t cap;               // band-list capacity
+  int32_t lists;             // band lists per row = n_splits * bands per split
+  int32_t n_splits;          // column splits
+  int32_t tiles_per_split;   // column tiles per split
+  int32_t n_col_tiles;       // column tiles of the job
+  float tau_f;               // tau rounded down to float (+inf: no threshold part)
+  float gmaxB[3];            // max over the job's B rows of {nrm, qnrm, qerr} (device-written)
+  long long tau_key;         // ceil(tau 2^60)
+  Exact tau_exact;           // ceil(tau 2^298)
+  int64_t *out_idx;          // device top-k outputs (nA x k)
+  float *out_score;
+  PairOut *out_pairs;        // device pair outputs
+  int64_t capacity;
+  int64_t n_pairs;           // device-written: pairs of the job
+};
+
+// One work unit of the scoring kernels: a 128-row block of a job's A against
+// one column split of its B.
+struct UnitDev {
+  int32_t job, rb, split, pad;
+};
+
+// Index of the job whose global rows hold x (row0 ascending, jobs[0].row0 = 0).
+__device__ __forceinline__ int find_job_row0(const JobDev *jobs, int n_jobs, int64_t x) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].row0 <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One range of the packed operand buffer: rows [prow0, next segment's prow0)
+// hold src's n rows followed by zero rows.  Both sides of every job live in
+// one packed buffer (a self-join shares one segment between its two sides).
+struct PackSeg {
+  const float *src;
+  int64_t n;
+  int64_t prow0;
+  int32_t job;
+  int32_t side;      // 0: A rows, 1: B rows, 2: both (self-join); B rows feed jobs[job].gmaxB
+};
+cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows,
+                           int64_t d, PackFormat fmt, void *Xp, int64_t dp, RowMeta *meta,
                            Counters *ctr, cudaStream_t st);
 
-// Everything the scoring kernels need for one join.
+// Everything the scoring kernels need.
 struct ScoreArgs {
-  const void *Ap;          // packed A rows (stride dp elements), rows padded
-  const void *Bp;          // packed B rows
-  int64_t nA, nB, dp;      // true row counts, padded width
-  const RowMeta *metaA;    // per-row bounds of A
-  const float *gmaxB;      // device: max over B of {nrm, qnrm, qerr}
-  float acc_coef;          // accumulation error allowance per unit norm product
-  int k;                   // top-k (0: no top-k)
-  float tau_f;             // float tau rounded down (+inf: no threshold)
-  int n_splits;            // column splits per row block
-  int bands_per_split;     // band lists per (row, split): one per epilogue column group
-  int64_t tiles_per_split; // column tiles per split
-  int64_t n_units;         // row blocks x splits
-  Cand *band;              // [nA][n_splits * bands_per_split][cap]
-  int cap;
-  int *band_cnt;           // [nA][n_splits * bands_per_split]; -(cnt + 1): overflowed
-  ThrCand *thr;            // threshold candidates
+  const JobDev *jobs;
+  int n_jobs;
+  const UnitDev *units;
+  int64_t n_units;
+  const void *Ap, *Bp;       // packed operands (stride dp elements)
+  int64_t dp;
+  const RowMeta *metaA;      // per packed row
+  float acc_coef;            // accumulation error allowance per unit norm product
+  int bands_per_split;       // band lists per (row, split): epilogue column groups
+  Cand *band;
+  int *band_cnt;             // per slot; -(cnt + 1) marks an overflowed list
+  ThrCand *thr;              // threshold candidates
   unsigned long long thr_cap;
   Counters *ctr;
 };
@@ -44,22 +104,19 @@ constexpr int kTcBM = 128, kTcBN = 256;
 
 cudaError_t launch_score_simt(const ScoreArgs &a, int grid, cudaStream_t st);
 
-// Finalisation.
+// Top-k finalisation over global rows.
 struct TopkFinalArgs {
-  const float *A;          // original float32 rows (stride d)
-  const float *B;
-  int64_t nA, nB, d;
-  const RowMeta *metaA, *metaB;
-  const float *gmaxB;
+  const JobDev *jobs;
+  int n_jobs;
+  int64_t rows;            // global rows
+  int64_t d;
+  const RowMeta *metaA, *metaB;  // per packed row
   float acc_coef;
-  int k, n_splits, cap;    // n_splits here counts band lists per row
   const Cand *band;
   const int *band_cnt;
   float dot2_coef_key;     // Dot2 error bound per unit norm product, key units
-  int64_t *out_idx;
-  float *out_score;
   int *tier2_rows;         // rows with more candidates than the first tier holds
-  int *overflow_rows;      // rows whose band list overflowed (rescan fallback)
+  int *overflow_rows;      // rows for the rescan fallback (global)
   long long *overflow_key; // their rescan key bounds
   Counters *ctr;
 };
@@ -67,17 +124,17 @@ cudaError_t launch_topk_finalize(const TopkFinalArgs &a, cudaStream_t st);
 cudaError_t launch_topk_finalize_tier2(const TopkFinalArgs &a, int n_rows, cudaStream_t st);
 
 // Fallback of the top-k finalisation: rescan B for rows whose candidates did
-// not fit, then rank the resulting short lists.
+// not fit, then rank the resulting short lists.  One job per launch.
 struct KeyCand {
   long long U, L;  // key interval of the exact score
   int32_t j, pad;
 };
 struct RescanArgs {
-  const float *A, *B;
+  const float *A, *B;      // the job's float32 rows
   int64_t nB, d;
-  const RowMeta *metaA, *metaB;
+  const RowMeta *metaA, *metaB;  // offset to the job's packed rows
   float dot2_coef_key;
-  const int *rows;         // left rows to rescan
+  const int *rows;         // local left rows to rescan
   const long long *keys;   // per row: keep j when its upper key >= keys[r]
   int n_rows;
   KeyCand *lists;          // n_rows x cap
@@ -88,17 +145,17 @@ struct RescanArgs {
 cudaError_t launch_topk_rescan(const RescanArgs &a, cudaStream_t st);
 
 struct RankListArgs {
-  const float *A, *B;
+  const float *A, *B;      // the job's float32 rows
   int64_t d;
   int k;
-  const int *rows;
+  const int *rows;         // local left rows
   int n_rows;
   const KeyCand *lists;
   const int *count;
   int cap;
   int *redo;               // list slots cut off at cap
   int *big;                // list slots longer than the shared-memory ranker takes
-  int64_t *out_idx;
+  int64_t *out_idx;        // the job's outputs
   float *out_score;
   Counters *ctr;
 };
@@ -107,39 +164,43 @@ size_t topk_rank_global_row_bytes(int64_t n);
 cudaError_t launch_topk_rank_global(const RankListArgs &a, const int *big, int n_big,
                                     void *scratch, size_t per_row, cudaStream_t st);
 
+// Threshold finalisation over the batch's candidate list.
 struct ThrFinalArgs {
-  const float *A, *B;
-  int64_t nA, nB, d;
+  const JobDev *jobs;
+  int n_jobs;
+  int64_t d;
   const RowMeta *metaA, *metaB;
   float dot2_coef_key;
-  long long tau_key;       // ceil(tau 2^60)
-  Exact tau_exact;         // ceil(tau 2^298) in the exact format
   const ThrCand *cand;
-  int64_t n_cand;
-  int64_t *row_count;      // [nA], zeroed by the caller
-  ThrCand *accepted;       // accepted pairs (score in v), capacity n_cand
+  const unsigned long long *n_cand;  // device count (clamped to cand_cap)
+  int64_t cand_cap;
+  int64_t *row_count;      // [rows], zeroed by the caller
+  ThrCand *accepted;       // accepted pairs (score in v), capacity cand_cap
   Counters *ctr;
 };
-cudaError_t launch_thr_rescore(const ThrFinalArgs &a, cudaStream_t st);
+cudaError_t launch_thr_rescore(const ThrFinalArgs &a, int grid, cudaStream_t st);
 
 // Exclusive scan of n int64 values (in place allowed); total written to *total.
 size_t scan_scratch_bytes(int64_t n);
 cudaError_t launch_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
                                   void *scratch, cudaStream_t st);
 
-struct PairOut {  // layout of sj_pair
-  int64_t i, j;
-  float score;
-  int32_t pad;
-};
-cudaError_t launch_thr_scatter(const ThrCand *accepted, const int64_t *n_acc_dev,
-                               int64_t n_acc_cap, const int64_t *row_off, int64_t *row_fill,
-                               PairOut *out, cudaStream_t st);
-cudaError_t launch_thr_sort_rows(PairOut *out, const int64_t *row_off, const int64_t *row_count,
-                                 int64_t nA, int *big_rows, int *n_big, int big_cap,
-                                 cudaStream_t st);
-cudaError_t launch_thr_sort_big(PairOut *out, PairOut *tmp, const int64_t *row_off,
-                                const int64_t *row_count, const int *big_rows, const int *n_big,
-                                int n_big_host, cudaStream_t st);
+// Per-job pair totals from the scanned row counts: jobs[q].n_pairs and
+// job_info[2q] = n_pairs, job_info[2q + 1] = offset of the job's first pair
+// in the concatenated (global row) order.
+cudaError_t launch_job_pairs(JobDev *jobs, int n_jobs, int64_t rows, const int64_t *row_off,
+                             const int64_t *total, int64_t *job_info, cudaStream_t st);
+// Pairs of a job within capacity go to jobs[q].out_pairs, or (out_pairs null)
+// to `staging` in the concatenated order; a job over capacity writes nothing.
+cudaError_t launch_thr_scatter(const JobDev *jobs, int n_jobs, const ThrCand *accepted,
+                               const unsigned long long *n_acc, int64_t acc_cap,
+                               const int64_t *row_off, int64_t *row_fill, PairOut *staging,
+                               int grid, cudaStream_t st);
+cudaError_t launch_thr_sort_rows(const JobDev *jobs, int n_jobs, int64_t rows,
+                                 const int64_t *row_off, const int64_t *row_count,
+                                 PairOut *staging, int *big_rows, int *n_big, cudaStream_t st);
+cudaError_t launch_thr_sort_big(const JobDev *jobs, int n_jobs, PairOut *staging, PairOut *tmp,
+                                const int64_t *row_off, const int64_t *row_count,
+                                const int *big_rows, const int *n_big, int grid, cudaStream_t st);
 
 }  // namespace sj

@@ -242,3 +242,71 @@ def test_fallback_paths_massive_ties(sjmod, prec, nA, nB, keys, k):
     J.close()
     assert_topk(idx, sc, A, B, k)
     assert st["n_overflow_rows"] > 0
+
+
+def _rows_or_empty(n, d, K, seed, stream):
+    if n == 0:
+        return np.zeros((0, d), np.float32)
+    return datagen.clustered(int(n), d, K, 0.1, seed=seed, stream=stream)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_uneven_mixed_jobs(sjmod, prec):
+    """One pipeline over many uneven jobs: sizes log-uniform in [1, 2500] per
+    side plus empty sides, top-k only / threshold only / both, k on both sides
+    of the shared-memory heap limit, self-joins sharing one packed segment,
+    host-pointer jobs and one job whose pairs exceed its first capacity."""
+    d, n_jobs = 64, 48
+    sa = datagen.log_uniform_sizes(n_jobs, 1, 2500, seed=5, stream=0)
+    sb = datagen.log_uniform_sizes(n_jobs, 1, 2500, seed=5, stream=1)
+    sa[3], sb[7], sa[11], sb[11] = 0, 0, 0, 0
+    J = join(sjmod, d, prec)
+    jobs, data = [], []
+    for q in range(n_jobs):
+        A = _rows_or_empty(sa[q], d, 12, 100 + q, 0)
+        self_join = q % 9 == 4
+        B = A if self_join else _rows_or_empty(sb[q], d, 12, 100 + q, 1)
+        host = q % 7 == 2
+        tA = torch.from_numpy(A) if host else dev(A)
+        tB = tA if self_join else (torch.from_numpy(B) if host else dev(B))
+        jb = {"A": tA, "B": tB}
+        mode = q % 3
+        k = (1, 5, 20, 40, 64)[q % 5]
+        tau = (0.8, 0.6, 0.9)[q % 3]
+        if mode in (0, 2):
+            jb["k"] = k
+        if mode in (1, 2):
+            jb["tau"] = tau
+            if q == 10:
+                jb["capacity"] = 1  # forces the capacity retry of this job only
+        jobs.append(jb)
+        data.append((A, B, jb.get("k"), jb.get("tau")))
+    outs, st = J.batch(jobs, with_stats=True)
+    assert st["n_launches"] > 0
+    for q, ((A, B, k, tau), o) in enumerate(zip(data, outs)):
+        if k:
+            if A.shape[0] == 0:
+                assert o["idx"].shape == (0, k)
+            else:
+                assert_topk(o["idx"], o["score"], A, B, k)
+        if tau is not None:
+            assert_thr((o["i"], o["j"], o["pair_score"]), A, B, tau)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_fallback_rows_in_several_jobs(sjmod, prec):
+    """Band-list overflow in two jobs of one batch: the fallback rows are
+    grouped per job and rescanned against that job's B only."""
+    keys = 2
+    J = sjmod.SimilarityJoin(keys, prec=prec, device=0, flags=sjmod.SJ_FLAG_SINGLE_SPLIT)
+    jobs, data = [], []
+    for q, (nA, nB) in enumerate([(30, 1300), (7, 50), (20, 3000), (1, 1)]):
+        A = datagen.one_hot(datagen.keys(nA, keys, 40 + q, 0), keys)
+        B = datagen.one_hot(datagen.keys(nB, keys, 40 + q, 1), keys)
+        jobs.append({"A": dev(A), "B": dev(B), "k": 10})
+        data.append((A, B))
+    outs, st = J.batch(jobs, with_stats=True)
+    J.close()
+    for (A, B), o in zip(data, outs):
+        assert_topk(o["idx"], o["score"], A, B, 10)
+    assert st["n_overflow_rows"] > 0
