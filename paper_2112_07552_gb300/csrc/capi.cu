@@ -363,9 +363,21 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     jd.tiles_per_split = (int32_t)tps;
     jd.n_splits = (int32_t)S;
     jd.k = r.k;
-    // band list per row: the k best plus the margin band (often ~60-150 rows
-    // for BF16 scores of d = 768 embeddings near the k-th score)
-    jd.cap = r.k > 0 ? (int32_t)round_up(4 * (int64_t)r.k + 256, 32) : 0;
+    // Band list per (row, list): the k best plus the margin band plus room for
+    // one round of visits (64).  With an exact running k-th (tensor-core path,
+    // k <= 32) the margin band is the only slack; it grows with the columns a
+    // list covers (about 60-150 entries for 500k columns of d = 768 BF16
+    // scores), so it is sized at columns / 512, within [32, 256].  Otherwise
+    // the running k-th is refreshed lazily and needs 4k + 256.
+    if (r.k > 0) {
+      const int64_t cols = tps * BN / P.bands;
+      const bool exact_running = h->cfg.prec != SJ_FP32 && r.k <= kTcHeapMaxK;
+      const int64_t slack = std::min<int64_t>(256, std::max<int64_t>(32, cols / 512));
+      jd.cap = (int32_t)(exact_running ? round_up(2 * (int64_t)r.k + 64 + slack, 32)
+                                       : round_up(4 * (int64_t)r.k + 256, 32));
+    } else {
+      jd.cap = 0;
+    }
     jd.lists = r.k > 0 ? (int32_t)(S * P.bands) : 0;
     jd.slot0 = P.slots;
     jd.band0 = P.band_entries;
@@ -392,15 +404,27 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     jd.capacity = r.thr ? r.capacity : 0;
   }
   if (P.rows >= (1ll << 31) - 1024 || P.prows >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
-  // longest units first: the persistent grid takes them round-robin
-  auto tiles = [&](const UnitDev &u) {
-    const JobDev &jd = P.jobs[u.job];
-    const int64_t c0 = (int64_t)u.split * jd.tiles_per_split;
-    return std::min<int64_t>(jd.n_col_tiles, c0 + jd.tiles_per_split) - c0;
-  };
-  if (n > 1)
-    std::stable_sort(P.units.begin(), P.units.end(),
-                     [&](const UnitDev &x, const UnitDev &y) { return tiles(x) > tiles(y); });
+  // Job-major unit order, jobs by decreasing unit length: the persistent grid
+  // takes units round-robin, so CTAs running at the same time work on the same
+  // job and share its B tiles in L2, and the schedule ends with the shortest
+  // units.
+  if (n > 1) {
+    std::vector<int> order(n);
+    for (int q = 0; q < n; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return P.jobs[x].tiles_per_split > P.jobs[y].tiles_per_split;
+    });
+    std::vector<int64_t> first(n + 1, 0);
+    for (int q = 0; q < n; ++q) {
+      const JobDev &jd = P.jobs[q];
+      first[q + 1] = first[q] + (jd.nA > 0 && jd.nB > 0 ? ((jd.nA + BM - 1) / BM) * jd.n_splits : 0);
+    }
+    std::vector<UnitDev> sorted;
+    sorted.reserve(P.units.size());
+    for (int q : order)
+      sorted.insert(sorted.end(), P.units.begin() + first[q], P.units.begin() + first[q + 1]);
+    P.units.swap(sorted);
+  }
   return SJ_OK;
 }
 
@@ -415,7 +439,7 @@ struct Bufs {
   void *packed = nullptr;
   std::vector<float *> stA, stB;
   Cand *band = nullptr;
-  int *band_cnt = nullptr, *tier2 = nullptr, *ovf = nullptr;
+  int *band_cnt = nullptr, *defer = nullptr, *tier2 = nullptr, *ovf = nullptr;
   long long *ovf_key = nullptr;
   std::vector<int64_t *> st_idx;
   std::vector<float *> st_score;
@@ -454,6 +478,7 @@ bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long lo
   if (P.any_topk) {
     B.band = static_cast<Cand *>(take(sizeof(Cand) * std::max<int64_t>(P.band_entries, 1)));
     B.band_cnt = static_cast<int *>(take(4 * (size_t)std::max<int64_t>(P.slots, 1)));
+    B.defer = static_cast<int *>(take(4 * (size_t)rows1));
     B.tier2 = static_cast<int *>(take(4 * (size_t)rows1));
     B.ovf = static_cast<int *>(take(4 * (size_t)rows1));
     B.ovf_key = static_cast<long long *>(take(8 * (size_t)rows1));
@@ -618,26 +643,25 @@ sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, uns
 
 // All jobs of a batch share one validation/packing pass, one scoring launch
 // and one finalisation pipeline.
-sj_status join_batch(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
-  if (!h || n < 0 || (n > 0 && !reqs)) return SJ_ERR_INVALID_ARG;
-  for (int q = 0; q < n; ++q) {
-    sj_status s = check_req(reqs[q]);
-    if (s != SJ_OK) return s;
-  }
+// First size of the threshold candidate list (grown and rerun when exceeded).
+unsigned long long initial_thr_cap(const BatchPlan &P) {
+  if (!P.any_thr) return 0;
+  return (unsigned long long)std::max<int64_t>(
+      {(int64_t)1 << 16, 2 * P.rows_thr,
+       std::min<int64_t>(P.cap_sum + P.cap_sum / 4, 32 * P.rows_thr + (1 << 20))});
+}
+
+// One group of jobs as one pipeline (inputs already validated).
+sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
   if (st) std::memset(st, 0, sizeof *st);
   if (n == 0) return SJ_OK;
-  SJ_CUDA(cudaSetDevice(h->cfg.device));
   cudaStream_t stm = h->stream;
   Events ev{h};
   int64_t launches = 0;
   BatchPlan P;
   sj_status s = make_batch_plan(h, reqs, n, P);
   if (s != SJ_OK) return s;
-  unsigned long long thr_cap = 0;
-  if (P.any_thr)
-    thr_cap = (unsigned long long)std::max<int64_t>(
-        {(int64_t)1 << 16, 2 * P.rows_thr,
-         std::min<int64_t>(P.cap_sum + P.cap_sum / 4, 32 * P.rows_thr + (1 << 20))});
+  unsigned long long thr_cap = initial_thr_cap(P);
 
   for (int attempt = 0; attempt < 3; ++attempt) {
     Bufs B;
@@ -746,23 +770,17 @@ sj_status join_batch(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
       fa.band = B.band;
       fa.band_cnt = B.band_cnt;
       fa.dot2_coef_key = dot2_coef_key(P.d);
+      fa.defer_rows = B.defer;
       fa.tier2_rows = B.tier2;
       fa.overflow_rows = B.ovf;
       fa.overflow_key = B.ovf_key;
       fa.ctr = B.ctr;
-      SJ_CUDA(launch_topk_finalize(fa, stm));
-      launches += P.rows > 0 ? 1 : 0;
+      SJ_CUDA(launch_topk_finalize(fa, h->sm_count, stm));
+      launches += P.rows > 0 ? 3 : 0;
       s = read_counters(h, B.ctr);
       if (s != SJ_OK) return s;
       s = flags_status(h->h_ctr->err_flags);
       if (s != SJ_OK) return s;
-      const unsigned n_t2 = h->h_ctr->tier2_rows;
-      if (n_t2 > 0) {
-        SJ_CUDA(launch_topk_finalize_tier2(fa, (int)n_t2, stm));
-        launches += 1;
-        s = read_counters(h, B.ctr);
-        if (s != SJ_OK) return s;
-      }
       const unsigned n_ovf = h->h_ctr->overflow_rows;
       if (n_ovf > 0) {
         s = topk_fallback_all(h, P, B, n_ovf, ar, launches);
@@ -798,7 +816,7 @@ sj_status join_batch(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
         ta.row_count = B.row_count;
         ta.accepted = B.acc;
         ta.ctr = B.ctr;
-        const int g_res = (int)std::min<unsigned long long>((n_cand + 7) / 8, 152ull * 32);
+        const int g_res = (int)std::min<unsigned long long>((n_cand + 31) / 32, (unsigned long long)h->sm_count * 16);
         SJ_CUDA(launch_thr_rescore(ta, g_res, stm));
         SJ_CUDA(launch_exclusive_scan(B.row_count, B.row_off, P.rows, B.total, B.scan, stm));
         SJ_CUDA(launch_job_pairs(B.jobs, n, P.rows, B.row_off, B.total, B.job_info, stm));
@@ -850,6 +868,88 @@ sj_status join_batch(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
     return over_cap ? SJ_ERR_CAPACITY : SJ_OK;
   }
   return SJ_ERR_INTERNAL;
+}
+
+// Workspace bytes of one group of jobs as planned.
+size_t group_bytes(const sj_handle *h, const JoinReq *reqs, int n, sj_status &s) {
+  BatchPlan P;
+  s = make_batch_plan(h, reqs, n, P);
+  if (s != SJ_OK) return 0;
+  Arena meas;
+  meas.measure = true;
+  Bufs B;
+  layout(meas, P, reqs, initial_thr_cap(P), B);
+  return meas.used + 4096;
+}
+
+void add_stats(sj_stats *acc, const sj_stats &one) {
+  acc->ms_prepare += one.ms_prepare;
+  acc->ms_score += one.ms_score;
+  acc->ms_select += one.ms_select;
+  acc->ms_total += one.ms_total;
+  acc->n_candidates += one.n_candidates;
+  acc->n_rescored += one.n_rescored;
+  acc->n_exact += one.n_exact;
+  acc->n_overflow_rows += one.n_overflow_rows;
+  acc->n_pairs += one.n_pairs;
+  acc->n_launches += one.n_launches;
+  acc->n_tier2_rows += one.n_tier2_rows;
+  acc->max_abs_err_lowprec = std::max(acc->max_abs_err_lowprec, one.max_abs_err_lowprec);
+}
+
+// Jobs [lo, hi) in as few groups as the workspace budget allows: a range
+// that does not fit is halved by rows (nA + nB) until it does.  A single job
+// over the budget runs alone (and may fail with SJ_ERR_OOM).
+sj_status run_range(sj_handle *h, const JoinReq *reqs, int lo, int hi, size_t budget,
+                    sj_stats *acc) {
+  if (hi - lo > 1) {
+    sj_status s = SJ_OK;
+    const size_t bytes = group_bytes(h, reqs + lo, hi - lo, s);
+    if (s != SJ_OK) return s;
+    if (bytes > budget) {
+      int64_t tot = 0;
+      for (int q = lo; q < hi; ++q) tot += reqs[q].nA + reqs[q].nB + 1;
+      int mid = lo + 1;
+      for (int64_t run = 0; mid < hi - 1; ++mid) {
+        run += reqs[mid - 1].nA + reqs[mid - 1].nB + 1;
+        if (2 * run >= tot) break;
+      }
+      sj_status s1 = run_range(h, reqs, lo, mid, budget, acc);
+      if (s1 != SJ_OK && s1 != SJ_ERR_CAPACITY) return s1;
+      sj_status s2 = run_range(h, reqs, mid, hi, budget, acc);
+      if (s2 != SJ_OK) return s2;
+      return s1;
+    }
+  }
+  sj_stats one;
+  sj_status s = join_group(h, reqs + lo, hi - lo, &one);
+  add_stats(acc, one);
+  return s;
+}
+
+sj_status join_batch(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
+  if (!h || n < 0 || (n > 0 && !reqs)) return SJ_ERR_INVALID_ARG;
+  for (int q = 0; q < n; ++q) {
+    sj_status s = check_req(reqs[q]);
+    if (s != SJ_OK) return s;
+  }
+  sj_stats acc{};
+  if (n == 0) {
+    if (st) *st = acc;
+    return SJ_OK;
+  }
+  SJ_CUDA(cudaSetDevice(h->cfg.device));
+  size_t budget = h->cfg.workspace_limit;
+  if (!budget) {
+    size_t free_b = 0, total_b = 0;
+    SJ_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t reserve = std::max<size_t>((size_t)1 << 30, total_b / 50);
+    const size_t avail = free_b + h->ws_size;
+    budget = avail > reserve ? avail - reserve : 0;
+  }
+  sj_status s = run_range(h, reqs, 0, n, budget, &acc);
+  if (st) *st = acc;
+  return s;
 }
 
 sj_status topk_impl(sj_handle *h, const float *A, int64_t nA, const float *B, int64_t nB,

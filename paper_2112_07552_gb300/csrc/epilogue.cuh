@@ -13,9 +13,11 @@
 // columns seen so far, which never exceeds the final value, so the band list
 // is a superset of the final candidates.  theta_i is refreshed only when the
 // list is nearly full: the warp then finds the exact k-th largest banded score
-// (bisection on order-preserving integer keys) and compacts the list.  The
-// row's k best scores always pass and are never compacted away, so the final
-// list holds them and the finaliser recomputes s~_(k) from it.
+// (bisection on order-preserving integer keys) and compacts the list, unless
+// the kernel tracks the running k best exactly (a sorted register array in the
+// tensor-core epilogue), in which case theta is always exact.  The row's k
+// best scores always pass and are never compacted away, so the final list
+// holds them and the finaliser recomputes s~_(k) from it.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -35,38 +37,25 @@ struct RowCtx {
   int last;       // fill right after the last refresh of theta
   int overflow;   // band list could not be compacted below the limit
   Cand *band;     // cap entries
-  float *heap;    // shared-memory min-heap of the k best s~ (stride kHeapStride), or null
+  bool exact;     // theta tracks the running k-th best exactly (kept by the caller)
   int32_t i;      // global left row
 };
 
-// Shared-memory heaps are stored transposed (element t of heap h at
-// heap[t * kHeapStride + h]) so the heaps of a warp's rows fall in distinct
-// banks; a CTA holds up to kHeapStride heaps.
-constexpr int kHeapStride = 256;
+// Running k best of a row in registers, for k <= kTopKRegs: a descending
+// array whose first kTopKRegs - k slots hold +inf sentinels, so the k-th best
+// is always the last slot (static index, no local memory).
+constexpr int kTopKRegs = 32;
 
-__device__ __forceinline__ void heap_init(float *h, int k) {
-  for (int t = 0; t < k; ++t) h[t * kHeapStride] = -INFINITY;
+__device__ __forceinline__ void topk_regs_init(float (&h)[kTopKRegs], int k) {
+#pragma unroll
+  for (int t = 0; t < kTopKRegs; ++t) h[t] = t < kTopKRegs - k ? INFINITY : -INFINITY;
 }
 
-// Replace the minimum (root) of a k-element min-heap by v and sift down.
-__device__ __forceinline__ void heap_replace_min(float *h, int k, float v) {
-  int p = 0;
-  while (true) {
-    int c = 2 * p + 1;
-    if (c >= k) break;
-    float hc = h[c * kHeapStride];
-    if (c + 1 < k) {
-      const float h2 = h[(c + 1) * kHeapStride];
-      if (h2 < hc) {
-        hc = h2;
-        c += 1;
-      }
-    }
-    if (hc >= v) break;
-    h[p * kHeapStride] = hc;
-    p = c;
-  }
-  h[p * kHeapStride] = v;
+// Insert v (> h[last]) and drop the smallest: branch-free shift-insert.
+__device__ __forceinline__ void topk_regs_insert(float (&h)[kTopKRegs], float v) {
+#pragma unroll
+  for (int t = kTopKRegs - 1; t >= 1; --t) h[t] = fmaxf(h[t], fminf(v, h[t - 1]));
+  h[0] = fmaxf(h[0], v);
 }
 
 // Append a threshold candidate (warp-aggregated atomic on the global count).
@@ -106,7 +95,6 @@ __device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, const J
   r.slot = jb.slot0 + local * jb.lists + list;
   r.band = a.band + jb.band0 + (local * jb.lists + list) * (int64_t)jb.cap;
   r.theta = jb.k > 0 ? -INFINITY : INFINITY;
-  if (r.heap) heap_init(r.heap, jb.k);
 }
 
 // Band count of the (row, split); an overflowed list stores -(cnt + 1), its
@@ -116,17 +104,26 @@ __device__ __forceinline__ void row_end(const RowCtx &r, const ScoreArgs &a) {
 }
 
 // Visit one score that passed min(theta, tau_lo).  The band list always has
-// room for a chunk of 32 visits (the owner compacts before each chunk).  With
-// a heap, theta tracks the running k-th best exactly.
+// room for a chunk of 32 visits (the owner compacts before each chunk).
 __device__ __forceinline__ void row_push(RowCtx &r, const ScoreArgs &a, float v, int32_t j) {
+  if (v >= r.theta && !r.overflow) {
+    r.band[r.cnt] = Cand{v, j};
+    r.cnt += 1;
+  }
+  if (v >= r.tau_lo) push_thr(a, r.i, j, v);
+}
+
+// The same with the running k best in registers: theta is exact at all times.
+__device__ __forceinline__ void row_push_regs(RowCtx &r, float (&h)[kTopKRegs],
+                                              const ScoreArgs &a, float v, int32_t j) {
   if (v >= r.theta) {
     if (!r.overflow) {
       r.band[r.cnt] = Cand{v, j};
       r.cnt += 1;
     }
-    if (r.heap && v > r.heap[0]) {
-      heap_replace_min(r.heap, r.k, v);
-      r.theta = __fsub_rd(r.heap[0], r.two_m);
+    if (v > h[kTopKRegs - 1]) {
+      topk_regs_insert(h, v);
+      r.theta = __fsub_rd(h[kTopKRegs - 1], r.two_m);
     }
   }
   if (v >= r.tau_lo) push_thr(a, r.i, j, v);
@@ -149,8 +146,8 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 constexpr int kRefresh = 32;
 __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int limit) {
   const int lane = threadIdx.x & 31;
-  // with a heap theta is always exact: compact only when the list is full
-  const bool due = r.heap ? r.cnt > limit
+  // with an exact theta: compact only when the list is full
+  const bool due = r.exact ? r.cnt > limit
                           : (r.cnt > limit || (r.cnt >= k && r.cnt >= r.last + kRefresh));
   unsigned need = __ballot_sync(0xffffffffu, has_row && !r.overflow && due);
   while (need) {
@@ -162,7 +159,7 @@ __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int
     Cand *band = reinterpret_cast<Cand *>((uintptr_t)bp);
     const float two_m = __shfl_sync(0xffffffffu, r.two_m, src);
     const float theta_old = __shfl_sync(0xffffffffu, r.theta, src);
-    const bool exact = __shfl_sync(0xffffffffu, r.heap != nullptr ? 1 : 0, src) != 0;
+    const bool exact = __shfl_sync(0xffffffffu, r.exact ? 1 : 0, src) != 0;
     float theta = theta_old;
     if (!exact) {
       // k-th largest banded score: the largest key T with #{key >= T} >= k

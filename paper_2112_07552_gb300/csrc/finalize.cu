@@ -1,6 +1,6 @@
 // finalize.cu -- from low-precision candidates to exact results.
 //
-// Top-k (per left row, one CTA):
+// Top-k, per left row (one warp for the common case, one CTA otherwise):
 //   1. theta = (k-th best s~ over all splits) - 2 m_i; keep band entries with
 //      s~ >= theta.  They contain the exact top-k (see RowFilter).
 //   2. Dot2 (compensated FP32) for each candidate -> a 64-bit key interval
@@ -13,8 +13,12 @@
 //      exact value (fixed-point accumulator); sort those groups by
 //      (exact desc, j asc).  Scores: float32 rounding of the interval when
 //      both ends round alike, else of the exact value.
-// A row whose band list overflowed, or with more candidates than fit in
-// shared memory, is re-ranked from scratch against all of B (fallback).
+// The warp finaliser takes rows with at most 512 banded entries, at most 64
+// candidates and no multi-member group in the needed prefix (no exact value
+// needed); every other row goes to the CTA finaliser, in two tiers of
+// shared-memory capacity.  A row whose band list overflowed, or with more
+// candidates than the last tier holds, is re-ranked from scratch against all
+// of B (fallback).
 //
 // Threshold: per candidate, Dot2 decides s >= tau unless tau lies inside the
 // interval, where the exact value decides; accepted pairs are counted per row,
@@ -51,21 +55,16 @@ struct FinSmemLayout {
   uint8_t flag[CMAX];
 };
 
-// rows == nullptr: the global row is blockIdx.x; otherwise rows[blockIdx.x].
-// A row whose band list overflowed goes to the rescan list with its key
-// bound; a row with more than CMAX candidates goes to `defer` (with its key
-// bound in defer_key when given: the last tier defers to the rescan list).
+// One row (global row g) by the whole CTA.  A row whose band list overflowed
+// goes to the rescan list with its key bound; a row with more than CMAX
+// candidates goes to `defer` (with its key bound in defer_key when given: the
+// last tier defers to the rescan list).
 template <int CMAX>
-__global__ void __launch_bounds__(kFinThreads)
-    topk_finalize_kernel(TopkFinalArgs a, const int *rows, int *defer, long long *defer_key,
-                         unsigned *n_defer) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FinSmemLayout<CMAX> &sm = *reinterpret_cast<FinSmemLayout<CMAX> *>(smem_raw);
-  float *a_row = reinterpret_cast<float *>(smem_raw + sizeof(FinSmemLayout<CMAX>));
+__device__ void fin_row(const TopkFinalArgs &a, int64_t g, FinSmemLayout<CMAX> &sm, float *a_row,
+                        int *defer, long long *defer_key, unsigned *n_defer) {
   __shared__ int s_n, s_overflow;
   __shared__ unsigned int s_maxerr;
   __shared__ unsigned s_cnt[kFinThreads / 32];
-  const int64_t g = rows ? rows[blockIdx.x] : (int64_t)blockIdx.x;
   if (g >= a.rows) return;
   const JobDev &jb = a.jobs[find_job_row0(a.jobs, a.n_jobs, g)];
   const int k = jb.k;
@@ -182,6 +181,248 @@ __global__ void __launch_bounds__(kFinThreads)
   }
   CandArrays c{sm.U, sm.L, sm.j, sm.v, sm.perm, sm.perm2, sm.grp, sm.flag, sm.sc, sm.ex};
   rank_and_emit(c, n, k, a_src, B, d, jb.out_idx + i * k, jb.out_score + i * k, a.ctr);
+}
+
+// CTA finaliser over a list of rows whose length a previous launch wrote.
+template <int CMAX>
+__global__ void __launch_bounds__(kFinThreads)
+    topk_finalize_kernel(TopkFinalArgs a, const int *rows, const unsigned *n_rows, int *defer,
+                         long long *defer_key, unsigned *n_defer) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FinSmemLayout<CMAX> &sm = *reinterpret_cast<FinSmemLayout<CMAX> *>(smem_raw);
+  float *a_row = reinterpret_cast<float *>(smem_raw + sizeof(FinSmemLayout<CMAX>));
+  const unsigned nr = *n_rows;
+  for (unsigned r = blockIdx.x; r < nr; r += gridDim.x) {
+    fin_row<CMAX>(a, rows[r], sm, a_row, defer, defer_key, n_defer);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp finaliser.  Steps 1-4 of the CTA finaliser for one row per warp, in a
+// per-warp shared-memory area: the band entries as order-preserving keys, the
+// k-th banded score by bisection with warp reductions, the candidates' Dot2
+// key intervals, a bitonic sort of their indices by (U desc, j asc) and the
+// group sweep as a running minimum of L.  Rows it cannot finish without an
+// exact value, or whose lists are too long, are appended to `defer`
+// untouched (nothing of the row is written).
+constexpr int kWarpMaxEntries = 512;
+constexpr int kWarpMaxCand = 256;
+constexpr int kFinWarps = 4;
+
+struct KeyJ {
+  uint32_t key;
+  int32_t j;
+};
+struct WarpFinSmem {
+  KeyJ ent[kWarpMaxEntries];
+  long long U[kWarpMaxCand], L[kWarpMaxCand];
+  int32_t j[kWarpMaxCand];
+  float v[kWarpMaxCand];
+  int16_t perm[kWarpMaxCand];
+  uint8_t open[kWarpMaxCand];  // position opens a group
+};
+
+__device__ __forceinline__ bool cand_before(const WarpFinSmem &w, int x, int y) {
+  return w.U[x] > w.U[y] || (w.U[x] == w.U[y] && w.j[x] < w.j[y]);
+}
+
+__global__ void __launch_bounds__(kFinWarps * 32)
+    topk_finalize_warp_kernel(TopkFinalArgs a, int *defer, unsigned *n_defer) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpFinSmem &w = reinterpret_cast<WarpFinSmem *>(smem_raw)[wib];
+  const int64_t d = a.d;
+  unsigned long long my_cand = 0;
+  float my_err = 0.f;
+  const int64_t nwarps = (int64_t)gridDim.x * kFinWarps;
+  const int64_t g0 = (int64_t)blockIdx.x * kFinWarps + wib;
+  int q = g0 < a.rows ? find_job_row0(a.jobs, a.n_jobs, g0) : 0;
+  for (int64_t g = g0; g < a.rows; g += nwarps) {
+    q = advance_job_row0(a.jobs, a.n_jobs, q, g);
+    const JobDev &jb = a.jobs[q];
+    const int k = jb.k;
+    if (k == 0) continue;
+    const int64_t i = g - jb.row0;
+    const int S = jb.lists;
+    int c = 0;
+    if (S <= 32 && lane < S) c = a.band_cnt[jb.slot0 + i * S + lane];
+    int pre = c;  // inclusive prefix of the list counts
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(FULL, pre, off);
+      if (lane >= off) pre += y;
+    }
+    const int n_all = __shfl_sync(FULL, pre, 31);
+    pre -= c;
+    if (S > 32 || __any_sync(FULL, c < 0) || n_all > kWarpMaxEntries) {
+      if (lane == 0) defer[atomicAdd(n_defer, 1u)] = (int)g;
+      continue;
+    }
+    const Cand *bands = a.band + jb.band0 + i * S * (int64_t)jb.cap;
+    for (int s = 0; s < S; ++s) {
+      const int cs = __shfl_sync(FULL, c, s), ps = __shfl_sync(FULL, pre, s);
+      const Cand *bl = bands + s * (int64_t)jb.cap;
+      for (int q = lane; q < cs; q += 32) {
+        const Cand cd = bl[q];
+        w.ent[ps + q] = KeyJ{fkey(cd.v), cd.j};
+      }
+    }
+    __syncwarp();
+    // k-th largest banded score: the largest key T with #{key >= T} >= k
+    float kth = -INFINITY;
+    if (n_all >= k) {
+      uint32_t T = 0;
+      for (int b = 31; b >= 0; --b) {
+        const uint32_t tt = T | (1u << b);
+        unsigned cnt = 0;
+        for (int e = lane; e < n_all; e += 32) cnt += w.ent[e].key >= tt;
+        if (__reduce_add_sync(FULL, cnt) >= (unsigned)k) T = tt;
+      }
+      kth = fkey_inv(T);
+    }
+    const float m = row_margin(a.metaA[jb.a_prow0 + i], jb.gmaxB, a.acc_coef);
+    const uint32_t tkey = fkey(__fsub_rd(kth, __fmul_ru(2.f, m)));
+    unsigned nc = 0;
+    for (int e = lane; e < n_all; e += 32) nc += w.ent[e].key >= tkey;
+    const int n = (int)__reduce_add_sync(FULL, nc);
+    if (n > kWarpMaxCand) {
+      if (lane == 0) defer[atomicAdd(n_defer, 1u)] = (int)g;
+      continue;
+    }
+    {
+      int base = 0;
+      for (int e0 = 0; e0 < n_all; e0 += 32) {
+        const int e = e0 + lane;
+        const KeyJ kj = e < n_all ? w.ent[e] : KeyJ{0u, 0};
+        const bool cd = e < n_all && kj.key >= tkey;
+        const unsigned bal = __ballot_sync(FULL, cd);
+        if (cd) {
+          const int p = base + __popc(bal & ((1u << lane) - 1u));
+          w.j[p] = kj.j;
+          w.v[p] = fkey_inv(kj.key);
+        }
+        base += __popc(bal);
+      }
+    }
+    __syncwarp();
+    // Dot2 key intervals of the candidates
+    const float *a_src = jb.A + i * d;
+    const float *B = jb.B;
+    const RowMeta *metaB = a.metaB + jb.b_prow0;
+    const float nrm_a = a.metaA[jb.a_prow0 + i].nrm;
+    float err = 0.f;
+    constexpr int NC = 4;
+    for (int p0 = 0; p0 < n; p0 += NC) {
+      const float *ap[NC], *bp[NC];
+      int32_t jq[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        jq[q] = w.j[p0 + q < n ? p0 + q : p0];
+        ap[q] = a_src;
+        bp[q] = B + (int64_t)jq[q] * d;
+      }
+      float hi[NC], lo[NC];
+      dot2_warp_n<NC>(ap, bp, d, hi, lo);
+      if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          const int p = p0 + q;
+          if (p >= n) break;
+          const long long K = dot2_key(hi[q], lo[q]);
+          const long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, metaB[jq[q]].nrm);
+          w.U[p] = K + D;
+          w.L[p] = K - D;
+          err = fmaxf(err, fabsf(__fsub_rn(__fsub_rn(w.v[p], hi[q]), lo[q])));
+        }
+      }
+    }
+    // sort candidate indices by (U desc, j asc); padding indices sort last
+    int n_pad = 1;
+    while (n_pad < n) n_pad <<= 1;
+    for (int t = lane; t < n_pad; t += 32) w.perm[t] = (int16_t)(t < n ? t : -1);
+    __syncwarp();
+    for (int size = 2; size <= n_pad; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = lane; t < (n_pad >> 1); t += 32) {
+          const int x = 2 * t - (t & (stride - 1));
+          const int y = x + stride;
+          const bool asc = (x & size) == 0;
+          const int px = w.perm[x], py = w.perm[y];
+          // "before": a real candidate earlier in (U desc, j asc); padding last
+          const bool y_first = py >= 0 && (px < 0 || cand_before(w, py, px));
+          if (asc == y_first) {
+            w.perm[x] = (int16_t)py;
+            w.perm[y] = (int16_t)px;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // group openings: U_p below every L before position p
+    long long carry = LLONG_MAX;
+    int n_need = n;
+    for (int p0 = 0; p0 < n; p0 += 32) {
+      const int p = p0 + lane;
+      const int x = p < n ? w.perm[p] : 0;
+      const long long Lp = p < n ? w.L[x] : LLONG_MAX;
+      long long incl = Lp;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl = y < incl ? y : incl;
+      }
+      long long excl = __shfl_up_sync(FULL, incl, 1);
+      if (lane == 0) excl = LLONG_MAX;
+      excl = excl < carry ? excl : carry;
+      const bool op = p < n && (p == 0 || w.U[x] < excl);
+      if (p < n) w.open[p] = op ? 1 : 0;
+      const unsigned bal = __ballot_sync(FULL, op && p >= k);
+      if (bal && n_need == n) n_need = p0 + __ffs(bal) - 1;
+      const long long tot = __shfl_sync(FULL, incl, 31);
+      carry = tot < carry ? tot : carry;
+    }
+    __syncwarp();
+    // needed positions must be single-member groups whose interval rounds to
+    // one float32; otherwise the CTA finaliser resolves the row exactly
+    const int kk = k < n ? k : n;
+    bool bad = false;
+    for (int p = lane; p < n_need; p += 32) {
+      if (p >= 1 && !w.open[p]) bad = true;
+      if (p < kk) {
+        float sc;
+        const int x = w.perm[p];
+        if (!key_interval_round(w.L[x], w.U[x], sc)) bad = true;
+      }
+    }
+    if (__any_sync(FULL, bad)) {
+      if (lane == 0) defer[atomicAdd(n_defer, 1u)] = (int)g;
+      __syncwarp();
+      continue;
+    }
+    int64_t *oi = jb.out_idx + i * k;
+    float *os = jb.out_score + i * k;
+    for (int r = lane; r < k; r += 32) {
+      int64_t jo = -1;
+      float so = -INFINITY;
+      if (r < kk) {
+        const int x = w.perm[r];
+        jo = w.j[x];
+        key_interval_round(w.L[x], w.U[x], so);
+      }
+      oi[r] = jo;
+      os[r] = so;
+    }
+    __syncwarp();
+    my_cand += (unsigned long long)n;
+    my_err = fmaxf(my_err, err);
+  }
+  if (lane == 0 && my_cand) {
+    atomicAdd(&a.ctr->n_candidates, my_cand);
+    atomicAdd(&a.ctr->n_rescored, my_cand);
+    atomicMax(&a.ctr->max_err_bits, __float_as_uint(my_err));
+  }
 }
 
 // Fallback for rows whose candidates did not fit: rescan all of B with Dot2
@@ -325,50 +566,66 @@ __global__ void __launch_bounds__(1024) topk_rank_global_kernel(RankListArgs a, 
 // ---------------------------------------------------------------------------
 // Threshold
 
+// One warp evaluates four candidates at a time (Dot2 gathers interleaved).
 __global__ void thr_rescore_kernel(ThrFinalArgs a) {
+  constexpr int NC = 4;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n_cand = min64((int64_t)*a.n_cand, a.cand_cap);
   const int64_t d = a.d;
   unsigned long long n_exact = 0;
-  for (int64_t c = w0; c < n_cand; c += nw) {
-    const ThrCand t = a.cand[c];
-    const JobDev &jb = a.jobs[find_job_row0(a.jobs, a.n_jobs, t.i)];
-    const int64_t li = t.i - jb.row0;
-    const float *ar = jb.A + li * d;
-    const float *br = jb.B + (int64_t)t.j * d;
-    float hi, lo;
-    dot2_warp(ar, br, d, hi, lo);
-    const long long K = dot2_key(hi, lo);
-    const long long D = dot2_halfwidth(a.dot2_coef_key, a.metaA[jb.a_prow0 + li].nrm,
-                                       a.metaB[jb.b_prow0 + t.j].nrm);
-    int in;
-    bool have_ex = false;
-    Exact ex;
-    if (K - D >= jb.tau_key) {
-      in = 1;
-    } else if (K + D < jb.tau_key) {
-      in = 0;
-    } else {
-      ex = exact_dot_warp(ar, br, d);
-      have_ex = true;
-      ++n_exact;
-      in = exact_cmp(ex, jb.tau_exact) >= 0;
+  int hint = 0;  // candidates arrive grouped by job (pushed per scoring unit)
+  for (int64_t c0 = w0 * NC; c0 < n_cand; c0 += nw * NC) {
+    ThrCand t[NC];
+    const JobDev *jq[NC];
+    int64_t li[NC];
+    const float *ap[NC], *bp[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      t[q] = a.cand[c0 + q < n_cand ? c0 + q : c0];
+      hint = find_job_row0_hint(a.jobs, a.n_jobs, hint, t[q].i);
+      jq[q] = &a.jobs[hint];
+      li[q] = t[q].i - jq[q]->row0;
+      ap[q] = jq[q]->A + li[q] * d;
+      bp[q] = jq[q]->B + (int64_t)t[q].j * d;
     }
-    if (!in) continue;
-    float s;
-    if (!key_interval_round(K - D, K + D, s)) {
-      if (!have_ex) {
-        ex = exact_dot_warp(ar, br, d);
+    float hi[NC], lo[NC];
+    dot2_warp_n<NC>(ap, bp, d, hi, lo);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      if (c0 + q >= n_cand) break;
+      const JobDev &jb = *jq[q];
+      const long long K = dot2_key(hi[q], lo[q]);
+      const long long D = dot2_halfwidth(a.dot2_coef_key, a.metaA[jb.a_prow0 + li[q]].nrm,
+                                         a.metaB[jb.b_prow0 + t[q].j].nrm);
+      int in;
+      bool have_ex = false;
+      Exact ex;
+      if (K - D >= jb.tau_key) {
+        in = 1;
+      } else if (K + D < jb.tau_key) {
+        in = 0;
+      } else {
+        ex = exact_dot_warp(ap[q], bp[q], d);
+        have_ex = true;
         ++n_exact;
+        in = exact_cmp(ex, jb.tau_exact) >= 0;
       }
-      s = exact_to_float(ex);
-    }
-    if (lane == 0) {
-      atomicAdd(reinterpret_cast<unsigned long long *>(a.row_count + t.i), 1ull);
-      unsigned long long slot = atomicAdd(&a.ctr->n_pairs, 1ull);
-      a.accepted[slot] = ThrCand{t.i, t.j, s, 0};
+      if (!in) continue;
+      float s;
+      if (!key_interval_round(K - D, K + D, s)) {
+        if (!have_ex) {
+          ex = exact_dot_warp(ap[q], bp[q], d);
+          ++n_exact;
+        }
+        s = exact_to_float(ex);
+      }
+      if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.row_count + t[q].i), 1ull);
+        unsigned long long slot = atomicAdd(&a.ctr->n_pairs, 1ull);
+        a.accepted[slot] = ThrCand{t[q].i, t[q].j, s, 0};
+      }
     }
   }
   if (lane == 0 && n_exact) atomicAdd(&a.ctr->n_exact, n_exact);
@@ -576,30 +833,39 @@ __global__ void thr_sort_big_kernel(const JobDev *jobs, int n_jobs, PairOut *sta
 }  // namespace
 
 template <int CMAX>
-static cudaError_t launch_fin(const TopkFinalArgs &a, const int *rows, int n_rows, int *defer,
-                              long long *defer_key, unsigned *n_defer, cudaStream_t st) {
+static cudaError_t launch_fin(const TopkFinalArgs &a, const int *rows, const unsigned *n_rows,
+                              int grid, int *defer, long long *defer_key, unsigned *n_defer,
+                              cudaStream_t st) {
   const size_t smem =
       sizeof(FinSmemLayout<CMAX>) + (a.d <= kRowInSmemMax ? (size_t)a.d * sizeof(float) : 0);
   cudaError_t e = cudaFuncSetAttribute(topk_finalize_kernel<CMAX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  topk_finalize_kernel<CMAX><<<(unsigned)n_rows, kFinThreads, smem, st>>>(a, rows, defer, defer_key,
-                                                                          n_defer);
+  topk_finalize_kernel<CMAX><<<(unsigned)grid, kFinThreads, smem, st>>>(a, rows, n_rows, defer,
+                                                                       defer_key, n_defer);
   return cudaGetLastError();
 }
 
-cudaError_t launch_topk_finalize(const TopkFinalArgs &a, cudaStream_t st) {
+cudaError_t launch_topk_finalize(const TopkFinalArgs &a, int sm_count, cudaStream_t st) {
   if (a.rows == 0) return cudaSuccess;
-  // every row: candidates up to kCSmall; rows beyond go to tier2_rows
-  return launch_fin<kCSmall>(a, nullptr, (int)a.rows, a.tier2_rows, nullptr, &a.ctr->tier2_rows,
-                             st);
-}
-
-cudaError_t launch_topk_finalize_tier2(const TopkFinalArgs &a, int n_rows, cudaStream_t st) {
-  if (n_rows == 0) return cudaSuccess;
-  // rows with more than kCMax candidates join the rescan list
-  return launch_fin<kCMax>(a, a.tier2_rows, n_rows, a.overflow_rows, a.overflow_key,
-                           &a.ctr->overflow_rows, st);
+  // warp finaliser over every row; the rows it defers go to the first CTA
+  // tier, whose rows beyond kCSmall candidates go to the second, whose rows
+  // beyond kCMax go to the rescan list.  Counts stay on the device.
+  const int64_t want = (a.rows + kFinWarps - 1) / kFinWarps;
+  const int gw = (int)min64(want, (int64_t)sm_count * 8);
+  const size_t wsm = sizeof(WarpFinSmem) * kFinWarps;
+  cudaError_t e = cudaFuncSetAttribute(topk_finalize_warp_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+  if (e != cudaSuccess) return e;
+  topk_finalize_warp_kernel<<<(unsigned)gw, kFinWarps * 32, wsm, st>>>(a, a.defer_rows,
+                                                                       &a.ctr->defer_rows);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_fin<kCSmall>(a, a.defer_rows, &a.ctr->defer_rows, sm_count * 4, a.tier2_rows,
+                          nullptr, &a.ctr->tier2_rows, st);
+  if (e != cudaSuccess) return e;
+  return launch_fin<kCMax>(a, a.tier2_rows, &a.ctr->tier2_rows, sm_count * 2, a.overflow_rows,
+                           a.overflow_key, &a.ctr->overflow_rows, st);
 }
 
 size_t topk_rank_global_row_bytes(int64_t n) {

@@ -61,56 +61,105 @@ __device__ __forceinline__ int find_seg(const PackSeg *segs, int n_segs, int64_t
   return lo;
 }
 
+constexpr int kPrepWarps = 8;
+
+// One warp per packed row, kPrepWarps rows per block.  Segments hold at least
+// 128 rows, so a block's rows fall in at most two segments: one binary search
+// per block, and the B-side maxima are reduced per block before the atomics.
 template <typename OutT>
-__global__ void prepare_kernel(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows,
-                               int64_t d, OutT *__restrict__ Xp, int64_t dp,
-                               RowMeta *__restrict__ meta, Counters *ctr) {
-  const int lane = threadIdx.x & 31;
-  const int64_t prow = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (prow >= prows) return;
-  const PackSeg sg = segs[find_seg(segs, n_segs, prow)];
-  const int64_t local = prow - sg.prow0;
-  OutT *dst = Xp + prow * dp;
-  if (local >= sg.n) {
-    for (int64_t k = lane; k < dp; k += 32) dst[k] = OutT(0.f);
-    if (lane == 0) meta[prow] = RowMeta{0.f, 0.f, 0.f, 0};
-    return;
+__global__ void __launch_bounds__(kPrepWarps * 32)
+    prepare_kernel(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows, int64_t d,
+                   OutT *__restrict__ Xp, int64_t dp, RowMeta *__restrict__ meta,
+                   Counters *ctr) {
+  __shared__ int s_seg0;
+  __shared__ int s_seg[kPrepWarps];
+  __shared__ float s_m[kPrepWarps][3];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * kPrepWarps;
+  if (threadIdx.x == 0) s_seg0 = find_seg(segs, n_segs, row0);
+  __syncthreads();
+  const int64_t prow = row0 + wib;
+  int si = s_seg0;
+  while (si + 1 < n_segs && segs[si + 1].prow0 <= prow) ++si;
+  float mx[3] = {0.f, 0.f, 0.f};
+  if (prow < prows) {
+    const PackSeg sg = segs[si];
+    const int64_t local = prow - sg.prow0;
+    OutT *dst = Xp + prow * dp;
+    if (local >= sg.n) {
+      for (int64_t k = lane; k < dp; k += 32) dst[k] = OutT(0.f);
+      if (lane == 0) meta[prow] = RowMeta{0.f, 0.f, 0.f, 0};
+    } else {
+      const float *src = sg.src + local * d;
+      float ns = 0.f, nc = 0.f;   // ||x||^2
+      float qs = 0.f, qc = 0.f;   // ||x~||^2
+      float es = 0.f, ec = 0.f;   // ||x~ - x||^2
+      bool bad = false;
+      for (int64_t k0 = 0; k0 < dp; k0 += 128) {
+        float xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t k = k0 + 32 * u + lane;
+          xv[u] = k < d ? src[k] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t k = k0 + 32 * u + lane;
+          if (k >= dp) break;
+          float x = xv[u];
+          if (!isfinite(x)) { bad = true; x = 0.f; }
+          OutT qv = OutT(x);
+          float qf = float(qv);
+          dst[k] = qv;
+          acc_sq(x, ns, nc);
+          acc_sq(qf, qs, qc);
+          acc_sq(__fsub_rn(qf, x), es, ec);  // exact difference of x and its rounding
+        }
+      }
+      bool any_bad = __any_sync(0xffffffffu, bad);
+      float n2 = warp_sumsq2(ns, nc);
+      float q2 = warp_sumsq2(qs, qc);
+      float e2 = warp_sumsq2(es, ec);
+      if (lane == 0) {
+        unsigned flags = 0;
+        if (any_bad) flags |= kErrNonFinite;
+        else if (!(fabsf(n2 - 1.0f) <= 1e-5f)) flags |= kErrNotUnit;
+        if (flags) atomicOr(&ctr->err_flags, flags);
+        RowMeta m;
+        m.nrm = sqrt_up(n2);
+        m.qnrm = sqrt_up(q2);
+        m.qerr = e2 > 0.f ? sqrt_up(e2) : 0.f;
+        m.sexp = 0;
+        meta[prow] = m;
+        if (sg.side != 0) {
+          mx[0] = m.nrm;
+          mx[1] = m.qnrm;
+          mx[2] = m.qerr;
+        }
+      }
+    }
   }
-  const float *src = sg.src + local * d;
-  float ns = 0.f, nc = 0.f;   // ||x||^2
-  float qs = 0.f, qc = 0.f;   // ||x~||^2
-  float es = 0.f, ec = 0.f;   // ||x~ - x||^2
-  bool bad = false;
-  for (int64_t k = lane; k < dp; k += 32) {
-    float x = k < d ? src[k] : 0.f;
-    if (!isfinite(x)) { bad = true; x = 0.f; }
-    OutT qv = OutT(x);
-    float qf = float(qv);
-    dst[k] = qv;
-    acc_sq(x, ns, nc);
-    acc_sq(qf, qs, qc);
-    acc_sq(__fsub_rn(qf, x), es, ec);  // exact difference of x and its rounding
-  }
-  bool any_bad = __any_sync(0xffffffffu, bad);
-  float n2 = warp_sumsq2(ns, nc);
-  float q2 = warp_sumsq2(qs, qc);
-  float e2 = warp_sumsq2(es, ec);
   if (lane == 0) {
-    unsigned flags = 0;
-    if (any_bad) flags |= kErrNonFinite;
-    else if (!(fabsf(n2 - 1.0f) <= 1e-5f)) flags |= kErrNotUnit;
-    if (flags) atomicOr(&ctr->err_flags, flags);
-    RowMeta m;
-    m.nrm = sqrt_up(n2);
-    m.qnrm = sqrt_up(q2);
-    m.qerr = e2 > 0.f ? sqrt_up(e2) : 0.f;
-    m.sexp = 0;
-    meta[prow] = m;
-    if (sg.side != 0) {
-      float *g = jobs[sg.job].gmaxB;
-      atomic_max_pos(g + 0, m.nrm);
-      atomic_max_pos(g + 1, m.qnrm);
-      atomic_max_pos(g + 2, m.qerr);
+    s_seg[wib] = prow < prows ? si : -1;
+    s_m[wib][0] = mx[0];
+    s_m[wib][1] = mx[1];
+    s_m[wib][2] = mx[2];
+  }
+  __syncthreads();
+  // B-side maxima: one set of atomics per segment present in the block
+  if (threadIdx.x < 3) {
+    const int c = threadIdx.x;
+    int cur = -1;
+    float v = 0.f;
+    for (int w = 0; w <= kPrepWarps; ++w) {
+      const int sw = w < kPrepWarps ? s_seg[w] : -1;
+      if (sw != cur) {
+        if (cur >= 0 && segs[cur].side != 0 && v > 0.f)
+          atomic_max_pos(jobs[segs[cur].job].gmaxB + c, v);
+        cur = sw;
+        v = 0.f;
+      }
+      if (w < kPrepWarps) v = fmaxf(v, s_m[w][c]);
     }
   }
 }
@@ -121,8 +170,7 @@ cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_
                            int64_t d, PackFormat fmt, void *Xp, int64_t dp, RowMeta *meta,
                            Counters *ctr, cudaStream_t st) {
   if (prows == 0 || n_segs == 0) return cudaSuccess;
-  const int warps = 8;
-  dim3 grid((unsigned)((prows + warps - 1) / warps)), block(32 * warps);
+  dim3 grid((unsigned)((prows + kPrepWarps - 1) / kPrepWarps)), block(32 * kPrepWarps);
   switch (fmt) {
     case PackFormat::kF32:
       prepare_kernel<float><<<grid, block, 0, st>>>(segs, n_segs, jobs, prows, d,

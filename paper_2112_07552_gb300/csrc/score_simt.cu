@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
     rc.k = jb.k;
     rc.theta = INFINITY;
     rc.tau_lo = INFINITY;
-    rc.heap = nullptr;  // theta refreshed lazily from the band list
+    rc.exact = false;  // theta refreshed lazily from the band list
     const bool owner = tid < BM && lrow < jb.nA;
     if (owner) row_begin(rc, a, jb, lrow, un.split);
     const int64_t nB = jb.nB;

@@ -41,7 +41,7 @@ constexpr int BN = kTcBN;       // 256 columns of B per tile (TMEM columns)
 constexpr int BK = 64;          // k-block: 64 bf16 = 128 bytes = one swizzle row
 constexpr int STAGES = 4;
 constexpr int kEpiChunks = 2;  // 32-column chunks per TMEM round trip
-constexpr int kHeapMaxK = 32;  // top-k sizes tracked by shared-memory heaps
+static_assert(kTcHeapMaxK == kTopKRegs, "register top-k size");
 constexpr int kEpiWarps = 8;    // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTileABytes = BM * BK * 2;
@@ -58,13 +58,15 @@ struct alignas(1024) TcSmem {
   uint64_t tmem_empty[2];
   uint64_t drain;
   uint64_t never;  // debug-timeout hook: nothing ever arrives here
-  float heap[kHeapMaxK * kHeapStride];  // per-row top-k min-heaps (k <= kHeapMaxK)
   uint32_t tmem_base;
   int abort;
 };
 
 // Fused filter over 32 scores of the thread's row, columns jb .. jb+31.
-__device__ __forceinline__ void epilogue_chunk(RowCtx &rc, const ScoreArgs &a, const float (&v)[32],
+// EXACT: the running k best are kept in h (k <= kTopKRegs).
+template <bool EXACT>
+__device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[kTopKRegs],
+                                               const ScoreArgs &a, const float (&v)[32],
                                                int64_t jb, int64_t nB) {
   // fast path: one compare per 32 scores (balanced max tree)
   float p16[16], q8[8];
@@ -102,7 +104,10 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, const ScoreArgs &a, c
 #pragma unroll 1
       for (int e = 0; e < 4; ++e) {
         const float x = e == 0 ? x0 : e == 1 ? x1 : e == 2 ? x2 : x3;
-        if (x >= fminf(rc.theta, rc.tau_lo) && jq + e < nB) row_push(rc, a, x, (int32_t)(jq + e));
+        if (x >= fminf(rc.theta, rc.tau_lo) && jq + e < nB) {
+          if (EXACT) row_push_regs(rc, h, a, x, (int32_t)(jq + e));
+          else row_push(rc, a, x, (int32_t)(jq + e));
+        }
       }
     }
   }
@@ -264,7 +269,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       rc.k = kj;
       rc.theta = INFINITY;
       rc.tau_lo = INFINITY;
-      rc.heap = (kj > 0 && kj <= kHeapMaxK) ? sm.heap + half * BM + r_in_tile : nullptr;
+      rc.exact = kj > 0 && kj <= kTopKRegs;
+      float h[kTopKRegs];
+      topk_regs_init(h, kj);
       const int list = un.split * a.bands_per_split + half;
       if (owner) row_begin(rc, a, jb, row, list);
       const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
@@ -291,8 +298,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld32_nowait(taddr + c0 + 32, v1);
           tmem_wait_ld(v0, v1);
           if (owner) {
-            epilogue_chunk(rc, a, v0, col0 + c0, nB);
-            epilogue_chunk(rc, a, v1, col0 + c0 + 32, nB);
+            if (rc.exact) {
+              epilogue_chunk<true>(rc, h, a, v0, col0 + c0, nB);
+              epilogue_chunk<true>(rc, h, a, v1, col0 + c0 + 32, nB);
+            } else {
+              epilogue_chunk<false>(rc, h, a, v0, col0 + c0, nB);
+              epilogue_chunk<false>(rc, h, a, v1, col0 + c0 + 32, nB);
+            }
           }
         }
         fence_before();

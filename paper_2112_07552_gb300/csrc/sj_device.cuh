@@ -63,7 +63,7 @@ struct Counters {
   unsigned int redo_rows;           // rescan lists cut off at their capacity
   unsigned int redo_cap;            // capacity they need
   unsigned int big_rows;            // rescan lists for the global-memory ranker
-  unsigned int pad;
+  unsigned int defer_rows;          // rows the warp finaliser hands to the block tiers
 };
 
 constexpr unsigned kErrNonFinite = 1u;
@@ -127,6 +127,52 @@ __device__ __forceinline__ void dot2_warp(const float *a, const float *b, int64_
   }
   hi = s;
   lo = c;
+}
+
+// NC independent Dot2 evaluations by one warp, interleaved so that 4 * NC
+// gathers per lane are in flight.  Each evaluation has exactly the lane chains
+// and combination tree of dot2_warp (same values, same error bound).
+template <int NC>
+__device__ __forceinline__ void dot2_warp_n(const float *const (&a)[NC],
+                                            const float *const (&b)[NC], int64_t d,
+                                            float (&hi)[NC], float (&lo)[NC]) {
+  const int lane = threadIdx.x & 31;
+  float s[NC], c[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) s[q] = c[q] = 0.f;
+  int64_t k = lane;
+  for (; k + 96 < d; k += 128) {
+    float x[NC][4], y[NC][4];
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        x[q][u] = a[q][k + 32 * u];
+        y[q][u] = __ldg(b[q] + k + 32 * u);
+      }
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dot2_step(x[q][u], y[q][u], s[q], c[q]);
+  }
+  for (; k < d; k += 32) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) dot2_step(a[q][k], __ldg(b[q] + k), s[q], c[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      float s2 = __shfl_xor_sync(0xffffffffu, s[q], off);
+      float c2 = __shfl_xor_sync(0xffffffffu, c[q], off);
+      float t, e;
+      two_sum(s[q], s2, t, e);
+      s[q] = t;
+      c[q] = __fadd_rn(__fadd_rn(c[q], c2), e);
+    }
+    hi[q] = s[q];
+    lo[q] = c[q];
+  }
 }
 
 // Key of an unevaluated sum hi + lo: round(hi 2^60) + round(lo 2^60), within

@@ -76,6 +76,22 @@ struct PackSeg {
   int32_t job;
   int32_t side;      // 0: A rows, 1: B rows, 2: both (self-join); B rows feed jobs[job].gmaxB
 };
+// Job of global row x given a job q0 <= the answer (rows visited in
+// increasing order): walks forward from q0.
+__device__ __forceinline__ int advance_job_row0(const JobDev *jobs, int n_jobs, int q0, int64_t x) {
+  int q = q0;
+  while (q + 1 < n_jobs && jobs[q + 1].row0 <= x) ++q;
+  return q;
+}
+
+// Job of global row x, trying the hint first.
+__device__ __forceinline__ int find_job_row0_hint(const JobDev *jobs, int n_jobs, int hint,
+                                                  int64_t x) {
+  const JobDev &h = jobs[hint];
+  if (h.row0 <= x && x < h.row0 + h.nA) return hint;
+  return find_job_row0(jobs, n_jobs, x);
+}
+
 cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows,
                            int64_t d, PackFormat fmt, void *Xp, int64_t dp, RowMeta *meta,
                            Counters *ctr, cudaStream_t st);
@@ -101,6 +117,7 @@ struct ScoreArgs {
 // Tile sizes of the scoring kernels (rows x columns of one score tile).
 constexpr int kSimtBM = 128, kSimtBN = 128, kSimtBK = 16;
 constexpr int kTcBM = 128, kTcBN = 256;
+constexpr int kTcHeapMaxK = 32;  // k tracked exactly by the tensor-core epilogue's heaps
 
 cudaError_t launch_score_simt(const ScoreArgs &a, int grid, cudaStream_t st);
 
@@ -115,13 +132,15 @@ struct TopkFinalArgs {
   const Cand *band;
   const int *band_cnt;
   float dot2_coef_key;     // Dot2 error bound per unit norm product, key units
+  int *defer_rows;         // rows the warp finaliser leaves to the CTA tiers
   int *tier2_rows;         // rows with more candidates than the first tier holds
   int *overflow_rows;      // rows for the rescan fallback (global)
   long long *overflow_key; // their rescan key bounds
   Counters *ctr;
 };
-cudaError_t launch_topk_finalize(const TopkFinalArgs &a, cudaStream_t st);
-cudaError_t launch_topk_finalize_tier2(const TopkFinalArgs &a, int n_rows, cudaStream_t st);
+// Three launches (warp finaliser, two CTA tiers) with device-side row counts;
+// rows left for the fallback are counted in ctr->overflow_rows.
+cudaError_t launch_topk_finalize(const TopkFinalArgs &a, int sm_count, cudaStream_t st);
 
 // Fallback of the top-k finalisation: rescan B for rows whose candidates did
 // not fit, then rank the resulting short lists.  One job per launch.

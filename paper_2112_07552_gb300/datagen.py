@@ -168,3 +168,64 @@ def log_uniform_sizes(n_jobs: int, lo: int, hi: int, seed: int, stream: int) -> 
     u = _rng(seed, 8000 + stream, 0).random(n_jobs)
     return np.minimum(hi, np.floor(np.exp(np.log(lo) + u * (np.log(hi + 1) - np.log(lo))))
                       ).astype(np.int64)
+
+
+def batch_centre_counts(sizes_a: np.ndarray, sizes_b: np.ndarray) -> np.ndarray:
+    """Centres per job of an uneven batch: max(1, max(nA, nB) // 10)."""
+    return np.maximum(1, np.maximum(sizes_a, sizes_b) // 10).astype(np.int64)
+
+
+def clustered_batch_device(sizes_a, sizes_b, d: int, sigma: float = 0.1, seed: int = 0,
+                           device="cuda", chunk_rows: int = 1 << 20):
+    """An uneven batch of clustered joins drawn on a torch device.
+
+    Job q has K_q = max(1, max(nA_q, nB_q) // 10) centres uniform on the unit
+    sphere, shared by its A and B; every row picks one of its job's centres
+    iid uniformly, adds isotropic Gaussian noise of total expected squared
+    norm sigma^2 (per-coordinate std sigma / sqrt(d)) and is renormalised in
+    float64 before rounding to float32.  Draws come from torch's Philox
+    generator on the device, seeded with `seed`, in a fixed order (centres,
+    then A rows, then B rows, chunk_rows rows at a time), so the arrays are a
+    deterministic function of (sizes, d, sigma, seed, chunk_rows) for a given
+    torch build.  (Batches of tens of millions of rows are out of reach of the
+    host generator within a benchmark's time.)
+
+    Returns (A, B, a_off, b_off): float32 device tensors holding every job's
+    rows back to back, and the row offsets of the jobs (int64, n_jobs + 1).
+    """
+    import torch
+
+    sizes_a = np.asarray(sizes_a, np.int64)
+    sizes_b = np.asarray(sizes_b, np.int64)
+    n_jobs = len(sizes_a)
+    K = batch_centre_counts(sizes_a, sizes_b)
+    c_off = np.concatenate([[0], np.cumsum(K)])
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    C = torch.empty((int(c_off[-1]), d), dtype=torch.float32, device=device)
+    for c0 in range(0, C.shape[0], chunk_rows):
+        c1 = min(C.shape[0], c0 + chunk_rows)
+        x = torch.randn((c1 - c0, d), generator=g, dtype=torch.float64, device=device)
+        C[c0:c1] = (x / x.norm(dim=1, keepdim=True)).float()
+    Kd = torch.from_numpy(K).to(device)
+    cod = torch.from_numpy(c_off[:-1]).to(device)
+
+    def side(sizes):
+        off = np.concatenate([[0], np.cumsum(sizes)])
+        X = torch.empty((int(off[-1]), d), dtype=torch.float32, device=device)
+        job = torch.from_numpy(np.repeat(np.arange(n_jobs, dtype=np.int64), sizes)).to(device)
+        for r0 in range(0, X.shape[0], chunk_rows):
+            r1 = min(X.shape[0], r0 + chunk_rows)
+            jr = job[r0:r1]
+            u = torch.rand(r1 - r0, generator=g, dtype=torch.float64, device=device)
+            local = torch.minimum((u * Kd[jr]).long(), Kd[jr] - 1)
+            x = C[cod[jr] + local].double()
+            x += torch.randn((r1 - r0, d), generator=g, dtype=torch.float64,
+                             device=device) * (sigma / np.sqrt(d))
+            X[r0:r1] = (x / x.norm(dim=1, keepdim=True)).float()
+        return X, off
+
+    A, a_off = side(sizes_a)
+    B, b_off = side(sizes_b)
+    del C
+    return A, B, a_off, b_off

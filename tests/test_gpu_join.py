@@ -310,3 +310,28 @@ def test_batch_fallback_rows_in_several_jobs(sjmod, prec):
     for (A, B), o in zip(data, outs):
         assert_topk(o["idx"], o["score"], A, B, 10)
     assert st["n_overflow_rows"] > 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_split_into_groups_under_workspace_limit(sjmod, prec):
+    """A batch whose workspace exceeds the handle's limit runs as several
+    groups (halved by rows until each fits); results are unchanged."""
+    d = 64
+    sizes = [(900, 700), (40, 1200), (1500, 300), (600, 600), (1, 2000), (800, 900)]
+    data = [(datagen.clustered(na, d, 12, 0.1, seed=300 + q, stream=0),
+             datagen.clustered(nb, d, 12, 0.1, seed=300 + q, stream=1))
+            for q, (na, nb) in enumerate(sizes)]
+    jobs = [{"A": dev(A), "B": dev(B), "k": 7, "tau": 0.85} for A, B in data]
+    J_all = sjmod.SimilarityJoin(d, prec=prec, device=0)
+    _, st_all = J_all.batch(jobs, with_stats=True)
+    J_all.close()
+    # the whole batch needs about 15 MB of workspace in bf16 and 50 MB in fp32
+    # (wider band lists); these limits force a split yet fit every single job
+    limit = (12 << 20) if prec == "bf16" else (32 << 20)
+    J = sjmod.SimilarityJoin(d, prec=prec, device=0, workspace_limit=limit)
+    outs, st = J.batch(jobs, with_stats=True)
+    J.close()
+    for (A, B), o in zip(data, outs):
+        assert_topk(o["idx"], o["score"], A, B, 7)
+        assert_thr((o["i"], o["j"], o["pair_score"]), A, B, 0.85)
+    assert st["n_launches"] > st_all["n_launches"]
