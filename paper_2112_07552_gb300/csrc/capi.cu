@@ -305,7 +305,7 @@ struct BatchPlan {
   std::vector<JobHost> host;
   std::vector<PackSeg> segs;
   std::vector<UnitDev> units;
-  int64_t rows = 0, prows = 0, slots = 0, band_entries = 0;
+  int64_t rows = 0, prows = 0, slots = 0, band_entries = 0, topv_entries = 0;
   int64_t rows_thr = 0, cap_sum = 0;
   bool any_topk = false, any_thr = false, any_op_host = false;
 };
@@ -383,6 +383,12 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     jd.band0 = P.band_entries;
     P.slots += r.nA * jd.lists;
     P.band_entries += r.nA * jd.lists * (int64_t)jd.cap;
+    // exact per-list top-k values (tensor-core epilogue, k <= 32)
+    jd.topv0 = -1;
+    if (r.k > 0 && r.k <= kTcHeapMaxK && h->cfg.prec != SJ_FP32) {
+      jd.topv0 = P.topv_entries;
+      P.topv_entries += r.nA * jd.lists * (int64_t)r.k;
+    }
     for (int64_t b = 0; b < rb; ++b)
       for (int64_t sp = 0; sp < S; ++sp) P.units.push_back(UnitDev{q, (int32_t)b, (int32_t)sp, 0});
     // |s| <= ||a|| ||b|| < 1.00001 for validated rows: clamping tau to [-4, 4]
@@ -439,6 +445,7 @@ struct Bufs {
   void *packed = nullptr;
   std::vector<float *> stA, stB;
   Cand *band = nullptr;
+  float *topv = nullptr;
   int *band_cnt = nullptr, *defer = nullptr, *tier2 = nullptr, *ovf = nullptr;
   long long *ovf_key = nullptr;
   std::vector<int64_t *> st_idx;
@@ -478,6 +485,7 @@ bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long lo
   if (P.any_topk) {
     B.band = static_cast<Cand *>(take(sizeof(Cand) * std::max<int64_t>(P.band_entries, 1)));
     B.band_cnt = static_cast<int *>(take(4 * (size_t)std::max<int64_t>(P.slots, 1)));
+    B.topv = static_cast<float *>(take(4 * (size_t)std::max<int64_t>(P.topv_entries, 1)));
     B.defer = static_cast<int *>(take(4 * (size_t)rows1));
     B.tier2 = static_cast<int *>(take(4 * (size_t)rows1));
     B.ovf = static_cast<int *>(take(4 * (size_t)rows1));
@@ -728,6 +736,7 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
       sa.bands_per_split = P.bands;
       sa.band = B.band;
       sa.band_cnt = B.band_cnt;
+      sa.topv = B.topv;
       sa.thr = B.cand;
       sa.thr_cap = thr_cap;
       sa.ctr = B.ctr;
@@ -769,6 +778,7 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
       fa.acc_coef = (float)P.pp.acc_coef;
       fa.band = B.band;
       fa.band_cnt = B.band_cnt;
+      fa.topv = B.topv;
       fa.dot2_coef_key = dot2_coef_key(P.d);
       fa.defer_rows = B.defer;
       fa.tier2_rows = B.tier2;

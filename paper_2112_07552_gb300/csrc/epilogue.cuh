@@ -41,20 +41,22 @@ struct RowCtx {
   int32_t i;      // global left row
 };
 
-// Running k best of a row in registers, for k <= kTopKRegs: a descending
-// array whose first kTopKRegs - k slots hold +inf sentinels, so the k-th best
-// is always the last slot (static index, no local memory).
+// Running k best of a row in registers, for k <= KM (KM = 16 or 32): a
+// descending array whose first KM - k slots hold +inf sentinels, so the k-th
+// best is always the last slot (static index, no local memory).
 constexpr int kTopKRegs = 32;
 
-__device__ __forceinline__ void topk_regs_init(float (&h)[kTopKRegs], int k) {
+template <int KM>
+__device__ __forceinline__ void topk_regs_init(float (&h)[KM], int k) {
 #pragma unroll
-  for (int t = 0; t < kTopKRegs; ++t) h[t] = t < kTopKRegs - k ? INFINITY : -INFINITY;
+  for (int t = 0; t < KM; ++t) h[t] = t < KM - k ? INFINITY : -INFINITY;
 }
 
 // Insert v (> h[last]) and drop the smallest: branch-free shift-insert.
-__device__ __forceinline__ void topk_regs_insert(float (&h)[kTopKRegs], float v) {
+template <int KM>
+__device__ __forceinline__ void topk_regs_insert(float (&h)[KM], float v) {
 #pragma unroll
-  for (int t = kTopKRegs - 1; t >= 1; --t) h[t] = fmaxf(h[t], fminf(v, h[t - 1]));
+  for (int t = KM - 1; t >= 1; --t) h[t] = fmaxf(h[t], fminf(v, h[t - 1]));
   h[0] = fmaxf(h[0], v);
 }
 
@@ -114,16 +116,17 @@ __device__ __forceinline__ void row_push(RowCtx &r, const ScoreArgs &a, float v,
 }
 
 // The same with the running k best in registers: theta is exact at all times.
-__device__ __forceinline__ void row_push_regs(RowCtx &r, float (&h)[kTopKRegs],
-                                              const ScoreArgs &a, float v, int32_t j) {
+template <int KM>
+__device__ __forceinline__ void row_push_regs(RowCtx &r, float (&h)[KM], const ScoreArgs &a,
+                                              float v, int32_t j) {
   if (v >= r.theta) {
     if (!r.overflow) {
       r.band[r.cnt] = Cand{v, j};
       r.cnt += 1;
     }
-    if (v > h[kTopKRegs - 1]) {
-      topk_regs_insert(h, v);
-      r.theta = __fsub_rd(h[kTopKRegs - 1], r.two_m);
+    if (v > h[KM - 1]) {
+      topk_regs_insert<KM>(h, v);
+      r.theta = __fsub_rd(h[KM - 1], r.two_m);
     }
   }
   if (v >= r.tau_lo) push_thr(a, r.i, j, v);

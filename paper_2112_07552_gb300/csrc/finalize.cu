@@ -199,23 +199,19 @@ __global__ void __launch_bounds__(kFinThreads)
 }
 
 // ---------------------------------------------------------------------------
-// Warp finaliser.  Steps 1-4 of the CTA finaliser for one row per warp, in a
-// per-warp shared-memory area: the band entries as order-preserving keys, the
-// k-th banded score by bisection with warp reductions, the candidates' Dot2
-// key intervals, a bitonic sort of their indices by (U desc, j asc) and the
-// group sweep as a running minimum of L.  Rows it cannot finish without an
-// exact value, or whose lists are too long, are appended to `defer`
-// untouched (nothing of the row is written).
-constexpr int kWarpMaxEntries = 512;
-constexpr int kWarpMaxCand = 256;
-constexpr int kFinWarps = 4;
+// Warp finaliser.  Steps 1-4 of the CTA finaliser for one row per warp.  The
+// k-th banded score comes from the lists' exact top-k values when the scoring
+// pass kept them (the union's k best lie in the per-list k best), else from a
+// bisection over the band entries; candidates are compacted into a per-warp
+// shared-memory area holding their Dot2 key intervals, sorted by index with a
+// bitonic network on (U desc, j asc); the group sweep is a running minimum of
+// L.  Rows it cannot finish without an exact value, or with too many
+// candidates, are appended to `defer` untouched (nothing of the row is
+// written).
+constexpr int kWarpMaxCand = 128;
+constexpr int kFinWarps = 8;
 
-struct KeyJ {
-  uint32_t key;
-  int32_t j;
-};
 struct WarpFinSmem {
-  KeyJ ent[kWarpMaxEntries];
   long long U[kWarpMaxCand], L[kWarpMaxCand];
   int32_t j[kWarpMaxCand];
   float v[kWarpMaxCand];
@@ -225,6 +221,20 @@ struct WarpFinSmem {
 
 __device__ __forceinline__ bool cand_before(const WarpFinSmem &w, int x, int y) {
   return w.U[x] > w.U[y] || (w.U[x] == w.U[y] && w.j[x] < w.j[y]);
+}
+
+// Largest key T with #{values with key >= T} >= k over n values at
+// vals[0 .. n) (warp-cooperative bisection).
+template <typename Get>
+__device__ __forceinline__ uint32_t warp_kth_key(int n, int k, Get get) {
+  uint32_t T = 0;
+  for (int b = 31; b >= 0; --b) {
+    const uint32_t tt = T | (1u << b);
+    unsigned cnt = 0;
+    for (int e = threadIdx.x & 31; e < n; e += 32) cnt += fkey(get(e)) >= tt;
+    if (__reduce_add_sync(0xffffffffu, cnt) >= (unsigned)k) T = tt;
+  }
+  return T;
 }
 
 __global__ void __launch_bounds__(kFinWarps * 32)
@@ -255,56 +265,55 @@ __global__ void __launch_bounds__(kFinWarps * 32)
       if (lane >= off) pre += y;
     }
     const int n_all = __shfl_sync(FULL, pre, 31);
-    pre -= c;
-    if (S > 32 || __any_sync(FULL, c < 0) || n_all > kWarpMaxEntries) {
+    if (S > 32 || __any_sync(FULL, c < 0)) {
       if (lane == 0) defer[atomicAdd(n_defer, 1u)] = (int)g;
       continue;
     }
     const Cand *bands = a.band + jb.band0 + i * S * (int64_t)jb.cap;
-    for (int s = 0; s < S; ++s) {
-      const int cs = __shfl_sync(FULL, c, s), ps = __shfl_sync(FULL, pre, s);
-      const Cand *bl = bands + s * (int64_t)jb.cap;
-      for (int q = lane; q < cs; q += 32) {
-        const Cand cd = bl[q];
-        w.ent[ps + q] = KeyJ{fkey(cd.v), cd.j};
-      }
-    }
-    __syncwarp();
-    // k-th largest banded score: the largest key T with #{key >= T} >= k
+    // k-th largest banded score
     float kth = -INFINITY;
-    if (n_all >= k) {
+    if (jb.topv0 >= 0) {
+      const float *tv = a.topv + jb.topv0 + i * S * (int64_t)k;
+      kth = fkey_inv(warp_kth_key(S * k, k, [&](int e) { return tv[e]; }));
+    } else if (n_all >= k) {
+      // bisection over the band entries, list by list (uniform list loop)
       uint32_t T = 0;
       for (int b = 31; b >= 0; --b) {
         const uint32_t tt = T | (1u << b);
         unsigned cnt = 0;
-        for (int e = lane; e < n_all; e += 32) cnt += w.ent[e].key >= tt;
+        for (int s = 0; s < S; ++s) {
+          const int cs = __shfl_sync(FULL, c, s);
+          const Cand *bl = bands + s * (int64_t)jb.cap;
+          for (int qq = lane; qq < cs; qq += 32) cnt += fkey(bl[qq].v) >= tt;
+        }
         if (__reduce_add_sync(FULL, cnt) >= (unsigned)k) T = tt;
       }
       kth = fkey_inv(T);
     }
     const float m = row_margin(a.metaA[jb.a_prow0 + i], jb.gmaxB, a.acc_coef);
-    const uint32_t tkey = fkey(__fsub_rd(kth, __fmul_ru(2.f, m)));
-    unsigned nc = 0;
-    for (int e = lane; e < n_all; e += 32) nc += w.ent[e].key >= tkey;
-    const int n = (int)__reduce_add_sync(FULL, nc);
+    const float theta = __fsub_rd(kth, __fmul_ru(2.f, m));
+    // candidates: band entries >= theta, compacted in list order
+    int n = 0;
+    for (int s = 0; s < S; ++s) {
+      const int cs = __shfl_sync(FULL, c, s);
+      const Cand *bl = bands + s * (int64_t)jb.cap;
+      for (int q0 = 0; q0 < cs; q0 += 32) {
+        const int qq = q0 + lane;
+        const Cand cd = qq < cs ? bl[qq] : Cand{-INFINITY, 0};
+        const bool pass = qq < cs && cd.v >= theta;
+        const unsigned bal = __ballot_sync(FULL, pass);
+        const int p = n + __popc(bal & ((1u << lane) - 1u));
+        if (pass && p < kWarpMaxCand) {
+          w.j[p] = cd.j;
+          w.v[p] = cd.v;
+        }
+        n += __popc(bal);
+      }
+    }
     if (n > kWarpMaxCand) {
       if (lane == 0) defer[atomicAdd(n_defer, 1u)] = (int)g;
+      __syncwarp();
       continue;
-    }
-    {
-      int base = 0;
-      for (int e0 = 0; e0 < n_all; e0 += 32) {
-        const int e = e0 + lane;
-        const KeyJ kj = e < n_all ? w.ent[e] : KeyJ{0u, 0};
-        const bool cd = e < n_all && kj.key >= tkey;
-        const unsigned bal = __ballot_sync(FULL, cd);
-        if (cd) {
-          const int p = base + __popc(bal & ((1u << lane) - 1u));
-          w.j[p] = kj.j;
-          w.v[p] = fkey_inv(kj.key);
-        }
-        base += __popc(bal);
-      }
     }
     __syncwarp();
     // Dot2 key intervals of the candidates
@@ -318,23 +327,22 @@ __global__ void __launch_bounds__(kFinWarps * 32)
       const float *ap[NC], *bp[NC];
       int32_t jq[NC];
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        jq[q] = w.j[p0 + q < n ? p0 + q : p0];
-        ap[q] = a_src;
-        bp[q] = B + (int64_t)jq[q] * d;
+      for (int t = 0; t < NC; ++t) {
+        jq[t] = w.j[p0 + t < n ? p0 + t : p0];
+        ap[t] = a_src;
+        bp[t] = B + (int64_t)jq[t] * d;
       }
       float hi[NC], lo[NC];
       dot2_warp_n<NC>(ap, bp, d, hi, lo);
-      if (lane == 0) {
+      // lane t < NC finishes candidate p0 + t
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          const int p = p0 + q;
-          if (p >= n) break;
-          const long long K = dot2_key(hi[q], lo[q]);
-          const long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, metaB[jq[q]].nrm);
-          w.U[p] = K + D;
-          w.L[p] = K - D;
-          err = fmaxf(err, fabsf(__fsub_rn(__fsub_rn(w.v[p], hi[q]), lo[q])));
+      for (int t = 0; t < NC; ++t) {
+        if (lane == t && p0 + t < n) {
+          const long long K = dot2_key(hi[t], lo[t]);
+          const long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, metaB[jq[t]].nrm);
+          w.U[p0 + t] = K + D;
+          w.L[p0 + t] = K - D;
+          err = fmaxf(err, fabsf(__fsub_rn(__fsub_rn(w.v[p0 + t], hi[t]), lo[t])));
         }
       }
     }
@@ -418,6 +426,8 @@ __global__ void __launch_bounds__(kFinWarps * 32)
     my_cand += (unsigned long long)n;
     my_err = fmaxf(my_err, err);
   }
+  my_err = fmaxf(my_err, __shfl_xor_sync(FULL, my_err, 1));
+  my_err = fmaxf(my_err, __shfl_xor_sync(FULL, my_err, 2));
   if (lane == 0 && my_cand) {
     atomicAdd(&a.ctr->n_candidates, my_cand);
     atomicAdd(&a.ctr->n_rescored, my_cand);
@@ -852,7 +862,7 @@ cudaError_t launch_topk_finalize(const TopkFinalArgs &a, int sm_count, cudaStrea
   // tier, whose rows beyond kCSmall candidates go to the second, whose rows
   // beyond kCMax go to the rescan list.  Counts stay on the device.
   const int64_t want = (a.rows + kFinWarps - 1) / kFinWarps;
-  const int gw = (int)min64(want, (int64_t)sm_count * 8);
+  const int gw = (int)min64(want, (int64_t)sm_count * 4);
   const size_t wsm = sizeof(WarpFinSmem) * kFinWarps;
   cudaError_t e = cudaFuncSetAttribute(topk_finalize_warp_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);

@@ -63,9 +63,9 @@ struct alignas(1024) TcSmem {
 };
 
 // Fused filter over 32 scores of the thread's row, columns jb .. jb+31.
-// EXACT: the running k best are kept in h (k <= kTopKRegs).
-template <bool EXACT>
-__device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[kTopKRegs],
+// KM > 0: the running k best are kept in h (k <= KM); KM == 0: lazy theta.
+template <int KM>
+__device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? KM : 1],
                                                const ScoreArgs &a, const float (&v)[32],
                                                int64_t jb, int64_t nB) {
   // fast path: one compare per 32 scores (balanced max tree)
@@ -105,7 +105,7 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[kTopKRegs]
       for (int e = 0; e < 4; ++e) {
         const float x = e == 0 ? x0 : e == 1 ? x1 : e == 2 ? x2 : x3;
         if (x >= fminf(rc.theta, rc.tau_lo) && jq + e < nB) {
-          if (EXACT) row_push_regs(rc, h, a, x, (int32_t)(jq + e));
+          if constexpr (KM > 0) row_push_regs<KM>(rc, h, a, x, (int32_t)(jq + e));
           else row_push(rc, a, x, (int32_t)(jq + e));
         }
       }
@@ -116,6 +116,74 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[kTopKRegs]
 __device__ __forceinline__ void flag_timeout(TcSmem &sm, Counters *ctr) {
   *(volatile int *)&sm.abort = 1;
   atomicOr(&ctr->err_flags, kErrTimeout);
+}
+
+// The epilogue warps' share of one unit: the row's (or no) running top-k in
+// registers (KM slots; KM == 0: lazy theta), every tile of the unit's column
+// range from tensor memory through the fused filter, then the row's band
+// count and exact top-k values.
+template <int KM>
+__device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, const UnitDev &un,
+                                              const JobDev &jb, int64_t row, bool owner,
+                                              int list, uint32_t tmem, int quarter, int half,
+                                              uint64_t limit_ns, uint64_t &tile, bool &ok) {
+  volatile int *abort = &sm.abort;
+  const int kj = jb.k;
+  const int limit = jb.cap - 32 * kEpiChunks;  // room for one round of visits
+  const int64_t nB = jb.nB;
+  RowCtx rc;
+  rc.cnt = 0;
+  rc.overflow = 0;
+  rc.k = kj;
+  rc.theta = INFINITY;
+  rc.tau_lo = INFINITY;
+  rc.exact = KM > 0;
+  float h[KM > 0 ? KM : 1];
+  if constexpr (KM > 0) topk_regs_init<KM>(h, kj);
+  if (owner) row_begin(rc, a, jb, row, list);
+  const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
+  const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
+  for (int64_t ct = ct0; ct < ct1; ++ct, ++tile) {
+    const int acc = (int)(tile & 1);
+    const uint32_t aph = (uint32_t)((tile >> 1) & 1);
+    // warp-uniform outcome: the TMEM loads below are .sync.aligned
+    const bool w = mbar_wait(&sm.tmem_full[acc], aph, limit_ns, abort);
+    if (!__all_sync(0xffffffffu, w)) {
+      flag_timeout(sm, a.ctr);
+      ok = false;
+      break;
+    }
+    fence_after();
+    const int64_t col0 = ct * BN;
+    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+    // two 32-column chunks per TMEM round trip
+#pragma unroll 1
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 64) {
+      if (kj > 0) warp_compact(rc, owner, kj, limit);
+      float v0[32], v1[32];
+      tmem_ld32_nowait(taddr + c0, v0);
+      tmem_ld32_nowait(taddr + c0 + 32, v1);
+      tmem_wait_ld(v0, v1);
+      if (owner) {
+        epilogue_chunk<KM>(rc, h, a, v0, col0 + c0, nB);
+        epilogue_chunk<KM>(rc, h, a, v1, col0 + c0 + 32, nB);
+      }
+    }
+    fence_before();
+    mbar_arrive(&sm.tmem_empty[acc]);
+  }
+  if (owner) {
+    row_end(rc, a);
+    if constexpr (KM > 0) {
+      if (jb.topv0 >= 0) {
+        // the list's k best, descending (the last k register slots)
+        float *tv = a.topv + jb.topv0 + (row * jb.lists + list) * (int64_t)kj;
+#pragma unroll
+        for (int t = 0; t < KM; ++t)
+          if (t >= KM - kj) tv[t - (KM - kj)] = h[t];
+      }
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -261,56 +329,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row = (int64_t)un.rb * BM + r_in_tile;  // local row of the job
       const bool owner = row < jb.nA;
       const int kj = jb.k;
-      const int limit = jb.cap - 32 * kEpiChunks;  // room for one round of visits
-      const int64_t nB = jb.nB;
-      RowCtx rc;
-      rc.cnt = 0;
-      rc.overflow = 0;
-      rc.k = kj;
-      rc.theta = INFINITY;
-      rc.tau_lo = INFINITY;
-      rc.exact = kj > 0 && kj <= kTopKRegs;
-      float h[kTopKRegs];
-      topk_regs_init(h, kj);
       const int list = un.split * a.bands_per_split + half;
-      if (owner) row_begin(rc, a, jb, row, list);
-      const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
-      const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
-      for (int64_t ct = ct0; ct < ct1; ++ct, ++tile) {
-        const int acc = (int)(tile & 1);
-        const uint32_t aph = (uint32_t)((tile >> 1) & 1);
-        // warp-uniform outcome: the TMEM loads below are .sync.aligned
-        const bool w = mbar_wait(&sm.tmem_full[acc], aph, limit_ns, abort);
-        if (!__all_sync(0xffffffffu, w)) {
-          flag_timeout(sm, a.ctr);
-          ok = false;
-          break;
-        }
-        fence_after();
-        const int64_t col0 = ct * BN;
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
-        // two 32-column chunks per TMEM round trip
-#pragma unroll 1
-        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 64) {
-          if (kj > 0) warp_compact(rc, owner, kj, limit);
-          float v0[32], v1[32];
-          tmem_ld32_nowait(taddr + c0, v0);
-          tmem_ld32_nowait(taddr + c0 + 32, v1);
-          tmem_wait_ld(v0, v1);
-          if (owner) {
-            if (rc.exact) {
-              epilogue_chunk<true>(rc, h, a, v0, col0 + c0, nB);
-              epilogue_chunk<true>(rc, h, a, v1, col0 + c0 + 32, nB);
-            } else {
-              epilogue_chunk<false>(rc, h, a, v0, col0 + c0, nB);
-              epilogue_chunk<false>(rc, h, a, v1, col0 + c0 + 32, nB);
-            }
-          }
-        }
-        fence_before();
-        mbar_arrive(&sm.tmem_empty[acc]);
-      }
-      if (owner) row_end(rc, a);
+      if (kj > 0 && kj <= 16)
+        epilogue_unit<16>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
+      else if (kj > 0 && kj <= kTopKRegs)
+        epilogue_unit<kTopKRegs>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns,
+                                 tile, ok);
+      else
+        epilogue_unit<0>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
     }
   }
 

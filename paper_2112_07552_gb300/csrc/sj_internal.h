@@ -32,6 +32,7 @@ struct JobDev {
   int64_t row0;              // first global row
   int64_t slot0;             // first band-list slot (row-major: local row * lists + list)
   int64_t band0;             // first band-list entry (slots of this job hold cap entries)
+  int64_t topv0;             // first exact top-k value per slot (k per slot), -1: none
   int32_t k;                 // 0: no top-k part
   int32_t cap;               // band-list capacity
   int32_t lists;             // band lists per row = n_splits * bands per split
@@ -109,6 +110,7 @@ struct ScoreArgs {
   int bands_per_split;       // band lists per (row, split): epilogue column groups
   Cand *band;
   int *band_cnt;             // per slot; -(cnt + 1) marks an overflowed list
+  float *topv;               // per slot: the list's k best s~, descending (jobs with topv0 >= 0)
   ThrCand *thr;              // threshold candidates
   unsigned long long thr_cap;
   Counters *ctr;
@@ -131,6 +133,7 @@ struct TopkFinalArgs {
   float acc_coef;
   const Cand *band;
   const int *band_cnt;
+  const float *topv;       // per-slot exact k best s~ (jobs with topv0 >= 0)
   float dot2_coef_key;     // Dot2 error bound per unit norm product, key units
   int *defer_rows;         // rows the warp finaliser leaves to the CTA tiers
   int *tier2_rows;         // rows with more candidates than the first tier holds
