@@ -71,6 +71,7 @@ typedef enum {
 #define SJ_FLAG_SINGLE_SPLIT 0x2u  /* one column split per row block (each row's
                                       candidates collected in one list; lowers
                                       parallelism when nA is small) */
+#define SJ_FLAG_NO_GRAPH 0x4u      /* never replay joins from a captured CUDA graph */
 #define SJ_FLAG_DEBUG_TIMEOUT 0x100u /* test hook: device waits give up at once */
 
 typedef struct {
@@ -106,6 +107,7 @@ typedef struct {
   double max_abs_err_lowprec;/* max |s~ - s| seen over rescored top-k candidates */
   int64_t n_launches;        /* kernels this call launched */
   int64_t n_tier2_rows;      /* rows finalised with the large candidate tier */
+  int64_t graph_replayed;    /* job groups run from a captured CUDA graph */
 } sj_stats;
 
 typedef struct sj_handle sj_handle;
@@ -210,6 +212,11 @@ const char *sj_status_string(sj_status s);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int sj_version(void);
+
+/* Detail of the last CUDA failure behind an SJ_ERR_CUDA / SJ_ERR_OOM status
+ * returned to the calling thread (error name, location, message); "" if none.
+ * The string is owned by the library and valid until the thread's next call. */
+const char *sj_last_error_detail(void);
 
 #ifdef __cplusplus
 }

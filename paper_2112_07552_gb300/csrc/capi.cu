@@ -63,6 +63,13 @@ double gamma_n(double n, double u) { return n * u / (1.0 - n * u); }
 
 }  // namespace
 
+// A join pipeline captured as a CUDA graph, replayed for groups of the same
+// shape (the key) while the workspace and the pinned tables stay in place.
+struct GraphEntry {
+  std::vector<int64_t> key;
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct sj_handle {
   sj_config cfg{};
   cudaStream_t stream = nullptr;
@@ -72,7 +79,12 @@ struct sj_handle {
   size_t ws_size = 0;
   Counters *h_ctr = nullptr;   // pinned
   int64_t *h_i64 = nullptr;    // pinned scratch for small readbacks
+  void *h_tab = nullptr;       // pinned: job/segment/unit tables, then per-job pair counts
+  size_t h_tab_size = 0;
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  std::vector<GraphEntry> graphs;
   cudaEvent_t ev[6]{};
+  cudaEvent_t gev[4]{};  // stage events recorded only by captured graphs
   sj::TcContext *tc = nullptr;
 };
 
@@ -84,15 +96,33 @@ sj_status cuda_status(cudaError_t e) {
   return SJ_ERR_CUDA;
 }
 
+// Detail of the last CUDA failure seen by this thread (sj_last_error_detail).
+thread_local char g_err_detail[320] = "";
+
+void note_cuda_error(cudaError_t e, const char *what, int line) {
+  std::snprintf(g_err_detail, sizeof g_err_detail, "%s at capi.cu:%d (%s): %s",
+                cudaGetErrorName(e), line, what, cudaGetErrorString(e));
+}
+
 #define SJ_CUDA(call)                          \
   do {                                         \
     cudaError_t e__ = (call);                  \
-    if (e__ != cudaSuccess) return cuda_status(e__); \
+    if (e__ != cudaSuccess) {                  \
+      note_cuda_error(e__, #call, __LINE__);   \
+      return cuda_status(e__);                 \
+    }                                          \
   } while (0)
+
+void drop_graphs(sj_handle *h) {
+  for (GraphEntry &g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
 
 sj_status ensure_ws(sj_handle *h, size_t bytes) {
   if (bytes <= h->ws_size) return SJ_OK;
   if (h->cfg.workspace_limit && bytes > h->cfg.workspace_limit) return SJ_ERR_OOM;
+  drop_graphs(h);  // captured pipelines hold workspace addresses
   if (h->ws) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->ws);
@@ -211,10 +241,19 @@ Exact tau_to_exact(double tau) {
 
 struct Events {
   sj_handle *h;
-  void rec(int t) { cudaEventRecord(h->ev[t], h->stream); }
+  cudaStream_t st;
+  bool capturing = false;  // record the graph-owned events as record nodes
+  // Inside a stream capture, external records become event record nodes, so
+  // stage times stay measurable when the pipeline replays as a graph; those
+  // events belong to the graphs alone.
+  void rec(int t) {
+    if (capturing) cudaEventRecordWithFlags(h->gev[t], st, cudaEventRecordExternal);
+    else cudaEventRecord(h->ev[t], st);
+  }
   double ms(int a, int b) {
     float v = 0.f;
-    if (cudaEventElapsedTime(&v, h->ev[a], h->ev[b]) != cudaSuccess) {
+    cudaEvent_t *e = capturing ? h->gev : h->ev;
+    if (cudaEventElapsedTime(&v, e[a], e[b]) != cudaSuccess) {
       cudaGetLastError();
       return 0.0;
     }
@@ -365,14 +404,19 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     jd.k = r.k;
     // Band list per (row, list): the k best plus the margin band plus room for
     // one round of visits (64).  With an exact running k-th (tensor-core path,
-    // k <= 32) the margin band is the only slack; it grows with the columns a
-    // list covers (about 60-150 entries for 500k columns of d = 768 BF16
-    // scores), so it is sized at columns / 512, within [32, 256].  Otherwise
-    // the running k-th is refreshed lazily and needs 4k + 256.
+    // k <= 32) the margin band is the only slack: up to about k entries where
+    // the k-th score lies in the bulk of a short row, and growing with the
+    // columns a list covers (about 60-150 entries for 500k columns of d = 768
+    // BF16 scores), so it is sized at k + columns / 2048, the latter within
+    // [32, 192].  Lists are
+    // kept short on purpose: the lists of the rows in flight (152 CTAs x 128
+    // rows x 2) compete with the operand tiles for L2, and a list that still
+    // overflows after compaction goes to the rescan fallback.  Otherwise the
+    // running k-th is refreshed lazily and needs 4k + 256.
     if (r.k > 0) {
       const int64_t cols = tps * BN / P.bands;
       const bool exact_running = h->cfg.prec != SJ_FP32 && r.k <= kTcHeapMaxK;
-      const int64_t slack = std::min<int64_t>(256, std::max<int64_t>(32, cols / 512));
+      const int64_t slack = std::min<int64_t>(192, std::max<int64_t>(32, cols / 2048));
       jd.cap = (int32_t)(exact_running ? round_up(2 * (int64_t)r.k + 64 + slack, 32)
                                        : round_up(4 * (int64_t)r.k + 256, 32));
     } else {
@@ -434,6 +478,18 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
   return SJ_OK;
 }
 
+// Byte offsets of the job, segment and unit tables in one block.
+struct TableLayout {
+  size_t segs, units, bytes;
+};
+TableLayout table_layout(const BatchPlan &P) {
+  TableLayout t;
+  t.segs = align_up(sizeof(JobDev) * std::max<size_t>(P.jobs.size(), 1), 256);
+  t.units = t.segs + align_up(sizeof(PackSeg) * std::max<size_t>(P.segs.size(), 1), 256);
+  t.bytes = t.units + sizeof(UnitDev) * std::max<size_t>(P.units.size(), 1);
+  return t;
+}
+
 // Device buffers of one call, carved from the workspace.  The same sequence of
 // takes runs once on a measuring arena to size the workspace.
 struct Bufs {
@@ -469,9 +525,13 @@ bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long lo
     return p;
   };
   B.ctr = static_cast<Counters *>(take(sizeof(Counters)));
-  B.jobs = static_cast<JobDev *>(take(sizeof(JobDev) * std::max(n, 1)));
-  B.segs = static_cast<PackSeg *>(take(sizeof(PackSeg) * std::max<size_t>(P.segs.size(), 1)));
-  B.units = static_cast<UnitDev *>(take(sizeof(UnitDev) * std::max<size_t>(P.units.size(), 1)));
+  // job, segment and unit tables back to back (one copy from the pinned host
+  // tables, same offsets)
+  const TableLayout tl = table_layout(P);
+  unsigned char *tab = static_cast<unsigned char *>(take(tl.bytes));
+  B.jobs = reinterpret_cast<JobDev *>(tab);
+  B.segs = reinterpret_cast<PackSeg *>(tab + tl.segs);
+  B.units = reinterpret_cast<UnitDev *>(tab + tl.units);
   B.meta = static_cast<RowMeta *>(take(sizeof(RowMeta) * std::max<int64_t>(P.prows, 1)));
   B.packed = take((size_t)std::max<int64_t>(P.prows, 1) * P.pp.dp * P.pp.elem);
   B.stA.assign(n, nullptr);
@@ -659,17 +719,233 @@ unsigned long long initial_thr_cap(const BatchPlan &P) {
        std::min<int64_t>(P.cap_sum + P.cap_sum / 4, 32 * P.rows_thr + (1 << 20))});
 }
 
+// Pinned host tables: the job/segment/unit tables (table_layout offsets),
+// then two int64 per job for the pair counts read back.
+sj_status ensure_host_tables(sj_handle *h, size_t bytes) {
+  if (bytes <= h->h_tab_size) return SJ_OK;
+  drop_graphs(h);  // captured pipelines copy from this buffer
+  if (h->h_tab) {
+    SJ_CUDA(cudaStreamSynchronize(h->stream));
+    cudaFreeHost(h->h_tab);
+    h->h_tab = nullptr;
+    h->h_tab_size = 0;
+  }
+  const size_t want = align_up(bytes + bytes / 4, 1 << 16);
+  SJ_CUDA(cudaMallocHost(&h->h_tab, want));
+  h->h_tab_size = want;
+  return SJ_OK;
+}
+
+// Every device step of one group, asynchronous on `stm` and free of host
+// reads, so that it can be captured as a graph: tables in, validation and
+// packing, scoring with the fused filter, top-k finalisation (warp and CTA
+// tiers), threshold rescoring, placement and ordering, then the counters and
+// per-job pair counts back to pinned host memory.  Kernels skip their work
+// once validation has flagged an input.
+sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const BatchPlan &P,
+                      const Bufs &B, unsigned long long thr_cap, int64_t &launches) {
+  const int n = (int)P.jobs.size();
+  Events ev{h, stm, capturing};
+  const TableLayout tl = table_layout(P);
+  int64_t *h_info = reinterpret_cast<int64_t *>(static_cast<unsigned char *>(h->h_tab) +
+                                                align_up(tl.bytes, 256));
+  ev.rec(0);
+  SJ_CUDA(cudaMemcpyAsync(B.jobs, h->h_tab, tl.bytes, cudaMemcpyHostToDevice, stm));
+  SJ_CUDA(cudaMemsetAsync(B.ctr, 0, sizeof(Counters), stm));
+  SJ_CUDA(launch_prepare(B.segs, (int)P.segs.size(), B.jobs, P.prows, P.d, P.pp.fmt, B.packed,
+                         P.pp.dp, B.meta, B.ctr, stm));
+  launches += P.prows > 0 ? 1 : 0;
+  ev.rec(1);
+  // ---- scoring pass with the fused filter ----
+  if (P.any_topk && P.slots > 0) SJ_CUDA(cudaMemsetAsync(B.band_cnt, 0, (size_t)P.slots * 4, stm));
+  if (!P.units.empty()) {
+    ScoreArgs sa{};
+    sa.jobs = B.jobs;
+    sa.n_jobs = n;
+    sa.units = B.units;
+    sa.n_units = (int64_t)P.units.size();
+    sa.Ap = B.packed;
+    sa.Bp = B.packed;
+    sa.dp = P.pp.dp;
+    sa.metaA = B.meta;
+    sa.acc_coef = (float)P.pp.acc_coef;
+    sa.bands_per_split = P.bands;
+    sa.band = B.band;
+    sa.band_cnt = B.band_cnt;
+    sa.topv = B.topv;
+    sa.thr = B.cand;
+    sa.thr_cap = thr_cap;
+    sa.ctr = B.ctr;
+    if (h->cfg.prec == SJ_FP32) {
+      const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count * 2);
+      SJ_CUDA(launch_score_simt(sa, grid, stm));
+    } else {
+      TcMaps maps;
+      sj_status s = tc_make_maps(h->tc, B.packed, P.prows, B.packed, P.prows, P.pp.dp, &maps);
+      if (s != SJ_OK) return s;
+      const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count);
+      SJ_CUDA(launch_score_tc(sa, grid, &maps, h->cfg.flags, stm));
+    }
+    launches += 1;
+  }
+  ev.rec(2);
+  // ---- top-k finalisation (warp finaliser, two CTA tiers) ----
+  if (P.any_topk) {
+    TopkFinalArgs fa{};
+    fa.jobs = B.jobs;
+    fa.n_jobs = n;
+    fa.rows = P.rows;
+    fa.d = P.d;
+    fa.metaA = B.meta;
+    fa.metaB = B.meta;
+    fa.acc_coef = (float)P.pp.acc_coef;
+    fa.band = B.band;
+    fa.band_cnt = B.band_cnt;
+    fa.topv = B.topv;
+    fa.dot2_coef_key = dot2_coef_key(P.d);
+    fa.defer_rows = B.defer;
+    fa.tier2_rows = B.tier2;
+    fa.overflow_rows = B.ovf;
+    fa.overflow_key = B.ovf_key;
+    fa.ctr = B.ctr;
+    SJ_CUDA(launch_topk_finalize(fa, h->sm_count, stm));
+    launches += P.rows > 0 ? 3 : 0;
+  }
+  // ---- threshold finalisation ----
+  if (P.any_thr && P.rows > 0) {
+    SJ_CUDA(cudaMemsetAsync(B.row_count, 0, (size_t)P.rows * 8, stm));
+    SJ_CUDA(cudaMemsetAsync(B.row_fill, 0, (size_t)P.rows * 8, stm));
+    SJ_CUDA(cudaMemsetAsync(B.n_big, 0, sizeof(int), stm));
+    ThrFinalArgs ta{};
+    ta.jobs = B.jobs;
+    ta.n_jobs = n;
+    ta.d = P.d;
+    ta.metaA = B.meta;
+    ta.metaB = B.meta;
+    ta.dot2_coef_key = dot2_coef_key(P.d);
+    ta.cand = B.cand;
+    ta.n_cand = &B.ctr->thr_count;
+    ta.cand_cap = (int64_t)thr_cap;
+    ta.row_count = B.row_count;
+    ta.accepted = B.acc;
+    ta.ctr = B.ctr;
+    const int g_res = (int)std::min<unsigned long long>((thr_cap + 31) / 32,
+                                                        (unsigned long long)h->sm_count * 16);
+    SJ_CUDA(launch_thr_rescore(ta, g_res, stm));
+    SJ_CUDA(launch_exclusive_scan(B.row_count, B.row_off, P.rows, B.total, B.scan, stm));
+    SJ_CUDA(launch_job_pairs(B.jobs, n, P.rows, B.row_off, B.total, B.job_info, stm));
+    const int g_sc = (int)std::min<unsigned long long>((thr_cap + 255) / 256,
+                                                       (unsigned long long)h->sm_count * 16);
+    SJ_CUDA(launch_thr_scatter(B.jobs, n, B.acc, &B.ctr->n_pairs, (int64_t)thr_cap, B.row_off,
+                               B.row_fill, B.staging, g_sc, stm));
+    SJ_CUDA(launch_thr_sort_rows(B.jobs, n, P.rows, B.row_off, B.row_count, B.staging,
+                                 B.big_rows, B.n_big, stm));
+    SJ_CUDA(launch_thr_sort_big(B.jobs, n, B.staging, B.tmp, B.row_off, B.row_count, B.big_rows,
+                                B.n_big, 2 * h->sm_count, stm));
+    launches += 9;
+    SJ_CUDA(cudaMemcpyAsync(h_info, B.job_info, 16 * (size_t)n, cudaMemcpyDeviceToHost, stm));
+  }
+  SJ_CUDA(cudaMemcpyAsync(h->h_ctr, B.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, stm));
+  ev.rec(3);
+  return SJ_OK;
+}
+
+// Kernels issue_group launches for this plan.
+void issue_count(const BatchPlan &P, int64_t &l) {
+  l += P.prows > 0 ? 1 : 0;
+  l += P.units.empty() ? 0 : 1;
+  l += P.any_topk && P.rows > 0 ? 3 : 0;
+  l += P.any_thr && P.rows > 0 ? 9 : 0;
+}
+
+// Shape of a group as far as a captured pipeline depends on it.
+std::vector<int64_t> graph_key(const sj_handle *h, const BatchPlan &P, const JoinReq *reqs,
+                               unsigned long long thr_cap) {
+  std::vector<int64_t> key;
+  key.reserve(8 + 4 * P.jobs.size());
+  key.push_back((int64_t)(uintptr_t)h->ws);
+  key.push_back((int64_t)h->ws_size);
+  key.push_back((int64_t)(uintptr_t)h->h_tab);
+  key.push_back((int64_t)thr_cap);
+  key.push_back((int64_t)h->cfg.flags);
+  key.push_back((int64_t)P.jobs.size());
+  for (size_t q = 0; q < P.jobs.size(); ++q) {
+    key.push_back(reqs[q].nA);
+    key.push_back(reqs[q].nB);
+    key.push_back(((int64_t)reqs[q].k << 2) | (reqs[q].thr ? 2 : 0) | (P.host[q].self ? 1 : 0));
+  }
+  return key;
+}
+
+// Launch the group's pipeline: a captured graph when every input and output
+// is in device memory (captured on first use of the shape, then replayed),
+// else the launches themselves.
+sj_status run_group_device(sj_handle *h, const BatchPlan &P, const Bufs &B, const JoinReq *reqs,
+                           unsigned long long thr_cap, bool graphable, int64_t &launches,
+                           bool &used_graph) {
+  used_graph = false;
+  if (!graphable) return issue_group(h, h->stream, false, P, B, thr_cap, launches);
+  std::vector<int64_t> key = graph_key(h, P, reqs, thr_cap);
+  for (GraphEntry &g : h->graphs)
+    if (g.key == key) {
+      SJ_CUDA(cudaGraphLaunch(g.exec, h->stream));
+      used_graph = true;
+      int64_t l = 0;  // same launch count as the captured sequence
+      issue_count(P, l);
+      launches += l;
+      return SJ_OK;
+    }
+  if (!h->cap_stream) SJ_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  // the captured copies read the pinned tables when the graph runs; the
+  // tables are rewritten only after the previous call drained its stream
+  cudaGraph_t graph = nullptr;
+  SJ_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int64_t l = 0;
+  sj_status s = issue_group(h, h->cap_stream, true, P, B, thr_cap, l);
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (s != SJ_OK || e != cudaSuccess || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return issue_group(h, h->stream, false, P, B, thr_cap, launches);
+  }
+  GraphEntry ent;
+  ent.key = std::move(key);
+  e = cudaGraphInstantiate(&ent.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return issue_group(h, h->stream, false, P, B, thr_cap, launches);
+  }
+  if (h->graphs.size() >= 8) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(std::move(ent));
+  SJ_CUDA(cudaGraphLaunch(h->graphs.back().exec, h->stream));
+  used_graph = true;
+  launches += l;
+  return SJ_OK;
+}
+
 // One group of jobs as one pipeline (inputs already validated).
 sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
   if (st) std::memset(st, 0, sizeof *st);
   if (n == 0) return SJ_OK;
   cudaStream_t stm = h->stream;
-  Events ev{h};
+  Events ev{h, stm};
   int64_t launches = 0;
   BatchPlan P;
   sj_status s = make_batch_plan(h, reqs, n, P);
   if (s != SJ_OK) return s;
   unsigned long long thr_cap = initial_thr_cap(P);
+  bool any_host = false;
+  for (const JobHost &hh : P.host) any_host |= hh.a_host || hh.b_host || hh.ot_host || hh.op_host;
+  const bool graphable = !any_host && !(h->cfg.flags & SJ_FLAG_NO_GRAPH);
+  const TableLayout tl = table_layout(P);
+  s = ensure_host_tables(h, align_up(tl.bytes, 256) + 16 * (size_t)n);
+  if (s != SJ_OK) return s;
+  int64_t *h_info = reinterpret_cast<int64_t *>(static_cast<unsigned char *>(h->h_tab) +
+                                                align_up(tl.bytes, 256));
 
   for (int attempt = 0; attempt < 3; ++attempt) {
     Bufs B;
@@ -682,8 +958,7 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
     }
     Arena ar{static_cast<unsigned char *>(h->ws), h->ws_size, 0};
     if (!layout(ar, P, reqs, thr_cap, B)) return SJ_ERR_INTERNAL;
-    ev.rec(0);
-    // device pointers of every job
+    // device pointers of every job; host inputs staged into the workspace
     for (int q = 0; q < n; ++q) {
       const JoinReq &r = reqs[q];
       JobDev &jd = P.jobs[q];
@@ -702,176 +977,67 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
         SJ_CUDA(cudaMemcpyAsync(B.stB[q], r.B, (size_t)r.nB * P.d * 4, cudaMemcpyHostToDevice, stm));
     }
     for (PackSeg &sg : P.segs) sg.src = sg.side == 1 ? P.jobs[sg.job].B : P.jobs[sg.job].A;
-    SJ_CUDA(cudaMemsetAsync(B.ctr, 0, sizeof(Counters), stm));
-    SJ_CUDA(cudaMemcpyAsync(B.jobs, P.jobs.data(), sizeof(JobDev) * n, cudaMemcpyHostToDevice, stm));
-    if (!P.segs.empty())
-      SJ_CUDA(cudaMemcpyAsync(B.segs, P.segs.data(), sizeof(PackSeg) * P.segs.size(),
-                              cudaMemcpyHostToDevice, stm));
+    unsigned char *tab = static_cast<unsigned char *>(h->h_tab);
+    std::memcpy(tab, P.jobs.data(), sizeof(JobDev) * n);
+    if (!P.segs.empty()) std::memcpy(tab + tl.segs, P.segs.data(), sizeof(PackSeg) * P.segs.size());
     if (!P.units.empty())
-      SJ_CUDA(cudaMemcpyAsync(B.units, P.units.data(), sizeof(UnitDev) * P.units.size(),
-                              cudaMemcpyHostToDevice, stm));
-    SJ_CUDA(launch_prepare(B.segs, (int)P.segs.size(), B.jobs, P.prows, P.d, P.pp.fmt, B.packed,
-                           P.pp.dp, B.meta, B.ctr, stm));
-    launches += P.prows > 0 ? 1 : 0;
-    ev.rec(1);
-    s = read_counters(h, B.ctr);
+      std::memcpy(tab + tl.units, P.units.data(), sizeof(UnitDev) * P.units.size());
+    std::memset(h_info, 0, 16 * (size_t)n);
+    bool used_graph = false;
+    s = run_group_device(h, P, B, reqs, thr_cap, graphable && attempt == 0, launches, used_graph);
     if (s != SJ_OK) return s;
-    s = flags_status(h->h_ctr->err_flags);
+    SJ_CUDA(cudaStreamSynchronize(stm));
+    const Counters c1 = *h->h_ctr;
+    s = flags_status(c1.err_flags);
     if (s != SJ_OK) return s;
-
-    // ---- scoring pass with the fused filter ----
-    if (P.any_topk && P.slots > 0)
-      SJ_CUDA(cudaMemsetAsync(B.band_cnt, 0, (size_t)P.slots * 4, stm));
-    if (!P.units.empty()) {
-      ScoreArgs sa{};
-      sa.jobs = B.jobs;
-      sa.n_jobs = n;
-      sa.units = B.units;
-      sa.n_units = (int64_t)P.units.size();
-      sa.Ap = B.packed;
-      sa.Bp = B.packed;
-      sa.dp = P.pp.dp;
-      sa.metaA = B.meta;
-      sa.acc_coef = (float)P.pp.acc_coef;
-      sa.bands_per_split = P.bands;
-      sa.band = B.band;
-      sa.band_cnt = B.band_cnt;
-      sa.topv = B.topv;
-      sa.thr = B.cand;
-      sa.thr_cap = thr_cap;
-      sa.ctr = B.ctr;
-      if (h->cfg.prec == SJ_FP32) {
-        const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count * 2);
-        SJ_CUDA(launch_score_simt(sa, grid, stm));
-      } else {
-        TcMaps maps;
-        s = tc_make_maps(h->tc, B.packed, P.prows, B.packed, P.prows, P.pp.dp, &maps);
-        if (s != SJ_OK) return s;
-        const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count);
-        SJ_CUDA(launch_score_tc(sa, grid, &maps, h->cfg.flags, stm));
-      }
-      launches += 1;
+    if (P.any_thr && c1.thr_count > thr_cap) {
+      // rerun with room for every candidate (and without the captured graph)
+      thr_cap = c1.thr_count + c1.thr_count / 8 + 1024;
+      continue;
     }
-    ev.rec(2);
-    unsigned long long n_cand = 0;
-    if (P.any_thr) {
-      s = read_counters(h, B.ctr);
+    if (P.any_topk && c1.overflow_rows > 0) {
+      s = topk_fallback_all(h, P, B, c1.overflow_rows, ar, launches);
       if (s != SJ_OK) return s;
-      s = flags_status(h->h_ctr->err_flags);
-      if (s != SJ_OK) return s;
-      n_cand = h->h_ctr->thr_count;
-      if (n_cand > thr_cap) {
-        thr_cap = n_cand + n_cand / 8 + 1024;  // rerun with room for every candidate
-        continue;
-      }
     }
-
-    // ---- top-k finalisation (+ fallback rows) ----
-    if (P.any_topk) {
-      TopkFinalArgs fa{};
-      fa.jobs = B.jobs;
-      fa.n_jobs = n;
-      fa.rows = P.rows;
-      fa.d = P.d;
-      fa.metaA = B.meta;
-      fa.metaB = B.meta;
-      fa.acc_coef = (float)P.pp.acc_coef;
-      fa.band = B.band;
-      fa.band_cnt = B.band_cnt;
-      fa.topv = B.topv;
-      fa.dot2_coef_key = dot2_coef_key(P.d);
-      fa.defer_rows = B.defer;
-      fa.tier2_rows = B.tier2;
-      fa.overflow_rows = B.ovf;
-      fa.overflow_key = B.ovf_key;
-      fa.ctr = B.ctr;
-      SJ_CUDA(launch_topk_finalize(fa, h->sm_count, stm));
-      launches += P.rows > 0 ? 3 : 0;
-      s = read_counters(h, B.ctr);
-      if (s != SJ_OK) return s;
-      s = flags_status(h->h_ctr->err_flags);
-      if (s != SJ_OK) return s;
-      const unsigned n_ovf = h->h_ctr->overflow_rows;
-      if (n_ovf > 0) {
-        s = topk_fallback_all(h, P, B, n_ovf, ar, launches);
-        if (s != SJ_OK) return s;
+    for (int q = 0; q < n; ++q)
+      if (P.host[q].ot_host) {
+        const size_t e = (size_t)reqs[q].nA * reqs[q].k;
+        SJ_CUDA(cudaMemcpyAsync(reqs[q].out_idx, B.st_idx[q], e * 8, cudaMemcpyDeviceToHost, stm));
+        SJ_CUDA(cudaMemcpyAsync(reqs[q].out_score, B.st_score[q], e * 4, cudaMemcpyDeviceToHost, stm));
       }
-      for (int q = 0; q < n; ++q)
-        if (P.host[q].ot_host) {
-          const size_t e = (size_t)reqs[q].nA * reqs[q].k;
-          SJ_CUDA(cudaMemcpyAsync(reqs[q].out_idx, B.st_idx[q], e * 8, cudaMemcpyDeviceToHost, stm));
-          SJ_CUDA(cudaMemcpyAsync(reqs[q].out_score, B.st_score[q], e * 4, cudaMemcpyDeviceToHost, stm));
-        }
-    }
-
-    // ---- threshold finalisation ----
     int64_t n_pairs_all = 0;
     bool over_cap = false;
-    if (P.any_thr) {
-      std::vector<int64_t> info(2 * (size_t)n, 0);
-      if (n_cand > 0) {
-        SJ_CUDA(cudaMemsetAsync(B.row_count, 0, (size_t)P.rows * 8, stm));
-        SJ_CUDA(cudaMemsetAsync(B.row_fill, 0, (size_t)P.rows * 8, stm));
-        SJ_CUDA(cudaMemsetAsync(B.n_big, 0, sizeof(int), stm));
-        ThrFinalArgs ta{};
-        ta.jobs = B.jobs;
-        ta.n_jobs = n;
-        ta.d = P.d;
-        ta.metaA = B.meta;
-        ta.metaB = B.meta;
-        ta.dot2_coef_key = dot2_coef_key(P.d);
-        ta.cand = B.cand;
-        ta.n_cand = &B.ctr->thr_count;
-        ta.cand_cap = (int64_t)thr_cap;
-        ta.row_count = B.row_count;
-        ta.accepted = B.acc;
-        ta.ctr = B.ctr;
-        const int g_res = (int)std::min<unsigned long long>((n_cand + 31) / 32, (unsigned long long)h->sm_count * 16);
-        SJ_CUDA(launch_thr_rescore(ta, g_res, stm));
-        SJ_CUDA(launch_exclusive_scan(B.row_count, B.row_off, P.rows, B.total, B.scan, stm));
-        SJ_CUDA(launch_job_pairs(B.jobs, n, P.rows, B.row_off, B.total, B.job_info, stm));
-        const int g_sc = (int)std::min<unsigned long long>((n_cand + 255) / 256, 152ull * 16);
-        SJ_CUDA(launch_thr_scatter(B.jobs, n, B.acc, &B.ctr->n_pairs, (int64_t)thr_cap,
-                                   B.row_off, B.row_fill, B.staging, g_sc, stm));
-        SJ_CUDA(launch_thr_sort_rows(B.jobs, n, P.rows, B.row_off, B.row_count, B.staging,
-                                     B.big_rows, B.n_big, stm));
-        SJ_CUDA(launch_thr_sort_big(B.jobs, n, B.staging, B.tmp, B.row_off, B.row_count,
-                                    B.big_rows, B.n_big, 2 * h->sm_count, stm));
-        launches += 9;
-        SJ_CUDA(cudaMemcpyAsync(info.data(), B.job_info, 16 * (size_t)n, cudaMemcpyDeviceToHost, stm));
-        SJ_CUDA(cudaStreamSynchronize(stm));
+    for (int q = 0; q < n; ++q) {
+      const JoinReq &r = reqs[q];
+      if (!r.thr) continue;
+      const int64_t np = h_info[2 * q], off = h_info[2 * q + 1];
+      n_pairs_all += np;
+      if (P.host[q].nout_dev) {
+        SJ_CUDA(cudaMemcpyAsync(r.n_out, &h_info[2 * q], 8, cudaMemcpyHostToDevice, stm));
+      } else {
+        *r.n_out = np;
       }
-      for (int q = 0; q < n; ++q) {
-        const JoinReq &r = reqs[q];
-        if (!r.thr) continue;
-        const int64_t np = info[2 * q], off = info[2 * q + 1];
-        n_pairs_all += np;
-        if (P.host[q].nout_dev) {
-          SJ_CUDA(cudaMemcpyAsync(r.n_out, &info[2 * q], 8, cudaMemcpyHostToDevice, stm));
-        } else {
-          *r.n_out = np;
-        }
-        if (np > r.capacity) {
-          over_cap = true;
-        } else if (np > 0 && P.host[q].op_host) {
-          SJ_CUDA(cudaMemcpyAsync(r.out, B.staging + off, (size_t)np * sizeof(PairOut),
-                                  cudaMemcpyDeviceToHost, stm));
-        }
+      if (np > r.capacity) {
+        over_cap = true;
+      } else if (np > 0 && P.host[q].op_host) {
+        SJ_CUDA(cudaMemcpyAsync(r.out, B.staging + off, (size_t)np * sizeof(PairOut),
+                                cudaMemcpyDeviceToHost, stm));
       }
     }
-    ev.rec(3);
-    s = read_counters(h, B.ctr);  // also drains the stream
+    s = read_counters(h, B.ctr);  // drains the stream; counters after any fallback
     if (s != SJ_OK) return s;
     if (st) {
       fill_common_stats(st, *h->h_ctr);
-      st->n_candidates += (int64_t)n_cand;
+      st->n_candidates += (int64_t)c1.thr_count;
       st->n_pairs = n_pairs_all;
       st->n_launches = launches;
+      ev.capturing = used_graph;  // read the graph-owned events after a replay
       st->ms_prepare = ev.ms(0, 1);
       st->ms_score = ev.ms(1, 2);
       st->ms_select = ev.ms(2, 3);
       st->ms_total = ev.ms(0, 3);
       st->margin_max = 0.0;
+      st->graph_replayed = used_graph ? 1 : 0;
     }
     s = flags_status(h->h_ctr->err_flags);
     if (s != SJ_OK) return s;
@@ -904,6 +1070,7 @@ void add_stats(sj_stats *acc, const sj_stats &one) {
   acc->n_pairs += one.n_pairs;
   acc->n_launches += one.n_launches;
   acc->n_tier2_rows += one.n_tier2_rows;
+  acc->graph_replayed += one.graph_replayed;
   acc->max_abs_err_lowprec = std::max(acc->max_abs_err_lowprec, one.max_abs_err_lowprec);
 }
 
@@ -1006,6 +1173,7 @@ sj_status sj_create(sj_handle **out, const sj_config *cfg) {
   cudaError_t e = cudaMallocHost(&h->h_ctr, sizeof(Counters));
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_i64, 64);
   for (int t = 0; t < 6 && e == cudaSuccess; ++t) e = cudaEventCreate(&h->ev[t]);
+  for (int t = 0; t < 4 && e == cudaSuccess; ++t) e = cudaEventCreate(&h->gev[t]);
   if (e == cudaSuccess && cfg->prec != SJ_FP32) {
     sj_status s = tc_create(&h->tc);
     if (s != SJ_OK) {
@@ -1026,11 +1194,16 @@ sj_status sj_destroy(sj_handle *h) {
   cudaSetDevice(h->cfg.device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ws) cudaFree(h->ws);
   if (h->h_ctr) cudaFreeHost(h->h_ctr);
   if (h->h_i64) cudaFreeHost(h->h_i64);
+  if (h->h_tab) cudaFreeHost(h->h_tab);
   for (int t = 0; t < 6; ++t)
     if (h->ev[t]) cudaEventDestroy(h->ev[t]);
+  for (int t = 0; t < 4; ++t)
+    if (h->gev[t]) cudaEventDestroy(h->gev[t]);
   if (h->tc) tc_destroy(h->tc);
   delete h;
   return SJ_OK;
@@ -1218,5 +1391,7 @@ const char *sj_status_string(sj_status s) {
 }
 
 int sj_version(void) { return kVersion; }
+
+const char *sj_last_error_detail(void) { return g_err_detail; }
 
 }  // extern "C"

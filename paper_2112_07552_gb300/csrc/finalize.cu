@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(kFinThreads)
   FinSmemLayout<CMAX> &sm = *reinterpret_cast<FinSmemLayout<CMAX> *>(smem_raw);
   float *a_row = reinterpret_cast<float *>(smem_raw + sizeof(FinSmemLayout<CMAX>));
   const unsigned nr = *n_rows;
+  if (a.ctr->err_flags) return;
   for (unsigned r = blockIdx.x; r < nr; r += gridDim.x) {
     fin_row<CMAX>(a, rows[r], sm, a_row, defer, defer_key, n_defer);
     __syncthreads();
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(kFinWarps * 32)
   const int64_t d = a.d;
   unsigned long long my_cand = 0;
   float my_err = 0.f;
+  if (a.ctr->err_flags) return;
   const int64_t nwarps = (int64_t)gridDim.x * kFinWarps;
   const int64_t g0 = (int64_t)blockIdx.x * kFinWarps + wib;
   int q = g0 < a.rows ? find_job_row0(a.jobs, a.n_jobs, g0) : 0;
@@ -582,7 +584,7 @@ __global__ void thr_rescore_kernel(ThrFinalArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t n_cand = min64((int64_t)*a.n_cand, a.cand_cap);
+  const int64_t n_cand = a.ctr->err_flags ? 0 : min64((int64_t)*a.n_cand, a.cand_cap);
   const int64_t d = a.d;
   unsigned long long n_exact = 0;
   int hint = 0;  // candidates arrive grouped by job (pushed per scoring unit)

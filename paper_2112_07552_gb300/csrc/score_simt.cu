@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
   const float *Bp = static_cast<const float *>(a.Bp);
   const int64_t dp = a.dp;
   const int64_t nkt = dp / BK;
+  if (*(volatile unsigned *)&a.ctr->err_flags & (kErrNonFinite | kErrNotUnit)) return;
 
   for (int64_t unit = blockIdx.x; unit < a.n_units; unit += gridDim.x) {
     const UnitDev un = a.units[unit];

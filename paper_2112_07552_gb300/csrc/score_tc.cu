@@ -41,7 +41,8 @@ constexpr int BN = kTcBN;       // 256 columns of B per tile (TMEM columns)
 constexpr int BK = 64;          // k-block: 64 bf16 = 128 bytes = one swizzle row
 constexpr int STAGES = 4;
 constexpr int kEpiChunks = 2;  // 32-column chunks per TMEM round trip
-static_assert(kTcHeapMaxK == kTopKRegs, "register top-k size");
+constexpr int kRegsMaxK = 16;  // k kept in registers; 16 < k <= kTcHeapMaxK in the smem heap
+static_assert(kRegsMaxK <= kTopKRegs, "register top-k size");
 constexpr int kEpiWarps = 8;    // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTileABytes = BM * BK * 2;
@@ -58,16 +59,18 @@ struct alignas(1024) TcSmem {
   uint64_t tmem_empty[2];
   uint64_t drain;
   uint64_t never;  // debug-timeout hook: nothing ever arrives here
+  float heap[kTcHeapMaxK * kHeapStride];  // per-row top-k min-heaps (16 < k <= 32)
   uint32_t tmem_base;
   int abort;
 };
 
 // Fused filter over 32 scores of the thread's row, columns jb .. jb+31.
-// KM > 0: the running k best are kept in h (k <= KM); KM == 0: lazy theta.
+// KM > 0: the running k best are kept in h (k <= KM); KM < 0: in the row's
+// shared-memory heap rc_heap; KM == 0: lazy theta.
 template <int KM>
 __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? KM : 1],
-                                               const ScoreArgs &a, const float (&v)[32],
-                                               int64_t jb, int64_t nB) {
+                                               float *rc_heap, const ScoreArgs &a,
+                                               const float (&v)[32], int64_t jb, int64_t nB) {
   // fast path: one compare per 32 scores (balanced max tree)
   float p16[16], q8[8];
 #pragma unroll
@@ -106,6 +109,7 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? K
         const float x = e == 0 ? x0 : e == 1 ? x1 : e == 2 ? x2 : x3;
         if (x >= fminf(rc.theta, rc.tau_lo) && jq + e < nB) {
           if constexpr (KM > 0) row_push_regs<KM>(rc, h, a, x, (int32_t)(jq + e));
+          else if constexpr (KM < 0) row_push_heap(rc, rc_heap, a, x, (int32_t)(jq + e));
           else row_push(rc, a, x, (int32_t)(jq + e));
         }
       }
@@ -118,10 +122,10 @@ __device__ __forceinline__ void flag_timeout(TcSmem &sm, Counters *ctr) {
   atomicOr(&ctr->err_flags, kErrTimeout);
 }
 
-// The epilogue warps' share of one unit: the row's (or no) running top-k in
-// registers (KM slots; KM == 0: lazy theta), every tile of the unit's column
-// range from tensor memory through the fused filter, then the row's band
-// count and exact top-k values.
+// The epilogue warps' share of one unit: the row's running top-k in
+// registers (KM > 0 slots), in a shared-memory heap (KM < 0) or none (KM == 0:
+// lazy theta), every tile of the unit's column range from tensor memory
+// through the fused filter, then the row's band count and exact top-k values.
 template <int KM>
 __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, const UnitDev &un,
                                               const JobDev &jb, int64_t row, bool owner,
@@ -137,9 +141,11 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
   rc.k = kj;
   rc.theta = INFINITY;
   rc.tau_lo = INFINITY;
-  rc.exact = KM > 0;
+  rc.exact = KM != 0;
   float h[KM > 0 ? KM : 1];
+  float *heap = sm.heap + half * BM + (row - (int64_t)un.rb * BM);  // this thread's heap
   if constexpr (KM > 0) topk_regs_init<KM>(h, kj);
+  if constexpr (KM < 0) heap_init(heap, kj);
   if (owner) row_begin(rc, a, jb, row, list);
   const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
   const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
@@ -165,8 +171,8 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
       tmem_ld32_nowait(taddr + c0 + 32, v1);
       tmem_wait_ld(v0, v1);
       if (owner) {
-        epilogue_chunk<KM>(rc, h, a, v0, col0 + c0, nB);
-        epilogue_chunk<KM>(rc, h, a, v1, col0 + c0 + 32, nB);
+        epilogue_chunk<KM>(rc, h, heap, a, v0, col0 + c0, nB);
+        epilogue_chunk<KM>(rc, h, heap, a, v1, col0 + c0 + 32, nB);
       }
     }
     fence_before();
@@ -174,13 +180,15 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
   }
   if (owner) {
     row_end(rc, a);
-    if constexpr (KM > 0) {
-      if (jb.topv0 >= 0) {
-        // the list's k best, descending (the last k register slots)
-        float *tv = a.topv + jb.topv0 + (row * jb.lists + list) * (int64_t)kj;
+    if (jb.topv0 >= 0) {
+      // the list's k best (any order)
+      float *tv = a.topv + jb.topv0 + (row * jb.lists + list) * (int64_t)kj;
+      if constexpr (KM > 0) {
 #pragma unroll
         for (int t = 0; t < KM; ++t)
           if (t >= KM - kj) tv[t - (KM - kj)] = h[t];
+      } else if constexpr (KM < 0) {
+        for (int t = 0; t < kj; ++t) tv[t] = heap[t * kHeapStride];
       }
     }
   }
@@ -196,6 +204,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool debug_timeout = (flags & SJ_FLAG_DEBUG_TIMEOUT) != 0;
   const uint64_t limit_ns = 4000000000ull;  // 4 s per wait
   volatile int *abort = &sm.abort;
+  // inputs that failed validation: nothing to score (uniform over the grid)
+  if (*(volatile unsigned *)&a.ctr->err_flags & (kErrNonFinite | kErrNotUnit)) return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -330,11 +340,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool owner = row < jb.nA;
       const int kj = jb.k;
       const int list = un.split * a.bands_per_split + half;
-      if (kj > 0 && kj <= 16)
-        epilogue_unit<16>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
-      else if (kj > 0 && kj <= kTopKRegs)
-        epilogue_unit<kTopKRegs>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns,
+      if (kj > 0 && kj <= kRegsMaxK)
+        epilogue_unit<kRegsMaxK>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns,
                                  tile, ok);
+      else if (kj > 0 && kj <= kTcHeapMaxK)
+        epilogue_unit<-1>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile,
+                          ok);
       else
         epilogue_unit<0>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
     }

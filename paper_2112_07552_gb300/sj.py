@@ -36,12 +36,13 @@ PRECISIONS = {"fp32": SJ_FP32, "bf16": SJ_BF16, "fp8": SJ_FP8_E4M3}
 
 SJ_FLAG_SYM_INFONCE = 0x1
 SJ_FLAG_SINGLE_SPLIT = 0x2
+SJ_FLAG_NO_GRAPH = 0x4
 SJ_FLAG_DEBUG_TIMEOUT = 0x100
 
 # every symbol include/sj.h declares
 EXPORTS = ("sj_create", "sj_destroy", "sj_topk", "sj_threshold", "sj_batch",
            "sj_contrastive_fwd", "sj_backward", "sj_topk_noalloc", "sj_status_string",
-           "sj_version")
+           "sj_version", "sj_last_error_detail")
 
 I64, P = ctypes.c_int64, ctypes.c_void_p
 
@@ -57,7 +58,7 @@ class SjStats(ctypes.Structure):
                 ("n_candidates", I64), ("n_rescored", I64), ("n_exact", I64),
                 ("n_overflow_rows", I64), ("n_pairs", I64),
                 ("margin_max", ctypes.c_double), ("max_abs_err_lowprec", ctypes.c_double),
-                ("n_launches", I64), ("n_tier2_rows", I64)]
+                ("n_launches", I64), ("n_tier2_rows", I64), ("graph_replayed", I64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -76,7 +77,12 @@ class SjJob(ctypes.Structure):
 class SJError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__("%s failed: %s (status %d)" % (where, status_string(code), code))
+        msg = "%s failed: %s (status %d)" % (where, status_string(code), code)
+        if code in (SJ_ERR_CUDA, SJ_ERR_OOM) and _lib is not None:
+            detail = _lib.sj_last_error_detail()
+            if detail:
+                msg += " [%s]" % detail.decode(errors="replace")
+        super().__init__(msg)
 
 
 _lock = threading.Lock()
@@ -98,6 +104,8 @@ def lib() -> ctypes.CDLL:
             _build.build()
         L = ctypes.CDLL(path)
         st = ctypes.c_int
+        L.sj_last_error_detail.restype = ctypes.c_char_p
+        L.sj_last_error_detail.argtypes = []
         L.sj_create.restype = st
         L.sj_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(SjConfig)]
         L.sj_destroy.restype = st

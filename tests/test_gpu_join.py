@@ -335,3 +335,45 @@ def test_batch_split_into_groups_under_workspace_limit(sjmod, prec):
         assert_topk(o["idx"], o["score"], A, B, 7)
         assert_thr((o["i"], o["j"], o["pair_score"]), A, B, 0.85)
     assert st["n_launches"] > st_all["n_launches"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_graph_replay_new_data_and_outputs(sjmod, prec):
+    """A batch of device jobs is captured as a CUDA graph on its first call and
+    replayed on later calls of the same shapes, with new inputs and new output
+    buffers each time (they travel in the job table, not in the graph)."""
+    d = 48
+    sizes = [(300, 500), (1, 900), (700, 64), (257, 257)]
+    J = sjmod.SimilarityJoin(d, prec=prec, device=0)
+    replayed = []
+    for call in range(3):
+        data = [(datagen.clustered(na, d, 9, 0.1, seed=500 + 10 * call + q, stream=0),
+                 datagen.clustered(nb, d, 9, 0.1, seed=500 + 10 * call + q, stream=1))
+                for q, (na, nb) in enumerate(sizes)]
+        jobs = [{"A": dev(A), "B": dev(B), "k": 6, "tau": 0.8} for A, B in data]
+        outs, st = J.batch(jobs, with_stats=True)
+        replayed.append(st["graph_replayed"])
+        for (A, B), o in zip(data, outs):
+            assert_topk(o["idx"], o["score"], A, B, 6)
+            assert_thr((o["i"], o["j"], o["pair_score"]), A, B, 0.8)
+    J.close()
+    assert replayed[1] >= 1 and replayed[2] >= 1  # the wrapper may retry for capacity
+    # a validation error inside a replayed graph is still reported
+    A = datagen.clustered(300, d, 9, 0.1, seed=1, stream=0)
+    B = datagen.clustered(500, d, 9, 0.1, seed=1, stream=1)
+    J = sjmod.SimilarityJoin(d, prec=prec, device=0)
+    J.topk(dev(A), dev(B), 6)
+    bad = A.copy()
+    bad[5, 3] = np.nan
+    with pytest.raises(sjmod.SJError) as ei:
+        J.topk(dev(bad), dev(B), 6)
+    assert ei.value.code == sjmod.SJ_ERR_NONFINITE
+    idx, sc = J.topk(dev(A), dev(B), 6)
+    assert_topk(idx, sc, A, B, 6)
+    J.close()
+    # SJ_FLAG_NO_GRAPH: launches only
+    J = sjmod.SimilarityJoin(d, prec=prec, device=0, flags=sjmod.SJ_FLAG_NO_GRAPH)
+    for _ in range(2):
+        _, _, st = J.topk(dev(A), dev(B), 6, with_stats=True)
+        assert st["graph_replayed"] == 0
+    J.close()
