@@ -319,7 +319,6 @@ def run_batch(args):
     sa = datagen.log_uniform_sizes(nj, w["lo"], w["hi"], w["seed"], 0)
     sb = datagen.log_uniform_sizes(nj, w["lo"], w["hi"], w["seed"], 1)
     pair_scores = float(np.sum(sa.astype(np.float64) * sb))
-    padded = float(np.sum(np.ceil(sa / 128) * 128 * np.ceil(sb / 256) * 256))
     _build.build()
     L = sj.lib()
     dev = torch.device("cuda", 0)
@@ -329,6 +328,14 @@ def run_batch(args):
     t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.current_stream(dev)
     J = sj.SimilarityJoin(d, prec="bf16", device=0, stream=stream)
+    # tile widths per right-side size class from the autotuner (untimed)
+    import tempfile
+    with tempfile.TemporaryDirectory() as td:
+        t_tune = time.perf_counter()
+        J.autotune(k, os.path.join(td, "tiles.txt"))
+        t_tune = time.perf_counter() - t_tune
+        widths = {int(r[3]): int(r[4]) for r in
+                  (line.split() for line in open(os.path.join(td, "tiles.txt")))}
     caps = 16 * sa + 1024
     po = np.concatenate([[0], np.cumsum(caps)])
     n_out = (sj.I64 * nj)()
@@ -376,6 +383,7 @@ def run_batch(args):
     ms = e0.elapsed_time(e1) / args.steps
     ms_score = statistics.mean(s.ms_score for s in stats)
     n_pairs_all = int(sum(n_out[q] for q in range(nj)))
+    padded = float(stats[-1].padded_pair_scores)
 
     # parity on sampled rows of sampled jobs, and the oracle's time on them
     import oracle
@@ -449,7 +457,8 @@ def run_batch(args):
                    "rows_B": int(bo[-1]), "pair_scores": pair_scores, "d": d, "k": k,
                    "tau": tau, "seed": w["seed"],
                    "l2": "inputs %.0f GB > L2, no flush" % ((ao[-1] + bo[-1]) * d * 4 / 1e9),
-                   "parallelism": "dp1"},
+                   "parallelism": "dp1",
+                   "tile_widths_by_nB_class": widths, "autotune_s": t_tune},
         "roofline": {"bound": "tensor", "kernel": "score_tc_kernel", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": src + " bf16_tflops_sustained", "traffic": None,

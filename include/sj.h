@@ -72,6 +72,7 @@ typedef enum {
                                       candidates collected in one list; lowers
                                       parallelism when nA is small) */
 #define SJ_FLAG_NO_GRAPH 0x4u      /* never replay joins from a captured CUDA graph */
+#define SJ_FLAG_NARROW_TILES 0x8u  /* test hook: 128-column score tiles for every job */
 #define SJ_FLAG_DEBUG_TIMEOUT 0x100u /* test hook: device waits give up at once */
 
 typedef struct {
@@ -108,6 +109,7 @@ typedef struct {
   int64_t n_launches;        /* kernels this call launched */
   int64_t n_tier2_rows;      /* rows finalised with the large candidate tier */
   int64_t graph_replayed;    /* job groups run from a captured CUDA graph */
+  double padded_pair_scores; /* pair-scores the score tiles computed, padding included */
 } sj_stats;
 
 typedef struct sj_handle sj_handle;
@@ -168,6 +170,23 @@ typedef struct {
  * capacity writes no pairs and sets *n_out to the required count; the other
  * jobs complete and the call returns SJ_ERR_CAPACITY. */
 sj_status sj_batch(sj_handle *h, const sj_job *jobs, int32_t n_jobs, sj_stats *st);
+
+/* Autotuner of the score tile shape per size class of the right side (the
+ * paper has no counterpart: its joins are single products).  For every class
+ * c = 6..16 (nB in (2^(c-1), 2^c]) it times a synthetic top-k join of 8,192
+ * unit rows against 0.75 * 2^c rows with 128- and 256-column tiles, and
+ * keeps the faster width for later jobs of this handle with the same k and
+ * class (untuned jobs use 128 columns up to nB = 128, else 256).  If `path`
+ * is non-NULL the table is merged into that text file (one
+ * "d precision k class width" line per entry).  Results never depend on the
+ * width; only speed does.  Takes about a second.
+ * Errors: SJ_ERR_INVALID_ARG (k outside 1..1024, unwritable path),
+ * SJ_ERR_UNSUPPORTED (SJ_FP32: one tile shape), SJ_ERR_CUDA, SJ_ERR_OOM. */
+sj_status sj_autotune(sj_handle *h, int32_t k, const char *path);
+
+/* Load the widths that sj_autotune wrote to `path` for this handle's d and
+ * precision.  Errors: SJ_ERR_INVALID_ARG (null or unreadable path). */
+sj_status sj_autotune_load(sj_handle *h, const char *path);
 
 /* Contrastive (InfoNCE) join over N paired rows, positives on the diagonal:
  * S = A B^T / T, l_i = logsumexp_j S_ij, loss = (1/N) sum_i (l_i - S_ii)

@@ -11,8 +11,10 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/sj.h"
@@ -83,6 +85,8 @@ struct sj_handle {
   size_t h_tab_size = 0;
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
   std::vector<GraphEntry> graphs;
+  std::map<std::pair<int, int>, int> tile_width;  // (k, right-side size class) -> tile width
+  int force_bn = 0;                               // autotuner: width under test
   cudaEvent_t ev[6]{};
   cudaEvent_t gev[4]{};  // stage events recorded only by captured graphs
   sj::TcContext *tc = nullptr;
@@ -346,8 +350,28 @@ struct BatchPlan {
   std::vector<UnitDev> units;
   int64_t rows = 0, prows = 0, slots = 0, band_entries = 0, topv_entries = 0;
   int64_t rows_thr = 0, cap_sum = 0;
+  double padded_pairs = 0.0;  // pair-scores the score tiles compute (incl. padding)
   bool any_topk = false, any_thr = false, any_op_host = false;
 };
+
+// Size class of a right side: nB in (2^(c-1), 2^c].
+int size_class(int64_t n) {
+  int c = 0;
+  while (c < 62 && ((int64_t)1 << c) < n) ++c;
+  return c;
+}
+
+// Column tile width of a job on the tensor-core pass: the width under test
+// while autotuning, the test hook, the autotuned width of its (k, size
+// class), else 128 columns for right sides of at most 128 rows and 256 above.
+int tile_width(const sj_handle *h, int64_t nB, int k) {
+  if (h->cfg.prec == SJ_FP32) return kSimtBN;
+  if (h->force_bn) return h->force_bn;
+  if (h->cfg.flags & SJ_FLAG_NARROW_TILES) return kTcBNNarrow;
+  auto it = h->tile_width.find({k, size_class(nB)});
+  if (it != h->tile_width.end()) return it->second;
+  return nB <= kTcBNNarrow ? kTcBNNarrow : kTcBN;
+}
 
 // Column splits: a unit covers at most total_tiles / (2 SMs) column tiles, so
 // a small batch still yields about two units per SM and a large one keeps
@@ -391,14 +415,18 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
       if (r.nB > 0) P.segs.push_back(PackSeg{nullptr, r.nB, P.prows, q, 1});
       P.prows += round_up(r.nB, BN);
     }
-    const int64_t rb = (r.nA + BM - 1) / BM, ct = (r.nB + BN - 1) / BN;
+    const int64_t bn = tile_width(h, r.nB, r.k);
+    const int64_t rb = (r.nA + BM - 1) / BM, ct = (r.nB + bn - 1) / bn;
+    jd.bn = (int32_t)bn;
     int64_t S = 0, tps = 1;
     if (rb > 0 && ct > 0) {
-      tps = (h->cfg.flags & SJ_FLAG_SINGLE_SPLIT) ? ct : std::min(ct, tps_target);
+      // tps_target counts tiles of BN columns
+      tps = (h->cfg.flags & SJ_FLAG_SINGLE_SPLIT) ? ct : std::min(ct, tps_target * (BN / bn));
       if ((ct + tps - 1) / tps > 256) tps = (ct + 255) / 256;
       S = (ct + tps - 1) / tps;
     }
     jd.n_col_tiles = (int32_t)ct;
+    P.padded_pairs += (double)(rb * BM) * (double)(ct * bn);
     jd.tiles_per_split = (int32_t)tps;
     jd.n_splits = (int32_t)S;
     jd.k = r.k;
@@ -414,7 +442,7 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     // overflows after compaction goes to the rescan fallback.  Otherwise the
     // running k-th is refreshed lazily and needs 4k + 256.
     if (r.k > 0) {
-      const int64_t cols = tps * BN / P.bands;
+      const int64_t cols = tps * bn / P.bands;
       const bool exact_running = h->cfg.prec != SJ_FP32 && r.k <= kTcHeapMaxK;
       const int64_t slack = std::min<int64_t>(192, std::max<int64_t>(32, cols / 2048));
       jd.cap = (int32_t)(exact_running ? round_up(2 * (int64_t)r.k + 64 + slack, 32)
@@ -873,6 +901,7 @@ std::vector<int64_t> graph_key(const sj_handle *h, const BatchPlan &P, const Joi
     key.push_back(reqs[q].nA);
     key.push_back(reqs[q].nB);
     key.push_back(((int64_t)reqs[q].k << 2) | (reqs[q].thr ? 2 : 0) | (P.host[q].self ? 1 : 0));
+    key.push_back(P.jobs[q].bn);
   }
   return key;
 }
@@ -1038,6 +1067,7 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
       st->ms_total = ev.ms(0, 3);
       st->margin_max = 0.0;
       st->graph_replayed = used_graph ? 1 : 0;
+      st->padded_pair_scores = P.padded_pairs;
     }
     s = flags_status(h->h_ctr->err_flags);
     if (s != SJ_OK) return s;
@@ -1071,6 +1101,7 @@ void add_stats(sj_stats *acc, const sj_stats &one) {
   acc->n_launches += one.n_launches;
   acc->n_tier2_rows += one.n_tier2_rows;
   acc->graph_replayed += one.graph_replayed;
+  acc->padded_pair_scores += one.padded_pair_scores;
   acc->max_abs_err_lowprec = std::max(acc->max_abs_err_lowprec, one.max_abs_err_lowprec);
 }
 
@@ -1145,9 +1176,135 @@ sj_status threshold_impl(sj_handle *h, const float *A, int64_t nA, const float *
   return join_batch(h, &r, 1, st);
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the column tile width per right-side size class.
+
+// Unit-norm rows for timing only: uniform entries from a 64-bit mix of
+// (seed, row, column), normalised in double.  One thread per row.
+__global__ void tune_rows_kernel(float *X, int64_t n, int64_t d, uint64_t seed) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  auto mix = [](uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+  };
+  double s = 0.0;
+  for (int64_t c = 0; c < d; ++c) {
+    const double u = (double)(mix(seed ^ mix((uint64_t)r * 0x9e3779b97f4a7c15ull + c)) >> 11) *
+                         0x1p-53 * 2.0 - 1.0;
+    s += u * u;
+  }
+  const double inv = 1.0 / sqrt(s > 0.0 ? s : 1.0);
+  for (int64_t c = 0; c < d; ++c) {
+    const double u = (double)(mix(seed ^ mix((uint64_t)r * 0x9e3779b97f4a7c15ull + c)) >> 11) *
+                         0x1p-53 * 2.0 - 1.0;
+    X[r * d + c] = (float)(u * inv);
+  }
+}
+
+constexpr int kTuneClassLo = 6, kTuneClassHi = 16;  // right sides of 48 .. 49,152 rows
+constexpr int64_t kTuneRowsA = 8192;
+
+// Table file: one "d precision k class width" line per entry.
+sj_status write_tile_table(const sj_handle *h, const char *path) {
+  std::vector<std::string> keep;
+  if (FILE *f = std::fopen(path, "r")) {
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+      long long d;
+      int prec, k, c, w;
+      if (std::sscanf(line, "%lld %d %d %d %d", &d, &prec, &k, &c, &w) != 5) continue;
+      if (d == h->cfg.d && prec == (int)h->cfg.prec && h->tile_width.count({k, c})) continue;
+      keep.push_back(line);
+    }
+    std::fclose(f);
+  }
+  FILE *f = std::fopen(path, "w");
+  if (!f) return SJ_ERR_INVALID_ARG;
+  for (const std::string &l : keep) std::fputs(l.c_str(), f);
+  for (const auto &e : h->tile_width)
+    std::fprintf(f, "%lld %d %d %d %d\n", (long long)h->cfg.d, (int)h->cfg.prec, e.first.first,
+                 e.first.second, e.second);
+  return std::fclose(f) == 0 ? SJ_OK : SJ_ERR_INVALID_ARG;
+}
+
 }  // namespace
 
 extern "C" {
+
+sj_status sj_autotune(sj_handle *h, int32_t k, const char *path) {
+  if (!h || k < 1 || k > 1024) return SJ_ERR_INVALID_ARG;
+  if (h->cfg.prec == SJ_FP32) return SJ_ERR_UNSUPPORTED;
+  SJ_CUDA(cudaSetDevice(h->cfg.device));
+  const int64_t d = h->cfg.d, nB_max = (int64_t)3 << (kTuneClassHi - 2);
+  float *A = nullptr, *B = nullptr;
+  int64_t *idx = nullptr;
+  float *sc = nullptr;
+  cudaError_t e = cudaMalloc(&A, (size_t)kTuneRowsA * d * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&B, (size_t)nB_max * d * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&idx, (size_t)kTuneRowsA * k * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&sc, (size_t)kTuneRowsA * k * 4);
+  sj_status s = SJ_OK;
+  if (e == cudaSuccess) {
+    tune_rows_kernel<<<(unsigned)((kTuneRowsA + 127) / 128), 128, 0, h->stream>>>(A, kTuneRowsA,
+                                                                                d, 1);
+    tune_rows_kernel<<<(unsigned)((nB_max + 127) / 128), 128, 0, h->stream>>>(B, nB_max, d, 2);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    note_cuda_error(e, "autotune buffers", __LINE__);
+    s = cuda_status(e);
+  }
+  for (int c = kTuneClassLo; c <= kTuneClassHi && s == SJ_OK; ++c) {
+    const int64_t nB = (int64_t)3 << (c - 2);  // three quarters of the class's upper end
+    double best = 1e300;
+    int best_w = kTcBN;
+    for (int w : {kTcBNNarrow, kTcBN}) {
+      h->force_bn = w;
+      double t = 1e300;
+      for (int rep = 0; rep < 3 && s == SJ_OK; ++rep) {
+        JoinReq r{A, kTuneRowsA, B, nB, k, idx, sc, false, 0.0, nullptr, 0, nullptr};
+        sj_stats st{};
+        s = join_batch(h, &r, 1, &st);
+        if (rep > 0) t = std::min(t, st.ms_total);
+      }
+      if (t < best) {
+        best = t;
+        best_w = w;
+      }
+    }
+    h->force_bn = 0;
+    h->tile_width[{k, c}] = best_w;
+  }
+  h->force_bn = 0;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(idx);
+  cudaFree(sc);
+  if (s == SJ_OK && path) s = write_tile_table(h, path);
+  return s;
+}
+
+sj_status sj_autotune_load(sj_handle *h, const char *path) {
+  if (!h || !path) return SJ_ERR_INVALID_ARG;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return SJ_ERR_INVALID_ARG;
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    long long d;
+    int prec, k, c, w;
+    if (std::sscanf(line, "%lld %d %d %d %d", &d, &prec, &k, &c, &w) != 5) continue;
+    if (d != h->cfg.d || prec != (int)h->cfg.prec) continue;
+    if (w != kTcBN && w != kTcBNNarrow) continue;
+    h->tile_width[{k, c}] = w;
+  }
+  std::fclose(f);
+  return SJ_OK;
+}
 
 sj_status sj_create(sj_handle **out, const sj_config *cfg) {
   if (!out || !cfg || cfg->d < 1) return SJ_ERR_INVALID_ARG;

@@ -49,6 +49,7 @@ constexpr uint32_t kTileABytes = BM * BK * 2;
 constexpr uint32_t kTileBBytes = BN * BK * 2;
 constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators
 constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
+constexpr uint32_t kIdescNarrow = idesc_bf16(BM, kTcBNNarrow);
 
 struct alignas(1024) TcSmem {
   unsigned char a[STAGES][kTileABytes];  // each 1024-byte aligned
@@ -160,11 +161,12 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
       break;
     }
     fence_after();
-    const int64_t col0 = ct * BN;
+    const int bn = jb.bn;
+    const int64_t col0 = ct * bn;
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
     // two 32-column chunks per TMEM round trip
 #pragma unroll 1
-    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 64) {
+    for (int c0 = half * (bn / 2); c0 < (half + 1) * (bn / 2); c0 += 64) {
       if (kj > 0) warp_compact(rc, owner, kj, limit);
       float v0[32], v1[32];
       tmem_ld32_nowait(taddr + c0, v0);
@@ -196,7 +198,8 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
 
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const __grid_constant__ CUtensorMap tmA,
-                    const __grid_constant__ CUtensorMap tmB, ScoreArgs a, uint32_t flags) {
+                    const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ CUtensorMap tmB128, ScoreArgs a, uint32_t flags) {
   extern __shared__ unsigned char smem_raw[];
   TcSmem &sm = *reinterpret_cast<TcSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -246,7 +249,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
         const int arow = (int)(jb.a_prow0 + (int64_t)un.rb * BM);
         for (int64_t ct = ct0; ct < ct1 && ok; ++ct) {
-          const int brow = (int)(jb.b_prow0 + ct * BN);
+          const bool narrow = jb.bn == kTcBNNarrow;
+          const int brow = (int)(jb.b_prow0 + ct * jb.bn);
           for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
             const int s = (int)(it % STAGES);
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
@@ -255,9 +259,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(&sm.full[s], kTileABytes + kTileBBytes);
+            mbar_arrive_expect_tx(&sm.full[s],
+                                  kTileABytes + (narrow ? kTileBBytes / 2 : kTileBBytes));
             tma_load_2d(sm.a[s], &tmA, (int)(kb * BK), arow, &sm.full[s]);
-            tma_load_2d(sm.b[s], &tmB, (int)(kb * BK), brow, &sm.full[s]);
+            tma_load_2d(sm.b[s], narrow ? &tmB128 : &tmB, (int)(kb * BK), brow, &sm.full[s]);
           }
         }
       }
@@ -281,6 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const JobDev &jb = a.jobs[un.job];
         const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
         const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
+        const uint32_t idesc = jb.bn == kTcBNNarrow ? kIdescNarrow : kIdesc;
         for (int64_t ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
           const int acc = (int)(tile & 1);
           const uint32_t aph = (uint32_t)((tile >> 1) & 1);
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a0 = su32(sm.a[s]), b0 = su32(sm.b[s]);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-              mma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), kIdesc,
+              mma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
                        (kb > 0 || kk > 0) ? 1u : 0u);
             }
             mma_commit(&sm.empty[s]);  // frees the smem stage once these MMAs finish
@@ -412,8 +418,9 @@ sj_status tc_make_maps(TcContext *ctx, const void *Ap, int64_t nA_pad, const voi
   // B tiles never cross a segment end (segments are padded to BN rows)
   if (dp % BK != 0 || nA_pad % BM != 0 || nB_pad < BN) return SJ_ERR_INTERNAL;
   sj_status s = tc_encode_2d(ctx, Ap, dp, nA_pad, BK, BM, out->a);
-  if (s != SJ_OK) return s;
-  return tc_encode_2d(ctx, Bp, dp, nB_pad, BK, BN, out->b);
+  if (s == SJ_OK) s = tc_encode_2d(ctx, Bp, dp, nB_pad, BK, BN, out->b);
+  if (s == SJ_OK) s = tc_encode_2d(ctx, Bp, dp, nB_pad, BK, kTcBNNarrow, out->b128);
+  return s;
 }
 
 cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, uint32_t flags,
@@ -424,10 +431,11 @@ cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, ui
   cudaError_t e = cudaFuncSetAttribute(score_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  CUtensorMap ma, mb;
+  CUtensorMap ma, mb, mb128;
   std::memcpy(&ma, maps->a, sizeof ma);
   std::memcpy(&mb, maps->b, sizeof mb);
-  score_tc_kernel<<<grid, kThreads, smem, st>>>(ma, mb, a, flags);
+  std::memcpy(&mb128, maps->b128, sizeof mb128);
+  score_tc_kernel<<<grid, kThreads, smem, st>>>(ma, mb, mb128, a, flags);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,8 @@ struct JobDev {
   int32_t n_splits;          // column splits
   int32_t tiles_per_split;   // column tiles per split
   int32_t n_col_tiles;       // column tiles of the job
+  int32_t bn;                // column tile width of the job (tensor-core pass: 128 or 256)
+  int32_t pad_bn;
   float tau_f;               // tau rounded down to float (+inf: no threshold part)
   float gmaxB[3];            // max over the job's B rows of {nrm, qnrm, qerr} (device-written)
   long long tau_key;         // ceil(tau 2^60)
@@ -118,7 +120,7 @@ struct ScoreArgs {
 
 // Tile sizes of the scoring kernels (rows x columns of one score tile).
 constexpr int kSimtBM = 128, kSimtBN = 128, kSimtBK = 16;
-constexpr int kTcBM = 128, kTcBN = 256;
+constexpr int kTcBM = 128, kTcBN = 256, kTcBNNarrow = 128;
 constexpr int kTcHeapMaxK = 32;  // k tracked exactly by the tensor-core epilogue's heaps
 
 cudaError_t launch_score_simt(const ScoreArgs &a, int grid, cudaStream_t st);

@@ -10,11 +10,12 @@ namespace sj {
 
 struct TcContext;
 
-// Two TMA tensor maps (opaque 128-byte CUtensorMap objects) for the packed
-// A and B operands.
+// TMA tensor maps (opaque 128-byte CUtensorMap objects) for the packed
+// operands: A tiles (128 rows), B tiles of 256 and of 128 rows.
 struct TcMaps {
   alignas(64) unsigned char a[128];
   alignas(64) unsigned char b[128];
+  alignas(64) unsigned char b128[128];
 };
 
 sj_status tc_create(TcContext **out);

@@ -37,12 +37,13 @@ PRECISIONS = {"fp32": SJ_FP32, "bf16": SJ_BF16, "fp8": SJ_FP8_E4M3}
 SJ_FLAG_SYM_INFONCE = 0x1
 SJ_FLAG_SINGLE_SPLIT = 0x2
 SJ_FLAG_NO_GRAPH = 0x4
+SJ_FLAG_NARROW_TILES = 0x8
 SJ_FLAG_DEBUG_TIMEOUT = 0x100
 
 # every symbol include/sj.h declares
 EXPORTS = ("sj_create", "sj_destroy", "sj_topk", "sj_threshold", "sj_batch",
            "sj_contrastive_fwd", "sj_backward", "sj_topk_noalloc", "sj_status_string",
-           "sj_version", "sj_last_error_detail")
+           "sj_version", "sj_last_error_detail", "sj_autotune", "sj_autotune_load")
 
 I64, P = ctypes.c_int64, ctypes.c_void_p
 
@@ -58,7 +59,8 @@ class SjStats(ctypes.Structure):
                 ("n_candidates", I64), ("n_rescored", I64), ("n_exact", I64),
                 ("n_overflow_rows", I64), ("n_pairs", I64),
                 ("margin_max", ctypes.c_double), ("max_abs_err_lowprec", ctypes.c_double),
-                ("n_launches", I64), ("n_tier2_rows", I64), ("graph_replayed", I64)]
+                ("n_launches", I64), ("n_tier2_rows", I64), ("graph_replayed", I64),
+                ("padded_pair_scores", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -106,6 +108,10 @@ def lib() -> ctypes.CDLL:
         st = ctypes.c_int
         L.sj_last_error_detail.restype = ctypes.c_char_p
         L.sj_last_error_detail.argtypes = []
+        L.sj_autotune.restype = st
+        L.sj_autotune.argtypes = [P, ctypes.c_int32, ctypes.c_char_p]
+        L.sj_autotune_load.restype = st
+        L.sj_autotune_load.argtypes = [P, ctypes.c_char_p]
         L.sj_create.restype = st
         L.sj_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(SjConfig)]
         L.sj_destroy.restype = st
@@ -213,6 +219,17 @@ class SimilarityJoin:
         import torch
         dev = A.device if hasattr(A, "device") else torch.device("cpu")
         return torch.empty(shape, dtype=dtype, device=dev)
+
+    def autotune(self, k: int, path: str | None = None):
+        """Time 128- and 256-column score tiles per right-side size class for
+        joins with this k; later calls use the faster width.  With `path`,
+        the table is merged into that file (see sj_autotune)."""
+        _check(lib().sj_autotune(self._h, int(k), path.encode() if path else None),
+               "sj_autotune")
+
+    def autotune_load(self, path: str):
+        """Use the widths sj_autotune wrote to `path` (this d and precision)."""
+        _check(lib().sj_autotune_load(self._h, path.encode()), "sj_autotune_load")
 
     def topk(self, A, B, k: int, with_stats: bool = False):
         """(idx int64 [nA, k], score float32 [nA, k]) ordered (score desc, j asc)."""

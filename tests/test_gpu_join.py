@@ -377,3 +377,42 @@ def test_batch_graph_replay_new_data_and_outputs(sjmod, prec):
         _, _, st = J.topk(dev(A), dev(B), 6, with_stats=True)
         assert st["graph_replayed"] == 0
     J.close()
+
+
+@pytest.mark.parametrize("nA,nB", [(300, 60), (129, 128), (257, 129), (700, 1000), (65, 2049)])
+def test_narrow_tiles_parity(sjmod, nA, nB):
+    """128-column score tiles (the tile shape the autotuner may pick) give the
+    same exact results; padded work counts 128 x 128 tiles."""
+    d, k, tau = 64, 7, 0.8
+    A = datagen.clustered(nA, d, 11, 0.1, seed=nA, stream=0)
+    B = datagen.clustered(nB, d, 11, 0.1, seed=nB, stream=1)
+    J = sjmod.SimilarityJoin(d, prec="bf16", device=0, flags=sjmod.SJ_FLAG_NARROW_TILES)
+    outs, st = J.batch([{"A": dev(A), "B": dev(B), "k": k, "tau": tau}], with_stats=True)
+    J.close()
+    o = outs[0]
+    assert_topk(o["idx"], o["score"], A, B, k)
+    assert_thr((o["i"], o["j"], o["pair_score"]), A, B, tau)
+    padded = (-(-nA // 128) * 128) * (-(-nB // 128) * 128)
+    assert st["padded_pair_scores"] == padded
+
+
+def test_autotune_table_round_trip(sjmod, tmp_path):
+    """sj_autotune times both tile widths per size class, writes the table,
+    and a new handle that loads it joins exactly."""
+    d, k = 64, 5
+    path = str(tmp_path / "tiles.txt")
+    J = sjmod.SimilarityJoin(d, prec="bf16", device=0)
+    J.autotune(k, path)
+    J.close()
+    rows = [tuple(int(x) for x in line.split()) for line in open(path)]
+    assert len(rows) == 11
+    assert all(r[0] == d and r[1] == 1 and r[2] == k and r[4] in (128, 256) for r in rows)
+    assert sorted(r[3] for r in rows) == list(range(6, 17))
+    J = sjmod.SimilarityJoin(d, prec="bf16", device=0)
+    J.autotune_load(path)
+    for nA, nB in [(200, 100), (333, 700), (90, 5000)]:
+        A = datagen.clustered(nA, d, 11, 0.1, seed=nA + 7, stream=0)
+        B = datagen.clustered(nB, d, 11, 0.1, seed=nB + 7, stream=1)
+        idx, sc = J.topk(dev(A), dev(B), k)
+        assert_topk(idx, sc, A, B, k)
+    J.close()
