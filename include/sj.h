@@ -63,7 +63,7 @@ typedef enum {
 typedef enum {
   SJ_FP32 = 0,     /* CUDA-core FP32 FMA tiles (no tensor cores) */
   SJ_BF16 = 1,     /* bfloat16 operands, FP32 accumulation in TMEM */
-  SJ_FP8_E4M3 = 2  /* e4m3 with a power-of-two scale per row (reserved) */
+  SJ_FP8_E4M3 = 2  /* E4M3 with power-of-two scales: per row for A, per job for B */
 } sj_precision;
 
 /* cfg.flags */

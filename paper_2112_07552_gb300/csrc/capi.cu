@@ -169,6 +169,18 @@ PrecPlan plan_prec(sj_precision p, int64_t d) {
     q.dp = round_up(d, kSimtBK);
     // FMA chain of d steps, one rounding each: gamma_d (u = 2^-24), doubled.
     q.acc_coef = 2.0 * gamma_n((double)d + 2.0, std::ldexp(1.0, -24));
+  } else if (p == SJ_FP8_E4M3) {
+    q.fmt = PackFormat::kFP8;
+    q.elem = 1;
+    q.BM = kTcBM;
+    q.BN = kTcBN;
+    q.dp = round_up(d, 128);
+    // Exact E4M3 x E4M3 products (8-bit significands) summed by the tensor
+    // core, whose FP8 accumulation precision is not documented (earlier FP8
+    // tensor cores kept about 14 significant bits while adding).  Allow every
+    // one of the d + 32 additions a relative error of 2^-13 of the sum of
+    // |products| (<= ||a~|| ||b~||): (d + 32) 2^-13.
+    q.acc_coef = ((double)d + 32.0) * std::ldexp(1.0, -13);
   } else {
     q.fmt = PackFormat::kBF16;
     q.elem = 2;
@@ -782,7 +794,7 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
   SJ_CUDA(cudaMemsetAsync(B.ctr, 0, sizeof(Counters), stm));
   SJ_CUDA(launch_prepare(B.segs, (int)P.segs.size(), B.jobs, P.prows, P.d, P.pp.fmt, B.packed,
                          P.pp.dp, B.meta, B.ctr, stm));
-  launches += P.prows > 0 ? 1 : 0;
+  launches += P.prows > 0 ? (P.pp.fmt == PackFormat::kFP8 ? 2 : 1) : 0;
   ev.rec(1);
   // ---- scoring pass with the fused filter ----
   if (P.any_topk && P.slots > 0) SJ_CUDA(cudaMemsetAsync(B.band_cnt, 0, (size_t)P.slots * 4, stm));
@@ -809,10 +821,11 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
       SJ_CUDA(launch_score_simt(sa, grid, stm));
     } else {
       TcMaps maps;
-      sj_status s = tc_make_maps(h->tc, B.packed, P.prows, B.packed, P.prows, P.pp.dp, &maps);
+      sj_status s = tc_make_maps(h->tc, B.packed, P.prows, B.packed, P.prows, P.pp.dp, &maps,
+                                 P.pp.elem);
       if (s != SJ_OK) return s;
       const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count);
-      SJ_CUDA(launch_score_tc(sa, grid, &maps, h->cfg.flags, stm));
+      SJ_CUDA(launch_score_tc(sa, grid, &maps, h->cfg.flags, h->cfg.prec == SJ_FP8_E4M3, stm));
     }
     launches += 1;
   }
@@ -880,7 +893,7 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
 
 // Kernels issue_group launches for this plan.
 void issue_count(const BatchPlan &P, int64_t &l) {
-  l += P.prows > 0 ? 1 : 0;
+  l += P.prows > 0 ? (P.pp.fmt == PackFormat::kFP8 ? 2 : 1) : 0;
   l += P.units.empty() ? 0 : 1;
   l += P.any_topk && P.rows > 0 ? 3 : 0;
   l += P.any_thr && P.rows > 0 ? 9 : 0;
@@ -999,6 +1012,8 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
       jd.out_pairs = (r.thr && !hh.op_host && r.capacity > 0) ? reinterpret_cast<PairOut *>(r.out)
                                                               : nullptr;
       jd.gmaxB[0] = jd.gmaxB[1] = jd.gmaxB[2] = 0.f;
+      jd.bmax = 0.f;
+      jd.eB = 0;
       jd.n_pairs = 0;
       if (hh.a_host)
         SJ_CUDA(cudaMemcpyAsync(B.stA[q], r.A, (size_t)r.nA * P.d * 4, cudaMemcpyHostToDevice, stm));
@@ -1319,8 +1334,7 @@ sj_status sj_create(sj_handle **out, const sj_config *cfg) {
   cudaDeviceProp prop;
   SJ_CUDA(cudaGetDeviceProperties(&prop, cfg->device));
   const int cc = prop.major * 10 + prop.minor;
-  if (cfg->prec == SJ_FP8_E4M3) return SJ_ERR_UNSUPPORTED;
-  if (cfg->prec == SJ_BF16 && cc != 103) return SJ_ERR_UNSUPPORTED;
+  if (cfg->prec != SJ_FP32 && cc != 103) return SJ_ERR_UNSUPPORTED;
   sj_handle *h = new (std::nothrow) sj_handle();
   if (!h) return SJ_ERR_OOM;
   h->cfg = *cfg;

@@ -38,6 +38,8 @@ struct RowCtx {
   int overflow;   // band list could not be compacted below the limit
   Cand *band;     // cap entries
   bool exact;     // theta tracks the running k-th best exactly (kept by the caller)
+  float to_s;     // stored score = visited value * to_s (a power of two; E4M3 scoring
+                  // visits accumulator units, with theta, tau_lo, two_m in those units)
   int32_t i;      // global left row
 };
 
@@ -108,7 +110,7 @@ __device__ __forceinline__ void row_push_heap(RowCtx &r, float *heap, const Scor
                                               float v, int32_t j) {
   if (v >= r.theta) {
     if (!r.overflow) {
-      r.band[r.cnt] = Cand{v, j};
+      r.band[r.cnt] = Cand{v * r.to_s, j};
       r.cnt += 1;
     }
     if (v > heap[0]) {
@@ -116,7 +118,7 @@ __device__ __forceinline__ void row_push_heap(RowCtx &r, float *heap, const Scor
       r.theta = __fsub_rd(heap[0], r.two_m);
     }
   }
-  if (v >= r.tau_lo) push_thr(a, r.i, j, v);
+  if (v >= r.tau_lo) push_thr(a, r.i, j, v * r.to_s);
 }
 
 // Margin m_i: |s~_ij - s_ij| <= m_i for every j.
@@ -145,6 +147,7 @@ __device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, const J
   r.slot = jb.slot0 + local * jb.lists + list;
   r.band = a.band + jb.band0 + (local * jb.lists + list) * (int64_t)jb.cap;
   r.theta = jb.k > 0 ? -INFINITY : INFINITY;
+  r.to_s = 1.f;
 }
 
 // Band count of the (row, split); an overflowed list stores -(cnt + 1), its
@@ -157,10 +160,10 @@ __device__ __forceinline__ void row_end(const RowCtx &r, const ScoreArgs &a) {
 // room for a chunk of 32 visits (the owner compacts before each chunk).
 __device__ __forceinline__ void row_push(RowCtx &r, const ScoreArgs &a, float v, int32_t j) {
   if (v >= r.theta && !r.overflow) {
-    r.band[r.cnt] = Cand{v, j};
+    r.band[r.cnt] = Cand{v * r.to_s, j};
     r.cnt += 1;
   }
-  if (v >= r.tau_lo) push_thr(a, r.i, j, v);
+  if (v >= r.tau_lo) push_thr(a, r.i, j, v * r.to_s);
 }
 
 // The same with the running k best in registers: theta is exact at all times.
@@ -169,7 +172,7 @@ __device__ __forceinline__ void row_push_regs(RowCtx &r, float (&h)[KM], const S
                                               float v, int32_t j) {
   if (v >= r.theta) {
     if (!r.overflow) {
-      r.band[r.cnt] = Cand{v, j};
+      r.band[r.cnt] = Cand{v * r.to_s, j};
       r.cnt += 1;
     }
     if (v > h[KM - 1]) {
@@ -177,7 +180,7 @@ __device__ __forceinline__ void row_push_regs(RowCtx &r, float (&h)[KM], const S
       r.theta = __fsub_rd(h[KM - 1], r.two_m);
     }
   }
-  if (v >= r.tau_lo) push_thr(a, r.i, j, v);
+  if (v >= r.tau_lo) push_thr(a, r.i, j, v * r.to_s);
 }
 
 // Order-preserving map of non-NaN floats to unsigned integers.
@@ -208,8 +211,11 @@ __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int
     const unsigned long long bp =
         __shfl_sync(0xffffffffu, (unsigned long long)reinterpret_cast<uintptr_t>(r.band), src);
     Cand *band = reinterpret_cast<Cand *>((uintptr_t)bp);
-    const float two_m = __shfl_sync(0xffffffffu, r.two_m, src);
-    const float theta_old = __shfl_sync(0xffffffffu, r.theta, src);
+    // band values are scores; the row's thresholds are in its visiting units
+    // (score / to_s): convert exactly (to_s is a power of two)
+    const float to_s = __shfl_sync(0xffffffffu, r.to_s, src);
+    const float two_m = __shfl_sync(0xffffffffu, r.two_m, src) * to_s;
+    const float theta_old = __shfl_sync(0xffffffffu, r.theta, src) * to_s;
     const bool exact = __shfl_sync(0xffffffffu, r.exact ? 1 : 0, src) != 0;
     float theta = theta_old;
     if (!exact) {
@@ -237,7 +243,7 @@ __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int
     }
     __syncwarp();
     if (lane == src) {
-      r.theta = theta;
+      r.theta = theta / to_s;
       r.cnt = w;
       r.last = w;
       if (w > limit) r.overflow = 1;  // the band near the k-th score is too dense

@@ -8,6 +8,9 @@
 // columns is exact for the products.  This is the analogue of the on-device
 // table -> matrix transformation of Sec. 4.2.2 ("data transformation" cost).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <type_traits>
 
 #include "sj_device.cuh"
 #include "sj_internal.h"
@@ -63,6 +66,66 @@ __device__ __forceinline__ int find_seg(const PackSeg *segs, int n_segs, int64_t
 
 constexpr int kPrepWarps = 8;
 
+// E4M3 scale exponent: the largest e with mx 2^e <= 448 (the largest finite
+// E4M3 value, 0.875 2^9), clamped to [-60, 60]; 0 for mx == 0.
+__device__ __forceinline__ int e4m3_exponent(float mx) {
+  if (!(mx > 0.f) || !isfinite(mx)) return 0;
+  int E;
+  const float f = frexpf(mx, &E);  // mx = f 2^E, f in [0.5, 1)
+  const int e = f <= 0.875f ? 9 - E : 8 - E;
+  return e < -60 ? -60 : (e > 60 ? 60 : e);
+}
+
+__device__ __forceinline__ float warp_absmax(const float *src, int64_t d) {
+  float m = 0.f;
+  for (int64_t k = threadIdx.x & 31; k < d; k += 32) {
+    const float x = fabsf(src[k]);
+    if (x > m) m = x;  // NaN never wins; non-finite rows are flagged by the packing pass
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  return m;
+}
+
+// E4M3 packing, first pass: max |x| over each job's B rows (jobs[q].bmax).
+__global__ void __launch_bounds__(kPrepWarps * 32)
+    bmax_kernel(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows, int64_t d) {
+  __shared__ int s_seg0;
+  __shared__ int s_seg[kPrepWarps];
+  __shared__ float s_m[kPrepWarps];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * kPrepWarps;
+  if (threadIdx.x == 0) s_seg0 = find_seg(segs, n_segs, row0);
+  __syncthreads();
+  const int64_t prow = row0 + wib;
+  int si = s_seg0;
+  while (si + 1 < n_segs && segs[si + 1].prow0 <= prow) ++si;
+  float mx = 0.f;
+  if (prow < prows) {
+    const PackSeg sg = segs[si];
+    const int64_t local = prow - sg.prow0;
+    if (sg.side != 0 && local < sg.n) mx = warp_absmax(sg.src + local * d, d);
+  }
+  if (lane == 0) {
+    s_seg[wib] = prow < prows ? si : -1;
+    s_m[wib] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int cur = -1;
+    float v = 0.f;
+    for (int w = 0; w <= kPrepWarps; ++w) {
+      const int sw = w < kPrepWarps ? s_seg[w] : -1;
+      if (sw != cur) {
+        if (cur >= 0 && segs[cur].side != 0 && v > 0.f) atomic_max_pos(&jobs[segs[cur].job].bmax, v);
+        cur = sw;
+        v = 0.f;
+      }
+      if (w < kPrepWarps) v = fmaxf(v, s_m[w]);
+    }
+  }
+}
+
 // One warp per packed row, kPrepWarps rows per block.  Segments hold at least
 // 128 rows, so a block's rows fall in at most two segments: one binary search
 // per block, and the B-side maxima are reduced per block before the atomics.
@@ -91,6 +154,17 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
       if (lane == 0) meta[prow] = RowMeta{0.f, 0.f, 0.f, 0};
     } else {
       const float *src = sg.src + local * d;
+      constexpr bool kE4M3 = std::is_same<OutT, __nv_fp8_e4m3>::value;
+      int e = 0;  // stored value = x 2^e (E4M3), dequantised = stored 2^-e
+      if constexpr (kE4M3) {
+        if (sg.side == 0) {
+          e = e4m3_exponent(warp_absmax(src, d));
+        } else {
+          e = e4m3_exponent(jobs[sg.job].bmax);
+          if (lane == 0) jobs[sg.job].eB = e;  // same value from every B row
+        }
+      }
+      const float up = __int_as_float((127 + e) << 23), down = __int_as_float((127 - e) << 23);
       float ns = 0.f, nc = 0.f;   // ||x||^2
       float qs = 0.f, qc = 0.f;   // ||x~||^2
       float es = 0.f, ec = 0.f;   // ||x~ - x||^2
@@ -108,8 +182,15 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
           if (k >= dp) break;
           float x = xv[u];
           if (!isfinite(x)) { bad = true; x = 0.f; }
-          OutT qv = OutT(x);
-          float qf = float(qv);
+          OutT qv;
+          float qf;
+          if constexpr (kE4M3) {
+            qv = OutT(x * up);  // round to nearest even, saturating
+            qf = float(qv) * down;
+          } else {
+            qv = OutT(x);
+            qf = float(qv);
+          }
           dst[k] = qv;
           acc_sq(x, ns, nc);
           acc_sq(qf, qs, qc);
@@ -129,7 +210,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
         m.nrm = sqrt_up(n2);
         m.qnrm = sqrt_up(q2);
         m.qerr = e2 > 0.f ? sqrt_up(e2) : 0.f;
-        m.sexp = 0;
+        m.sexp = e;
         meta[prow] = m;
         if (sg.side != 0) {
           mx[0] = m.nrm;
@@ -179,6 +260,11 @@ cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_
     case PackFormat::kBF16:
       prepare_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(
           segs, n_segs, jobs, prows, d, static_cast<__nv_bfloat16 *>(Xp), dp, meta, ctr);
+      break;
+    case PackFormat::kFP8:
+      bmax_kernel<<<grid, block, 0, st>>>(segs, n_segs, jobs, prows, d);
+      prepare_kernel<__nv_fp8_e4m3><<<grid, block, 0, st>>>(
+          segs, n_segs, jobs, prows, d, static_cast<__nv_fp8_e4m3 *>(Xp), dp, meta, ctr);
       break;
   }
   return cudaGetLastError();

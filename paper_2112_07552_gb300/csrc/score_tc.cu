@@ -38,7 +38,8 @@ using namespace tc;
 
 constexpr int BM = kTcBM;       // 128 rows of A per tile (TMEM lanes)
 constexpr int BN = kTcBN;       // 256 columns of B per tile (TMEM columns)
-constexpr int BK = 64;          // k-block: 64 bf16 = 128 bytes = one swizzle row
+constexpr int kRowBytes = 128;  // k-block: one 128-byte swizzle row per tile row
+constexpr int BK = 64;          // k-block elements, BF16 (E4M3: 128)
 constexpr int STAGES = 4;
 constexpr int kEpiChunks = 2;  // 32-column chunks per TMEM round trip
 constexpr int kRegsMaxK = 16;  // k kept in registers; 16 < k <= kTcHeapMaxK in the smem heap
@@ -50,6 +51,9 @@ constexpr uint32_t kTileBBytes = BN * BK * 2;
 constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators
 constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
 constexpr uint32_t kIdescNarrow = idesc_bf16(BM, kTcBNNarrow);
+constexpr uint32_t kIdesc8 = idesc_e4m3(BM, BN);
+constexpr uint32_t kIdesc8Narrow = idesc_e4m3(BM, kTcBNNarrow);
+constexpr int kMmaPerStage = 4;  // 32 bytes of K per instruction (16 BF16 or 32 E4M3)
 
 struct alignas(1024) TcSmem {
   unsigned char a[STAGES][kTileABytes];  // each 1024-byte aligned
@@ -127,7 +131,7 @@ __device__ __forceinline__ void flag_timeout(TcSmem &sm, Counters *ctr) {
 // registers (KM > 0 slots), in a shared-memory heap (KM < 0) or none (KM == 0:
 // lazy theta), every tile of the unit's column range from tensor memory
 // through the fused filter, then the row's band count and exact top-k values.
-template <int KM>
+template <int KM, bool FP8>
 __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, const UnitDev &un,
                                               const JobDev &jb, int64_t row, bool owner,
                                               int list, uint32_t tmem, int quarter, int half,
@@ -148,6 +152,19 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
   if constexpr (KM > 0) topk_regs_init<KM>(h, kj);
   if constexpr (KM < 0) heap_init(heap, kj);
   if (owner) row_begin(rc, a, jb, row, list);
+  if constexpr (FP8) {
+    // E4M3 scores come out of the tensor core as acc = s~ 2^(e_i + e_B): the
+    // filter works on acc (thresholds scaled exactly by the power of two)
+    // and stored values are scaled back
+    if (owner) {
+      const int e = a.metaA[jb.a_prow0 + row].sexp + jb.eB;
+      rc.to_s = __int_as_float((127 - e) << 23);
+      const float sc = __int_as_float((127 + e) << 23);
+      rc.theta *= sc;
+      rc.tau_lo *= sc;
+      rc.two_m *= sc;
+    }
+  }
   const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
   const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
   for (int64_t ct = ct0; ct < ct1; ++ct, ++tile) {
@@ -188,14 +205,15 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
       if constexpr (KM > 0) {
 #pragma unroll
         for (int t = 0; t < KM; ++t)
-          if (t >= KM - kj) tv[t - (KM - kj)] = h[t];
+          if (t >= KM - kj) tv[t - (KM - kj)] = h[t] * rc.to_s;
       } else if constexpr (KM < 0) {
-        for (int t = 0; t < kj; ++t) tv[t] = heap[t * kHeapStride];
+        for (int t = 0; t < kj; ++t) tv[t] = heap[t * kHeapStride] * rc.to_s;
       }
     }
   }
 }
 
+template <bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                     const __grid_constant__ CUtensorMap tmB,
@@ -235,7 +253,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   fence_after();
   const uint32_t tmem = sm.tmem_base;
 
-  const int64_t nkb = a.dp / BK;
+  constexpr int BKE = FP8 ? 2 * BK : BK;  // elements per 128-byte k-block
+  const int64_t nkb = a.dp / BKE;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -261,8 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             mbar_arrive_expect_tx(&sm.full[s],
                                   kTileABytes + (narrow ? kTileBBytes / 2 : kTileBBytes));
-            tma_load_2d(sm.a[s], &tmA, (int)(kb * BK), arow, &sm.full[s]);
-            tma_load_2d(sm.b[s], narrow ? &tmB128 : &tmB, (int)(kb * BK), brow, &sm.full[s]);
+            tma_load_2d(sm.a[s], &tmA, (int)(kb * BKE), arow, &sm.full[s]);
+            tma_load_2d(sm.b[s], narrow ? &tmB128 : &tmB, (int)(kb * BKE), brow, &sm.full[s]);
           }
         }
       }
@@ -286,7 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const JobDev &jb = a.jobs[un.job];
         const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
         const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
-        const uint32_t idesc = jb.bn == kTcBNNarrow ? kIdescNarrow : kIdesc;
+        const uint32_t idesc = FP8 ? (jb.bn == kTcBNNarrow ? kIdesc8Narrow : kIdesc8)
+                                   : (jb.bn == kTcBNNarrow ? kIdescNarrow : kIdesc);
         for (int64_t ct = ct0; ct < ct1 && ok; ++ct, ++tile) {
           const int acc = (int)(tile & 1);
           const uint32_t aph = (uint32_t)((tile >> 1) & 1);
@@ -308,9 +328,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_after();
             const uint32_t a0 = su32(sm.a[s]), b0 = su32(sm.b[s]);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              mma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
-                       (kb > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < kMmaPerStage; ++kk) {
+              if constexpr (FP8)
+                mma_e4m3(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
+                         (kb > 0 || kk > 0) ? 1u : 0u);
+              else
+                mma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
+                         (kb > 0 || kk > 0) ? 1u : 0u);
             }
             mma_commit(&sm.empty[s]);  // frees the smem stage once these MMAs finish
           }
@@ -347,13 +371,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int kj = jb.k;
       const int list = un.split * a.bands_per_split + half;
       if (kj > 0 && kj <= kRegsMaxK)
-        epilogue_unit<kRegsMaxK>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns,
+        epilogue_unit<kRegsMaxK, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns,
                                  tile, ok);
       else if (kj > 0 && kj <= kTcHeapMaxK)
-        epilogue_unit<-1>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile,
+        epilogue_unit<-1, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile,
                           ok);
       else
-        epilogue_unit<0>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
+        epilogue_unit<0, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
     }
   }
 
@@ -394,15 +418,17 @@ sj_status tc_create(TcContext **out) {
 void tc_destroy(TcContext *ctx) { delete ctx; }
 
 sj_status tc_encode_2d(TcContext *ctx, const void *base, int64_t inner, int64_t rows,
-                       int box_inner, int box_rows, unsigned char out[128]) {
+                       int box_inner, int box_rows, unsigned char out[128], int elem) {
   if (!ctx || !ctx->encode) return SJ_ERR_UNSUPPORTED;
   CUtensorMap m;
   std::memset(&m, 0, sizeof m);
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(inner * 2)};
+  cuuint64_t strides[1] = {(cuuint64_t)(inner * elem)};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = ctx->encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base),
+  CUresult r = ctx->encode(&m, elem == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, const_cast<void *>(base),
                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -413,29 +439,31 @@ sj_status tc_encode_2d(TcContext *ctx, const void *base, int64_t inner, int64_t 
 }
 
 sj_status tc_make_maps(TcContext *ctx, const void *Ap, int64_t nA_pad, const void *Bp,
-                       int64_t nB_pad, int64_t dp, TcMaps *out) {
+                       int64_t nB_pad, int64_t dp, TcMaps *out, int elem) {
   if (!ctx || !ctx->encode) return SJ_ERR_UNSUPPORTED;
   // B tiles never cross a segment end (segments are padded to BN rows)
-  if (dp % BK != 0 || nA_pad % BM != 0 || nB_pad < BN) return SJ_ERR_INTERNAL;
-  sj_status s = tc_encode_2d(ctx, Ap, dp, nA_pad, BK, BM, out->a);
-  if (s == SJ_OK) s = tc_encode_2d(ctx, Bp, dp, nB_pad, BK, BN, out->b);
-  if (s == SJ_OK) s = tc_encode_2d(ctx, Bp, dp, nB_pad, BK, kTcBNNarrow, out->b128);
+  const int box = kRowBytes / elem;  // elements per 128-byte swizzle row
+  if (dp % box != 0 || nA_pad % BM != 0 || nB_pad < BN) return SJ_ERR_INTERNAL;
+  sj_status s = tc_encode_2d(ctx, Ap, dp, nA_pad, box, BM, out->a, elem);
+  if (s == SJ_OK) s = tc_encode_2d(ctx, Bp, dp, nB_pad, box, BN, out->b, elem);
+  if (s == SJ_OK) s = tc_encode_2d(ctx, Bp, dp, nB_pad, box, kTcBNNarrow, out->b128, elem);
   return s;
 }
 
 cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, uint32_t flags,
-                            cudaStream_t st) {
+                            bool fp8, cudaStream_t st) {
   if (a.n_units == 0) return cudaSuccess;
   if (a.bands_per_split != 2) return cudaErrorInvalidValue;  // one list per column half
   const size_t smem = sizeof(TcSmem) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(score_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = fp8 ? score_tc_kernel<true> : score_tc_kernel<false>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CUtensorMap ma, mb, mb128;
   std::memcpy(&ma, maps->a, sizeof ma);
   std::memcpy(&mb, maps->b, sizeof mb);
   std::memcpy(&mb128, maps->b128, sizeof mb128);
-  score_tc_kernel<<<grid, kThreads, smem, st>>>(ma, mb, mb128, a, flags);
+  kern<<<grid, kThreads, smem, st>>>(ma, mb, mb128, a, flags);
   return cudaGetLastError();
 }
 

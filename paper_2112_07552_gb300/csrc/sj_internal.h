@@ -16,7 +16,7 @@
 
 namespace sj {
 
-enum class PackFormat { kF32, kBF16 };
+enum class PackFormat { kF32, kBF16, kFP8 };
 
 struct PairOut {  // layout of sj_pair
   int64_t i, j;
@@ -40,7 +40,9 @@ struct JobDev {
   int32_t tiles_per_split;   // column tiles per split
   int32_t n_col_tiles;       // column tiles of the job
   int32_t bn;                // column tile width of the job (tensor-core pass: 128 or 256)
-  int32_t pad_bn;
+  int32_t eB;                // E4M3 packing: the job's B rows are stored as x 2^eB
+  float bmax;                // E4M3 packing: max |x| over the job's B rows (device-written)
+  int32_t pad_e;
   float tau_f;               // tau rounded down to float (+inf: no threshold part)
   float gmaxB[3];            // max over the job's B rows of {nrm, qnrm, qerr} (device-written)
   long long tau_key;         // ceil(tau 2^60)
@@ -95,6 +97,10 @@ __device__ __forceinline__ int find_job_row0_hint(const JobDev *jobs, int n_jobs
   return find_job_row0(jobs, n_jobs, x);
 }
 
+// For E4M3 (kFP8) two launches: the B-side maxima, then the packing; an A
+// row is stored as q = RNE_sat(x 2^e) with its own e (largest with max|x| 2^e
+// <= 448), a B row with its job's common eB (from the maxima), a self-join
+// segment with eB in both roles.  meta.sexp holds the row's exponent.
 cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows,
                            int64_t d, PackFormat fmt, void *Xp, int64_t dp, RowMeta *meta,
                            Counters *ctr, cudaStream_t st);

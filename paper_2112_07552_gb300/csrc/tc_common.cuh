@@ -95,6 +95,22 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t 
       "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
 }
 
+// Instruction descriptor, kind::f8f6f4: FP32 accumulator, E4M3 A and B
+// (format code 0), both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (+)= A B^T for E4M3 operands: K = 32 elements (32 bytes) per instruction.
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

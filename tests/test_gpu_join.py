@@ -13,7 +13,7 @@ from paper_2112_07552_gb300 import datagen
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECS = ("bf16", "fp32")
+PRECS = ("bf16", "fp32", "fp8")
 
 
 @pytest.fixture(scope="module")
@@ -312,7 +312,7 @@ def test_batch_fallback_rows_in_several_jobs(sjmod, prec):
     assert st["n_overflow_rows"] > 0
 
 
-@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("prec", ("bf16", "fp32"))
 def test_batch_split_into_groups_under_workspace_limit(sjmod, prec):
     """A batch whose workspace exceeds the handle's limit runs as several
     groups (halved by rows until each fits); results are unchanged."""
@@ -416,3 +416,31 @@ def test_autotune_table_round_trip(sjmod, tmp_path):
         idx, sc = J.topk(dev(A), dev(B), k)
         assert_topk(idx, sc, A, B, k)
     J.close()
+
+
+def _e4m3_exponent(mx):
+    """Largest e with mx 2^e <= 448 (as the packing does)."""
+    f, E = np.frexp(mx)
+    return np.where(f <= 0.875, 9 - E, 8 - E)
+
+
+def test_fp8_scores_within_their_bound(sjmod):
+    """E4M3 scoring: the largest |s~ - s| over the rescored candidates stays
+    within the quantisation error (recomputed here from E4M3 rounding of the
+    scaled rows) plus the accumulation allowance (d + 32) 2^-13."""
+    nA, nB, d, k = 600, 2500, 256, 20
+    A = datagen.clustered(nA, d, 50, 0.1, seed=71, stream=0)
+    B = datagen.clustered(nB, d, 50, 0.1, seed=71, stream=1)
+    J = sjmod.SimilarityJoin(d, prec="fp8", device=0)
+    idx, sc, st = J.topk(dev(A), dev(B), k, with_stats=True)
+    J.close()
+    assert_topk(idx, sc, A, B, k)
+    eA = _e4m3_exponent(np.abs(A).max(axis=1))[:, None].astype(np.float64)
+    eB = float(_e4m3_exponent(np.abs(B).max()))
+    qa = (torch.from_numpy(A.astype(np.float64) * 2.0 ** eA).float()
+          .to(torch.float8_e4m3fn).double().numpy()) * 2.0 ** -eA
+    qb = (torch.from_numpy(B.astype(np.float64) * 2.0 ** eB).float()
+          .to(torch.float8_e4m3fn).double().numpy()) * 2.0 ** -eB
+    quant = np.abs(qa @ qb.T - A.astype(np.float64) @ B.astype(np.float64).T).max()
+    acc = (d + 32) * 2.0 ** -13 * np.linalg.norm(qa, axis=1).max() * np.linalg.norm(qb, axis=1).max()
+    assert 0 < st["max_abs_err_lowprec"] <= quant + acc
