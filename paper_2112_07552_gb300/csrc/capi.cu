@@ -613,98 +613,142 @@ bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long lo
   return ok;
 }
 
-// Rows whose candidates did not fit (one job): rescan all of B with Dot2
-// against the row's key bound, then rank the lists (shared memory, or global
-// memory for very long ones).  Lists cut off at their capacity are rescanned
-// once more with the capacity they need.  `rows` are local rows.
-sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const JobDev &jd,
-                        int64_t d, const int *rows, const long long *keys, int n_rows,
-                        Arena &ar, int64_t &launches) {
+// One rescan pass over rows[0 .. n) (local rows of one job; device arrays,
+// with host copies hrows/hkeys) with lists of `cap` entries: rescan all of B
+// with Dot2 against each row's key bound, then rank the lists (shared memory,
+// or global memory for very long ones).  Rows whose list was cut off at `cap`
+// are appended to redo_rows/redo_keys with the capacity they need.
+sj_status topk_rescan_pass(sj_handle *h, Counters *ctr, const RowMeta *meta, const JobDev &jd,
+                           int64_t d, const int *rows, const long long *keys, const int *hrows,
+                           const long long *hkeys, int n, int cap, Arena &ar, int64_t &launches,
+                           std::vector<int> &redo_rows, std::vector<long long> &redo_keys,
+                           int64_t &redo_cap) {
   cudaStream_t stm = h->stream;
-  const int64_t nB = jd.nB;
-  int cap = (int)std::min<int64_t>(nB, 4096);
-  Scratch count_s, redo_s, big_s, rows2_s, keys2_s;
-  SJ_CUDA(count_s.get(ar, (size_t)n_rows * 4 + 256));
-  SJ_CUDA(redo_s.get(ar, (size_t)n_rows * 4 + 256));
-  SJ_CUDA(big_s.get(ar, (size_t)n_rows * 4 + 256));
-  SJ_CUDA(rows2_s.get(ar, (size_t)n_rows * 4 + 256));
-  SJ_CUDA(keys2_s.get(ar, (size_t)n_rows * 8 + 256));
-  const int *cur_rows = rows;
-  const long long *cur_keys = keys;
-  int n_cur = n_rows;
-  for (int pass = 0; pass < 2 && n_cur > 0; ++pass) {
-    Scratch lists;
-    SJ_CUDA(lists.get(ar, (size_t)n_cur * cap * sizeof(KeyCand)));
-    int *count = static_cast<int *>(count_s.p);
-    SJ_CUDA(cudaMemsetAsync(count, 0, (size_t)n_cur * 4, stm));
-    SJ_CUDA(cudaMemsetAsync(&ctr->redo_rows, 0, 4 * sizeof(unsigned), stm));
-    RescanArgs ra{};
-    ra.A = jd.A;
-    ra.B = jd.B;
-    ra.nB = nB;
-    ra.d = d;
-    ra.metaA = meta + jd.a_prow0;
-    ra.metaB = meta + jd.b_prow0;
-    ra.dot2_coef_key = dot2_coef_key(d);
-    ra.rows = cur_rows;
-    ra.keys = cur_keys;
-    ra.n_rows = n_cur;
-    ra.lists = static_cast<KeyCand *>(lists.p);
-    ra.count = count;
-    ra.cap = cap;
-    ra.ctr = ctr;
-    SJ_CUDA(launch_topk_rescan(ra, stm));
-    RankListArgs la{};
-    la.A = jd.A;
-    la.B = jd.B;
-    la.d = d;
-    la.k = jd.k;
-    la.rows = cur_rows;
-    la.n_rows = n_cur;
-    la.lists = ra.lists;
-    la.count = count;
-    la.cap = cap;
-    la.redo = static_cast<int *>(redo_s.p);
-    la.big = static_cast<int *>(big_s.p);
-    la.out_idx = jd.out_idx;
-    la.out_score = jd.out_score;
-    la.ctr = ctr;
-    SJ_CUDA(launch_topk_rank_lists(la, stm));
-    launches += 2;
-    sj_status s = read_counters(h, ctr);
-    if (s != SJ_OK) return s;
-    const unsigned n_big = h->h_ctr->big_rows;
-    if (n_big > 0) {
-      const size_t per_row = topk_rank_global_row_bytes(cap);
-      Scratch g;
-      SJ_CUDA(g.get(ar, (size_t)n_big * per_row));
-      SJ_CUDA(launch_topk_rank_global(la, la.big, (int)n_big, g.p, per_row, stm));
-      launches += 1;
-      SJ_CUDA(cudaStreamSynchronize(stm));
-    }
-    const unsigned n_redo = h->h_ctr->redo_rows;
-    if (n_redo == 0) break;
-    if (pass == 1) return SJ_ERR_INTERNAL;  // a full-capacity rescan cannot be cut off
-    // gather the rows (and keys) to redo, with the capacity they need
-    std::vector<int> slots(n_redo), hrows(n_redo), all_rows(n_cur);
-    std::vector<long long> hkeys(n_redo), all_keys(n_cur);
+  Scratch lists, count_s, redo_s, big_s, redo_k;
+  SJ_CUDA(lists.get(ar, (size_t)n * cap * sizeof(KeyCand)));
+  SJ_CUDA(count_s.get(ar, (size_t)n * 4 + 256));
+  SJ_CUDA(redo_s.get(ar, (size_t)n * 4 + 256));
+  SJ_CUDA(redo_k.get(ar, (size_t)n * 8 + 256));
+  SJ_CUDA(big_s.get(ar, (size_t)n * 4 + 256));
+  int *count = static_cast<int *>(count_s.p);
+  SJ_CUDA(cudaMemsetAsync(count, 0, (size_t)n * 4, stm));
+  SJ_CUDA(cudaMemsetAsync(&ctr->redo_rows, 0, 4 * sizeof(unsigned), stm));
+  RescanArgs ra{};
+  ra.A = jd.A;
+  ra.B = jd.B;
+  ra.nB = jd.nB;
+  ra.d = d;
+  ra.metaA = meta + jd.a_prow0;
+  ra.metaB = meta + jd.b_prow0;
+  ra.dot2_coef_key = dot2_coef_key(d);
+  ra.rows = rows;
+  ra.keys = keys;
+  ra.n_rows = n;
+  ra.lists = static_cast<KeyCand *>(lists.p);
+  ra.count = count;
+  ra.cap = cap;
+  ra.ctr = ctr;
+  SJ_CUDA(launch_topk_rescan(ra, stm));
+  RankListArgs la{};
+  la.A = jd.A;
+  la.B = jd.B;
+  la.d = d;
+  la.k = jd.k;
+  la.rows = rows;
+  la.keys = keys;
+  la.n_rows = n;
+  la.lists = ra.lists;
+  la.count = count;
+  la.cap = cap;
+  la.redo = static_cast<int *>(redo_s.p);
+  la.redo_key = static_cast<long long *>(redo_k.p);
+  la.big = static_cast<int *>(big_s.p);
+  la.out_idx = jd.out_idx;
+  la.out_score = jd.out_score;
+  la.ctr = ctr;
+  SJ_CUDA(launch_topk_rank_lists(la, stm));
+  launches += 2;
+  sj_status s = read_counters(h, ctr);
+  if (s != SJ_OK) return s;
+  const unsigned n_big = h->h_ctr->big_rows;
+  if (n_big > 0) {
+    const size_t per_row = topk_rank_global_row_bytes(cap);
+    Scratch g;
+    SJ_CUDA(g.get(ar, (size_t)n_big * per_row));
+    SJ_CUDA(launch_topk_rank_global(la, la.big, (int)n_big, g.p, per_row, stm));
+    launches += 1;
+    SJ_CUDA(cudaStreamSynchronize(stm));
+  }
+  const unsigned n_redo = h->h_ctr->redo_rows;
+  if (n_redo > 0) {
+    redo_cap = std::max<int64_t>(redo_cap, (int64_t)h->h_ctr->redo_cap);
+    std::vector<int> slots(n_redo);
+    std::vector<long long> tight(n_redo);
     SJ_CUDA(cudaMemcpyAsync(slots.data(), la.redo, n_redo * 4, cudaMemcpyDeviceToHost, stm));
-    SJ_CUDA(cudaMemcpyAsync(all_rows.data(), cur_rows, (size_t)n_cur * 4, cudaMemcpyDeviceToHost, stm));
-    SJ_CUDA(cudaMemcpyAsync(all_keys.data(), cur_keys, (size_t)n_cur * 8, cudaMemcpyDeviceToHost, stm));
+    SJ_CUDA(cudaMemcpyAsync(tight.data(), la.redo_key, n_redo * 8, cudaMemcpyDeviceToHost, stm));
     SJ_CUDA(cudaStreamSynchronize(stm));
+    (void)hkeys;
     for (unsigned q = 0; q < n_redo; ++q) {
-      hrows[q] = all_rows[slots[q]];
-      hkeys[q] = all_keys[slots[q]];
+      redo_rows.push_back(hrows[slots[q]]);
+      redo_keys.push_back(tight[q]);
     }
-    SJ_CUDA(cudaMemcpyAsync(rows2_s.p, hrows.data(), n_redo * 4, cudaMemcpyHostToDevice, stm));
-    SJ_CUDA(cudaMemcpyAsync(keys2_s.p, hkeys.data(), n_redo * 8, cudaMemcpyHostToDevice, stm));
-    SJ_CUDA(cudaStreamSynchronize(stm));
-    cur_rows = static_cast<int *>(rows2_s.p);
-    cur_keys = static_cast<long long *>(keys2_s.p);
-    n_cur = (int)n_redo;
-    cap = (int)std::min<int64_t>(nB, (int64_t)h->h_ctr->redo_cap);
   }
   return SJ_OK;
+}
+
+// Rows whose candidates did not fit (one job): rescan passes in chunks of
+// rows whose lists fit in a bounded scratch (a list can hold all of B), first
+// with 4,096-entry lists, then the cut-off rows once more with the capacity
+// they need.  `rows`/`keys` are device arrays, hrows/hkeys their host copies.
+sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const JobDev &jd,
+                        int64_t d, const int *rows, const long long *keys, const int *hrows,
+                        const long long *hkeys, int n_rows, Arena &ar, int64_t &launches) {
+  cudaStream_t stm = h->stream;
+  const size_t kScratch = (size_t)2 << 30;  // lists + global ranking per chunk
+  const int64_t nB = jd.nB;
+  std::vector<int> redo_rows;
+  std::vector<long long> redo_keys;
+  int64_t redo_cap = 0;
+  auto run = [&](const int *dr, const long long *dk, const int *hr, const long long *hk, int n,
+                 int cap, std::vector<int> &rr, std::vector<long long> &rk, int64_t &rc) {
+    const size_t per_row = (size_t)cap * sizeof(KeyCand) + topk_rank_global_row_bytes(cap);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n, kScratch / per_row));
+    for (int c0 = 0; c0 < n; c0 += chunk) {
+      const int nc = std::min(chunk, n - c0);
+      sj_status s = topk_rescan_pass(h, ctr, meta, jd, d, dr + c0, dk + c0, hr + c0, hk + c0, nc,
+                                     cap, ar, launches, rr, rk, rc);
+      if (s != SJ_OK) return s;
+    }
+    return SJ_OK;
+  };
+  // pass 1: lists of 4,096 entries; pass 2: the cut-off rows with their key
+  // bounds tightened to the k-th best lower bound seen; pass 3: rows still cut
+  // off (massive exact ties) with the capacity they need
+  const int cap0 = (int)std::min<int64_t>(nB, 4096);
+  sj_status s = run(rows, keys, hrows, hkeys, n_rows, cap0, redo_rows, redo_keys, redo_cap);
+  std::vector<int> again;
+  std::vector<long long> again_k;
+  int64_t again_cap = 0;
+  for (int pass = 2; pass <= 3 && s == SJ_OK && !redo_rows.empty(); ++pass) {
+    const int n_redo = (int)redo_rows.size();
+    Scratch rows2, keys2;
+    SJ_CUDA(rows2.get(ar, (size_t)n_redo * 4 + 256));
+    SJ_CUDA(keys2.get(ar, (size_t)n_redo * 8 + 256));
+    SJ_CUDA(cudaMemcpyAsync(rows2.p, redo_rows.data(), (size_t)n_redo * 4, cudaMemcpyHostToDevice, stm));
+    SJ_CUDA(cudaMemcpyAsync(keys2.p, redo_keys.data(), (size_t)n_redo * 8, cudaMemcpyHostToDevice, stm));
+    SJ_CUDA(cudaStreamSynchronize(stm));
+    again.clear();
+    again_k.clear();
+    again_cap = 0;
+    const int cap = pass == 2 ? cap0 : (int)std::min<int64_t>(nB, redo_cap);
+    s = run(static_cast<int *>(rows2.p), static_cast<long long *>(keys2.p), redo_rows.data(),
+            redo_keys.data(), n_redo, cap, again, again_k, again_cap);
+    redo_rows.swap(again);
+    redo_keys.swap(again_k);
+    redo_cap = again_cap;
+  }
+  if (s != SJ_OK) return s;
+  return redo_rows.empty() ? SJ_OK : SJ_ERR_INTERNAL;  // a list of all of B cannot be cut off
 }
 
 // Fallback rows of the whole batch, grouped by job.
@@ -741,8 +785,8 @@ sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, uns
     while (t1 < n_ovf && by_job[t1].first == by_job[t0].first) ++t1;
     const JobDev &jd = P.jobs[by_job[t0].first];
     sj_status s = topk_fallback(h, B.ctr, B.meta, jd, P.d, static_cast<int *>(rows_s.p) + t0,
-                                static_cast<long long *>(keys_s.p) + t0, (int)(t1 - t0), ar,
-                                launches);
+                                static_cast<long long *>(keys_s.p) + t0, lrow.data() + t0,
+                                lkey.data() + t0, (int)(t1 - t0), ar, launches);
     if (s != SJ_OK) return s;
     t0 = t1;
   }

@@ -507,21 +507,44 @@ __global__ void __launch_bounds__(kFinThreads) topk_rank_lists_kernel(RankListAr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FinSmemLayout<kCMax> &sm = *reinterpret_cast<FinSmemLayout<kCMax> *>(smem_raw);
   float *a_row = reinterpret_cast<float *>(smem_raw + sizeof(FinSmemLayout<kCMax>));
+  __shared__ unsigned s_cnt[kFinThreads / 32];
   const int r = blockIdx.x;
   if (r >= a.n_rows) return;
   const int64_t i = a.rows[r];
   const int n = a.count[r];
-  if (n > a.cap || n > kCMax) {
-    if (threadIdx.x == 0) {
-      if (n > a.cap) {
-        unsigned q = atomicAdd(&a.ctr->redo_rows, 1u);
-        a.redo[q] = r;
-        atomicMax(&a.ctr->redo_cap, (unsigned)n);
-      } else {
-        unsigned q = atomicAdd(&a.ctr->big_rows, 1u);
-        a.big[q] = r;
+  if (n > a.cap) {
+    // Cut off: the k-th largest lower bound L among the stored entries bounds
+    // the row's k-th exact score from below (k real scores are at least it),
+    // so the redo only needs the columns whose upper bound reaches it.
+    const KeyCand *lst = a.lists + (int64_t)r * a.cap;
+    long long Lk = LLONG_MIN;
+    if (a.cap >= a.k) {
+      unsigned long long T = 0;  // order-preserving image of L: L ^ sign bit
+      for (int b = 63; b >= 0; --b) {
+        const unsigned long long t = T | (1ull << b);
+        unsigned c = 0;
+        for (int q = threadIdx.x; q < a.cap; q += blockDim.x)
+          c += ((unsigned long long)lst[q].L ^ 0x8000000000000000ull) >= t;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = c;
+        __syncthreads();
+        unsigned tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_cnt[w];
+        __syncthreads();
+        if (tot >= (unsigned)a.k) T = t;
       }
+      Lk = (long long)(T ^ 0x8000000000000000ull);
     }
+    if (threadIdx.x == 0) {
+      unsigned q = atomicAdd(&a.ctr->redo_rows, 1u);
+      a.redo[q] = r;
+      a.redo_key[q] = Lk > a.keys[r] ? Lk : a.keys[r];
+      atomicMax(&a.ctr->redo_cap, (unsigned)n);
+    }
+    return;
+  }
+  if (n > kCMax) {
+    if (threadIdx.x == 0) a.big[atomicAdd(&a.ctr->big_rows, 1u)] = r;
     return;
   }
   const KeyCand *lst = a.lists + (int64_t)r * a.cap;

@@ -179,11 +179,13 @@ struct RankListArgs {
   int64_t d;
   int k;
   const int *rows;         // local left rows
+  const long long *keys;   // their rescan key bounds
   int n_rows;
   const KeyCand *lists;
   const int *count;
   int cap;
   int *redo;               // list slots cut off at cap
+  long long *redo_key;     // their tightened key bounds
   int *big;                // list slots longer than the shared-memory ranker takes
   int64_t *out_idx;        // the job's outputs
   float *out_score;
