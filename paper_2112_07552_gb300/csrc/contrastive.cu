@@ -43,7 +43,9 @@ using namespace tc;
 constexpr int TM = 128;             // rows per tile (TMEM lanes)
 constexpr int TN = 128;             // columns per tile
 constexpr int BK = 64;              // k-block (128 bytes of BF16)
-constexpr int kSStages = 2;         // S operand ring
+// S operand ring: TMA latency bounds a shallow ring (one 64-wide k-block of a
+// 128 x 128 tile is ~270 tensor-core cycles).  The forward has 6 stages; the
+// backward's Z^T and G' buffers leave room for 2.
 constexpr int kMaxChunk = 384;      // output dimensions per backward unit
 constexpr int kPiece = 192;         // N of one backward MMA
 constexpr int kZBox = 64;           // rows of one Z^T TMA box
@@ -53,11 +55,13 @@ constexpr uint32_t kZBytes = kMaxChunk * BK * 2;  // one Z^T k-block (48 KB)
 constexpr uint32_t kGBytes = TM * TN * 2;         // one G tile (32 KB)
 constexpr float kLog2e = 1.4426950408889634f;
 
+template <bool BWD>
 struct alignas(1024) CSmem {
+  static constexpr int kSStages = BWD ? 2 : 6;
   unsigned char x[kSStages][kOpBytes];
   unsigned char y[kSStages][kOpBytes];
-  unsigned char z[2][kZBytes];      // the two 64-wide k-blocks of a column tile
-  unsigned char g[2][kGBytes];      // double-buffered G' tiles
+  unsigned char z[2][BWD ? kZBytes : 1024];  // the two 64-wide k-blocks of a column tile
+  unsigned char g[2][BWD ? kGBytes : 1024];  // double-buffered G' tiles
   uint64_t full[kSStages], empty[kSStages];
   uint64_t zfull[2], zempty[2];
   uint64_t s_full[2], s_empty[2];
@@ -74,7 +78,8 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
-__device__ __forceinline__ void flag_timeout(CSmem &sm, unsigned *err) {
+template <typename SM>
+__device__ __forceinline__ void flag_timeout(SM &sm, unsigned *err) {
   *(volatile int *)&sm.abort = 1;
   atomicOr(err, 4u);  // kErrTimeout
 }
@@ -90,8 +95,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                        const __grid_constant__ CUtensorMap tmY,
                        const __grid_constant__ CUtensorMap tmZ, ContrastiveArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  CSmem &sm = *reinterpret_cast<CSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                         ~(uintptr_t)1023);
+  using Smem = CSmem<BWD>;
+  constexpr int kSStages = Smem::kSStages;
+  Smem &sm = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                       ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t limit_ns = 4000000000ull;
   volatile int *abort = &sm.abort;
@@ -307,13 +314,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_arrive(&sm.s_empty[buf]);  // S buffer free for the next tile
         const int64_t col0 = (int64_t)t * TN;
         if (!BWD) {
+          const bool cols_full = col0 + TN <= a.n;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             float x[32];
             float cm = -INFINITY;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-              x[q] = (col0 + c * 32 + q < a.n) ? v[c][q] * c1 : -INFINITY;
+              x[q] = v[c][q] * c1;
+              if (!cols_full && col0 + c * 32 + q >= a.n) x[q] = -INFINITY;
               cm = fmaxf(cm, x[q]);
             }
             if (cm > m) {
@@ -344,7 +353,38 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          // G'_t, BF16, into the 128B-swizzled K-major layout the MMA reads
+          // G'_t = w_r (P - I) + w_c (Q - I), computed in place: one ex2 per
+          // term and element; the column log-sum-exp (log2 domain) comes one
+          // value per lane and is broadcast by shuffles; the diagonal and the
+          // ragged last tile are fixed up apart from the element loop
+          const float wr = a.wr, wc = a.wc;
+          const bool cols_full = col0 + TN <= a.n;
+          const int64_t dr = row - col0;  // position of the diagonal in the tile
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float lcq = INFINITY;
+            if (wc != 0.f) {
+              const int64_t jj = col0 + c * 32 + lane;
+              if (jj < a.n) lcq = __ldg(a.lse_c + jj) * kLog2e;
+            }
+            const int dq = (int)(dr - c * 32);  // 0..31 when the diagonal is in this chunk
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const float x = v[c][q] * c1;
+              float gv = 0.f;
+              if (wr != 0.f) gv = wr * ex2(x - lr2);
+              if (wc != 0.f) gv = fmaf(wc, ex2(x - __shfl_sync(0xffffffffu, lcq, q)), gv);
+              if (q == dq) gv -= wr + wc;
+              v[c][q] = gv;
+            }
+          }
+          if (!valid || !cols_full) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int q = 0; q < 32; ++q)
+                if (!valid || col0 + c * 32 + q >= a.n) v[c][q] = 0.f;
+          }
           const int gb = (int)(tile & 1);
           const uint32_t gph = (uint32_t)((tile >> 1) & 1);
           const bool we = mbar_wait(&sm.g_empty[gb], gph ^ 1, limit_ns, abort);
@@ -356,19 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char *gt = sm.g[gb];
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            float gq[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              const int64_t j = col0 + c * 32 + q;
-              const float x = v[c][q] * c1;
-              float gv = 0.f;
-              if (j < a.n && valid) {
-                const float dlt = (j == row) ? 1.f : 0.f;
-                if (a.wr != 0.f) gv += a.wr * (ex2(x - lr2) - dlt);
-                if (a.wc != 0.f) gv += a.wc * (ex2(x - __ldg(a.lse_c + j) * kLog2e) - dlt);
-              }
-              gq[q] = gv;
-            }
+            const float *gq = v[c];
             // 32 columns = 4 chunks of 16 bytes in k-block (c >> 1)
             unsigned char *kbase = gt + (c >> 1) * (TM * BK * 2) + r * 128;
 #pragma unroll
@@ -490,7 +518,9 @@ __global__ void contrastive_loss_kernel(const float *t1, const float *t2, int64_
 // ---------------------------------------------------------------------------
 // Host side
 
-size_t contrastive_smem_bytes() { return sizeof(CSmem) + 1024; }
+size_t contrastive_smem_bytes(bool bwd) {
+  return (bwd ? sizeof(CSmem<true>) : sizeof(CSmem<false>)) + 1024;
+}
 
 cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *Xp, void *XT,
                                     int64_t np, int64_t dp, unsigned *err, cudaStream_t st) {
@@ -508,7 +538,7 @@ cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n,
 
 cudaError_t launch_contrastive(bool bwd, const void *tmX, const void *tmY, const void *tmZ,
                                const ContrastiveArgs &a, int grid, cudaStream_t st) {
-  const size_t smem = contrastive_smem_bytes();
+  const size_t smem = contrastive_smem_bytes(bwd);
   CUtensorMap mx, my, mz;
   std::memcpy(&mx, tmX, sizeof mx);
   std::memcpy(&my, tmY, sizeof my);

@@ -27,7 +27,7 @@ struct ContrastiveArgs {
   int debug_timeout;
 };
 
-size_t contrastive_smem_bytes();
+size_t contrastive_smem_bytes(bool bwd);
 cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *Xp, void *XT,
                                     int64_t np, int64_t dp, unsigned *err, cudaStream_t st);
 cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n, float w1,
