@@ -43,13 +43,18 @@ using namespace tc;
 constexpr int TM = 128;             // rows per tile (TMEM lanes)
 constexpr int TN = 128;             // columns per tile
 constexpr int BK = 64;              // k-block (128 bytes of BF16)
-// S operand ring: TMA latency bounds a shallow ring (one 64-wide k-block of a
-// 128 x 128 tile is ~270 tensor-core cycles).  The forward has 6 stages; the
-// backward's Z^T and G' buffers leave room for 2.
+// S operand ring: the bytes in flight bound the S stream (one 64-wide k-block
+// of a 128 x 128 tile is ~270 tensor-core cycles, one L2 round trip several
+// times that).  The forward has 6 stages; the backward's Z^T buffers and its
+// single G' buffer leave room for 3.
 constexpr int kMaxChunk = 384;      // output dimensions per backward unit
 constexpr int kPiece = 192;         // N of one backward MMA
 constexpr int kZBox = 64;           // rows of one Z^T TMA box
-constexpr int kThreads = 192;       // producer, MMA, 4 epilogue warps
+// Producer and MMA warps, then the epilogue: 4 warps (one TMEM lane quarter
+// each, all 128 columns of a tile) in the forward, 8 in the backward (two per
+// lane quarter, one 64-column half each: one k-block of the G' tile).
+__host__ __device__ constexpr int epi_warps(bool bwd) { return bwd ? 8 : 4; }
+__host__ __device__ constexpr int cthreads(bool bwd) { return 64 + 32 * epi_warps(bwd); }
 constexpr uint32_t kOpBytes = TM * BK * 2;  // one operand k-block (16 KB)
 constexpr uint32_t kZBytes = kMaxChunk * BK * 2;  // one Z^T k-block (48 KB)
 constexpr uint32_t kGBytes = TM * TN * 2;         // one G tile (32 KB)
@@ -57,11 +62,11 @@ constexpr float kLog2e = 1.4426950408889634f;
 
 template <bool BWD>
 struct alignas(1024) CSmem {
-  static constexpr int kSStages = BWD ? 2 : 6;
+  static constexpr int kSStages = BWD ? 3 : 6;
   unsigned char x[kSStages][kOpBytes];
   unsigned char y[kSStages][kOpBytes];
   unsigned char z[2][BWD ? kZBytes : 1024];  // the two 64-wide k-blocks of a column tile
-  unsigned char g[2][BWD ? kGBytes : 1024];  // double-buffered G' tiles
+  unsigned char g[1][BWD ? kGBytes : 1024];  // the G' tile (one buffer)
   uint64_t full[kSStages], empty[kSStages];
   uint64_t zfull[2], zempty[2];
   uint64_t s_full[2], s_empty[2];
@@ -90,7 +95,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 template <bool BWD>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(cthreads(BWD), 1)
     contrastive_kernel(const __grid_constant__ CUtensorMap tmX,
                        const __grid_constant__ CUtensorMap tmY,
                        const __grid_constant__ CUtensorMap tmZ, ContrastiveArgs a) {
@@ -111,12 +116,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&sm.zfull[q], 1);
       mbar_init(&sm.zempty[q], 1);
       mbar_init(&sm.s_full[q], 1);
-      mbar_init(&sm.s_empty[q], 4 * 32);
-      mbar_init(&sm.g_full[q], 4 * 32);
+      mbar_init(&sm.s_empty[q], epi_warps(BWD) * 32);
+      mbar_init(&sm.g_full[q], epi_warps(BWD) * 32);
       mbar_init(&sm.g_empty[q], 1);
     }
     mbar_init(&sm.acc_full, 1);
-    mbar_init(&sm.acc_empty, 4 * 32);
+    mbar_init(&sm.acc_empty, epi_warps(BWD) * 32);
     mbar_init(&sm.drain, 1);
     mbar_init(&sm.never, 1);
     sm.abort = 0;
@@ -223,8 +228,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         // backward product of tile tl: acc += G'_tl Z_tl^T
         auto issue_g = [&](uint64_t tl, bool first) -> bool {
-          const int gb = (int)(tl & 1);
-          const uint32_t gph = (uint32_t)((tl >> 1) & 1);
+          const int gb = 0;
+          const uint32_t gph = (uint32_t)(tl & 1);
           if (!mbar_wait(&sm.g_full[gb], gph, limit_ns, abort)) return false;
           if (first && unit_n > 0) {
             if (!mbar_wait(&sm.acc_empty, (uint32_t)((unit_n - 1) & 1), limit_ns, abort))
@@ -276,6 +281,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue (warps 2..5) ----------------
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;  // row within the tile
+    constexpr int NC = BWD ? 2 : 4;     // 32-column chunks of a tile per warp
+    const int cb = BWD ? ((warp - 2) >> 2) * 2 : 0;  // first chunk of this warp
     uint64_t tile = 0, unit_n = 0;
     bool ok = true;
     if (a.debug_timeout) {
@@ -306,10 +313,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         fence_after();
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * TN);
-        float v[4][32];
+        float v[NC][32];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tmem_ld32_nowait(taddr + c * 32, v[c]);
-        tmem_wait_ld4(v);
+        for (int c = 0; c < NC; ++c) tmem_ld32_nowait(taddr + (cb + c) * 32, v[c]);
+        if constexpr (BWD) tmem_wait_ld(v[0], v[1]);
+        else tmem_wait_ld4(v);
         fence_before();
         mbar_arrive(&sm.s_empty[buf]);  // S buffer free for the next tile
         const int64_t col0 = (int64_t)t * TN;
@@ -361,13 +369,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool cols_full = col0 + TN <= a.n;
           const int64_t dr = row - col0;  // position of the diagonal in the tile
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int c = 0; c < NC; ++c) {
             float lcq = INFINITY;
             if (wc != 0.f) {
-              const int64_t jj = col0 + c * 32 + lane;
+              const int64_t jj = col0 + (cb + c) * 32 + lane;
               if (jj < a.n) lcq = __ldg(a.lse_c + jj) * kLog2e;
             }
-            const int dq = (int)(dr - c * 32);  // 0..31 when the diagonal is in this chunk
+            const int dq = (int)(dr - (cb + c) * 32);  // 0..31 when the diagonal is in this chunk
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
               const float x = v[c][q] * c1;
@@ -380,13 +388,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (!valid || !cols_full) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
+            for (int c = 0; c < NC; ++c)
 #pragma unroll
               for (int q = 0; q < 32; ++q)
-                if (!valid || col0 + c * 32 + q >= a.n) v[c][q] = 0.f;
+                if (!valid || col0 + (cb + c) * 32 + q >= a.n) v[c][q] = 0.f;
           }
-          const int gb = (int)(tile & 1);
-          const uint32_t gph = (uint32_t)((tile >> 1) & 1);
+          const int gb = 0;
+          const uint32_t gph = (uint32_t)(tile & 1);
           const bool we = mbar_wait(&sm.g_empty[gb], gph ^ 1, limit_ns, abort);
           if (!__all_sync(0xffffffffu, we)) {
             flag_timeout(sm, &a.ctr->err_flags);
@@ -395,13 +403,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           unsigned char *gt = sm.g[gb];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int c = 0; c < NC; ++c) {
             const float *gq = v[c];
-            // 32 columns = 4 chunks of 16 bytes in k-block (c >> 1)
-            unsigned char *kbase = gt + (c >> 1) * (TM * BK * 2) + r * 128;
+            const int cc = cb + c;  // chunk of the tile
+            // 32 columns = 4 chunks of 16 bytes in k-block (cc >> 1)
+            unsigned char *kbase = gt + (cc >> 1) * (TM * BK * 2) + r * 128;
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-              const int lc = (c & 1) * 4 + h;  // logical 16-byte chunk in the 128-byte row
+              const int lc = (cc & 1) * 4 + h;  // logical 16-byte chunk in the 128-byte row
               __nv_bfloat162 p0 = __floats2bfloat162_rn(gq[h * 8 + 0], gq[h * 8 + 1]);
               __nv_bfloat162 p1 = __floats2bfloat162_rn(gq[h * 8 + 2], gq[h * 8 + 3]);
               __nv_bfloat162 p2 = __floats2bfloat162_rn(gq[h * 8 + 4], gq[h * 8 + 5]);
@@ -437,7 +446,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float scale = __ldg(a.grad_loss) / ((float)a.n * a.T);
         const int c0 = ch * kMaxChunk;
         const int cw = (int)min64(kMaxChunk, a.dp - c0);
-        for (int c = 0; c < cw; c += 32) {
+        // each epilogue warp of a lane quarter stores its half of the chunk
+        const int hw = BWD ? cw / 2 : cw;
+        for (int c = (cb / 2) * hw; c < (cb / 2 + 1) * hw; c += 32) {
           float o[32];
           tmem_ld32_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(TN + c), o);
           tmem_wait_ld1(o);
@@ -548,12 +559,12 @@ cudaError_t launch_contrastive(bool bwd, const void *tmX, const void *tmY, const
     e = cudaFuncSetAttribute(contrastive_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    contrastive_kernel<true><<<grid, kThreads, smem, st>>>(mx, my, mz, a);
+    contrastive_kernel<true><<<grid, cthreads(true), smem, st>>>(mx, my, mz, a);
   } else {
     e = cudaFuncSetAttribute(contrastive_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    contrastive_kernel<false><<<grid, kThreads, smem, st>>>(mx, my, mz, a);
+    contrastive_kernel<false><<<grid, cthreads(false), smem, st>>>(mx, my, mz, a);
   }
   return cudaGetLastError();
 }
