@@ -80,7 +80,6 @@ struct sj_handle {
   void *ws = nullptr;
   size_t ws_size = 0;
   Counters *h_ctr = nullptr;   // pinned
-  int64_t *h_i64 = nullptr;    // pinned scratch for small readbacks
   void *h_tab = nullptr;       // pinned: job/segment/unit tables, then per-job pair counts
   size_t h_tab_size = 0;
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
@@ -614,13 +613,13 @@ bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long lo
 }
 
 // One rescan pass over rows[0 .. n) (local rows of one job; device arrays,
-// with host copies hrows/hkeys) with lists of `cap` entries: rescan all of B
+// with host copies of the rows in hrows) with lists of `cap` entries: rescan all of B
 // with Dot2 against each row's key bound, then rank the lists (shared memory,
 // or global memory for very long ones).  Rows whose list was cut off at `cap`
 // are appended to redo_rows/redo_keys with the capacity they need.
 sj_status topk_rescan_pass(sj_handle *h, Counters *ctr, const RowMeta *meta, const JobDev &jd,
                            int64_t d, const int *rows, const long long *keys, const int *hrows,
-                           const long long *hkeys, int n, int cap, Arena &ar, int64_t &launches,
+                           int n, int cap, Arena &ar, int64_t &launches,
                            std::vector<int> &redo_rows, std::vector<long long> &redo_keys,
                            int64_t &redo_cap) {
   cudaStream_t stm = h->stream;
@@ -687,7 +686,6 @@ sj_status topk_rescan_pass(sj_handle *h, Counters *ctr, const RowMeta *meta, con
     SJ_CUDA(cudaMemcpyAsync(slots.data(), la.redo, n_redo * 4, cudaMemcpyDeviceToHost, stm));
     SJ_CUDA(cudaMemcpyAsync(tight.data(), la.redo_key, n_redo * 8, cudaMemcpyDeviceToHost, stm));
     SJ_CUDA(cudaStreamSynchronize(stm));
-    (void)hkeys;
     for (unsigned q = 0; q < n_redo; ++q) {
       redo_rows.push_back(hrows[slots[q]]);
       redo_keys.push_back(tight[q]);
@@ -715,8 +713,8 @@ sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const 
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n, kScratch / per_row));
     for (int c0 = 0; c0 < n; c0 += chunk) {
       const int nc = std::min(chunk, n - c0);
-      sj_status s = topk_rescan_pass(h, ctr, meta, jd, d, dr + c0, dk + c0, hr + c0, hk + c0, nc,
-                                     cap, ar, launches, rr, rk, rc);
+      sj_status s = topk_rescan_pass(h, ctr, meta, jd, d, dr + c0, dk + c0, hr + c0, nc, cap, ar,
+                                     launches, rr, rk, rc);
       if (s != SJ_OK) return s;
     }
     return SJ_OK;
@@ -1386,7 +1384,6 @@ sj_status sj_create(sj_handle **out, const sj_config *cfg) {
   h->sm_count = prop.multiProcessorCount;
   h->cc = cc;
   cudaError_t e = cudaMallocHost(&h->h_ctr, sizeof(Counters));
-  if (e == cudaSuccess) e = cudaMallocHost(&h->h_i64, 64);
   for (int t = 0; t < 6 && e == cudaSuccess; ++t) e = cudaEventCreate(&h->ev[t]);
   for (int t = 0; t < 4 && e == cudaSuccess; ++t) e = cudaEventCreate(&h->gev[t]);
   if (e == cudaSuccess && cfg->prec != SJ_FP32) {
@@ -1413,7 +1410,6 @@ sj_status sj_destroy(sj_handle *h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ws) cudaFree(h->ws);
   if (h->h_ctr) cudaFreeHost(h->h_ctr);
-  if (h->h_i64) cudaFreeHost(h->h_i64);
   if (h->h_tab) cudaFreeHost(h->h_tab);
   for (int t = 0; t < 6; ++t)
     if (h->ev[t]) cudaEventDestroy(h->ev[t]);

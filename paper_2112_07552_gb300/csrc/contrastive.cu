@@ -503,8 +503,8 @@ __global__ void contrastive_pack_kernel(const float *__restrict__ X, int64_t n, 
 // loss = (w1 sum term1 + w2 sum term2) / N, compensated summation, one block.
 __global__ void contrastive_loss_kernel(const float *t1, const float *t2, int64_t n, float w1,
                                         float w2, float *loss) {
-  __shared__ float sh_s[32], sh_c[32];
-  float s = 0.f, c = 0.f;
+  __shared__ float sh_s[32];
+  float s = 0.f, c = 0.f;  // Kahan-compensated per-thread partial sum
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     float v = w1 * t1[i] + (t2 ? w2 * t2[i] : 0.f);
     float y = v - c;
@@ -521,7 +521,6 @@ __global__ void contrastive_loss_kernel(const float *t1, const float *t2, int64_
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh_s[w];
     *loss = tot / (float)n;
   }
-  (void)sh_c;
 }
 
 }  // namespace
