@@ -43,10 +43,12 @@ using namespace tc;
 constexpr int TM = 128;             // rows per tile (TMEM lanes)
 constexpr int TN = 128;             // columns per tile
 constexpr int BK = 64;              // k-block (128 bytes of BF16)
-// S operand ring: the bytes in flight bound the S stream (one 64-wide k-block
-// of a 128 x 128 tile is ~270 tensor-core cycles, one L2 round trip several
-// times that).  The forward has 6 stages; the backward's Z^T buffers and its
-// single G' buffer leave room for 3.
+// Operand ring of 32 KB slots: the bytes in flight bound the operand stream
+// (one 64-wide k-block of a 128 x 128 tile is ~270 tensor-core cycles, one L2
+// round trip several times that).  A slot holds an S k-block (X and Y, 16 KB
+// each) or, in the backward, a Z^T slice (up to 192 rows of a 64-wide
+// k-block, 24 KB), in the order the MMA warp consumes them: S(0), then for
+// t >= 1 S(t) and Z^T(t-1), then Z^T(last).  Six slots and one G' tile.
 constexpr int kMaxChunk = 384;      // output dimensions per backward unit
 constexpr int kPiece = 192;         // N of one backward MMA
 constexpr int kZBox = 64;           // rows of one Z^T TMA box
@@ -56,19 +58,15 @@ constexpr int kZBox = 64;           // rows of one Z^T TMA box
 __host__ __device__ constexpr int epi_warps(bool bwd) { return bwd ? 8 : 4; }
 __host__ __device__ constexpr int cthreads(bool bwd) { return 64 + 32 * epi_warps(bwd); }
 constexpr uint32_t kOpBytes = TM * BK * 2;  // one operand k-block (16 KB)
-constexpr uint32_t kZBytes = kMaxChunk * BK * 2;  // one Z^T k-block (48 KB)
 constexpr uint32_t kGBytes = TM * TN * 2;         // one G tile (32 KB)
 constexpr float kLog2e = 1.4426950408889634f;
 
 template <bool BWD>
 struct alignas(1024) CSmem {
-  static constexpr int kSStages = BWD ? 3 : 6;
-  unsigned char x[kSStages][kOpBytes];
-  unsigned char y[kSStages][kOpBytes];
-  unsigned char z[2][BWD ? kZBytes : 1024];  // the two 64-wide k-blocks of a column tile
+  static constexpr int kSStages = 6;
+  unsigned char slot[kSStages][2 * kOpBytes];
   unsigned char g[1][BWD ? kGBytes : 1024];  // the G' tile (one buffer)
   uint64_t full[kSStages], empty[kSStages];
-  uint64_t zfull[2], zempty[2];
   uint64_t s_full[2], s_empty[2];
   uint64_t g_full[2], g_empty[2];
   uint64_t acc_full, acc_empty;
@@ -113,8 +111,6 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
       mbar_init(&sm.empty[s], 1);
     }
     for (int q = 0; q < 2; ++q) {
-      mbar_init(&sm.zfull[q], 1);
-      mbar_init(&sm.zempty[q], 1);
       mbar_init(&sm.s_full[q], 1);
       mbar_init(&sm.s_empty[q], epi_warps(BWD) * 32);
       mbar_init(&sm.g_full[q], epi_warps(BWD) * 32);
@@ -147,59 +143,63 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      uint64_t it = 0, zt = 0;
+      uint64_t it = 0;
       bool ok = true;
+      auto take = [&](uint32_t bytes) -> int {  // next slot, armed for `bytes`
+        const int s = (int)(it % kSStages);
+        const uint32_t ph = (uint32_t)((it / kSStages) & 1);
+        if (!mbar_wait(&sm.empty[s], ph ^ 1, limit_ns, abort)) {
+          flag_timeout(sm, &a.ctr->err_flags);
+          ok = false;
+          return -1;
+        }
+        ++it;
+        mbar_arrive_expect_tx(&sm.full[s], bytes);
+        return s;
+      };
       for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
         const int rb = (int)(u / n_chunks), ch = (int)(u % n_chunks);
         const int c0 = ch * kMaxChunk;
         const int cw = (int)min64(kMaxChunk, a.dp - c0);
+        auto push_s = [&](int t) {
+          for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = take(2 * kOpBytes);
+            if (s < 0) break;
+            tma_load_2d(sm.slot[s], &tmX, kb * BK, rb * TM, &sm.full[s]);
+            tma_load_2d(sm.slot[s] + kOpBytes, &tmY, kb * BK, t * TN, &sm.full[s]);
+          }
+        };
+        // Z^T(t): per 64-wide k-block kz of the tile's columns, slices of up
+        // to kPiece output dimensions (rows of Z^T), kZBox rows per TMA box
+        auto push_z = [&](int t) {
+          for (int kz = 0; kz < 2 && ok; ++kz)
+            for (int p = 0; p < cw && ok; p += kPiece) {
+              const int pw = min(kPiece, cw - p);
+              const int s = take((uint32_t)pw * BK * 2);
+              if (s < 0) break;
+              for (int b = 0; b < pw; b += kZBox)
+                tma_load_2d(sm.slot[s] + b * BK * 2, &tmZ, t * TN + kz * BK, c0 + p + b,
+                            &sm.full[s]);
+            }
+        };
         for (int t = 0; t < n_tiles && ok; ++t) {
-          for (int kb = 0; kb < nkb; ++kb, ++it) {
-            const int s = (int)(it % kSStages);
-            const uint32_t ph = (uint32_t)((it / kSStages) & 1);
-            if (!mbar_wait(&sm.empty[s], ph ^ 1, limit_ns, abort)) {
-              flag_timeout(sm, &a.ctr->err_flags);
-              ok = false;
-              break;
-            }
-            mbar_arrive_expect_tx(&sm.full[s], 2 * kOpBytes);
-            tma_load_2d(sm.x[s], &tmX, kb * BK, rb * TM, &sm.full[s]);
-            tma_load_2d(sm.y[s], &tmY, kb * BK, t * TN, &sm.full[s]);
-          }
-          if (BWD && ok) {
-            for (int kz = 0; kz < 2; ++kz) {
-              const uint32_t ph = (uint32_t)(zt & 1);
-              if (!mbar_wait(&sm.zempty[kz], ph ^ 1, limit_ns, abort)) {
-                flag_timeout(sm, &a.ctr->err_flags);
-                ok = false;
-                break;
-              }
-              mbar_arrive_expect_tx(&sm.zfull[kz], (uint32_t)cw * BK * 2);
-              for (int p = 0; p < cw; p += kZBox)
-                tma_load_2d(sm.z[kz] + p * BK * 2, &tmZ, t * TN + kz * BK, c0 + p, &sm.zfull[kz]);
-            }
-            ++zt;
-          }
+          push_s(t);
+          if (BWD && t > 0) push_z(t - 1);
         }
+        if (BWD && ok) push_z(n_tiles - 1);
       }
-      // drain: the last copy into each buffer must have landed
+      // drain: the last copy into each slot must have landed
       for (uint64_t q = (it > kSStages ? it - kSStages : 0); q < it; ++q) {
         const uint64_t t0 = now_ns();
         while (!mbar_try(&sm.full[q % kSStages], (uint32_t)((q / kSStages) & 1)) &&
                now_ns() - t0 < limit_ns) {
         }
       }
-      if (BWD && zt > 0)
-        for (int kz = 0; kz < 2; ++kz) {
-          const uint64_t t0 = now_ns();
-          while (!mbar_try(&sm.zfull[kz], (uint32_t)((zt - 1) & 1)) && now_ns() - t0 < limit_ns) {
-          }
-        }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      uint64_t it = 0, tile = 0, zt = 0, unit_n = 0;
+      uint64_t it = 0, tile = 0, unit_n = 0;
       bool ok = true;
       for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++unit_n) {
         const int ch = (int)(u % n_chunks);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
             const uint32_t sp = (uint32_t)((it / kSStages) & 1);
             if (!mbar_wait(&sm.full[s], sp, limit_ns, abort)) return false;
             fence_after();
-            const uint32_t x0 = su32(sm.x[s]), y0 = su32(sm.y[s]);
+            const uint32_t x0 = su32(sm.slot[s]), y0 = x0 + kOpBytes;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
               mma_bf16(d, sdesc(x0 + kk * 32), sdesc(y0 + kk * 32), idesc_s,
@@ -237,22 +237,21 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
           }
           fence_after();
           for (int kz = 0; kz < 2; ++kz) {
-            if (!mbar_wait(&sm.zfull[kz], (uint32_t)(zt & 1), limit_ns, abort)) return false;
-            fence_after();
             const uint32_t g0 = su32(sm.g[gb]) + kz * (TM * BK * 2);
-            const uint32_t z0 = su32(sm.z[kz]);
+            for (int p = 0; p < cw; p += kPiece, ++it) {
+              const int pw = min(kPiece, cw - p);
+              const int s = (int)(it % kSStages);
+              const uint32_t sp = (uint32_t)((it / kSStages) & 1);
+              if (!mbar_wait(&sm.full[s], sp, limit_ns, abort)) return false;
+              fence_after();
+              const uint32_t z0 = su32(sm.slot[s]);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              for (int p = 0; p < cw; p += kPiece) {
-                const int pw = min(kPiece, cw - p);
-                mma_bf16(tmem + TN + (uint32_t)p, sdesc(g0 + kk * 32),
-                         sdesc(z0 + (uint32_t)p * BK * 2 + kk * 32), idesc_bf16(TM, pw),
-                         (first && kz == 0 && kk == 0) ? 0u : 1u);
-              }
+              for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem + TN + (uint32_t)p, sdesc(g0 + kk * 32), sdesc(z0 + kk * 32),
+                         idesc_bf16(TM, pw), (first && kz == 0 && kk == 0) ? 0u : 1u);
+              mma_commit(&sm.empty[s]);
             }
-            mma_commit(&sm.zempty[kz]);
           }
-          ++zt;
           mma_commit(&sm.g_empty[gb]);
           return true;
         };
