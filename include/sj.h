@@ -73,6 +73,7 @@ typedef enum {
                                       parallelism when nA is small) */
 #define SJ_FLAG_NO_GRAPH 0x4u      /* never replay joins from a captured CUDA graph */
 #define SJ_FLAG_NARROW_TILES 0x8u  /* test hook: 128-column score tiles for every job */
+#define SJ_FLAG_FUSED_BACKWARD 0x10u /* sj_backward: never materialise dL/dS (see there) */
 #define SJ_FLAG_DEBUG_TIMEOUT 0x100u /* test hook: device waits give up at once */
 
 typedef struct {
@@ -191,15 +192,24 @@ sj_status sj_autotune_load(sj_handle *h, const char *path);
 /* Contrastive (InfoNCE) join over N paired rows, positives on the diagonal:
  * S = A B^T / T, l_i = logsumexp_j S_ij, loss = (1/N) sum_i (l_i - S_ii)
  * (with SJ_FLAG_SYM_INFONCE also the column term, averaged).  A, B: N x d
- * bfloat16 (raw 16-bit patterns), DEVICE memory.  Writes loss[0] (device
- * float) and lse[N] (2N with the symmetric flag: rows then columns).
+ * float32 rows in DEVICE memory, rounded to bfloat16 (nearest even) inside;
+ * FP32 accumulation.  Writes loss[0] (device float) and lse[N] (2N with the
+ * symmetric flag: rows then columns).
  * Errors: SJ_ERR_INVALID_ARG, SJ_ERR_UNSUPPORTED, SJ_ERR_CUDA, SJ_ERR_OOM. */
 sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t N,
                              float T, float *loss, float *lse);
 
 /* Backward of sj_contrastive_fwd: given lse from the forward and the upstream
- * gradient grad_loss[0] (device float), writes dA, dB (N x d float32, device)
- * by recomputing the score tiles (no N x N matrix is stored). */
+ * gradient grad_loss[0] (device float), writes dA, dB (N x d float32, device).
+ * With G = dloss/dS rounded to bfloat16 (N x N, padded to multiples of 128):
+ * dA = G B / T and dB = G^T A / T.  When the workspace can hold G and G^T
+ * (2 x 2 Np^2 bytes, Np = N rounded up to 128) one pass over the score tiles
+ * writes both and two GEMMs read them (three products of 2 N^2 d flops);
+ * otherwise, or with SJ_FLAG_FUSED_BACKWARD, G is recomputed per output chunk
+ * of 384 dimensions and direction and never stored.  Both give the same G and
+ * differ only in FP32 summation order.
+ * Errors: SJ_ERR_INVALID_ARG, SJ_ERR_UNSUPPORTED, SJ_ERR_CUDA, SJ_ERR_OOM,
+ * SJ_ERR_NONFINITE, SJ_ERR_TIMEOUT. */
 sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, float T,
                       const float *lse, const float *grad_loss, float *dA, float *dB);
 

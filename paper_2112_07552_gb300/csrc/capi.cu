@@ -1457,13 +1457,16 @@ namespace {
 struct ContrastivePlan {
   int64_t n, d, np, dp;
   void *Ap, *Bp, *AT, *BT;
+  void *G, *GT;  // materialised backward: dL/dS and its transpose (np x np BF16)
   Counters *ctr;
   float *scratch;  // 2n floats (per-row loss terms)
-  unsigned char mA[128], mB[128], mAT[128], mBT[128];
+  unsigned char mA[128], mB[128], mAT[128], mBT[128], mG[128], mGT[128];
 };
 
+// `gmat`: also reserve and map G and G^T (fails with SJ_ERR_OOM before any
+// launch when the workspace cannot hold them).
 sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t N, bool bwd,
-                            ContrastivePlan &cp) {
+                            ContrastivePlan &cp, bool gmat = false) {
   if (!h || !A || !B || N < 1) return SJ_ERR_INVALID_ARG;
   if (N >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
   if (!is_device_ptr(A) || !is_device_ptr(B)) return SJ_ERR_INVALID_ARG;
@@ -1478,7 +1481,9 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
   cp.np = round_up(N, 128);
   cp.dp = round_up(cp.d, 64);
   const size_t op = (size_t)cp.np * cp.dp * 2;
-  size_t bytes = 2 * op + (bwd ? 2 * op : 0) + sizeof(Counters) + (size_t)2 * N * 4 + 8 * 256;
+  const size_t gsz = (size_t)cp.np * cp.np * 2;
+  size_t bytes = 2 * op + (bwd ? 2 * op : 0) + sizeof(Counters) + (size_t)2 * N * 4 + 8 * 256 +
+                 (gmat ? 2 * gsz + 2 * 256 : 0);
   sj_status s = ensure_ws(h, bytes);
   if (s != SJ_OK) return s;
   Arena ar{static_cast<unsigned char *>(h->ws), h->ws_size, 0};
@@ -1488,7 +1493,11 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
   cp.Bp = ar.take(op);
   cp.AT = bwd ? ar.take(op) : nullptr;
   cp.BT = bwd ? ar.take(op) : nullptr;
-  if (!cp.ctr || !cp.scratch || !cp.Ap || !cp.Bp || (bwd && (!cp.AT || !cp.BT))) return SJ_ERR_INTERNAL;
+  cp.G = gmat ? ar.take(gsz) : nullptr;
+  cp.GT = gmat ? ar.take(gsz) : nullptr;
+  if (!cp.ctr || !cp.scratch || !cp.Ap || !cp.Bp || (bwd && (!cp.AT || !cp.BT)) ||
+      (gmat && (!cp.G || !cp.GT)))
+    return SJ_ERR_INTERNAL;
   cudaStream_t st = h->stream;
   SJ_CUDA(cudaMemsetAsync(cp.ctr, 0, sizeof(Counters), st));
   SJ_CUDA(launch_contrastive_pack(static_cast<const float *>(A), N, cp.d, cp.Ap, cp.AT, cp.np, cp.dp,
@@ -1499,6 +1508,8 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
   if (s == SJ_OK) s = tc_encode_2d(h->tc, cp.Bp, cp.dp, cp.np, 64, 128, cp.mB);
   if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.AT, cp.np, cp.dp, 64, 64, cp.mAT);
   if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.BT, cp.np, cp.dp, 64, 64, cp.mBT);
+  if (s == SJ_OK && gmat) s = tc_encode_2d(h->tc, cp.G, cp.np, cp.np, 64, 128, cp.mG);
+  if (s == SJ_OK && gmat) s = tc_encode_2d(h->tc, cp.GT, cp.np, cp.np, 64, 128, cp.mGT);
   return s;
 }
 
@@ -1535,11 +1546,11 @@ sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t
   const int grid = (int)std::min<int64_t>(cp.np / 128, h->sm_count);
   a.lse_out = lse;
   a.term_out = cp.scratch;
-  SJ_CUDA(launch_contrastive(false, cp.mA, cp.mB, nullptr, a, grid, h->stream));
+  SJ_CUDA(launch_contrastive(kContrastiveFwd, cp.mA, cp.mB, nullptr, nullptr, a, grid, h->stream));
   if (sym) {
     a.lse_out = lse + N;
     a.term_out = cp.scratch + N;
-    SJ_CUDA(launch_contrastive(false, cp.mB, cp.mA, nullptr, a, grid, h->stream));
+    SJ_CUDA(launch_contrastive(kContrastiveFwd, cp.mB, cp.mA, nullptr, nullptr, a, grid, h->stream));
   }
   SJ_CUDA(launch_contrastive_loss(cp.scratch, sym ? cp.scratch + N : nullptr, N, sym ? 0.5f : 1.f,
                                   0.5f, loss, h->stream));
@@ -1553,7 +1564,13 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   if (!is_device_ptr(lse) || !is_device_ptr(grad_loss) || !is_device_ptr(dA) || !is_device_ptr(dB))
     return SJ_ERR_INVALID_ARG;
   ContrastivePlan cp;
-  sj_status s = contrastive_setup(h, A, B, N, true, cp);
+  // materialise G and G^T when the workspace allows, else the fused path
+  bool gmat = (h->cfg.flags & SJ_FLAG_FUSED_BACKWARD) == 0;
+  sj_status s = gmat ? contrastive_setup(h, A, B, N, true, cp, true) : SJ_ERR_OOM;
+  if (s == SJ_ERR_OOM) {
+    gmat = false;
+    s = contrastive_setup(h, A, B, N, true, cp, false);
+  }
   if (s != SJ_OK) return s;
   const bool sym = (h->cfg.flags & SJ_FLAG_SYM_INFONCE) != 0;
   ContrastiveArgs a{};
@@ -1563,17 +1580,48 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   a.dp = cp.dp;
   a.T = T;
   a.n_chunks = (int)((cp.dp + 383) / 384);
+  a.n_splits = 1;
+  a.tiles_per_split = (int)(cp.np / 128);
   a.grad_loss = grad_loss;
   a.ctr = cp.ctr;
   a.debug_timeout = (h->cfg.flags & SJ_FLAG_DEBUG_TIMEOUT) ? 1 : 0;
-  const int grid = (int)std::min<int64_t>((cp.np / 128) * a.n_chunks, h->sm_count);
-  // dA: rows of A against columns (rows of B); row term = softmax over j
+  // G = w_r (P - I) + w_c (Q - I): the row softmax P of A's rows, the column
+  // softmax Q (symmetric loss only)
   a.lse_r = lse;
   a.wr = sym ? 0.5f : 1.f;
   a.lse_c = sym ? lse + N : lse;
   a.wc = sym ? 0.5f : 0.f;
+  const int64_t n_rb = cp.np / 128;
+  if (gmat) {
+    // G pass: units = (row block, column split of ~64 tiles) for balance
+    const int64_t n_tiles = n_rb;
+    const int64_t want = std::max<int64_t>(1, (n_tiles + 63) / 64);
+    a.tiles_per_split = (int)((n_tiles + want - 1) / want);
+    a.n_splits = (int)((n_tiles + a.tiles_per_split - 1) / a.tiles_per_split);
+    const int grid = (int)std::min<int64_t>(n_rb * a.n_splits, h->sm_count);
+    SJ_CUDA(launch_contrastive(kContrastiveGprime, cp.mA, cp.mB, cp.mG, cp.mGT, a, grid,
+                               h->stream));
+    ContrastiveGemmArgs g{};
+    g.n = N;
+    g.d = cp.d;
+    g.np = cp.np;
+    g.dp = cp.dp;
+    g.T = T;
+    g.n_chunks = a.n_chunks;
+    g.grad_loss = grad_loss;
+    g.ctr = cp.ctr;
+    const int ggrid = (int)std::min<int64_t>(n_rb * g.n_chunks, h->sm_count);
+    g.dX = dA;  // dA = G B / T
+    SJ_CUDA(launch_contrastive_gemm(cp.mG, cp.mBT, g, ggrid, h->stream));
+    g.dX = dB;  // dB = G^T A / T
+    SJ_CUDA(launch_contrastive_gemm(cp.mGT, cp.mAT, g, ggrid, h->stream));
+    return contrastive_finish(h, cp);
+  }
+  const int grid = (int)std::min<int64_t>(n_rb * a.n_chunks, h->sm_count);
+  // dA: rows of A against columns (rows of B); row term = softmax over j
   a.dX = dA;
-  SJ_CUDA(launch_contrastive(true, cp.mA, cp.mB, cp.mBT, a, grid, h->stream));
+  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mA, cp.mB, cp.mBT, nullptr, a, grid,
+                             h->stream));
   // dB: rows of B against columns (rows of A); the row softmax term is indexed
   // by the kernel's columns, the column softmax term by its rows
   a.lse_r = sym ? lse + N : lse;
@@ -1581,7 +1629,8 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   a.lse_c = lse;
   a.wc = sym ? 0.5f : 1.f;
   a.dX = dB;
-  SJ_CUDA(launch_contrastive(true, cp.mB, cp.mA, cp.mAT, a, grid, h->stream));
+  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mB, cp.mA, cp.mAT, nullptr, a, grid,
+                             h->stream));
   return contrastive_finish(h, cp);
 }
 

@@ -48,25 +48,33 @@ constexpr int BK = 64;              // k-block (128 bytes of BF16)
 // round trip several times that).  A slot holds an S k-block (X and Y, 16 KB
 // each) or, in the backward, a Z^T slice (up to 192 rows of a 64-wide
 // k-block, 24 KB), in the order the MMA warp consumes them: S(0), then for
-// t >= 1 S(t) and Z^T(t-1), then Z^T(last).  Six slots and one G' tile.
+// t >= 1 S(t) and Z^T(t-1), then Z^T(last).  Six slots and one G' tile; the
+// G' pass has five slots and two staging tiles (G' and its transpose).
 constexpr int kMaxChunk = 384;      // output dimensions per backward unit
 constexpr int kPiece = 192;         // N of one backward MMA
 constexpr int kZBox = 64;           // rows of one Z^T TMA box
+// Kernel modes: the forward; the fused backward (G' recomputed per output
+// chunk and consumed in shared memory); the G' pass of the materialised
+// backward (G' and its transpose written to global memory).
+constexpr int kModeFwd = kContrastiveFwd, kModeBwd = kContrastiveBwdFused,
+              kModeGp = kContrastiveGprime;
 // Producer and MMA warps, then the epilogue: 4 warps (one TMEM lane quarter
-// each, all 128 columns of a tile) in the forward, 8 in the backward (two per
-// lane quarter, one 64-column half each: one k-block of the G' tile).
-__host__ __device__ constexpr int epi_warps(bool bwd) { return bwd ? 8 : 4; }
-__host__ __device__ constexpr int cthreads(bool bwd) { return 64 + 32 * epi_warps(bwd); }
+// each, all 128 columns of a tile) in the forward, 8 in the other modes (two
+// per lane quarter, one 64-column half each: one k-block of the G' tile).
+__host__ __device__ constexpr int epi_warps(int mode) { return mode == kModeFwd ? 4 : 8; }
+__host__ __device__ constexpr int cthreads(int mode) { return 64 + 32 * epi_warps(mode); }
 constexpr uint32_t kOpBytes = TM * BK * 2;  // one operand k-block (16 KB)
 constexpr uint32_t kGBytes = TM * TN * 2;         // one G tile (32 KB)
 constexpr float kLog2e = 1.4426950408889634f;
 
-template <bool BWD>
+template <int MODE>
 struct alignas(1024) CSmem {
-  static constexpr int kSStages = 6;
+  static constexpr int kSStages = MODE == kModeGp ? 5 : 6;
+  static constexpr int kGTiles = MODE == kModeGp ? 2 : 1;
   unsigned char slot[kSStages][2 * kOpBytes];
-  unsigned char g[1][BWD ? kGBytes : 1024];  // the G' tile (one buffer)
+  unsigned char g[kGTiles][MODE == kModeFwd ? 1024 : kGBytes];  // G' tile(s)
   uint64_t full[kSStages], empty[kSStages];
+  uint64_t st_full, st_free;  // G' pass: staging tiles written / read by the stores
   uint64_t s_full[2], s_empty[2];
   uint64_t g_full[2], g_empty[2];
   uint64_t acc_full, acc_empty;
@@ -92,13 +100,17 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <bool BWD>
-__global__ void __launch_bounds__(cthreads(BWD), 1)
+template <int MODE>
+__global__ void __launch_bounds__(cthreads(MODE), 1)
     contrastive_kernel(const __grid_constant__ CUtensorMap tmX,
                        const __grid_constant__ CUtensorMap tmY,
-                       const __grid_constant__ CUtensorMap tmZ, ContrastiveArgs a) {
+                       const __grid_constant__ CUtensorMap tmZ,
+                       const __grid_constant__ CUtensorMap tmW, ContrastiveArgs a) {
+  constexpr bool BWD = MODE == kModeBwd;
+  constexpr bool GP = MODE == kModeGp;
+  constexpr int kEpi = epi_warps(MODE) * 32;
   extern __shared__ unsigned char smem_raw[];
-  using Smem = CSmem<BWD>;
+  using Smem = CSmem<MODE>;
   constexpr int kSStages = Smem::kSStages;
   Smem &sm = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                        ~(uintptr_t)1023);
@@ -112,12 +124,14 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(&sm.s_full[q], 1);
-      mbar_init(&sm.s_empty[q], epi_warps(BWD) * 32);
-      mbar_init(&sm.g_full[q], epi_warps(BWD) * 32);
+      mbar_init(&sm.s_empty[q], kEpi);
+      mbar_init(&sm.g_full[q], kEpi);
       mbar_init(&sm.g_empty[q], 1);
     }
     mbar_init(&sm.acc_full, 1);
-    mbar_init(&sm.acc_empty, epi_warps(BWD) * 32);
+    mbar_init(&sm.acc_empty, kEpi);
+    mbar_init(&sm.st_full, kEpi);
+    mbar_init(&sm.st_free, 1);
     mbar_init(&sm.drain, 1);
     mbar_init(&sm.never, 1);
     sm.abort = 0;
@@ -137,7 +151,19 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
   const int n_tiles = (int)(a.np / TN);
   const int n_rb = (int)(a.np / TM);
   const int n_chunks = BWD ? a.n_chunks : 1;
-  const int64_t n_units = (int64_t)n_rb * n_chunks;
+  // G' pass: units also split the column tiles (no state crosses tiles there)
+  const int n_splits = GP ? a.n_splits : 1;
+  const int tps = GP ? a.tiles_per_split : n_tiles;
+  const int64_t n_units = (int64_t)n_rb * n_chunks * n_splits;
+  // unit u: row block, output chunk, column tiles [t0, t1)
+  auto unit_of = [&](int64_t u, int &rb, int &ch, int &t0, int &t1) {
+    const int64_t per_rb = (int64_t)n_chunks * n_splits;
+    rb = (int)(u / per_rb);
+    const int rem = (int)(u % per_rb);
+    ch = rem / n_splits;
+    t0 = (rem % n_splits) * tps;
+    t1 = min(n_tiles, t0 + tps);
+  };
   const uint32_t idesc_s = idesc_bf16(TM, TN);
 
   if (warp == 0) {
@@ -158,7 +184,8 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
         return s;
       };
       for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-        const int rb = (int)(u / n_chunks), ch = (int)(u % n_chunks);
+        int rb, ch, t0, t1;
+        unit_of(u, rb, ch, t0, t1);
         const int c0 = ch * kMaxChunk;
         const int cw = (int)min64(kMaxChunk, a.dp - c0);
         auto push_s = [&](int t) {
@@ -182,11 +209,11 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
                             &sm.full[s]);
             }
         };
-        for (int t = 0; t < n_tiles && ok; ++t) {
+        for (int t = t0; t < t1 && ok; ++t) {
           push_s(t);
-          if (BWD && t > 0) push_z(t - 1);
+          if (BWD && t > t0) push_z(t - 1);
         }
-        if (BWD && ok) push_z(n_tiles - 1);
+        if (BWD && ok && t1 > t0) push_z(t1 - 1);
       }
       // drain: the last copy into each slot must have landed
       for (uint64_t q = (it > kSStages ? it - kSStages : 0); q < it; ++q) {
@@ -202,7 +229,8 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
       uint64_t it = 0, tile = 0, unit_n = 0;
       bool ok = true;
       for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++unit_n) {
-        const int ch = (int)(u % n_chunks);
+        int rb, ch, t0, t1;
+        unit_of(u, rb, ch, t0, t1);
         const int cw = (int)min64(kMaxChunk, a.dp - ch * kMaxChunk);
         // S tiles use TMEM buffer (tile & 1) in the forward, buffer 0 in the backward
         auto issue_s = [&](uint64_t tl) -> bool {
@@ -255,18 +283,18 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
           mma_commit(&sm.g_empty[gb]);
           return true;
         };
-        for (int t = 0; t < n_tiles && ok; ++t, ++tile) {
+        for (int t = t0; t < t1 && ok; ++t, ++tile) {
           if (!issue_s(tile)) {
             ok = false;
             break;
           }
-          if (BWD && t > 0 && !issue_g(tile - 1, t == 1)) {
+          if (BWD && t > t0 && !issue_g(tile - 1, t == t0 + 1)) {
             ok = false;
             break;
           }
         }
-        if (BWD && ok) {
-          if (!issue_g(tile - 1, n_tiles == 1)) ok = false;
+        if (BWD && ok && t1 > t0) {
+          if (!issue_g(tile - 1, t1 - t0 == 1)) ok = false;
           else mma_commit(&sm.acc_full);
         }
         if (!ok) flag_timeout(sm, &a.ctr->err_flags);
@@ -277,11 +305,11 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+    // ---------------- epilogue (warps 2 and up) ----------------
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;  // row within the tile
-    constexpr int NC = BWD ? 2 : 4;     // 32-column chunks of a tile per warp
-    const int cb = BWD ? ((warp - 2) >> 2) * 2 : 0;  // first chunk of this warp
+    constexpr int NC = MODE == kModeFwd ? 4 : 2;  // 32-column chunks of a tile per warp
+    const int cb = MODE == kModeFwd ? 0 : ((warp - 2) >> 2) * 2;  // first chunk of this warp
     uint64_t tile = 0, unit_n = 0;
     bool ok = true;
     if (a.debug_timeout) {
@@ -293,15 +321,16 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
     }
     const float c1 = kLog2e / a.T;
     for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++unit_n) {
-      const int rb = (int)(u / n_chunks), ch = (int)(u % n_chunks);
+      int rb, ch, t0, t1;
+      unit_of(u, rb, ch, t0, t1);
       const int64_t row = (int64_t)rb * TM + r;
       const bool valid = row < a.n;
       // forward state (log2 domain); the running sum is compensated (TwoSum),
       // so its error does not grow with N
       float m = -INFINITY, l = 0.f, lc = 0.f, diag = 0.f;
       // backward: this row's own-term log-sum-exp (log2 domain)
-      const float lr2 = (BWD && valid && a.wr != 0.f) ? a.lse_r[row] * kLog2e : 0.f;
-      for (int t = 0; t < n_tiles; ++t, ++tile) {
+      const float lr2 = (MODE != kModeFwd && valid && a.wr != 0.f) ? a.lse_r[row] * kLog2e : 0.f;
+      for (int t = t0; t < t1; ++t, ++tile) {
         const int buf = BWD ? 0 : (int)(tile & 1);
         const uint32_t ph = BWD ? (uint32_t)(tile & 1) : (uint32_t)((tile >> 1) & 1);
         const bool w = mbar_wait(&sm.s_full[buf], ph, limit_ns, abort);
@@ -315,12 +344,12 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
         float v[NC][32];
 #pragma unroll
         for (int c = 0; c < NC; ++c) tmem_ld32_nowait(taddr + (cb + c) * 32, v[c]);
-        if constexpr (BWD) tmem_wait_ld(v[0], v[1]);
+        if constexpr (NC == 2) tmem_wait_ld(v[0], v[1]);
         else tmem_wait_ld4(v);
         fence_before();
         mbar_arrive(&sm.s_empty[buf]);  // S buffer free for the next tile
         const int64_t col0 = (int64_t)t * TN;
-        if (!BWD) {
+        if constexpr (MODE == kModeFwd) {
           const bool cols_full = col0 + TN <= a.n;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
@@ -392,15 +421,16 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
               for (int q = 0; q < 32; ++q)
                 if (!valid || col0 + (cb + c) * 32 + q >= a.n) v[c][q] = 0.f;
           }
-          const int gb = 0;
+          // the G' tile buffer is free once the MMA warp (fused backward) or
+          // the stores of the previous tile (G' pass) have read it
           const uint32_t gph = (uint32_t)(tile & 1);
-          const bool we = mbar_wait(&sm.g_empty[gb], gph ^ 1, limit_ns, abort);
+          const bool we = mbar_wait(GP ? &sm.st_free : &sm.g_empty[0], gph ^ 1, limit_ns, abort);
           if (!__all_sync(0xffffffffu, we)) {
             flag_timeout(sm, &a.ctr->err_flags);
             ok = false;
             break;
           }
-          unsigned char *gt = sm.g[gb];
+          unsigned char *gt = sm.g[0];
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const float *gq = v[c];
@@ -422,18 +452,61 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
               *reinterpret_cast<uint4 *>(kbase + ((lc ^ (r & 7)) * 16)) = pk;
             }
           }
+          if constexpr (GP) {
+            // the transposed tile (row j, column i), same swizzled layout:
+            // lanes 2m and 2m + 1 swap one value per column pair, then each
+            // stores two adjacent i of one j as a 32-bit word
+            unsigned char *tt = sm.g[1];
+            const int ic = r & ~1;  // even i of the lane pair
+            unsigned char *tbase = tt + (ic >> 6) * (TM * BK * 2) + (ic & 7) * 2;
+            const int ichunk = (ic & 63) >> 3;
+            const bool odd = (lane & 1) != 0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+#pragma unroll
+              for (int q = 0; q < 32; q += 2) {
+                const float send = odd ? v[c][q] : v[c][q + 1];
+                const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                const __nv_bfloat162 pr = odd ? __floats2bfloat162_rn(recv, v[c][q + 1])
+                                              : __floats2bfloat162_rn(v[c][q], recv);
+                const int j = (cb + c) * 32 + q + (odd ? 1 : 0);
+                *reinterpret_cast<__nv_bfloat162 *>(tbase + j * 128 + ((ichunk ^ (j & 7)) << 4)) =
+                    pr;
+              }
+            }
+          }
           fence_proxy_async_smem();
-          mbar_arrive(&sm.g_full[gb]);
+          if constexpr (GP) {
+            mbar_arrive(&sm.st_full);
+            if (threadIdx.x == 64) {
+              // one thread stores both tiles (two 64-column boxes each) once
+              // every epilogue thread has written its part
+              if (!mbar_wait(&sm.st_full, gph, limit_ns, abort)) {
+                flag_timeout(sm, &a.ctr->err_flags);
+              } else {
+                const int y0 = rb * TM, x0 = (int)col0;
+                tma_store_2d(&tmZ, sm.g[0], x0, y0);
+                tma_store_2d(&tmZ, sm.g[0] + TM * BK * 2, x0 + BK, y0);
+                tma_store_2d(&tmW, sm.g[1], y0, x0);
+                tma_store_2d(&tmW, sm.g[1] + TM * BK * 2, y0 + BK, x0);
+                bulk_commit();
+                bulk_wait_read_all();
+                mbar_arrive(&sm.st_free);
+              }
+            }
+          } else {
+            mbar_arrive(&sm.g_full[0]);
+          }
         }
       }
       if (!ok) break;
-      if (!BWD) {
+      if constexpr (MODE == kModeFwd) {
         if (valid) {
           const float lse = (m + log2f(__fadd_rn(l, lc))) * 0.69314718055994531f;  // natural log
           a.lse_out[row] = lse;
           a.term_out[row] = lse - diag / a.T;
         }
-      } else {
+      } else if constexpr (BWD) {
         // chunk accumulator -> dX[row, chunk] * (g / (N T))
         const bool w = mbar_wait(&sm.acc_full, (uint32_t)(unit_n & 1), limit_ns, abort);
         if (!__all_sync(0xffffffffu, w)) {
@@ -446,7 +519,7 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
         const int c0 = ch * kMaxChunk;
         const int cw = (int)min64(kMaxChunk, a.dp - c0);
         // each epilogue warp of a lane quarter stores its half of the chunk
-        const int hw = BWD ? cw / 2 : cw;
+        const int hw = cw / 2;
         for (int c = (cb / 2) * hw; c < (cb / 2 + 1) * hw; c += 32) {
           float o[32];
           tmem_ld32_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(TN + c), o);
@@ -462,6 +535,169 @@ __global__ void __launch_bounds__(cthreads(BWD), 1)
         fence_before();
         mbar_arrive(&sm.acc_empty);
       }
+    }
+    // G' pass: the last stores must complete before the CTA's shared memory goes
+    if (GP && threadIdx.x == 64) bulk_wait_all();
+  }
+
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Materialised backward, second half: dX = (g / (N T)) G Z for G (np x np,
+// BF16, row-major) and Z (np x d) given as Z^T (dp x np, BF16).  Unit =
+// (128-row block, chunk of <= 384 output dimensions), accumulated over
+// K = np in 64-wide k-blocks; a ring slot holds one k-block of G (16 KB) and
+// of the chunk's Z^T rows (<= 48 KB).  Warp 0: TMA, warp 1: MMA, warps 2-5:
+// readout (one TMEM lane quarter each).
+constexpr int kGemmStages = 3;
+constexpr uint32_t kGemmSlot = kOpBytes + kMaxChunk * BK * 2;  // 64 KB
+constexpr int kGemmThreads = 64 + 4 * 32;
+
+struct alignas(1024) GSmem {
+  unsigned char slot[kGemmStages][kGemmSlot];
+  uint64_t full[kGemmStages], empty[kGemmStages];
+  uint64_t acc_full, acc_empty, drain;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    contrastive_gemm_kernel(const __grid_constant__ CUtensorMap tmG,
+                            const __grid_constant__ CUtensorMap tmZ, ContrastiveGemmArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  GSmem &sm = *reinterpret_cast<GSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                         ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t limit_ns = 4000000000ull;
+  volatile int *abort = &sm.abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGemmStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    mbar_init(&sm.acc_full, 1);
+    mbar_init(&sm.acc_empty, 4 * 32);
+    mbar_init(&sm.drain, 1);
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&sm.tmem_base)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = sm.tmem_base;
+  const int nkb = (int)(a.np / BK);
+  const int64_t n_units = (a.np / TM) * a.n_chunks;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint64_t it = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const int rb = (int)(u / a.n_chunks), ch = (int)(u % a.n_chunks);
+        const int c0 = ch * kMaxChunk;
+        const int cw = (int)min64(kMaxChunk, a.dp - c0);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = (int)(it % kGemmStages);
+          const uint32_t ph = (uint32_t)((it / kGemmStages) & 1);
+          if (!mbar_wait(&sm.empty[s], ph ^ 1, limit_ns, abort)) {
+            flag_timeout(sm, &a.ctr->err_flags);
+            ok = false;
+            break;
+          }
+          ++it;
+          mbar_arrive_expect_tx(&sm.full[s], kOpBytes + (uint32_t)cw * BK * 2);
+          tma_load_2d(sm.slot[s], &tmG, kb * BK, rb * TM, &sm.full[s]);
+          for (int b = 0; b < cw; b += kZBox)
+            tma_load_2d(sm.slot[s] + kOpBytes + b * BK * 2, &tmZ, kb * BK, c0 + b, &sm.full[s]);
+        }
+      }
+      for (uint64_t q = (it > kGemmStages ? it - kGemmStages : 0); q < it; ++q) {
+        const uint64_t t0 = now_ns();
+        while (!mbar_try(&sm.full[q % kGemmStages], (uint32_t)((q / kGemmStages) & 1)) &&
+               now_ns() - t0 < limit_ns) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint64_t it = 0, unit_n = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++unit_n) {
+        const int ch = (int)(u % a.n_chunks);
+        const int cw = (int)min64(kMaxChunk, a.dp - ch * kMaxChunk);
+        if (unit_n > 0 &&
+            !mbar_wait(&sm.acc_empty, (uint32_t)((unit_n - 1) & 1), limit_ns, abort)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % kGemmStages);
+          if (!mbar_wait(&sm.full[s], (uint32_t)((it / kGemmStages) & 1), limit_ns, abort)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t g0 = su32(sm.slot[s]), z0 = g0 + kOpBytes;
+          for (int p = 0; p < cw; p += kPiece) {
+            const int pw = min(kPiece, cw - p);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_bf16(tmem + (uint32_t)p, sdesc(g0 + kk * 32),
+                       sdesc(z0 + (uint32_t)p * BK * 2 + kk * 32), idesc_bf16(TM, pw),
+                       (kb > 0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(&sm.empty[s]);
+        }
+        if (ok) mma_commit(&sm.acc_full);
+      }
+      if (!ok) flag_timeout(sm, &a.ctr->err_flags);
+      mma_commit(&sm.drain);
+      const uint64_t t0 = now_ns();
+      while (!mbar_try(&sm.drain, 0) && now_ns() - t0 < limit_ns) {
+      }
+    }
+  } else {
+    const int quarter = warp & 3;
+    const float scale = __ldg(a.grad_loss) / ((float)a.n * a.T);
+    uint64_t unit_n = 0;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++unit_n) {
+      const int rb = (int)(u / a.n_chunks), ch = (int)(u % a.n_chunks);
+      const int c0 = ch * kMaxChunk;
+      const int cw = (int)min64(kMaxChunk, a.dp - c0);
+      const bool w = mbar_wait(&sm.acc_full, (uint32_t)(unit_n & 1), limit_ns, abort);
+      if (!__all_sync(0xffffffffu, w)) {
+        flag_timeout(sm, &a.ctr->err_flags);
+        break;
+      }
+      fence_after();
+      const int64_t row = (int64_t)rb * TM + quarter * 32 + lane;
+      for (int c = 0; c < cw; c += 32) {
+        float o[32];
+        tmem_ld32_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, o);
+        tmem_wait_ld1(o);
+        if (row < a.n) {
+          float *dst = a.dX + row * a.d + c0 + c;
+          const int64_t lim = a.d - (c0 + c);
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (q < lim) dst[q] = o[q] * scale;
+        }
+      }
+      fence_before();
+      mbar_arrive(&sm.acc_empty);
     }
   }
 
@@ -527,8 +763,11 @@ __global__ void contrastive_loss_kernel(const float *t1, const float *t2, int64_
 // ---------------------------------------------------------------------------
 // Host side
 
-size_t contrastive_smem_bytes(bool bwd) {
-  return (bwd ? sizeof(CSmem<true>) : sizeof(CSmem<false>)) + 1024;
+size_t contrastive_smem_bytes(int mode) {
+  const size_t b = mode == kModeFwd ? sizeof(CSmem<kModeFwd>)
+                   : mode == kModeBwd ? sizeof(CSmem<kModeBwd>)
+                                      : sizeof(CSmem<kModeGp>);
+  return b + 1024;
 }
 
 cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *Xp, void *XT,
@@ -545,25 +784,46 @@ cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_contrastive(bool bwd, const void *tmX, const void *tmY, const void *tmZ,
-                               const ContrastiveArgs &a, int grid, cudaStream_t st) {
-  const size_t smem = contrastive_smem_bytes(bwd);
-  CUtensorMap mx, my, mz;
+template <int MODE>
+static cudaError_t launch_mode(const CUtensorMap &mx, const CUtensorMap &my, const CUtensorMap &mz,
+                               const CUtensorMap &mw, const ContrastiveArgs &a, int grid,
+                               cudaStream_t st) {
+  const size_t smem = contrastive_smem_bytes(MODE);
+  cudaError_t e = cudaFuncSetAttribute(contrastive_kernel<MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  contrastive_kernel<MODE><<<grid, cthreads(MODE), smem, st>>>(mx, my, mz, mw, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contrastive(int mode, const void *tmX, const void *tmY, const void *tmZ,
+                               const void *tmW, const ContrastiveArgs &a, int grid,
+                               cudaStream_t st) {
+  CUtensorMap mx, my, mz, mw;
   std::memcpy(&mx, tmX, sizeof mx);
   std::memcpy(&my, tmY, sizeof my);
   std::memcpy(&mz, tmZ ? tmZ : tmX, sizeof mz);
-  cudaError_t e;
-  if (bwd) {
-    e = cudaFuncSetAttribute(contrastive_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    contrastive_kernel<true><<<grid, cthreads(true), smem, st>>>(mx, my, mz, a);
-  } else {
-    e = cudaFuncSetAttribute(contrastive_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    contrastive_kernel<false><<<grid, cthreads(false), smem, st>>>(mx, my, mz, a);
+  std::memcpy(&mw, tmW ? tmW : tmX, sizeof mw);
+  switch (mode) {
+    case kModeFwd: return launch_mode<kModeFwd>(mx, my, mz, mw, a, grid, st);
+    case kModeBwd: return launch_mode<kModeBwd>(mx, my, mz, mw, a, grid, st);
+    case kModeGp: return launch_mode<kModeGp>(mx, my, mz, mw, a, grid, st);
+    default: return cudaErrorInvalidValue;
   }
+}
+
+size_t contrastive_gemm_smem_bytes() { return sizeof(GSmem) + 1024; }
+
+cudaError_t launch_contrastive_gemm(const void *tmG, const void *tmZ, const ContrastiveGemmArgs &a,
+                                    int grid, cudaStream_t st) {
+  CUtensorMap mg, mz;
+  std::memcpy(&mg, tmG, sizeof mg);
+  std::memcpy(&mz, tmZ, sizeof mz);
+  const size_t smem = contrastive_gemm_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(contrastive_gemm_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  contrastive_gemm_kernel<<<grid, kGemmThreads, smem, st>>>(mg, mz, a);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,9 @@ struct ContrastiveArgs {
   int64_t d;            // embedding width
   int64_t np, dp;       // padded rows (multiple of 128) and width (multiple of 64)
   float T;              // temperature
-  int n_chunks;         // backward: output-dimension chunks of <= 384
+  int n_chunks;         // fused backward: output-dimension chunks of <= 384
+  int n_splits;         // G' pass: column splits of a row block
+  int tiles_per_split;  // G' pass: 128-column tiles per split
   // forward outputs
   float *lse_out;       // [n] natural-log logsumexp of the kernel's rows
   float *term_out;      // [n] lse - S_ii
@@ -27,13 +29,35 @@ struct ContrastiveArgs {
   int debug_timeout;
 };
 
-size_t contrastive_smem_bytes(bool bwd);
+// Kernel modes of launch_contrastive.
+constexpr int kContrastiveFwd = 0;       // lse and loss terms of the kernel's rows
+constexpr int kContrastiveBwdFused = 1;  // dX with G' recomputed per output chunk
+constexpr int kContrastiveGprime = 2;    // G' (tmZ) and G'^T (tmW) written to memory
+
+// dX = (g / (N T)) G Z from a materialised G (np x np BF16) and Z^T (dp x np).
+struct ContrastiveGemmArgs {
+  int64_t n, d, np, dp;
+  float T;
+  int n_chunks;            // output-dimension chunks of <= 384
+  const float *grad_loss;  // device scalar
+  float *dX;               // [n][d]
+  Counters *ctr;
+};
+
+size_t contrastive_smem_bytes(int mode);
+size_t contrastive_gemm_smem_bytes();
 cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *Xp, void *XT,
                                     int64_t np, int64_t dp, unsigned *err, cudaStream_t st);
 cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n, float w1,
                                     float w2, float *loss, cudaStream_t st);
-// tmX/tmY/tmZ: 128-byte CUtensorMap objects (X, Y: box 64 x 128; Z: box 64 x 64)
-cudaError_t launch_contrastive(bool bwd, const void *tmX, const void *tmY, const void *tmZ,
-                               const ContrastiveArgs &a, int grid, cudaStream_t st);
+// tmX/tmY/tmZ/tmW: 128-byte CUtensorMap objects (X, Y: box 64 x 128; Z: box
+// 64 x 64 in the fused backward; G' and G'^T maps with box 64 x 128 in the
+// G' pass; null where the mode reads none)
+cudaError_t launch_contrastive(int mode, const void *tmX, const void *tmY, const void *tmZ,
+                               const void *tmW, const ContrastiveArgs &a, int grid,
+                               cudaStream_t st);
+// tmG: G or G^T (box 64 x 128); tmZ: Z^T (box 64 x 64)
+cudaError_t launch_contrastive_gemm(const void *tmG, const void *tmZ, const ContrastiveGemmArgs &a,
+                                    int grid, cudaStream_t st);
 
 }  // namespace sj

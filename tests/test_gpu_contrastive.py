@@ -31,9 +31,13 @@ def bf16_inputs(A, B):
     return bits(a), bits(b)
 
 
-def run(sjmod, A, B, T, sym=False, g=1.0):
+def run(sjmod, A, B, T, sym=False, g=1.0, fused=False):
+    """fused: the backward recomputes dL/dS per output chunk instead of
+    writing it and its transpose to memory (the default when they fit)."""
     d = A.shape[1]
     flags = sjmod.SJ_FLAG_SYM_INFONCE if sym else 0
+    if fused:
+        flags |= sjmod.SJ_FLAG_FUSED_BACKWARD
     with sjmod.SimilarityJoin(d, prec="bf16", device=0, flags=flags) as J:
         dA = torch.from_numpy(A).cuda()
         dB = torch.from_numpy(B).cuda()
@@ -89,14 +93,15 @@ def sjmod():
     return sj
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("sym", [False, True])
 @pytest.mark.parametrize("N,d,T", [(64, 32, 0.05), (100, 100, 0.1), (300, 64, 0.05),
-                                   (257, 200, 0.2)])
-def test_contrastive_matches_oracle(sjmod, N, d, T, sym):
+                                   (257, 200, 0.2), (640, 448, 0.05)])
+def test_contrastive_matches_oracle(sjmod, N, d, T, sym, fused):
     A, B = datagen.paired(N, d, max(2, N // 8), seed=N + d)
     ab, bb = bf16_inputs(A, B)
     loss_w, lse_w, lsec_w, dA_w, dB_w = oracle.infonce(ab, bb, T, sym=sym, g=0.7)
-    loss, lse, gA, gB = run(sjmod, A, B, T, sym=sym, g=0.7)
+    loss, lse, gA, gB = run(sjmod, A, B, T, sym=sym, g=0.7, fused=fused)
     assert abs(loss - loss_w) <= 5e-5 * max(1.0, abs(loss_w))
     assert np.max(np.abs(lse[:N] - lse_w)) <= 5e-5 * max(1.0, np.max(np.abs(lse_w)))
     if sym:
@@ -179,13 +184,21 @@ def test_contrastive_debug_timeout(sjmod):
     assert np.isfinite(loss)
 
 
-def test_contrastive_8192_full(sjmod):
-    # every output against the oracle at N = 8,192, d = 768
+@pytest.fixture(scope="module")
+def case_8192():
     N, d, T = 8192, 768, 0.05
     A, B = datagen.paired(N, d, 1000, seed=45)
     ab, bb = bf16_inputs(A, B)
-    loss_w, lse_w, _, dA_w, dB_w = oracle.infonce(ab, bb, T, g=1.0)
-    loss, lse, gA, gB = run(sjmod, A, B, T)
+    return A, B, ab, bb, T, oracle.infonce(ab, bb, T, g=1.0)
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_contrastive_8192_full(sjmod, case_8192, fused):
+    # every output against the oracle at N = 8,192, d = 768 (64 x 64 score
+    # tiles, two output chunks of 384)
+    A, B, ab, bb, T, want = case_8192
+    loss_w, lse_w, _, dA_w, dB_w = want
+    loss, lse, gA, gB = run(sjmod, A, B, T, fused=fused)
     assert abs(loss - loss_w) <= 5e-5 * max(1.0, abs(loss_w))
     assert np.max(np.abs(lse - lse_w)) <= 5e-5 * max(1.0, np.max(np.abs(lse_w)))
     bA, bB = grad_bounds(ab, bb, T, False, 1.0, np.abs(lse - lse_w))
