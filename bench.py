@@ -289,10 +289,10 @@ def run_infonce(args):
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": src + " bf16_tflops_sustained", "traffic": None,
                      "flops_per_step": flops},
-        # forward: two packs, the forward kernel, the loss reduction; backward:
-        # two packs, the dL/dS pass, two GEMMs (K forwards, one more for lse, K
-        # backwards in the timed region)
-        "gpu_launches": 4 * (args.steps + 1) + 5 * args.steps,
+        # forward: two packs, the forward kernel, the merge of its partial row
+        # states, the loss reduction; backward: two packs, the dL/dS pass, two
+        # GEMMs (K forwards, one more for lse, K backwards in the timed region)
+        "gpu_launches": 5 * (args.steps + 1) + 5 * args.steps,
         "clocks": clocks,
         "e2e": {"value": n * n / (e_ms / 1e3), "unit": METRIC, "ms_per_step": e_ms,
                 "h2d_bytes_per_step": int(2 * n * d * 4), "d2h_bytes_per_step": 4},

@@ -1458,9 +1458,11 @@ struct ContrastivePlan {
   int64_t n, d, np, dp;
   void *Ap, *Bp, *AT, *BT;
   void *G, *GT;  // materialised backward: dL/dS and its transpose (np x np BF16)
+  float *part;   // forward: partial row states (3 x 2 n_splits x np) and S_ii (np)
+  int n_splits, tiles_per_split;
   Counters *ctr;
   float *scratch;  // 2n floats (per-row loss terms)
-  unsigned char mA[128], mB[128], mAT[128], mBT[128], mG[128], mGT[128];
+  unsigned char mA[128], mB[128], mAT[128], mBT[128], mG[128];
 };
 
 // `gmat`: also reserve and map G and G^T (fails with SJ_ERR_OOM before any
@@ -1478,12 +1480,14 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
   }
   cp.n = N;
   cp.d = h->cfg.d;
-  cp.np = round_up(N, 128);
+  cp.np = round_up(N, 256);
   cp.dp = round_up(cp.d, 64);
+  contrastive_splits(cp.np, &cp.n_splits, &cp.tiles_per_split);
   const size_t op = (size_t)cp.np * cp.dp * 2;
   const size_t gsz = (size_t)cp.np * cp.np * 2;
+  const size_t psz = ((size_t)6 * cp.n_splits + 1) * cp.np * 4;
   size_t bytes = 2 * op + (bwd ? 2 * op : 0) + sizeof(Counters) + (size_t)2 * N * 4 + 8 * 256 +
-                 (gmat ? 2 * gsz + 2 * 256 : 0);
+                 (gmat ? 2 * gsz + 2 * 256 : 0) + (bwd ? 0 : psz + 256);
   sj_status s = ensure_ws(h, bytes);
   if (s != SJ_OK) return s;
   Arena ar{static_cast<unsigned char *>(h->ws), h->ws_size, 0};
@@ -1495,8 +1499,9 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
   cp.BT = bwd ? ar.take(op) : nullptr;
   cp.G = gmat ? ar.take(gsz) : nullptr;
   cp.GT = gmat ? ar.take(gsz) : nullptr;
+  cp.part = bwd ? nullptr : static_cast<float *>(ar.take(psz));
   if (!cp.ctr || !cp.scratch || !cp.Ap || !cp.Bp || (bwd && (!cp.AT || !cp.BT)) ||
-      (gmat && (!cp.G || !cp.GT)))
+      (gmat && (!cp.G || !cp.GT)) || (!bwd && !cp.part))
     return SJ_ERR_INTERNAL;
   cudaStream_t st = h->stream;
   SJ_CUDA(cudaMemsetAsync(cp.ctr, 0, sizeof(Counters), st));
@@ -1509,7 +1514,6 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
   if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.AT, cp.np, cp.dp, 64, 64, cp.mAT);
   if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.BT, cp.np, cp.dp, 64, 64, cp.mBT);
   if (s == SJ_OK && gmat) s = tc_encode_2d(h->tc, cp.G, cp.np, cp.np, 64, 128, cp.mG);
-  if (s == SJ_OK && gmat) s = tc_encode_2d(h->tc, cp.GT, cp.np, cp.np, 64, 128, cp.mGT);
   return s;
 }
 
@@ -1543,14 +1547,23 @@ sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t
   a.n_chunks = 1;
   a.ctr = cp.ctr;
   a.debug_timeout = (h->cfg.flags & SJ_FLAG_DEBUG_TIMEOUT) ? 1 : 0;
-  const int grid = (int)std::min<int64_t>(cp.np / 128, h->sm_count);
+  // units = (row block, column split) for balance across the SMs; the
+  // partial row states are merged by a second launch
+  a.n_splits = cp.n_splits;
+  a.tiles_per_split = cp.tiles_per_split;
+  const size_t pn = (size_t)2 * cp.n_splits * cp.np;
+  a.part_m = cp.part;
+  a.part_l = cp.part + pn;
+  a.part_c = cp.part + 2 * pn;
+  a.diag_out = cp.part + 3 * pn;
+  const int grid = (int)std::min<int64_t>((cp.np / 128) * cp.n_splits, h->sm_count);
   a.lse_out = lse;
   a.term_out = cp.scratch;
-  SJ_CUDA(launch_contrastive(kContrastiveFwd, cp.mA, cp.mB, nullptr, nullptr, a, grid, h->stream));
+  SJ_CUDA(launch_contrastive(kContrastiveFwd, cp.mA, cp.mB, nullptr, a, grid, h->stream));
   if (sym) {
     a.lse_out = lse + N;
     a.term_out = cp.scratch + N;
-    SJ_CUDA(launch_contrastive(kContrastiveFwd, cp.mB, cp.mA, nullptr, nullptr, a, grid, h->stream));
+    SJ_CUDA(launch_contrastive(kContrastiveFwd, cp.mB, cp.mA, nullptr, a, grid, h->stream));
   }
   SJ_CUDA(launch_contrastive_loss(cp.scratch, sym ? cp.scratch + N : nullptr, N, sym ? 0.5f : 1.f,
                                   0.5f, loss, h->stream));
@@ -1593,14 +1606,13 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   a.wc = sym ? 0.5f : 0.f;
   const int64_t n_rb = cp.np / 128;
   if (gmat) {
-    // G pass: units = (row block, column split of ~64 tiles) for balance
-    const int64_t n_tiles = n_rb;
-    const int64_t want = std::max<int64_t>(1, (n_tiles + 63) / 64);
-    a.tiles_per_split = (int)((n_tiles + want - 1) / want);
-    a.n_splits = (int)((n_tiles + a.tiles_per_split - 1) / a.tiles_per_split);
+    // G pass: units = (row block, column split) for balance; G through its
+    // tensor map (TMA stores), G^T by plain stores
+    a.n_splits = cp.n_splits;
+    a.tiles_per_split = cp.tiles_per_split;
+    a.gT = cp.GT;
     const int grid = (int)std::min<int64_t>(n_rb * a.n_splits, h->sm_count);
-    SJ_CUDA(launch_contrastive(kContrastiveGprime, cp.mA, cp.mB, cp.mG, cp.mGT, a, grid,
-                               h->stream));
+    SJ_CUDA(launch_contrastive(kContrastiveGprime, cp.mA, cp.mB, cp.mG, a, grid, h->stream));
     ContrastiveGemmArgs g{};
     g.n = N;
     g.d = cp.d;
@@ -1614,14 +1626,16 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
     g.dX = dA;  // dA = G B / T
     SJ_CUDA(launch_contrastive_gemm(cp.mG, cp.mBT, g, ggrid, h->stream));
     g.dX = dB;  // dB = G^T A / T
-    SJ_CUDA(launch_contrastive_gemm(cp.mGT, cp.mAT, g, ggrid, h->stream));
+    unsigned char mGT[128];
+    sj_status ms = tc_encode_2d(h->tc, cp.GT, cp.np, cp.np, 64, 128, mGT);
+    if (ms != SJ_OK) return ms;
+    SJ_CUDA(launch_contrastive_gemm(mGT, cp.mAT, g, ggrid, h->stream));
     return contrastive_finish(h, cp);
   }
   const int grid = (int)std::min<int64_t>(n_rb * a.n_chunks, h->sm_count);
   // dA: rows of A against columns (rows of B); row term = softmax over j
   a.dX = dA;
-  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mA, cp.mB, cp.mBT, nullptr, a, grid,
-                             h->stream));
+  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mA, cp.mB, cp.mBT, a, grid, h->stream));
   // dB: rows of B against columns (rows of A); the row softmax term is indexed
   // by the kernel's columns, the column softmax term by its rows
   a.lse_r = sym ? lse + N : lse;
@@ -1629,8 +1643,7 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   a.lse_c = lse;
   a.wc = sym ? 0.5f : 1.f;
   a.dX = dB;
-  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mB, cp.mA, cp.mAT, nullptr, a, grid,
-                             h->stream));
+  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mB, cp.mA, cp.mAT, a, grid, h->stream));
   return contrastive_finish(h, cp);
 }
 

@@ -1,5 +1,5 @@
 // contrastive.cu -- InfoNCE-style contrastive join: forward and backward on
-// sm_103a tensor cores, recomputing score tiles instead of storing S.
+// sm_103a tensor cores.
 //
 // S = A B^T / T over N paired rows (positives on the diagonal), BF16 operands
 // (round-to-nearest-even of the float32 inputs), FP32 accumulation in TMEM.
@@ -10,25 +10,33 @@
 //
 // One persistent kernel template, one CTA per SM, warp-specialised:
 //   warp 0: TMA producer, warp 1: TMEM allocator + MMA issuer,
-//   warps 2-5: epilogue (one TMEM lane quarter each, one row per thread).
-// Tiles are 128 rows x 128 columns.
-//   FWD  : S tiles double-buffered in TMEM; epilogue keeps an online
-//          (max, sum) per row with exp2 and records the diagonal.
-//   BWD  : unit = (128-row block of X, chunk of <= 384 output dimensions).
-//          Per column tile t: S_t = X_blk Y_t^T (TMEM cols 0..127); the
-//          epilogue turns S_t into G'_t = w_r (P - I) + w_c (Q - I) in BF16,
-//          written 128B-swizzled into shared memory; the MMA warp then adds
-//          G'_t Z_t^T to the chunk accumulator (TMEM cols 128..511), Z^T being
-//          a transposed BF16 copy of the other side.  The same kernel gives dA
-//          (X = A, Y = B, Z^T = B^T) and dB (X = B, Y = A, Z^T = A^T, the
-//          softmax terms swapped between rows and columns).  A 128 x 768 FP32
-//          block would exceed tensor memory (512 columns), hence the chunks.
+//   warps 2-9: epilogue (two per TMEM lane quarter, one row per thread, each
+//   owning half of a tile's columns).
+//   FWD : 128 x 256 score tiles double-buffered in TMEM; units = (128-row
+//         block, column split); the epilogue keeps an online (max, sum) per
+//         row and column half, written as partial states that a second
+//         launch merges into l_i and the loss terms.
+//   GP  : the G pass of the materialised backward: the same tiles turned into
+//         G' = w_r (P - I) + w_c (Q - I) in BF16, written as G' (through a
+//         shared-memory staging tile and TMA stores) and G'^T (plain
+//         coalesced stores); two GEMM launches (contrastive_gemm_kernel) then
+//         form dA = G' B and dB = G'^T A, scaled by g / (N T).
+//   BWD : the fused backward for when G' does not fit in memory: unit =
+//         (128-row block of X, chunk of <= 384 output dimensions); per
+//         128-column tile t, S_t = X_blk Y_t^T (TMEM cols 0..127), G'_t in
+//         shared memory, and the MMA warp adds G'_t Z_t^T to the chunk
+//         accumulator (TMEM cols 128..511), Z^T being a transposed BF16 copy
+//         of the other side.  The same kernel gives dA (X = A, Y = B, Z^T =
+//         B^T) and dB (X = B, Y = A, Z^T = A^T, the softmax terms swapped
+//         between rows and columns).  A 128 x 768 FP32 block would exceed
+//         tensor memory (512 columns), hence the chunks.
 // Every wait is bounded (globaltimer); a wait that gives up flags
 // SJ_ERR_TIMEOUT and the CTA drains its copies and MMAs before freeing TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "../../include/sj.h"
@@ -41,42 +49,52 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128;             // rows per tile (TMEM lanes)
-constexpr int TN = 128;             // columns per tile
 constexpr int BK = 64;              // k-block (128 bytes of BF16)
-// Operand ring of 32 KB slots: the bytes in flight bound the operand stream
-// (one 64-wide k-block of a 128 x 128 tile is ~270 tensor-core cycles, one L2
-// round trip several times that).  A slot holds an S k-block (X and Y, 16 KB
-// each) or, in the backward, a Z^T slice (up to 192 rows of a 64-wide
-// k-block, 24 KB), in the order the MMA warp consumes them: S(0), then for
-// t >= 1 S(t) and Z^T(t-1), then Z^T(last).  Six slots and one G' tile; the
-// G' pass has five slots and two staging tiles (G' and its transpose).
-constexpr int kMaxChunk = 384;      // output dimensions per backward unit
+constexpr int kMaxChunk = 384;      // output dimensions per fused-backward unit
 constexpr int kPiece = 192;         // N of one backward MMA
 constexpr int kZBox = 64;           // rows of one Z^T TMA box
+constexpr uint32_t kOpBytes = TM * BK * 2;  // one 128-row operand k-block (16 KB)
+constexpr uint32_t kGBytes = TM * 128 * 2;  // one 128 x 128 G' tile (32 KB)
+constexpr float kLog2e = 1.4426950408889634f;
+
 // Kernel modes: the forward; the fused backward (G' recomputed per output
 // chunk and consumed in shared memory); the G' pass of the materialised
 // backward (G' and its transpose written to global memory).
 constexpr int kModeFwd = kContrastiveFwd, kModeBwd = kContrastiveBwdFused,
               kModeGp = kContrastiveGprime;
-// Producer and MMA warps, then the epilogue: 4 warps (one TMEM lane quarter
-// each, all 128 columns of a tile) in the forward, 8 in the other modes (two
-// per lane quarter, one 64-column half each: one k-block of the G' tile).
-__host__ __device__ constexpr int epi_warps(int mode) { return mode == kModeFwd ? 4 : 8; }
-__host__ __device__ constexpr int cthreads(int mode) { return 64 + 32 * epi_warps(mode); }
-constexpr uint32_t kOpBytes = TM * BK * 2;  // one operand k-block (16 KB)
-constexpr uint32_t kGBytes = TM * TN * 2;         // one G tile (32 KB)
-constexpr float kLog2e = 1.4426950408889634f;
+
+// Per-mode shapes.  Score tiles are 128 x TN.  The operand stream bounds
+// these kernels (one k-block of a 128 x 256 tile is ~540 tensor-core cycles,
+// one L2 round trip several times that), so the forward and the G' pass use
+// 256-column tiles (a third fewer operand bytes per flop than 128) with S
+// double-buffered in TMEM (2 x 256 columns).  The fused backward keeps
+// 128-column tiles: its chunk accumulator takes the other 384 TMEM columns.
+// Ring slots hold one k-block of the X row block and of the Y tile, or (fused
+// backward) a Z^T slice of up to 192 rows, in the order the MMA warp consumes
+// them: S(0), then for t >= 1 S(t) and Z^T(t-1), then Z^T(last).
+// Epilogue: 8 warps, two per TMEM lane quarter, each owning half of a tile's
+// columns (NC chunks of 32).
+template <int MODE>
+struct CCfg {
+  static constexpr int TN = MODE == kModeBwd ? 128 : 256;
+  static constexpr uint32_t kSlot = kOpBytes + TN * BK * 2;
+  static constexpr int kStages = MODE == kModeBwd ? 6 : 4;
+  static constexpr int NC = TN / 64;
+};
+constexpr int kEpiWarps = 8;
+constexpr int kCThreads = 64 + 32 * kEpiWarps;
 
 template <int MODE>
 struct alignas(1024) CSmem {
-  static constexpr int kSStages = MODE == kModeGp ? 5 : 6;
-  static constexpr int kGTiles = MODE == kModeGp ? 2 : 1;
-  unsigned char slot[kSStages][2 * kOpBytes];
-  unsigned char g[kGTiles][MODE == kModeFwd ? 1024 : kGBytes];  // G' tile(s)
-  uint64_t full[kSStages], empty[kSStages];
-  uint64_t st_full, st_free;  // G' pass: staging tiles written / read by the stores
+  using C = CCfg<MODE>;
+  unsigned char slot[C::kStages][C::kSlot];
+  // fused backward: the G' operand tile; G' pass: staging of one 128 x 128
+  // half of a G' tile for the TMA stores
+  unsigned char g[MODE == kModeFwd ? 1024 : kGBytes];
+  uint64_t full[C::kStages], empty[C::kStages];
   uint64_t s_full[2], s_empty[2];
-  uint64_t g_full[2], g_empty[2];
+  uint64_t g_full, g_empty;
+  uint64_t st_full[2], st_free[2];  // G' pass: staging written / free, per column half
   uint64_t acc_full, acc_empty;
   uint64_t drain, never;
   uint32_t tmem_base;
@@ -95,43 +113,44 @@ __device__ __forceinline__ void flag_timeout(SM &sm, unsigned *err) {
   atomicOr(err, 4u);  // kErrTimeout
 }
 
-// fence the generic-proxy shared-memory writes before the tensor core reads them
+// fence the generic-proxy shared-memory writes before the async proxy
+// (tensor core, TMA store) reads them
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(cthreads(MODE), 1)
+__global__ void __launch_bounds__(kCThreads, 1)
     contrastive_kernel(const __grid_constant__ CUtensorMap tmX,
                        const __grid_constant__ CUtensorMap tmY,
-                       const __grid_constant__ CUtensorMap tmZ,
-                       const __grid_constant__ CUtensorMap tmW, ContrastiveArgs a) {
+                       const __grid_constant__ CUtensorMap tmZ, ContrastiveArgs a) {
   constexpr bool BWD = MODE == kModeBwd;
   constexpr bool GP = MODE == kModeGp;
-  constexpr int kEpi = epi_warps(MODE) * 32;
+  using C = CCfg<MODE>;
+  constexpr int TN = C::TN, NC = C::NC, kStages = C::kStages;
+  constexpr int kEpi = kEpiWarps * 32;
   extern __shared__ unsigned char smem_raw[];
   using Smem = CSmem<MODE>;
-  constexpr int kSStages = Smem::kSStages;
   Smem &sm = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                        ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t limit_ns = 4000000000ull;
   volatile int *abort = &sm.abort;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kSStages; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], 1);
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(&sm.s_full[q], 1);
       mbar_init(&sm.s_empty[q], kEpi);
-      mbar_init(&sm.g_full[q], kEpi);
-      mbar_init(&sm.g_empty[q], 1);
+      mbar_init(&sm.st_full[q], kEpi / 2);
+      mbar_init(&sm.st_free[q], 1);
     }
+    mbar_init(&sm.g_full, kEpi);
+    mbar_init(&sm.g_empty, 1);
     mbar_init(&sm.acc_full, 1);
     mbar_init(&sm.acc_empty, kEpi);
-    mbar_init(&sm.st_full, kEpi);
-    mbar_init(&sm.st_free, 1);
     mbar_init(&sm.drain, 1);
     mbar_init(&sm.never, 1);
     sm.abort = 0;
@@ -151,20 +170,21 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
   const int n_tiles = (int)(a.np / TN);
   const int n_rb = (int)(a.np / TM);
   const int n_chunks = BWD ? a.n_chunks : 1;
-  // G' pass: units also split the column tiles (no state crosses tiles there)
-  const int n_splits = GP ? a.n_splits : 1;
-  const int tps = GP ? a.tiles_per_split : n_tiles;
+  // the forward and the G' pass also split a row block's column tiles
+  const int n_splits = BWD ? 1 : a.n_splits;
+  const int tps = BWD ? n_tiles : a.tiles_per_split;
   const int64_t n_units = (int64_t)n_rb * n_chunks * n_splits;
-  // unit u: row block, output chunk, column tiles [t0, t1)
-  auto unit_of = [&](int64_t u, int &rb, int &ch, int &t0, int &t1) {
+  const uint32_t idesc_s = idesc_bf16(TM, TN);
+  // unit u: row block, output chunk, split, column tiles [t0, t1)
+  auto unit_of = [&](int64_t u, int &rb, int &ch, int &sp, int &t0, int &t1) {
     const int64_t per_rb = (int64_t)n_chunks * n_splits;
     rb = (int)(u / per_rb);
     const int rem = (int)(u % per_rb);
     ch = rem / n_splits;
-    t0 = (rem % n_splits) * tps;
+    sp = rem % n_splits;
+    t0 = sp * tps;
     t1 = min(n_tiles, t0 + tps);
   };
-  const uint32_t idesc_s = idesc_bf16(TM, TN);
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -172,8 +192,8 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
       uint64_t it = 0;
       bool ok = true;
       auto take = [&](uint32_t bytes) -> int {  // next slot, armed for `bytes`
-        const int s = (int)(it % kSStages);
-        const uint32_t ph = (uint32_t)((it / kSStages) & 1);
+        const int s = (int)(it % kStages);
+        const uint32_t ph = (uint32_t)((it / kStages) & 1);
         if (!mbar_wait(&sm.empty[s], ph ^ 1, limit_ns, abort)) {
           flag_timeout(sm, &a.ctr->err_flags);
           ok = false;
@@ -184,16 +204,18 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
         return s;
       };
       for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-        int rb, ch, t0, t1;
-        unit_of(u, rb, ch, t0, t1);
+        int rb, ch, sp, t0, t1;
+        unit_of(u, rb, ch, sp, t0, t1);
         const int c0 = ch * kMaxChunk;
         const int cw = (int)min64(kMaxChunk, a.dp - c0);
         auto push_s = [&](int t) {
           for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = take(2 * kOpBytes);
+            const int s = take(C::kSlot);
             if (s < 0) break;
             tma_load_2d(sm.slot[s], &tmX, kb * BK, rb * TM, &sm.full[s]);
-            tma_load_2d(sm.slot[s] + kOpBytes, &tmY, kb * BK, t * TN, &sm.full[s]);
+            for (int y = 0; y < TN; y += 128)
+              tma_load_2d(sm.slot[s] + kOpBytes + y * BK * 2, &tmY, kb * BK, t * TN + y,
+                          &sm.full[s]);
           }
         };
         // Z^T(t): per 64-wide k-block kz of the tile's columns, slices of up
@@ -216,9 +238,9 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
         if (BWD && ok && t1 > t0) push_z(t1 - 1);
       }
       // drain: the last copy into each slot must have landed
-      for (uint64_t q = (it > kSStages ? it - kSStages : 0); q < it; ++q) {
+      for (uint64_t q = (it > kStages ? it - kStages : 0); q < it; ++q) {
         const uint64_t t0 = now_ns();
-        while (!mbar_try(&sm.full[q % kSStages], (uint32_t)((q / kSStages) & 1)) &&
+        while (!mbar_try(&sm.full[q % kStages], (uint32_t)((q / kStages) & 1)) &&
                now_ns() - t0 < limit_ns) {
         }
       }
@@ -229,10 +251,11 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
       uint64_t it = 0, tile = 0, unit_n = 0;
       bool ok = true;
       for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++unit_n) {
-        int rb, ch, t0, t1;
-        unit_of(u, rb, ch, t0, t1);
+        int rb, ch, sp, t0, t1;
+        unit_of(u, rb, ch, sp, t0, t1);
         const int cw = (int)min64(kMaxChunk, a.dp - ch * kMaxChunk);
-        // S tiles use TMEM buffer (tile & 1) in the forward, buffer 0 in the backward
+        // S tiles use TMEM buffer (tile & 1), at column buf * TN; the fused
+        // backward has one buffer (its accumulator takes the rest)
         auto issue_s = [&](uint64_t tl) -> bool {
           const int buf = BWD ? 0 : (int)(tl & 1);
           const uint32_t ph = BWD ? (uint32_t)(tl & 1) : (uint32_t)((tl >> 1) & 1);
@@ -240,9 +263,9 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
           fence_after();
           const uint32_t d = tmem + (uint32_t)(buf * TN);
           for (int kb = 0; kb < nkb; ++kb, ++it) {
-            const int s = (int)(it % kSStages);
-            const uint32_t sp = (uint32_t)((it / kSStages) & 1);
-            if (!mbar_wait(&sm.full[s], sp, limit_ns, abort)) return false;
+            const int s = (int)(it % kStages);
+            const uint32_t spar = (uint32_t)((it / kStages) & 1);
+            if (!mbar_wait(&sm.full[s], spar, limit_ns, abort)) return false;
             fence_after();
             const uint32_t x0 = su32(sm.slot[s]), y0 = x0 + kOpBytes;
 #pragma unroll
@@ -254,23 +277,22 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
           mma_commit(&sm.s_full[buf]);
           return true;
         };
-        // backward product of tile tl: acc += G'_tl Z_tl^T
+        // fused backward, tile tl: acc += G'_tl Z_tl^T
         auto issue_g = [&](uint64_t tl, bool first) -> bool {
-          const int gb = 0;
           const uint32_t gph = (uint32_t)(tl & 1);
-          if (!mbar_wait(&sm.g_full[gb], gph, limit_ns, abort)) return false;
+          if (!mbar_wait(&sm.g_full, gph, limit_ns, abort)) return false;
           if (first && unit_n > 0) {
             if (!mbar_wait(&sm.acc_empty, (uint32_t)((unit_n - 1) & 1), limit_ns, abort))
               return false;
           }
           fence_after();
           for (int kz = 0; kz < 2; ++kz) {
-            const uint32_t g0 = su32(sm.g[gb]) + kz * (TM * BK * 2);
+            const uint32_t g0 = su32(sm.g) + kz * (TM * BK * 2);
             for (int p = 0; p < cw; p += kPiece, ++it) {
               const int pw = min(kPiece, cw - p);
-              const int s = (int)(it % kSStages);
-              const uint32_t sp = (uint32_t)((it / kSStages) & 1);
-              if (!mbar_wait(&sm.full[s], sp, limit_ns, abort)) return false;
+              const int s = (int)(it % kStages);
+              const uint32_t spar = (uint32_t)((it / kStages) & 1);
+              if (!mbar_wait(&sm.full[s], spar, limit_ns, abort)) return false;
               fence_after();
               const uint32_t z0 = su32(sm.slot[s]);
 #pragma unroll
@@ -280,7 +302,7 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
               mma_commit(&sm.empty[s]);
             }
           }
-          mma_commit(&sm.g_empty[gb]);
+          mma_commit(&sm.g_empty);
           return true;
         };
         for (int t = t0; t < t1 && ok; ++t, ++tile) {
@@ -305,11 +327,11 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2 and up) ----------------
+    // ---------------- epilogue (warps 2..9) ----------------
     const int quarter = warp & 3;
-    const int r = quarter * 32 + lane;  // row within the tile
-    constexpr int NC = MODE == kModeFwd ? 4 : 2;  // 32-column chunks of a tile per warp
-    const int cb = MODE == kModeFwd ? 0 : ((warp - 2) >> 2) * 2;  // first chunk of this warp
+    const int r = quarter * 32 + lane;      // row within the tile
+    const int half = (warp - 2) >> 2;       // column half of the tile
+    const int cb = half * NC;               // first 32-column chunk of this warp
     uint64_t tile = 0, unit_n = 0;
     bool ok = true;
     if (a.debug_timeout) {
@@ -321,13 +343,14 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
     }
     const float c1 = kLog2e / a.T;
     for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++unit_n) {
-      int rb, ch, t0, t1;
-      unit_of(u, rb, ch, t0, t1);
+      int rb, ch, sp, t0, t1;
+      unit_of(u, rb, ch, sp, t0, t1);
       const int64_t row = (int64_t)rb * TM + r;
       const bool valid = row < a.n;
-      // forward state (log2 domain); the running sum is compensated (TwoSum),
-      // so its error does not grow with N
-      float m = -INFINITY, l = 0.f, lc = 0.f, diag = 0.f;
+      // forward state of this row over this warp's columns of the unit's
+      // tiles (log2 domain); the running sum is compensated (TwoSum), so its
+      // error does not grow with N
+      float m = -INFINITY, l = 0.f, lc = 0.f;
       // backward: this row's own-term log-sum-exp (log2 domain)
       const float lr2 = (MODE != kModeFwd && valid && a.wr != 0.f) ? a.lse_r[row] * kLog2e : 0.f;
       for (int t = t0; t < t1; ++t, ++tile) {
@@ -352,14 +375,21 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
         if constexpr (MODE == kModeFwd) {
           const bool cols_full = col0 + TN <= a.n;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float x[32];
+          for (int c = 0; c < NC; ++c) {
+            // in place: scores -> log2-domain logits -> exponentials -> sum
+            const int64_t jb = col0 + (cb + c) * 32;
+            if (valid && row >= jb && row < jb + 32) {
+#pragma unroll
+              for (int q = 0; q < 32; ++q)
+                if (jb + q == row) a.diag_out[row] = v[c][q];
+            }
             float cm = -INFINITY;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-              x[q] = v[c][q] * c1;
-              if (!cols_full && col0 + c * 32 + q >= a.n) x[q] = -INFINITY;
-              cm = fmaxf(cm, x[q]);
+              float x = v[c][q] * c1;
+              if (!cols_full && jb + q >= a.n) x = -INFINITY;
+              v[c][q] = x;
+              cm = fmaxf(cm, x);
             }
             if (cm > m) {
               const float sc = (m == -INFINITY) ? 0.f : ex2(m - cm);
@@ -367,25 +397,20 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
               lc *= sc;
               m = cm;
             }
+            if (m == -INFINITY) continue;  // no valid column seen yet (padding)
             // pairwise sum of the chunk, then a compensated add into l
-            float e[32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) e[q] = ex2(x[q] - m);
+            for (int q = 0; q < 32; ++q) v[c][q] = ex2(v[c][q] - m);
 #pragma unroll
             for (int w2 = 16; w2 >= 1; w2 >>= 1)
 #pragma unroll
-              for (int q = 0; q < w2; ++q) e[q] += e[q + w2];
+              for (int q = 0; q < w2; ++q) v[c][q] += v[c][q + w2];
             {
-              const float t = __fadd_rn(l, e[0]);
-              const float bp = __fsub_rn(t, l);
-              lc = __fadd_rn(lc, __fadd_rn(__fsub_rn(l, __fsub_rn(t, bp)), __fsub_rn(e[0], bp)));
-              l = t;
-            }
-            const int64_t jb = col0 + c * 32;
-            if (row >= jb && row < jb + 32) {
-#pragma unroll
-              for (int q = 0; q < 32; ++q)
-                if (jb + q == row) diag = v[c][q];
+              const float e0 = v[c][0];
+              const float tt = __fadd_rn(l, e0);
+              const float bp = __fsub_rn(tt, l);
+              lc = __fadd_rn(lc, __fadd_rn(__fsub_rn(l, __fsub_rn(tt, bp)), __fsub_rn(e0, bp)));
+              l = tt;
             }
           }
         } else {
@@ -421,25 +446,51 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
               for (int q = 0; q < 32; ++q)
                 if (!valid || col0 + (cb + c) * 32 + q >= a.n) v[c][q] = 0.f;
           }
-          // the G' tile buffer is free once the MMA warp (fused backward) or
-          // the stores of the previous tile (G' pass) have read it
+          if constexpr (GP) {
+            // G'^T straight to memory: lanes 2m and 2m + 1 swap one value per
+            // column pair, then each stores two adjacent i of one j (32 bits);
+            // a warp store covers 64 contiguous bytes of two rows of G'^T
+            const bool odd = (lane & 1) != 0;
+            __nv_bfloat16 *gt_col =
+                static_cast<__nv_bfloat16 *>(a.gT) + (int64_t)rb * TM + (r & ~1) + (col0 + cb * 32 + (odd ? 1 : 0)) * a.np;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+#pragma unroll
+              for (int q = 0; q < 32; q += 2) {
+                const float send = odd ? v[c][q] : v[c][q + 1];
+                const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                const __nv_bfloat162 pr = odd ? __floats2bfloat162_rn(recv, v[c][q + 1])
+                                              : __floats2bfloat162_rn(v[c][q], recv);
+                *reinterpret_cast<__nv_bfloat162 *>(gt_col + (int64_t)(c * 32 + q) * a.np) = pr;
+              }
+            }
+          }
+          // G' into the shared tile (128B-swizzled K-major k-blocks of 64
+          // columns): the fused backward's MMA operand, or the G' pass's
+          // staging of this warp's column half (the two halves take turns)
           const uint32_t gph = (uint32_t)(tile & 1);
-          const bool we = mbar_wait(GP ? &sm.st_free : &sm.g_empty[0], gph ^ 1, limit_ns, abort);
+          bool we;
+          if constexpr (GP) {
+            // half 0 of tile t waits for half 1 of tile t - 1, half 1 for half 0 of tile t
+            const uint32_t par = half == 0 ? gph ^ 1u : gph;
+            we = mbar_wait(&sm.st_free[half], par, limit_ns, abort);
+          } else {
+            we = mbar_wait(&sm.g_empty, gph ^ 1, limit_ns, abort);
+          }
           if (!__all_sync(0xffffffffu, we)) {
             flag_timeout(sm, &a.ctr->err_flags);
             ok = false;
             break;
           }
-          unsigned char *gt = sm.g[0];
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const float *gq = v[c];
-            const int cc = cb + c;  // chunk of the tile
+            const int cc = GP ? c : cb + c;  // chunk within the shared 128-column tile
             // 32 columns = 4 chunks of 16 bytes in k-block (cc >> 1)
-            unsigned char *kbase = gt + (cc >> 1) * (TM * BK * 2) + r * 128;
+            unsigned char *kbase = sm.g + (cc >> 1) * (TM * BK * 2) + r * 128;
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-              const int lc = (cc & 1) * 4 + h;  // logical 16-byte chunk in the 128-byte row
+              const int l16 = (cc & 1) * 4 + h;  // logical 16-byte chunk in the 128-byte row
               __nv_bfloat162 p0 = __floats2bfloat162_rn(gq[h * 8 + 0], gq[h * 8 + 1]);
               __nv_bfloat162 p1 = __floats2bfloat162_rn(gq[h * 8 + 2], gq[h * 8 + 3]);
               __nv_bfloat162 p2 = __floats2bfloat162_rn(gq[h * 8 + 4], gq[h * 8 + 5]);
@@ -449,62 +500,39 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
               pk.y = *reinterpret_cast<uint32_t *>(&p1);
               pk.z = *reinterpret_cast<uint32_t *>(&p2);
               pk.w = *reinterpret_cast<uint32_t *>(&p3);
-              *reinterpret_cast<uint4 *>(kbase + ((lc ^ (r & 7)) * 16)) = pk;
-            }
-          }
-          if constexpr (GP) {
-            // the transposed tile (row j, column i), same swizzled layout:
-            // lanes 2m and 2m + 1 swap one value per column pair, then each
-            // stores two adjacent i of one j as a 32-bit word
-            unsigned char *tt = sm.g[1];
-            const int ic = r & ~1;  // even i of the lane pair
-            unsigned char *tbase = tt + (ic >> 6) * (TM * BK * 2) + (ic & 7) * 2;
-            const int ichunk = (ic & 63) >> 3;
-            const bool odd = (lane & 1) != 0;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-#pragma unroll
-              for (int q = 0; q < 32; q += 2) {
-                const float send = odd ? v[c][q] : v[c][q + 1];
-                const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
-                const __nv_bfloat162 pr = odd ? __floats2bfloat162_rn(recv, v[c][q + 1])
-                                              : __floats2bfloat162_rn(v[c][q], recv);
-                const int j = (cb + c) * 32 + q + (odd ? 1 : 0);
-                *reinterpret_cast<__nv_bfloat162 *>(tbase + j * 128 + ((ichunk ^ (j & 7)) << 4)) =
-                    pr;
-              }
+              *reinterpret_cast<uint4 *>(kbase + ((l16 ^ (r & 7)) * 16)) = pk;
             }
           }
           fence_proxy_async_smem();
           if constexpr (GP) {
-            mbar_arrive(&sm.st_full);
-            if (threadIdx.x == 64) {
-              // one thread stores both tiles (two 64-column boxes each) once
-              // every epilogue thread has written its part
-              if (!mbar_wait(&sm.st_full, gph, limit_ns, abort)) {
+            mbar_arrive(&sm.st_full[half]);
+            if (((warp - 2) & 3) == 0 && lane == 0) {
+              // the half's first warp stores its two 64-column boxes once the
+              // half's four warps have written them
+              if (!mbar_wait(&sm.st_full[half], gph, limit_ns, abort)) {
                 flag_timeout(sm, &a.ctr->err_flags);
               } else {
-                const int y0 = rb * TM, x0 = (int)col0;
-                tma_store_2d(&tmZ, sm.g[0], x0, y0);
-                tma_store_2d(&tmZ, sm.g[0] + TM * BK * 2, x0 + BK, y0);
-                tma_store_2d(&tmW, sm.g[1], y0, x0);
-                tma_store_2d(&tmW, sm.g[1] + TM * BK * 2, y0 + BK, x0);
+                const int y0 = rb * TM, x0 = (int)col0 + half * 128;
+                tma_store_2d(&tmZ, sm.g, x0, y0);
+                tma_store_2d(&tmZ, sm.g + TM * BK * 2, x0 + BK, y0);
                 bulk_commit();
                 bulk_wait_read_all();
-                mbar_arrive(&sm.st_free);
+                mbar_arrive(&sm.st_free[half ^ 1]);
               }
             }
           } else {
-            mbar_arrive(&sm.g_full[0]);
+            mbar_arrive(&sm.g_full);
           }
         }
       }
       if (!ok) break;
       if constexpr (MODE == kModeFwd) {
         if (valid) {
-          const float lse = (m + log2f(__fadd_rn(l, lc))) * 0.69314718055994531f;  // natural log
-          a.lse_out[row] = lse;
-          a.term_out[row] = lse - diag / a.T;
+          // partial state of (row, split, half): merged by the finishing kernel
+          const int64_t pi = (int64_t)(sp * 2 + half) * a.np + row;
+          a.part_m[pi] = m;
+          a.part_l[pi] = l;
+          a.part_c[pi] = lc;
         }
       } else if constexpr (BWD) {
         // chunk accumulator -> dX[row, chunk] * (g / (N T))
@@ -520,7 +548,7 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
         const int cw = (int)min64(kMaxChunk, a.dp - c0);
         // each epilogue warp of a lane quarter stores its half of the chunk
         const int hw = cw / 2;
-        for (int c = (cb / 2) * hw; c < (cb / 2 + 1) * hw; c += 32) {
+        for (int c = half * hw; c < (half + 1) * hw; c += 32) {
           float o[32];
           tmem_ld32_nowait(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(TN + c), o);
           tmem_wait_ld1(o);
@@ -537,7 +565,7 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
       }
     }
     // G' pass: the last stores must complete before the CTA's shared memory goes
-    if (GP && threadIdx.x == 64) bulk_wait_all();
+    if (GP && ((warp - 2) & 3) == 0 && lane == 0) bulk_wait_all();
   }
 
   fence_before();
@@ -546,6 +574,25 @@ __global__ void __launch_bounds__(cthreads(MODE), 1)
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
+}
+
+// Forward finish: lse_i from the partial (max, sum) of every (split, half)
+// of row i (sums in double), and the loss term lse_i - S_ii / T.
+__global__ void contrastive_merge_kernel(ContrastiveArgs a, int n_parts) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= a.n) return;
+  float M = -INFINITY;
+  for (int p = 0; p < n_parts; ++p) M = fmaxf(M, a.part_m[(int64_t)p * a.np + row]);
+  double s = 0.0;
+  for (int p = 0; p < n_parts; ++p) {
+    const int64_t pi = (int64_t)p * a.np + row;
+    const float mp = a.part_m[pi];
+    if (mp == -INFINITY) continue;  // no valid column in this part
+    s += ((double)a.part_l[pi] + (double)a.part_c[pi]) * (double)exp2f(mp - M);
+  }
+  const float lse = (M + (float)log2(s)) * 0.69314718055994531f;  // natural log
+  a.lse_out[row] = lse;
+  a.term_out[row] = lse - a.diag_out[row] / a.T;
 }
 
 // ---------------------------------------------------------------------------
@@ -770,6 +817,14 @@ size_t contrastive_smem_bytes(int mode) {
   return b + 1024;
 }
 
+void contrastive_splits(int64_t np, int *n_splits, int *tiles_per_split) {
+  const int64_t n_tiles = np / CCfg<kModeFwd>::TN;
+  const int64_t want = std::max<int64_t>(1, (n_tiles + 31) / 32);
+  const int64_t tps = (n_tiles + want - 1) / want;
+  *tiles_per_split = (int)tps;
+  *n_splits = (int)((n_tiles + tps - 1) / tps);
+}
+
 cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *Xp, void *XT,
                                     int64_t np, int64_t dp, unsigned *err, cudaStream_t st) {
   dim3 grid((unsigned)(dp / 32), (unsigned)(np / 32)), block(32, 8);
@@ -786,28 +841,30 @@ cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n,
 
 template <int MODE>
 static cudaError_t launch_mode(const CUtensorMap &mx, const CUtensorMap &my, const CUtensorMap &mz,
-                               const CUtensorMap &mw, const ContrastiveArgs &a, int grid,
-                               cudaStream_t st) {
+                               const ContrastiveArgs &a, int grid, cudaStream_t st) {
   const size_t smem = contrastive_smem_bytes(MODE);
   cudaError_t e = cudaFuncSetAttribute(contrastive_kernel<MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  contrastive_kernel<MODE><<<grid, cthreads(MODE), smem, st>>>(mx, my, mz, mw, a);
+  contrastive_kernel<MODE><<<grid, kCThreads, smem, st>>>(mx, my, mz, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_contrastive(int mode, const void *tmX, const void *tmY, const void *tmZ,
-                               const void *tmW, const ContrastiveArgs &a, int grid,
-                               cudaStream_t st) {
-  CUtensorMap mx, my, mz, mw;
+                               const ContrastiveArgs &a, int grid, cudaStream_t st) {
+  CUtensorMap mx, my, mz;
   std::memcpy(&mx, tmX, sizeof mx);
   std::memcpy(&my, tmY, sizeof my);
   std::memcpy(&mz, tmZ ? tmZ : tmX, sizeof mz);
-  std::memcpy(&mw, tmW ? tmW : tmX, sizeof mw);
+  cudaError_t e;
   switch (mode) {
-    case kModeFwd: return launch_mode<kModeFwd>(mx, my, mz, mw, a, grid, st);
-    case kModeBwd: return launch_mode<kModeBwd>(mx, my, mz, mw, a, grid, st);
-    case kModeGp: return launch_mode<kModeGp>(mx, my, mz, mw, a, grid, st);
+    case kModeFwd:
+      e = launch_mode<kModeFwd>(mx, my, mz, a, grid, st);
+      if (e != cudaSuccess) return e;
+      contrastive_merge_kernel<<<(unsigned)((a.n + 255) / 256), 256, 0, st>>>(a, 2 * a.n_splits);
+      return cudaGetLastError();
+    case kModeBwd: return launch_mode<kModeBwd>(mx, my, mz, a, grid, st);
+    case kModeGp: return launch_mode<kModeGp>(mx, my, mz, a, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

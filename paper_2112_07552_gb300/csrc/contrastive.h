@@ -11,20 +11,24 @@ namespace sj {
 struct ContrastiveArgs {
   int64_t n;            // paired rows
   int64_t d;            // embedding width
-  int64_t np, dp;       // padded rows (multiple of 128) and width (multiple of 64)
+  int64_t np, dp;       // padded rows (multiple of 256) and width (multiple of 64)
   float T;              // temperature
   int n_chunks;         // fused backward: output-dimension chunks of <= 384
-  int n_splits;         // G' pass: column splits of a row block
-  int tiles_per_split;  // G' pass: 128-column tiles per split
+  int n_splits;         // forward and G' pass: column splits of a row block
+  int tiles_per_split;  // forward and G' pass: 256-column tiles per split
   // forward outputs
   float *lse_out;       // [n] natural-log logsumexp of the kernel's rows
   float *term_out;      // [n] lse - S_ii
+  float *part_m, *part_l, *part_c;  // [2 n_splits][np] partial max / sum / sum
+                                    // compensation (log2 domain) per (split, half)
+  float *diag_out;      // [n] S_ii * T (accumulator units)
   // backward inputs / outputs
   const float *lse_r;   // row-indexed logsumexp used by the w_r term
   const float *lse_c;   // column-indexed logsumexp used by the w_c term
   float wr, wc;         // weights of the two softmax terms
   const float *grad_loss;  // device scalar
   float *dX;            // [n][d] gradient of the kernel's row operand
+  void *gT;             // G' pass: G'^T (np x np BF16), G' goes through tmZ
   Counters *ctr;
   int debug_timeout;
 };
@@ -45,17 +49,19 @@ struct ContrastiveGemmArgs {
 };
 
 size_t contrastive_smem_bytes(int mode);
+// Column splits of the forward and the G' pass for np padded rows.
+void contrastive_splits(int64_t np, int *n_splits, int *tiles_per_split);
 size_t contrastive_gemm_smem_bytes();
 cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *Xp, void *XT,
                                     int64_t np, int64_t dp, unsigned *err, cudaStream_t st);
 cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n, float w1,
                                     float w2, float *loss, cudaStream_t st);
-// tmX/tmY/tmZ/tmW: 128-byte CUtensorMap objects (X, Y: box 64 x 128; Z: box
-// 64 x 64 in the fused backward; G' and G'^T maps with box 64 x 128 in the
-// G' pass; null where the mode reads none)
+// tmX/tmY/tmZ: 128-byte CUtensorMap objects (X, Y: box 64 x 128; Z: Z^T with
+// box 64 x 64 in the fused backward, the G' map with box 64 x 128 in the G'
+// pass, null in the forward).  The forward also launches the merge of its
+// partial row states into lse_out and term_out.
 cudaError_t launch_contrastive(int mode, const void *tmX, const void *tmY, const void *tmZ,
-                               const void *tmW, const ContrastiveArgs &a, int grid,
-                               cudaStream_t st);
+                               const ContrastiveArgs &a, int grid, cudaStream_t st);
 // tmG: G or G^T (box 64 x 128); tmZ: Z^T (box 64 x 64)
 cudaError_t launch_contrastive_gemm(const void *tmG, const void *tmZ, const ContrastiveGemmArgs &a,
                                     int grid, cudaStream_t st);
