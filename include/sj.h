@@ -202,9 +202,9 @@ sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t
 /* Backward of sj_contrastive_fwd: given lse from the forward and the upstream
  * gradient grad_loss[0] (device float), writes dA, dB (N x d float32, device).
  * With G = dloss/dS rounded to bfloat16 (N x N, padded to multiples of 128):
- * dA = G B / T and dB = G^T A / T.  When the workspace can hold G and G^T
- * (2 x 2 Np^2 bytes, Np = N rounded up to 128) one pass over the score tiles
- * writes both and two GEMMs read them (three products of 2 N^2 d flops);
+ * dA = G B / T and dB = G^T A / T.  When the workspace can hold G (2 Np^2
+ * bytes, Np = N rounded up to 256) one pass over the score tiles writes it
+ * and two GEMMs read it (three products of 2 N^2 d flops);
  * otherwise, or with SJ_FLAG_FUSED_BACKWARD, G is recomputed per output chunk
  * of 384 dimensions and direction and never stored.  Both give the same G and
  * differ only in FP32 summation order.

@@ -1457,7 +1457,7 @@ namespace {
 struct ContrastivePlan {
   int64_t n, d, np, dp;
   void *Ap, *Bp, *AT, *BT;
-  void *G, *GT;  // materialised backward: dL/dS and its transpose (np x np BF16)
+  void *G;       // materialised backward: dL/dS (np x np BF16)
   float *part;   // forward: partial row states (3 x 2 n_splits x np) and S_ii (np)
   int n_splits, tiles_per_split;
   Counters *ctr;
@@ -1465,8 +1465,8 @@ struct ContrastivePlan {
   unsigned char mA[128], mB[128], mAT[128], mBT[128], mG[128];
 };
 
-// `gmat`: also reserve and map G and G^T (fails with SJ_ERR_OOM before any
-// launch when the workspace cannot hold them).
+// `gmat`: also reserve and map G (fails with SJ_ERR_OOM before any launch
+// when the workspace cannot hold it).
 sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t N, bool bwd,
                             ContrastivePlan &cp, bool gmat = false) {
   if (!h || !A || !B || N < 1) return SJ_ERR_INVALID_ARG;
@@ -1487,7 +1487,7 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
   const size_t gsz = (size_t)cp.np * cp.np * 2;
   const size_t psz = ((size_t)6 * cp.n_splits + 1) * cp.np * 4;
   size_t bytes = 2 * op + (bwd ? 2 * op : 0) + sizeof(Counters) + (size_t)2 * N * 4 + 8 * 256 +
-                 (gmat ? 2 * gsz + 2 * 256 : 0) + (bwd ? 0 : psz + 256);
+                 (gmat ? gsz + 256 : 0) + (bwd ? 0 : psz + 256);
   sj_status s = ensure_ws(h, bytes);
   if (s != SJ_OK) return s;
   Arena ar{static_cast<unsigned char *>(h->ws), h->ws_size, 0};
@@ -1498,10 +1498,9 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
   cp.AT = bwd ? ar.take(op) : nullptr;
   cp.BT = bwd ? ar.take(op) : nullptr;
   cp.G = gmat ? ar.take(gsz) : nullptr;
-  cp.GT = gmat ? ar.take(gsz) : nullptr;
   cp.part = bwd ? nullptr : static_cast<float *>(ar.take(psz));
   if (!cp.ctr || !cp.scratch || !cp.Ap || !cp.Bp || (bwd && (!cp.AT || !cp.BT)) ||
-      (gmat && (!cp.G || !cp.GT)) || (!bwd && !cp.part))
+      (gmat && !cp.G) || (!bwd && !cp.part))
     return SJ_ERR_INTERNAL;
   cudaStream_t st = h->stream;
   SJ_CUDA(cudaMemsetAsync(cp.ctr, 0, sizeof(Counters), st));
@@ -1577,7 +1576,7 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   if (!is_device_ptr(lse) || !is_device_ptr(grad_loss) || !is_device_ptr(dA) || !is_device_ptr(dB))
     return SJ_ERR_INVALID_ARG;
   ContrastivePlan cp;
-  // materialise G and G^T when the workspace allows, else the fused path
+  // materialise G when the workspace allows, else the fused path
   bool gmat = (h->cfg.flags & SJ_FLAG_FUSED_BACKWARD) == 0;
   sj_status s = gmat ? contrastive_setup(h, A, B, N, true, cp, true) : SJ_ERR_OOM;
   if (s == SJ_ERR_OOM) {
@@ -1606,11 +1605,10 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   a.wc = sym ? 0.5f : 0.f;
   const int64_t n_rb = cp.np / 128;
   if (gmat) {
-    // G pass: units = (row block, column split) for balance; G through its
-    // tensor map (TMA stores), G^T by plain stores
+    // G pass: units = (row block, column split) for balance; G written
+    // through its tensor map (TMA stores)
     a.n_splits = cp.n_splits;
     a.tiles_per_split = cp.tiles_per_split;
-    a.gT = cp.GT;
     const int grid = (int)std::min<int64_t>(n_rb * a.n_splits, h->sm_count);
     SJ_CUDA(launch_contrastive(kContrastiveGprime, cp.mA, cp.mB, cp.mG, a, grid, h->stream));
     ContrastiveGemmArgs g{};
@@ -1624,12 +1622,13 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
     g.ctr = cp.ctr;
     const int ggrid = (int)std::min<int64_t>(n_rb * g.n_chunks, h->sm_count);
     g.dX = dA;  // dA = G B / T
-    SJ_CUDA(launch_contrastive_gemm(cp.mG, cp.mBT, g, ggrid, h->stream));
+    SJ_CUDA(launch_contrastive_gemm(false, cp.mG, cp.mBT, g, ggrid, h->stream));
     g.dX = dB;  // dB = G^T A / T
-    unsigned char mGT[128];
-    sj_status ms = tc_encode_2d(h->tc, cp.GT, cp.np, cp.np, 64, 128, mGT);
+    // G^T as an MN-major operand: boxes of 64 columns x 64 rows of G
+    unsigned char mG64[128];
+    sj_status ms = tc_encode_2d(h->tc, cp.G, cp.np, cp.np, 64, 64, mG64);
     if (ms != SJ_OK) return ms;
-    SJ_CUDA(launch_contrastive_gemm(mGT, cp.mAT, g, ggrid, h->stream));
+    SJ_CUDA(launch_contrastive_gemm(true, mG64, cp.mAT, g, ggrid, h->stream));
     return contrastive_finish(h, cp);
   }
   const int grid = (int)std::min<int64_t>(n_rb * a.n_chunks, h->sm_count);

@@ -17,10 +17,10 @@
 //         row and column half, written as partial states that a second
 //         launch merges into l_i and the loss terms.
 //   GP  : the G pass of the materialised backward: the same tiles turned into
-//         G' = w_r (P - I) + w_c (Q - I) in BF16, written as G' (through a
-//         shared-memory staging tile and TMA stores) and G'^T (plain
-//         coalesced stores); two GEMM launches (contrastive_gemm_kernel) then
-//         form dA = G' B and dB = G'^T A, scaled by g / (N T).
+//         G' = w_r (P - I) + w_c (Q - I) in BF16 and written to memory
+//         (through a shared-memory staging tile and TMA stores); two GEMM
+//         launches (contrastive_gemm_kernel) then form dA = G' B and
+//         dB = G'^T A (G' read as an MN-major operand), scaled by g / (N T).
 //   BWD : the fused backward for when G' does not fit in memory: unit =
 //         (128-row block of X, chunk of <= 384 output dimensions); per
 //         128-column tile t, S_t = X_blk Y_t^T (TMEM cols 0..127), G'_t in
@@ -446,25 +446,6 @@ __global__ void __launch_bounds__(kCThreads, 1)
               for (int q = 0; q < 32; ++q)
                 if (!valid || col0 + (cb + c) * 32 + q >= a.n) v[c][q] = 0.f;
           }
-          if constexpr (GP) {
-            // G'^T straight to memory: lanes 2m and 2m + 1 swap one value per
-            // column pair, then each stores two adjacent i of one j (32 bits);
-            // a warp store covers 64 contiguous bytes of two rows of G'^T
-            const bool odd = (lane & 1) != 0;
-            __nv_bfloat16 *gt_col =
-                static_cast<__nv_bfloat16 *>(a.gT) + (int64_t)rb * TM + (r & ~1) + (col0 + cb * 32 + (odd ? 1 : 0)) * a.np;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-#pragma unroll
-              for (int q = 0; q < 32; q += 2) {
-                const float send = odd ? v[c][q] : v[c][q + 1];
-                const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
-                const __nv_bfloat162 pr = odd ? __floats2bfloat162_rn(recv, v[c][q + 1])
-                                              : __floats2bfloat162_rn(v[c][q], recv);
-                *reinterpret_cast<__nv_bfloat162 *>(gt_col + (int64_t)(c * 32 + q) * a.np) = pr;
-              }
-            }
-          }
           // G' into the shared tile (128B-swizzled K-major k-blocks of 64
           // columns): the fused backward's MMA operand, or the G' pass's
           // staging of this warp's column half (the two halves take turns)
@@ -513,8 +494,9 @@ __global__ void __launch_bounds__(kCThreads, 1)
                 flag_timeout(sm, &a.ctr->err_flags);
               } else {
                 const int y0 = rb * TM, x0 = (int)col0 + half * 128;
-                tma_store_2d(&tmZ, sm.g, x0, y0);
-                tma_store_2d(&tmZ, sm.g + TM * BK * 2, x0 + BK, y0);
+                const uint64_t pol = l2_policy_evict_first();
+                tma_store_2d_hint(&tmZ, sm.g, x0, y0, pol);
+                tma_store_2d_hint(&tmZ, sm.g + TM * BK * 2, x0 + BK, y0, pol);
                 bulk_commit();
                 bulk_wait_read_all();
                 mbar_arrive(&sm.st_free[half ^ 1]);
@@ -596,12 +578,15 @@ __global__ void contrastive_merge_kernel(ContrastiveArgs a, int n_parts) {
 }
 
 // ---------------------------------------------------------------------------
-// Materialised backward, second half: dX = (g / (N T)) G Z for G (np x np,
-// BF16, row-major) and Z (np x d) given as Z^T (dp x np, BF16).  Unit =
-// (128-row block, chunk of <= 384 output dimensions), accumulated over
-// K = np in 64-wide k-blocks; a ring slot holds one k-block of G (16 KB) and
-// of the chunk's Z^T rows (<= 48 KB).  Warp 0: TMA, warp 1: MMA, warps 2-5:
-// readout (one TMEM lane quarter each).
+// Materialised backward, second half: dX = (g / (N T)) P Z with P = G or
+// P = G^T, for G (np x np, BF16, row-major) and Z (np x d) given as Z^T
+// (dp x np, BF16).  Unit = (128-row block of P, chunk of <= 384 output
+// dimensions), accumulated over K = np in 64-wide k-blocks; a ring slot holds
+// one k-block of P (16 KB) and of the chunk's Z^T rows (<= 48 KB).  P = G is
+// read K-major (box of 64 columns x 128 rows); P = G^T is read from G itself
+// as an MN-major operand: two boxes of 64 columns (the output rows) x 64 rows
+// (the k-block), 8 KB apart.  Warp 0: TMA, warp 1: MMA, warps 2-5: readout
+// (one TMEM lane quarter each).
 constexpr int kGemmStages = 3;
 constexpr uint32_t kGemmSlot = kOpBytes + kMaxChunk * BK * 2;  // 64 KB
 constexpr int kGemmThreads = 64 + 4 * 32;
@@ -614,6 +599,7 @@ struct alignas(1024) GSmem {
   int abort;
 };
 
+template <bool TRANS>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     contrastive_gemm_kernel(const __grid_constant__ CUtensorMap tmG,
                             const __grid_constant__ CUtensorMap tmZ, ContrastiveGemmArgs a) {
@@ -665,7 +651,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
           ++it;
           mbar_arrive_expect_tx(&sm.full[s], kOpBytes + (uint32_t)cw * BK * 2);
-          tma_load_2d(sm.slot[s], &tmG, kb * BK, rb * TM, &sm.full[s]);
+          if (TRANS) {
+            tma_load_2d(sm.slot[s], &tmG, rb * TM, kb * BK, &sm.full[s]);
+            tma_load_2d(sm.slot[s] + kOpBytes / 2, &tmG, rb * TM + 64, kb * BK, &sm.full[s]);
+          } else {
+            tma_load_2d(sm.slot[s], &tmG, kb * BK, rb * TM, &sm.full[s]);
+          }
           for (int b = 0; b < cw; b += kZBox)
             tma_load_2d(sm.slot[s] + kOpBytes + b * BK * 2, &tmZ, kb * BK, c0 + b, &sm.full[s]);
         }
@@ -701,10 +692,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           for (int p = 0; p < cw; p += kPiece) {
             const int pw = min(kPiece, cw - p);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-              mma_bf16(tmem + (uint32_t)p, sdesc(g0 + kk * 32),
-                       sdesc(z0 + (uint32_t)p * BK * 2 + kk * 32), idesc_bf16(TM, pw),
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              // K = 16 per MMA: 32 bytes along a K-major row, or 16 rows of
+              // 128 bytes (two 8-row atoms) of the MN-major tile
+              const uint64_t ad = TRANS ? sdesc_mn(g0 + kk * 2048, kOpBytes / 2, 1024)
+                                        : sdesc(g0 + kk * 32);
+              mma_bf16(tmem + (uint32_t)p, ad, sdesc(z0 + (uint32_t)p * BK * 2 + kk * 32),
+                       TRANS ? idesc_bf16_amn(TM, pw) : idesc_bf16(TM, pw),
                        (kb > 0 || kk > 0) ? 1u : 0u);
+            }
           }
           mma_commit(&sm.empty[s]);
         }
@@ -871,16 +867,17 @@ cudaError_t launch_contrastive(int mode, const void *tmX, const void *tmY, const
 
 size_t contrastive_gemm_smem_bytes() { return sizeof(GSmem) + 1024; }
 
-cudaError_t launch_contrastive_gemm(const void *tmG, const void *tmZ, const ContrastiveGemmArgs &a,
-                                    int grid, cudaStream_t st) {
+cudaError_t launch_contrastive_gemm(bool trans, const void *tmG, const void *tmZ,
+                                    const ContrastiveGemmArgs &a, int grid, cudaStream_t st) {
   CUtensorMap mg, mz;
   std::memcpy(&mg, tmG, sizeof mg);
   std::memcpy(&mz, tmZ, sizeof mz);
   const size_t smem = contrastive_gemm_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(contrastive_gemm_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = trans ? contrastive_gemm_kernel<true> : contrastive_gemm_kernel<false>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  contrastive_gemm_kernel<<<grid, kGemmThreads, smem, st>>>(mg, mz, a);
+  kern<<<grid, kGemmThreads, smem, st>>>(mg, mz, a);
   return cudaGetLastError();
 }
 

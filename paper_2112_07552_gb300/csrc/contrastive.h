@@ -28,7 +28,6 @@ struct ContrastiveArgs {
   float wr, wc;         // weights of the two softmax terms
   const float *grad_loss;  // device scalar
   float *dX;            // [n][d] gradient of the kernel's row operand
-  void *gT;             // G' pass: G'^T (np x np BF16), G' goes through tmZ
   Counters *ctr;
   int debug_timeout;
 };
@@ -62,8 +61,9 @@ cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n,
 // partial row states into lse_out and term_out.
 cudaError_t launch_contrastive(int mode, const void *tmX, const void *tmY, const void *tmZ,
                                const ContrastiveArgs &a, int grid, cudaStream_t st);
-// tmG: G or G^T (box 64 x 128); tmZ: Z^T (box 64 x 64)
-cudaError_t launch_contrastive_gemm(const void *tmG, const void *tmZ, const ContrastiveGemmArgs &a,
-                                    int grid, cudaStream_t st);
+// dX = P Z * g / (N T) with P = G (trans false; tmG box 64 x 128) or P = G^T
+// (trans true; tmG over the same G with box 64 x 64); tmZ: Z^T (box 64 x 64)
+cudaError_t launch_contrastive_gemm(bool trans, const void *tmG, const void *tmZ,
+                                    const ContrastiveGemmArgs &a, int grid, cudaStream_t st);
 
 }  // namespace sj

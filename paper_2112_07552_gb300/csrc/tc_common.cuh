@@ -75,6 +75,21 @@ __device__ __forceinline__ void tma_store_2d(const void *tmap, const void *src, 
                "r"(su32(src)), "r"(x), "r"(y)
                : "memory");
 }
+// The same with an L2 eviction-priority policy (createpolicy), for output
+// streams that should not displace the operands held in L2.
+__device__ __forceinline__ void tma_store_2d_hint(const void *tmap, const void *src, int x, int y,
+                                                  uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint"
+      " [%0, {%2, %3}], [%1], %4;" ::"l"(reinterpret_cast<uint64_t>(tmap)),
+      "r"(su32(src)), "r"(x), "r"(y), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void bulk_commit() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
@@ -99,11 +114,32 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor for an MN-major operand with 128-byte
+// swizzling: each 128-byte row holds 64 consecutive M (or N) elements of one
+// k, 8 consecutive k rows form a 1024-byte swizzle atom; `lbo` = bytes from
+// one 64-element M block to the next, `sbo` = bytes from one group of 8 k
+// rows to the next.  This is the layout a TMA box of 64 elements (inner, M)
+// by k rows writes with 128-byte swizzling.
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, shape M x N (M = 64/128, N a multiple of 16 up to 256).
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with A MN-major (transpose-A bit), B K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_amn(int M, int N) {
+  return idesc_bf16(M, N) | (1u << 15);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
