@@ -63,7 +63,12 @@ typedef enum {
 typedef enum {
   SJ_FP32 = 0,     /* CUDA-core FP32 FMA tiles (no tensor cores) */
   SJ_BF16 = 1,     /* bfloat16 operands, FP32 accumulation in TMEM */
-  SJ_FP8_E4M3 = 2  /* E4M3 with power-of-two scales: per row for A, per job for B */
+  SJ_FP8_E4M3 = 2, /* E4M3 with power-of-two scales: per row for A, per job for B */
+  SJ_BF16X3 = 3    /* each float32 split into bfloat16 hi + lo; the tensor cores
+                      sum hi.hi + hi.lo + lo.hi (one 3d-wide product): a proven
+                      score error near 2^-16 plus accumulation instead of
+                      2^-8, for data whose near-ties crowd the k-th score;
+                      three times the BF16 work */
 } sj_precision;
 
 /* cfg.flags */
@@ -105,7 +110,8 @@ typedef struct {
   int64_t n_exact;           /* pairs evaluated with the exact accumulator */
   int64_t n_overflow_rows;   /* rows re-ranked against all of B (fallback) */
   int64_t n_pairs;           /* threshold: pairs emitted */
-  double margin_max;         /* reserved (0) */
+  double margin_max;         /* max proven bound m_i >= |s~ - s| over the rows whose
+                                top-k were finalised (0 without a top-k part) */
   double max_abs_err_lowprec;/* max |s~ - s| seen over rescored top-k candidates */
   int64_t n_launches;        /* kernels this call launched */
   int64_t n_tier2_rows;      /* rows finalised with the large candidate tier */

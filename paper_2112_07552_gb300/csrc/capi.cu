@@ -180,6 +180,14 @@ PrecPlan plan_prec(sj_precision p, int64_t d) {
     // one of the d + 32 additions a relative error of 2^-13 of the sum of
     // |products| (<= ||a~|| ||b~||): (d + 32) 2^-13.
     q.acc_coef = ((double)d + 32.0) * std::ldexp(1.0, -13);
+  } else if (p == SJ_BF16X3) {
+    q.fmt = PackFormat::kBF16X3;
+    q.elem = 2;
+    q.BM = kTcBM;
+    q.BN = kTcBN;
+    q.dp = round_up(3 * d, 64);
+    // The BF16 allowance below over the 3d products of the split.
+    q.acc_coef = (3.0 * (double)d + 32.0) * std::ldexp(1.0, -21);
   } else {
     q.fmt = PackFormat::kBF16;
     q.elem = 2;
@@ -296,9 +304,11 @@ void fill_common_stats(sj_stats *st, const Counters &c) {
   st->n_exact = (int64_t)c.n_exact;
   st->n_overflow_rows = (int64_t)c.overflow_rows;
   st->n_tier2_rows = (int64_t)c.tier2_rows;
-  float me;
+  float me, mm;
   std::memcpy(&me, &c.max_err_bits, sizeof me);
+  std::memcpy(&mm, &c.max_margin_bits, sizeof mm);
   st->max_abs_err_lowprec = me;
+  st->margin_max = mm;
 }
 
 // Scratch that the fallback takes from the workspace if it fits, else from a
@@ -405,7 +415,9 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     JobHost &hh = P.host[q];
     jd.nA = r.nA;
     jd.nB = r.nB;
-    hh.self = r.A == r.B && r.nA == r.nB;
+    // a self-join shares one packed copy, except with the hi/lo split, whose
+    // A and B rows are laid out differently
+    hh.self = r.A == r.B && r.nA == r.nB && h->cfg.prec != SJ_BF16X3;
     hh.a_host = r.nA > 0 && !is_device_ptr(r.A);
     hh.b_host = !hh.self && r.nB > 0 && !is_device_ptr(r.B);
     hh.ot_host = r.k > 0 && r.nA > 0 && (!is_device_ptr(r.out_idx) || !is_device_ptr(r.out_score));
@@ -542,6 +554,7 @@ struct Bufs {
   Cand *band = nullptr;
   float *topv = nullptr;
   int *band_cnt = nullptr, *defer = nullptr, *tier2 = nullptr, *ovf = nullptr;
+  int *ovf_band = nullptr;
   long long *ovf_key = nullptr;
   std::vector<int64_t *> st_idx;
   std::vector<float *> st_score;
@@ -589,6 +602,7 @@ bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long lo
     B.tier2 = static_cast<int *>(take(4 * (size_t)rows1));
     B.ovf = static_cast<int *>(take(4 * (size_t)rows1));
     B.ovf_key = static_cast<long long *>(take(8 * (size_t)rows1));
+    B.ovf_band = static_cast<int *>(take(4 * (size_t)rows1));
     for (int q = 0; q < n; ++q)
       if (P.host[q].ot_host) {
         B.st_idx[q] = static_cast<int64_t *>(take((size_t)reqs[q].nA * reqs[q].k * 8));
@@ -619,9 +633,9 @@ bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long lo
 // are appended to redo_rows/redo_keys with the capacity they need.
 sj_status topk_rescan_pass(sj_handle *h, Counters *ctr, const RowMeta *meta, const JobDev &jd,
                            int64_t d, const int *rows, const long long *keys, const int *hrows,
-                           int n, int cap, Arena &ar, int64_t &launches,
-                           std::vector<int> &redo_rows, std::vector<long long> &redo_keys,
-                           int64_t &redo_cap) {
+                           int n, int cap, const Cand *band, const int *band_cnt, Arena &ar,
+                           int64_t &launches, std::vector<int> &redo_rows,
+                           std::vector<long long> &redo_keys, int64_t &redo_cap) {
   cudaStream_t stm = h->stream;
   Scratch lists, count_s, redo_s, big_s, redo_k;
   SJ_CUDA(lists.get(ar, (size_t)n * cap * sizeof(KeyCand)));
@@ -647,6 +661,12 @@ sj_status topk_rescan_pass(sj_handle *h, Counters *ctr, const RowMeta *meta, con
   ra.count = count;
   ra.cap = cap;
   ra.ctr = ctr;
+  if (band) {  // candidates from the rows' complete band lists
+    ra.band = band + jd.band0;
+    ra.band_cnt = band_cnt + jd.slot0;
+    ra.band_lists = jd.lists;
+    ra.band_cap = jd.cap;
+  }
   SJ_CUDA(launch_topk_rescan(ra, stm));
   RankListArgs la{};
   la.A = jd.A;
@@ -698,9 +718,12 @@ sj_status topk_rescan_pass(sj_handle *h, Counters *ctr, const RowMeta *meta, con
 // rows whose lists fit in a bounded scratch (a list can hold all of B), first
 // with 4,096-entry lists, then the cut-off rows once more with the capacity
 // they need.  `rows`/`keys` are device arrays, hrows/hkeys their host copies.
+// With `band` (rows whose band lists are complete) the candidates are the
+// band entries instead of all of B.
 sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const JobDev &jd,
                         int64_t d, const int *rows, const long long *keys, const int *hrows,
-                        const long long *hkeys, int n_rows, Arena &ar, int64_t &launches) {
+                        const long long *hkeys, int n_rows, const Cand *band,
+                        const int *band_cnt, Arena &ar, int64_t &launches) {
   cudaStream_t stm = h->stream;
   const size_t kScratch = (size_t)2 << 30;  // lists + global ranking per chunk
   const int64_t nB = jd.nB;
@@ -713,8 +736,8 @@ sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const 
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n, kScratch / per_row));
     for (int c0 = 0; c0 < n; c0 += chunk) {
       const int nc = std::min(chunk, n - c0);
-      sj_status s = topk_rescan_pass(h, ctr, meta, jd, d, dr + c0, dk + c0, hr + c0, nc, cap, ar,
-                                     launches, rr, rk, rc);
+      sj_status s = topk_rescan_pass(h, ctr, meta, jd, d, dr + c0, dk + c0, hr + c0, nc, cap,
+                                     band, band_cnt, ar, launches, rr, rk, rc);
       if (s != SJ_OK) return s;
     }
     return SJ_OK;
@@ -722,7 +745,9 @@ sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const 
   // pass 1: lists of 4,096 entries; pass 2: the cut-off rows with their key
   // bounds tightened to the k-th best lower bound seen; pass 3: rows still cut
   // off (massive exact ties) with the capacity they need
-  const int cap0 = (int)std::min<int64_t>(nB, 4096);
+  // a band scan's list cannot outgrow the row's band entries
+  const int64_t most = band ? std::min<int64_t>(nB, (int64_t)jd.lists * jd.cap) : nB;
+  const int cap0 = (int)std::min<int64_t>(most, 4096);
   sj_status s = run(rows, keys, hrows, hkeys, n_rows, cap0, redo_rows, redo_keys, redo_cap);
   std::vector<int> again;
   std::vector<long long> again_k;
@@ -738,7 +763,7 @@ sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const 
     again.clear();
     again_k.clear();
     again_cap = 0;
-    const int cap = pass == 2 ? cap0 : (int)std::min<int64_t>(nB, redo_cap);
+    const int cap = pass == 2 ? cap0 : (int)std::min<int64_t>(most, redo_cap);
     s = run(static_cast<int *>(rows2.p), static_cast<long long *>(keys2.p), redo_rows.data(),
             redo_keys.data(), n_redo, cap, again, again_k, again_cap);
     redo_rows.swap(again);
@@ -753,16 +778,19 @@ sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const 
 sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, unsigned n_ovf,
                             Arena &ar, int64_t &launches) {
   cudaStream_t stm = h->stream;
-  std::vector<int> grow(n_ovf);
+  std::vector<int> grow(n_ovf), gband(n_ovf);
   std::vector<long long> gkey(n_ovf);
   SJ_CUDA(cudaMemcpyAsync(grow.data(), B.ovf, (size_t)n_ovf * 4, cudaMemcpyDeviceToHost, stm));
   SJ_CUDA(cudaMemcpyAsync(gkey.data(), B.ovf_key, (size_t)n_ovf * 8, cudaMemcpyDeviceToHost, stm));
+  SJ_CUDA(cudaMemcpyAsync(gband.data(), B.ovf_band, (size_t)n_ovf * 4, cudaMemcpyDeviceToHost,
+                          stm));
   SJ_CUDA(cudaStreamSynchronize(stm));
-  std::vector<std::pair<int, int>> by_job(n_ovf);  // (job, index)
+  // (job * 2 + band-complete, index): rows of one job and kind are contiguous
+  std::vector<std::pair<int, int>> by_job(n_ovf);
   for (unsigned t = 0; t < n_ovf; ++t) {
     auto it = std::upper_bound(P.jobs.begin(), P.jobs.end(), (int64_t)grow[t],
                                [](int64_t x, const JobDev &jd) { return x < jd.row0; });
-    by_job[t] = {(int)(it - P.jobs.begin()) - 1, (int)t};
+    by_job[t] = {((int)(it - P.jobs.begin()) - 1) * 2 + (gband[t] ? 1 : 0), (int)t};
   }
   std::sort(by_job.begin(), by_job.end());
   Scratch rows_s, keys_s;
@@ -771,7 +799,7 @@ sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, uns
   std::vector<int> lrow(n_ovf);
   std::vector<long long> lkey(n_ovf);
   for (unsigned t = 0; t < n_ovf; ++t) {
-    const int q = by_job[t].first, src = by_job[t].second;
+    const int q = by_job[t].first / 2, src = by_job[t].second;
     lrow[t] = (int)(grow[src] - P.jobs[q].row0);
     lkey[t] = gkey[src];
   }
@@ -781,10 +809,12 @@ sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, uns
   for (unsigned t0 = 0; t0 < n_ovf;) {
     unsigned t1 = t0;
     while (t1 < n_ovf && by_job[t1].first == by_job[t0].first) ++t1;
-    const JobDev &jd = P.jobs[by_job[t0].first];
+    const JobDev &jd = P.jobs[by_job[t0].first / 2];
+    const bool band = (by_job[t0].first & 1) != 0;
     sj_status s = topk_fallback(h, B.ctr, B.meta, jd, P.d, static_cast<int *>(rows_s.p) + t0,
                                 static_cast<long long *>(keys_s.p) + t0, lrow.data() + t0,
-                                lkey.data() + t0, (int)(t1 - t0), ar, launches);
+                                lkey.data() + t0, (int)(t1 - t0), band ? B.band : nullptr,
+                                B.band_cnt, ar, launches);
     if (s != SJ_OK) return s;
     t0 = t1;
   }
@@ -890,6 +920,7 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
     fa.tier2_rows = B.tier2;
     fa.overflow_rows = B.ovf;
     fa.overflow_key = B.ovf_key;
+    fa.overflow_band = B.ovf_band;
     fa.ctr = B.ctr;
     SJ_CUDA(launch_topk_finalize(fa, h->sm_count, stm));
     launches += P.rows > 0 ? 3 : 0;
@@ -1053,7 +1084,7 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
       jd.out_score = hh.ot_host ? B.st_score[q] : r.out_score;
       jd.out_pairs = (r.thr && !hh.op_host && r.capacity > 0) ? reinterpret_cast<PairOut *>(r.out)
                                                               : nullptr;
-      jd.gmaxB[0] = jd.gmaxB[1] = jd.gmaxB[2] = 0.f;
+      jd.gmaxB[0] = jd.gmaxB[1] = jd.gmaxB[2] = jd.gmaxB[3] = 0.f;
       jd.bmax = 0.f;
       jd.eB = 0;
       jd.n_pairs = 0;
@@ -1122,7 +1153,6 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
       st->ms_score = ev.ms(1, 2);
       st->ms_select = ev.ms(2, 3);
       st->ms_total = ev.ms(0, 3);
-      st->margin_max = 0.0;
       st->graph_replayed = used_graph ? 1 : 0;
       st->padded_pair_scores = P.padded_pairs;
     }
@@ -1160,6 +1190,7 @@ void add_stats(sj_stats *acc, const sj_stats &one) {
   acc->graph_replayed += one.graph_replayed;
   acc->padded_pair_scores += one.padded_pair_scores;
   acc->max_abs_err_lowprec = std::max(acc->max_abs_err_lowprec, one.max_abs_err_lowprec);
+  acc->margin_max = std::max(acc->margin_max, one.margin_max);
 }
 
 // Jobs [lo, hi) in as few groups as the workspace budget allows: a range
@@ -1365,7 +1396,8 @@ sj_status sj_autotune_load(sj_handle *h, const char *path) {
 
 sj_status sj_create(sj_handle **out, const sj_config *cfg) {
   if (!out || !cfg || cfg->d < 1) return SJ_ERR_INVALID_ARG;
-  if (cfg->prec != SJ_FP32 && cfg->prec != SJ_BF16 && cfg->prec != SJ_FP8_E4M3)
+  if (cfg->prec != SJ_FP32 && cfg->prec != SJ_BF16 && cfg->prec != SJ_FP8_E4M3 &&
+      cfg->prec != SJ_BF16X3)
     return SJ_ERR_INVALID_ARG;
   if (cfg->d > (1 << 20)) return SJ_ERR_UNSUPPORTED;
   *out = nullptr;

@@ -124,12 +124,17 @@ __device__ __forceinline__ void row_push_heap(RowCtx &r, float *heap, const Scor
 // Margin m_i: |s~_ij - s_ij| <= m_i for every j.
 //   <a,b> - <a~,b~> = <a - a~, b> + <a~, b - b~>  (Cauchy-Schwarz on each)
 //   plus the accumulation error of the scoring pass, acc_coef ||a~|| ||b~||.
+// With the hi/lo split the products summed are hi.hi + hi.lo + lo.hi =
+// <a~, b~> - <a_lo, b_lo> (a~ = a_hi + a_lo), so the dropped term adds
+// ||a_lo|| ||b_lo||, and the accumulation acts on a sum of |products| at most
+// (||a_hi|| + ||a_lo||)(||b_hi|| + ||b_lo||), the qnrm of the split.
 // All factors are upper bounds, combined with upward rounding.
 __device__ __forceinline__ float row_margin(const RowMeta &m, const float *gmaxB, float acc_coef) {
   float t1 = __fmul_ru(m.qerr, gmaxB[0]);
   float t2 = __fmul_ru(m.qnrm, gmaxB[2]);
   float t3 = __fmul_ru(__fmul_ru(acc_coef, m.qnrm), gmaxB[1]);
-  return __fadd_ru(__fadd_ru(t1, t2), t3);
+  float t4 = __fmul_ru(m.lonrm, gmaxB[3]);
+  return __fadd_ru(__fadd_ru(__fadd_ru(t1, t2), t3), t4);
 }
 
 // `local` is the row within its job; `list` numbers the row's band lists:

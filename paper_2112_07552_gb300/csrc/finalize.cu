@@ -110,12 +110,14 @@ __device__ void fin_row(const TopkFinalArgs &a, int64_t g, FinSmemLayout<CMAX> &
   }
   const float kth = n_all >= k ? fkey_inv(T) : -INFINITY;
   const float m = row_margin(a.metaA[jb.a_prow0 + i], jb.gmaxB, a.acc_coef);
+  if (threadIdx.x == 0) atomicMax(&a.ctr->max_margin_bits, __float_as_uint(m));
   if (s_overflow) {
     if (threadIdx.x == 0) {
       // At least k rows have s~ >= kth, hence s >= kth - m: every exact top-k
       // member has s >= kth - m.  Key of that bound, rounded down.
       unsigned slot = atomicAdd(&a.ctr->overflow_rows, 1u);
       a.overflow_rows[slot] = (int)g;
+      if (a.overflow_band) a.overflow_band[slot] = 0;  // needs the rescan of all of B
       a.overflow_key[slot] = kth == -INFINITY
                                  ? LLONG_MIN
                                  : __float2ll_rd(__fmul_rd(__fsub_rd(kth, m), 0x1p60f));
@@ -142,10 +144,12 @@ __device__ void fin_row(const TopkFinalArgs &a, int64_t g, FinSmemLayout<CMAX> &
     if (threadIdx.x == 0) {
       unsigned slot = atomicAdd(n_defer, 1u);
       defer[slot] = (int)g;
-      if (defer_key)
+      if (defer_key) {  // the last tier: to the fallback, which scans the band lists
         defer_key[slot] = kth == -INFINITY
                               ? LLONG_MIN
                               : __float2ll_rd(__fmul_rd(__fsub_rd(kth, m), 0x1p60f));
+        if (a.overflow_band) a.overflow_band[slot] = 1;
+      }
     }
     return;
   }
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(kFinWarps * 32)
   WarpFinSmem &w = reinterpret_cast<WarpFinSmem *>(smem_raw)[wib];
   const int64_t d = a.d;
   unsigned long long my_cand = 0;
-  float my_err = 0.f;
+  float my_err = 0.f, my_margin = 0.f;
   if (a.ctr->err_flags) return;
   const int64_t nwarps = (int64_t)gridDim.x * kFinWarps;
   const int64_t g0 = (int64_t)blockIdx.x * kFinWarps + wib;
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(kFinWarps * 32)
       kth = fkey_inv(T);
     }
     const float m = row_margin(a.metaA[jb.a_prow0 + i], jb.gmaxB, a.acc_coef);
+    my_margin = fmaxf(my_margin, m);
     const float theta = __fsub_rd(kth, __fmul_ru(2.f, m));
     // candidates: band entries >= theta, compacted in list order
     int n = 0;
@@ -430,6 +435,7 @@ __global__ void __launch_bounds__(kFinWarps * 32)
   }
   my_err = fmaxf(my_err, __shfl_xor_sync(FULL, my_err, 1));
   my_err = fmaxf(my_err, __shfl_xor_sync(FULL, my_err, 2));
+  if (lane == 0 && my_margin > 0.f) atomicMax(&a.ctr->max_margin_bits, __float_as_uint(my_margin));
   if (lane == 0 && my_cand) {
     atomicAdd(&a.ctr->n_candidates, my_cand);
     atomicAdd(&a.ctr->n_rescored, my_cand);
@@ -497,6 +503,45 @@ __global__ void __launch_bounds__(256) topk_rescan_kernel(RescanArgs a) {
   }
   if (threadIdx.x == 0)
     atomicAdd(&a.ctr->n_rescored, (unsigned long long)((c1 - c0) * (int64_t)nr));
+}
+
+// Fallback for rows whose band lists are complete but hold more candidates
+// than the block tiers take: Dot2 of every band entry of the row (a superset
+// of the candidates >= the row's key bound, since the lists are) instead of
+// all of B, kept when its upper bound reaches the key bound, into the same
+// (U, L, j) lists as the rescan.  One block per row.
+__global__ void __launch_bounds__(256) topk_bandscan_kernel(RescanArgs a) {
+  extern __shared__ __align__(16) float arow[];  // the row, d floats
+  const int r = blockIdx.x;
+  const int i = a.rows[r];
+  for (int64_t t = threadIdx.x; t < a.d; t += blockDim.x) arow[t] = a.A[(int64_t)i * a.d + t];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const float na = a.metaA[i].nrm;
+  const long long key = a.keys[r];
+  const int *cnts = a.band_cnt + (int64_t)i * a.band_lists;
+  const Cand *bands = a.band + (int64_t)i * a.band_lists * a.band_cap;
+  unsigned long long done = 0;
+  for (int s = 0; s < a.band_lists; ++s) {
+    const int cs = cnts[s];
+    const int cnt = min(cs < 0 ? -cs - 1 : cs, a.band_cap);
+    const Cand *bl = bands + (int64_t)s * a.band_cap;
+    for (int q = warp; q < cnt; q += nwarps) {
+      const int32_t j = bl[q].j;
+      float hi, lo;
+      dot2_warp(arow, a.B + (int64_t)j * a.d, a.d, hi, lo);
+      if (lane == 0) {
+        const long long K = dot2_key(hi, lo);
+        const long long D = dot2_halfwidth(a.dot2_coef_key, na, a.metaB[j].nrm);
+        if (K + D >= key) {
+          const int slot = atomicAdd(a.count + r, 1);
+          if (slot < a.cap) a.lists[(int64_t)r * a.cap + slot] = KeyCand{K + D, K - D, j, 0};
+        }
+        ++done;
+      }
+    }
+  }
+  if (lane == 0 && done) atomicAdd(&a.ctr->n_rescored, done);
 }
 
 // Rank each rescanned row from its (U, L, j) list.  Lists of up to kCMax
@@ -912,6 +957,15 @@ size_t topk_rank_global_row_bytes(int64_t n) {
 
 cudaError_t launch_topk_rescan(const RescanArgs &a, cudaStream_t st) {
   if (a.n_rows == 0 || a.nB == 0) return cudaSuccess;
+  if (a.band) {
+    const size_t smem = (size_t)a.d * sizeof(float);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(topk_bandscan_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    topk_bandscan_kernel<<<(unsigned)a.n_rows, 256, smem, st>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)kRescanRows * a.d * sizeof(float);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(topk_rescan_kernel,

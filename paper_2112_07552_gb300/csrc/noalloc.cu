@@ -32,6 +32,7 @@ constexpr int kNoAllocThreads = 256;
 // per slot: U, L (8 B), Exact (40 B), j, v, perm, perm2, grp, sc (4 B), flag (1 B)
 constexpr size_t kSlotBytes = (size_t)kNoAllocMaxB * (8 + 8 + sizeof(Exact) + 6 * 4 + 1);
 constexpr size_t kStatusBytes = 256;  // Counters of the current call, cleared per call
+static_assert(sizeof(Counters) <= kStatusBytes, "status area too small");
 constexpr size_t kScratchBytes = kStatusBytes + (size_t)kNoAllocBlocks * kSlotBytes;  // ~5.2 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];

@@ -129,14 +129,16 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
 // One warp per packed row, kPrepWarps rows per block.  Segments hold at least
 // 128 rows, so a block's rows fall in at most two segments: one binary search
 // per block, and the B-side maxima are reduced per block before the atomics.
-template <typename OutT>
+// X3: the hi/lo split, a row of 3d bfloat16 ([hi | hi | lo] for A rows,
+// [hi | lo | hi] for B rows; zeros after 3d).
+template <typename OutT, bool X3 = false>
 __global__ void __launch_bounds__(kPrepWarps * 32)
     prepare_kernel(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows, int64_t d,
                    OutT *__restrict__ Xp, int64_t dp, RowMeta *__restrict__ meta,
                    Counters *ctr) {
   __shared__ int s_seg0;
   __shared__ int s_seg[kPrepWarps];
-  __shared__ float s_m[kPrepWarps][3];
+  __shared__ float s_m[kPrepWarps][4];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t row0 = (int64_t)blockIdx.x * kPrepWarps;
   if (threadIdx.x == 0) s_seg0 = find_seg(segs, n_segs, row0);
@@ -144,14 +146,62 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
   const int64_t prow = row0 + wib;
   int si = s_seg0;
   while (si + 1 < n_segs && segs[si + 1].prow0 <= prow) ++si;
-  float mx[3] = {0.f, 0.f, 0.f};
+  float mx[4] = {0.f, 0.f, 0.f, 0.f};
   if (prow < prows) {
     const PackSeg sg = segs[si];
     const int64_t local = prow - sg.prow0;
     OutT *dst = Xp + prow * dp;
     if (local >= sg.n) {
       for (int64_t k = lane; k < dp; k += 32) dst[k] = OutT(0.f);
-      if (lane == 0) meta[prow] = RowMeta{0.f, 0.f, 0.f, 0};
+      if (lane == 0) meta[prow] = RowMeta{0.f, 0.f, 0.f, 0, 0.f};
+    } else if constexpr (X3) {
+      const float *src = sg.src + local * d;
+      float ns = 0.f, nc = 0.f;   // ||x||^2
+      float hs = 0.f, hc = 0.f;   // ||hi||^2
+      float ls = 0.f, lc = 0.f;   // ||lo||^2
+      float es = 0.f, ec = 0.f;   // ||x - hi - lo||^2
+      bool bad = false;
+      const bool a_side = sg.side == 0;
+      for (int64_t k = lane; k < d; k += 32) {
+        float x = src[k];
+        if (!isfinite(x)) { bad = true; x = 0.f; }
+        const OutT hi = OutT(x);
+        const float r = __fsub_rn(x, float(hi));  // exact: x minus its rounding
+        const OutT lo = OutT(r);
+        const float e = __fsub_rn(r, float(lo));  // exact as well
+        dst[k] = hi;
+        dst[d + k] = a_side ? hi : lo;
+        dst[2 * d + k] = a_side ? lo : hi;
+        acc_sq(x, ns, nc);
+        acc_sq(float(hi), hs, hc);
+        acc_sq(float(lo), ls, lc);
+        acc_sq(e, es, ec);
+      }
+      for (int64_t k = 3 * d + lane; k < dp; k += 32) dst[k] = OutT(0.f);
+      const bool any_bad = __any_sync(0xffffffffu, bad);
+      const float n2 = warp_sumsq2(ns, nc);
+      const float h2 = warp_sumsq2(hs, hc);
+      const float l2 = warp_sumsq2(ls, lc);
+      const float e2 = warp_sumsq2(es, ec);
+      if (lane == 0) {
+        unsigned flags = 0;
+        if (any_bad) flags |= kErrNonFinite;
+        else if (!(fabsf(n2 - 1.0f) <= 1e-5f)) flags |= kErrNotUnit;
+        if (flags) atomicOr(&ctr->err_flags, flags);
+        RowMeta m;
+        m.nrm = sqrt_up(n2);
+        m.lonrm = l2 > 0.f ? sqrt_up(l2) : 0.f;
+        m.qnrm = __fadd_ru(sqrt_up(h2), m.lonrm);
+        m.qerr = e2 > 0.f ? sqrt_up(e2) : 0.f;
+        m.sexp = 0;
+        meta[prow] = m;
+        if (sg.side != 0) {
+          mx[0] = m.nrm;
+          mx[1] = m.qnrm;
+          mx[2] = m.qerr;
+          mx[3] = m.lonrm;
+        }
+      }
     } else {
       const float *src = sg.src + local * d;
       constexpr bool kE4M3 = std::is_same<OutT, __nv_fp8_e4m3>::value;
@@ -211,6 +261,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
         m.qnrm = sqrt_up(q2);
         m.qerr = e2 > 0.f ? sqrt_up(e2) : 0.f;
         m.sexp = e;
+        m.lonrm = 0.f;
         meta[prow] = m;
         if (sg.side != 0) {
           mx[0] = m.nrm;
@@ -225,10 +276,11 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
     s_m[wib][0] = mx[0];
     s_m[wib][1] = mx[1];
     s_m[wib][2] = mx[2];
+    s_m[wib][3] = mx[3];
   }
   __syncthreads();
   // B-side maxima: one set of atomics per segment present in the block
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < 4) {
     const int c = threadIdx.x;
     int cur = -1;
     float v = 0.f;
@@ -259,6 +311,10 @@ cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_
       break;
     case PackFormat::kBF16:
       prepare_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(
+          segs, n_segs, jobs, prows, d, static_cast<__nv_bfloat16 *>(Xp), dp, meta, ctr);
+      break;
+    case PackFormat::kBF16X3:
+      prepare_kernel<__nv_bfloat16, true><<<grid, block, 0, st>>>(
           segs, n_segs, jobs, prows, d, static_cast<__nv_bfloat16 *>(Xp), dp, meta, ctr);
       break;
     case PackFormat::kFP8:

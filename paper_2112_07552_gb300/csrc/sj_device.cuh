@@ -64,6 +64,8 @@ struct Counters {
   unsigned int redo_cap;            // capacity they need
   unsigned int big_rows;            // rescan lists for the global-memory ranker
   unsigned int defer_rows;          // rows the warp finaliser hands to the block tiers
+  unsigned int max_margin_bits;     // max proven margin m_i over finalised top-k rows
+                                    // (float bits, >= 0)
 };
 
 constexpr unsigned kErrNonFinite = 1u;
@@ -74,9 +76,11 @@ constexpr unsigned kErrInternal = 8u;
 // Per-row metadata written by the prepare kernels.
 struct RowMeta {
   float nrm;    // upper bound on ||x|| (float32 row)
-  float qnrm;   // upper bound on ||x~|| (the row the scoring pass sees, dequantised)
-  float qerr;   // upper bound on ||x~ - x||
+  float qnrm;   // upper bound on ||x~|| (the row the scoring pass sees, dequantised;
+                // hi/lo split: on ||hi|| + ||lo||)
+  float qerr;   // upper bound on ||x~ - x|| (hi/lo split: x~ = hi + lo)
   int32_t sexp; // power-of-two scale exponent (FP8), else 0
+  float lonrm;  // hi/lo split: upper bound on ||lo||, else 0
 };
 
 // ---------------------------------------------------------------------------

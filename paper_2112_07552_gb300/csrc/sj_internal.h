@@ -16,7 +16,9 @@
 
 namespace sj {
 
-enum class PackFormat { kF32, kBF16, kFP8 };
+// kBF16X3: rows of 3d bfloat16, [hi | hi | lo] for A rows and [hi | lo | hi]
+// for B rows (x = hi + lo + r, hi = bf16(x), lo = bf16(x - hi)).
+enum class PackFormat { kF32, kBF16, kFP8, kBF16X3 };
 
 struct PairOut {  // layout of sj_pair
   int64_t i, j;
@@ -44,7 +46,8 @@ struct JobDev {
   float bmax;                // E4M3 packing: max |x| over the job's B rows (device-written)
   int32_t pad_e;
   float tau_f;               // tau rounded down to float (+inf: no threshold part)
-  float gmaxB[3];            // max over the job's B rows of {nrm, qnrm, qerr} (device-written)
+  float gmaxB[4];            // max over the job's B rows of {nrm, qnrm, qerr, lonrm}
+                             // (device-written)
   long long tau_key;         // ceil(tau 2^60)
   Exact tau_exact;           // ceil(tau 2^298)
   int64_t *out_idx;          // device top-k outputs (nA x k)
@@ -79,7 +82,8 @@ struct PackSeg {
   int64_t n;
   int64_t prow0;
   int32_t job;
-  int32_t side;      // 0: A rows, 1: B rows, 2: both (self-join); B rows feed jobs[job].gmaxB
+  int32_t side;      // 0: A rows, 1: B rows, 2: both (self-join, not with kBF16X3);
+                     // B rows feed jobs[job].gmaxB
 };
 // Job of global row x given a job q0 <= the answer (rows visited in
 // increasing order): walks forward from q0.
@@ -145,8 +149,11 @@ struct TopkFinalArgs {
   float dot2_coef_key;     // Dot2 error bound per unit norm product, key units
   int *defer_rows;         // rows the warp finaliser leaves to the CTA tiers
   int *tier2_rows;         // rows with more candidates than the first tier holds
-  int *overflow_rows;      // rows for the rescan fallback (global)
-  long long *overflow_key; // their rescan key bounds
+  int *overflow_rows;      // rows for the fallback (global)
+  long long *overflow_key; // their key bounds
+  int *overflow_band;      // per fallback row: 1 when its band lists are complete
+                           // (more candidates than the block tiers take), 0 when
+                           // a list overflowed
   Counters *ctr;
 };
 // Three launches (warp finaliser, two CTA tiers) with device-side row counts;
@@ -171,7 +178,13 @@ struct RescanArgs {
   int *count;              // n_rows (zeroed by the caller)
   int cap;
   Counters *ctr;
+  // band scan (band != nullptr): the candidates are the rows' band-list
+  // entries (lists complete) instead of all of B
+  const Cand *band;        // the job's band lists (job offset applied)
+  const int *band_cnt;     // the job's list counts (job offset applied)
+  int band_lists, band_cap;  // lists per row, entries per list
 };
+// Rescan (all of B) or band scan, by a.band.
 cudaError_t launch_topk_rescan(const RescanArgs &a, cudaStream_t st);
 
 struct RankListArgs {

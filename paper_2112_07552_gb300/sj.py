@@ -31,8 +31,8 @@ SJ_ERR_TIMEOUT = 7
 SJ_ERR_UNSUPPORTED = 8
 SJ_ERR_INTERNAL = 9
 
-SJ_FP32, SJ_BF16, SJ_FP8_E4M3 = 0, 1, 2
-PRECISIONS = {"fp32": SJ_FP32, "bf16": SJ_BF16, "fp8": SJ_FP8_E4M3}
+SJ_FP32, SJ_BF16, SJ_FP8_E4M3, SJ_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp32": SJ_FP32, "bf16": SJ_BF16, "fp8": SJ_FP8_E4M3, "bf16x3": SJ_BF16X3}
 
 SJ_FLAG_SYM_INFONCE = 0x1
 SJ_FLAG_SINGLE_SPLIT = 0x2

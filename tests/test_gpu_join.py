@@ -13,7 +13,7 @@ from paper_2112_07552_gb300 import datagen
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PRECS = ("bf16", "fp32", "fp8")
+PRECS = ("bf16", "fp32", "fp8", "bf16x3")
 
 
 @pytest.fixture(scope="module")
@@ -444,3 +444,29 @@ def test_fp8_scores_within_their_bound(sjmod):
     quant = np.abs(qa @ qb.T - A.astype(np.float64) @ B.astype(np.float64).T).max()
     acc = (d + 32) * 2.0 ** -13 * np.linalg.norm(qa, axis=1).max() * np.linalg.norm(qb, axis=1).max()
     assert 0 < st["max_abs_err_lowprec"] <= quant + acc
+    # the proven per-row margin bounds every pair's quantisation error and
+    # every observed error (it also carries the accumulation allowance)
+    assert st["margin_max"] >= quant and st["margin_max"] >= st["max_abs_err_lowprec"]
+
+
+def test_bf16x3_narrows_dense_bands(sjmod):
+    """One dense cluster (cosines near 0.99 with a spread near 1e-3), k = 50:
+    the BF16 margin band below the k-th score holds more candidates than the
+    lists keep, so rows go to the rescan fallback; the hi/lo split proves a
+    margin an order of magnitude tighter, and both stay exact."""
+    nA, nB, d, k = 256, 20000, 256, 50
+    C = datagen.centres(1, d, 73)
+    A = datagen.clustered(nA, d, 1, 0.1, seed=73, stream=0, C=C)
+    B = datagen.clustered(nB, d, 1, 0.1, seed=73, stream=1, C=C)
+    out = {}
+    for prec in ("bf16", "bf16x3"):
+        J = sjmod.SimilarityJoin(d, prec=prec, device=0)
+        idx, sc, st = J.topk(dev(A), dev(B), k, with_stats=True)
+        J.close()
+        assert_topk(idx, sc, A, B, k)
+        assert st["max_abs_err_lowprec"] <= st["margin_max"]
+        out[prec] = st
+    assert out["bf16x3"]["margin_max"] < out["bf16"]["margin_max"] / 4
+    assert out["bf16"]["n_overflow_rows"] > 0
+    assert out["bf16x3"]["n_overflow_rows"] < out["bf16"]["n_overflow_rows"]
+    assert out["bf16x3"]["n_rescored"] < out["bf16"]["n_rescored"]
