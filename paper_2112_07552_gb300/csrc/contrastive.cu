@@ -59,7 +59,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 
 // Kernel modes: the forward; the fused backward (G' recomputed per output
 // chunk and consumed in shared memory); the G' pass of the materialised
-// backward (G' and its transpose written to global memory).
+// backward (G' written to global memory).
 constexpr int kModeFwd = kContrastiveFwd, kModeBwd = kContrastiveBwdFused,
               kModeGp = kContrastiveGprime;
 

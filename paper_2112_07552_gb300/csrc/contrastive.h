@@ -35,7 +35,7 @@ struct ContrastiveArgs {
 // Kernel modes of launch_contrastive.
 constexpr int kContrastiveFwd = 0;       // lse and loss terms of the kernel's rows
 constexpr int kContrastiveBwdFused = 1;  // dX with G' recomputed per output chunk
-constexpr int kContrastiveGprime = 2;    // G' (tmZ) and G'^T (tmW) written to memory
+constexpr int kContrastiveGprime = 2;    // G' written to memory through tmZ
 
 // dX = (g / (N T)) G Z from a materialised G (np x np BF16) and Z^T (dp x np).
 struct ContrastiveGemmArgs {
