@@ -857,8 +857,10 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
-        "max_abs_err_bf16": float(stats[-1].max_abs_err_lowprec),
-        "margin_max_bf16": float(stats[-1].margin_max),
+        # largest observed |s~ - s| over rescored candidates and largest proven
+        # margin, in the scoring precision of this line
+        "max_abs_err_lowprec": float(stats[-1].max_abs_err_lowprec),
+        "margin_max": float(stats[-1].margin_max),
     }
     if fp8_sample is not None:
         out["fp8_sample"] = fp8_sample
