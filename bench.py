@@ -67,8 +67,9 @@ def parse():
     p.add_argument("--shape", default=None,
                    help="nA,nB override of the workload sizes (profiling runs)")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--prec", choices=["bf16", "bf16x3", "fp8"], default=None,
-                   help="scoring precision override (join and zipf workloads)")
+    p.add_argument("--prec", choices=["bf16", "bf16x3", "fp8", "fp32"], default=None,
+                   help="scoring precision override (join and zipf workloads); fp32 is "
+                        "the CUDA-core comparison form at the same exactness")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--workload", choices=["join", "infonce", "batch", "fp8", "zipf"],
@@ -817,6 +818,15 @@ def main():
     # tensor flops the scoring kernel issues: the hi/lo split multiplies 3d-wide rows
     flops = 2.0 * nA * nB * d * (3 if w["prec"] == "bf16x3" else 1)
     achieved = flops / (ms_score / 1e3) / 1e12
+    bound, peak_source = "tensor", src + " bf16_tflops_sustained"
+    if w["prec"] == "fp8":
+        peak, peak_source = 2.0 * peak, src + " bf16_tflops_sustained x 2 (nominal FP8/BF16)"
+    elif w["prec"] == "fp32":
+        # CUDA-core FMA rate: SMs x 128 FP32 lanes x 2 flop x the SM clock seen
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        bound, peak = "alu", sms * 128 * 2 * mhz * 1e6 / 1e12
+        peak_source = "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sampled)" % (sms, mhz)
     cpu = None
     if world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, A, B, args.cpu_seconds, gpu_out)
@@ -829,14 +839,15 @@ def main():
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": w["prec"], "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp8": "e4m3"}.get(w["prec"], w["prec"]), "data": "synthetic",
         "config": {"workload": w["workload"], "nA": nA, "nB": nB, "d": d, "k": k,
                    "tau": w["tau"], "clusters": w["clusters"], "zipf_s": w.get("zipf_s"),
                    "seed": w["seed"], "l2": "inputs %.1f GB > L2, no flush" % in_gb,
                    "parallelism": "dp%d" % world},
-        "roofline": {"bound": "tensor", "kernel": "score_tc_kernel", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": src + " bf16_tflops_sustained",
+        "roofline": {"bound": bound,
+                     "kernel": "score_simt_kernel" if w["prec"] == "fp32" else "score_tc_kernel",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "peak_source": peak_source,
                      # the kernel changed (margin term, row metadata) after the last
                      # DRAM capture: no traffic figure until it is captured again
                      "traffic": None,
