@@ -165,15 +165,15 @@ def cpu_baseline(w, A, B, budget_s, gpu_out=None):
     """Oracle on a bounded sample of left rows (all of B); returns a dict."""
     import oracle
     rng = np.random.default_rng(1234)
-    rows = rng.choice(w["nA"], size=max(2, oracle.num_threads()), replace=False)
+    rows = rng.choice(w["nA"], size=min(w["nA"], max(2, oracle.num_threads())), replace=False)
     thr = w["tau"] is not None
     t0 = time.perf_counter()
     oracle.topk(A, B, w["k"], rows=rows)
     if thr:
         oracle.threshold(A, B, w["tau"], rows=rows, want_s64=False)
     per_row = (time.perf_counter() - t0) / len(rows)
-    n = int(max(2, min(4096, budget_s / max(per_row, 1e-9))))
-    rows = np.sort(rng.choice(w["nA"], size=n, replace=False))
+    n = int(max(2, min(4096, w["nA"], budget_s / max(per_row, 1e-9))))
+    rows = np.sort(rng.choice(w["nA"], size=min(n, w["nA"]), replace=False))
     t0 = time.perf_counter()
     idx, s32, _ = oracle.topk(A, B, w["k"], rows=rows)
     if thr:
