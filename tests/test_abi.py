@@ -65,3 +65,16 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sj.SjPair) == 24
     assert ctypes.sizeof(sj.SjConfig) == 48
     assert ctypes.sizeof(sj.SjStats) == 4 * 8 + 5 * 8 + 2 * 8 + 3 * 8 + 8
+
+
+def test_header_is_plain_c():
+    """include/sj.h compiles as pedantic C99 (the ABI serves C callers)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    out = subprocess.run([gcc, "-fsyntax-only", "-std=c99", "-Wall", "-Wextra", "-pedantic",
+                          "-Werror", "-x", "c", os.path.join(ROOT, "include", "sj.h")],
+                         capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
