@@ -55,6 +55,8 @@ def _load():
                                       P, P, P]
         lib.sjo_exact_dot.restype = ctypes.c_int
         lib.sjo_exact_dot.argtypes = [P, P, I64, P, P, P]
+        lib.sjo_exact_dot_minus.restype = ctypes.c_int
+        lib.sjo_exact_dot_minus.argtypes = [P, P, I64, ctypes.c_double, P]
         lib.sjo_exact_dot_rounded.restype = None
         lib.sjo_exact_dot_rounded.argtypes = [P, P, I64, P, P]
         lib.sjo_num_threads.restype = ctypes.c_int
@@ -163,6 +165,24 @@ def exact_dot(a, b) -> Fraction:
     v = 0
     for t in range(nd.value - 1, -1, -1):
         v = (v << 32) | int(mag[t])
+    return sign * Fraction(v) * Fraction(2) ** lsb.value
+
+
+def exact_dot_minus(a, b, t: float) -> Fraction:
+    """Exact <a, b> - t (t a double, clamped like a threshold) as a Fraction:
+    the value whose sign decides s >= t."""
+    a = np.ascontiguousarray(a, dtype=np.float32).ravel()
+    b = np.ascontiguousarray(b, dtype=np.float32).ravel()
+    mag = np.zeros(64, np.uint32)
+    lib = _load()
+    sign = lib.sjo_exact_dot_minus(_p(a), _p(b), a.shape[0], _clamp_tau(t), _p(mag))
+    lsb = ctypes.c_int(0)
+    nd = ctypes.c_int(0)
+    lib.sjo_exact_dot(_p(a), _p(b), 0, _p(np.zeros(64, np.uint32)), ctypes.byref(lsb),
+                      ctypes.byref(nd))
+    v = 0
+    for q in range(nd.value - 1, -1, -1):
+        v = (v << 32) | int(mag[q])
     return sign * Fraction(v) * Fraction(2) ** lsb.value
 
 

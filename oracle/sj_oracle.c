@@ -53,10 +53,14 @@
 /* Exact fixed-point accumulator                                            */
 /* ------------------------------------------------------------------------ */
 
-/* value = sum_t dig[t] * 2^(32 t + LSB_EXP).  LSB_EXP is below the smallest
- * double (2^-1074), so products of floats and any double tau add exactly. */
+/* value = sum_t dig[t] * 2^(32 t + LSB_EXP).  A double t = M 2^(e - 53) with
+ * an integer mantissa M < 2^53 has e - 53 >= -1126 (the smallest subnormal,
+ * 2^-1074, is 2^52 2^-1126), and a product of two floats is an integer
+ * < 2^48 times 2^(>= -298); LSB_EXP = -1152 lies below both, so every
+ * product and any finite double tau add exactly.  The top is 2^384, far
+ * above |s| < 2^288 and the clamped |tau| <= 2^290. */
 #define NDIG 48
-#define LSB_EXP (-1120)
+#define LSB_EXP (-1152)
 
 typedef struct {
   int64_t dig[NDIG];
@@ -64,7 +68,8 @@ typedef struct {
 
 static void ex_zero(exact_t *x) { memset(x, 0, sizeof *x); }
 
-/* x += (neg ? -1 : 1) * mag * 2^e, with mag < 2^64 and e - LSB_EXP >= 0. */
+/* x += (neg ? -1 : 1) * mag * 2^e, with mag < 2^64 and e - LSB_EXP >= 0
+ * (true for every caller: see LSB_EXP). */
 static void ex_add(exact_t *x, int neg, uint64_t mag, int e) {
   int pos = e - LSB_EXP;
   int t = pos / 32, r = pos % 32;
@@ -386,6 +391,16 @@ int sjo_exact_dot(const float *a, const float *b, int64_t d, uint32_t *mag,
   exact_dot(a, b, d, &x);
   *lsb_exp = LSB_EXP;
   *ndig = NDIG;
+  return ex_sign_mag(&x, mag);
+}
+
+/* Exact <a, b> - t for a finite double t (|t| <= 2^290), as sign and NDIG
+ * magnitude digits like sjo_exact_dot: the difference every threshold
+ * decision takes the sign of. */
+int sjo_exact_dot_minus(const float *a, const float *b, int64_t d, double t, uint32_t *mag) {
+  exact_t x;
+  exact_dot(a, b, d, &x);
+  ex_sub_double(&x, t);
   return ex_sign_mag(&x, mag);
 }
 

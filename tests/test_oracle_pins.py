@@ -215,6 +215,40 @@ def test_threshold_is_inclusive():
     assert list(j) == [0, 1]
 
 
+@pytest.mark.parametrize("tau", [2.0 ** -1074, -2.0 ** -1074, 2.0 ** -1068, -2.0 ** -1068,
+                                 2.0 ** -1022, 2.0 ** -298, -2.0 ** -298, 0.0, -0.0])
+def test_threshold_subnormal_tau(tau):
+    # Every nonzero score is a multiple of 2^-298, so a tau between 0 and that
+    # quantum separates the exactly-zero pairs from the tiny positive ones:
+    # s = 0 is kept only for tau <= 0, s = 2^-298 for tau <= 2^-298.
+    t = np.float32(2.0 ** -149)
+    A = np.array([[1.0, 1.0, 0.0], [t, 0.0, 0.0]], np.float32)
+    B = np.array([[1.0, -1.0, 0.0],     # s = 0 with row 0
+                  [t, 0.0, 0.0],        # s = 2^-149 with row 0, 2^-298 with row 1
+                  [-t, 0.0, 0.0],       # negatives of the above
+                  [0.0, 0.0, 1.0]], np.float32)
+    check_threshold(A, B, tau)
+    _, j, _, _ = oracle.threshold(A[:1], B[:1], tau)
+    assert list(j) == ([0] if tau <= 0 else [])
+    # the exact difference s - tau every such decision takes the sign of
+    for a in A:
+        for b in B:
+            assert oracle.exact_dot_minus(a, b, tau) == fdot(a, b) - Fraction(tau)
+
+
+def test_exact_dot_minus_matches_fractions():
+    # s - t exactly, for t over the whole double range (subnormal to 2^290)
+    rng = np.random.default_rng(7)
+    ts = [2.0 ** -1074, 3 * 2.0 ** -1074, 2.0 ** -1060 * 1.75, 2.0 ** -1022, 2.0 ** -700,
+          0.85, 1.0 - 2.0 ** -53, 2.0 ** 100 * 1.5, 2.0 ** 290]
+    for trial in range(200):
+        d = int(rng.integers(1, 20))
+        a = rand_floats(rng, d, -140, 4)
+        b = rand_floats(rng, d, -140, 4)
+        t = ts[trial % len(ts)] * (-1.0 if trial % 2 else 1.0)
+        assert oracle.exact_dot_minus(a, b, t) == fdot(a, b) - Fraction(t), (trial, t)
+
+
 # --------------------------------------------------------------------------
 # the paper's construction: one-hot rows make the join an equi-join (Sec. 3.1)
 # --------------------------------------------------------------------------
