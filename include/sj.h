@@ -224,23 +224,44 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
  * allocator's pool, or they must not call cudaMalloc/cudaFree, which can
  * synchronise the device).  The paper has no counterpart: this is a
  * deployment variant of sj_topk.  No handle is needed; the work runs on
- * `stream` (cudaStream_t, NULL = legacy default stream) of the current device
- * and the call returns after that stream drains it.  Results equal sj_topk's.
+ * `stream` (cudaStream_t, NULL = legacy default stream) of the current device.
+ * Results equal sj_topk's.
  *
- * A, B: nA x d and nB x d float32 rows, out_idx/out_score: nA x k, all DEVICE
- * memory owned by the caller.  Limits: nB <= 2048 (larger nB returns
- * SJ_ERR_UNSUPPORTED), 1 <= k <= 1024 (k > nB pads with (-1, -inf)).
+ * A, B: nA x d and nB x d float32 rows, out_idx/out_score: nA x k, all memory
+ * of the CURRENT device (or managed memory) owned by the caller.  Limits:
+ * nB <= 2048 (larger nB returns SJ_ERR_UNSUPPORTED), 1 <= k <= 1024 (k > nB
+ * pads with (-1, -inf)).  Cost: one compensated FP32 dot product per pair on
+ * 32 blocks, far slower than sj_topk when nA is large.
  * Scratch: one fixed device array of about 5.2 MB inside the library, held by
  * every GPU that loads it until the process exits.  The first call on each
- * device resolves that array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls on a device share the
- * array and it keeps the previous call's contents: calls that overlap on the
- * GPU (other threads or streams) race and must be serialised by the caller.
- * Errors: SJ_ERR_INVALID_ARG (null or host pointers, bad sizes),
- * SJ_ERR_UNSUPPORTED, SJ_ERR_NONFINITE, SJ_ERR_NOT_UNIT_NORM, SJ_ERR_CUDA. */
+ * device resolves that array's device address (cudaGetSymbolAddress).  All
+ * calls on a device share the array and it keeps the previous call's contents
+ * (the call clears its status area first): calls that overlap on the GPU
+ * (other threads or streams) race and must be serialised by the caller.
+ * The call is synchronous: it reads its status back and returns after
+ * `stream` has drained its work, so it must not be called while `stream` is
+ * being captured into a CUDA graph (it then returns SJ_ERR_INVALID_ARG
+ * without enqueuing anything).
+ * Errors: SJ_ERR_INVALID_ARG (null, host or other-device pointers, bad sizes,
+ * stream under capture), SJ_ERR_UNSUPPORTED, SJ_ERR_NONFINITE,
+ * SJ_ERR_NOT_UNIT_NORM, SJ_ERR_CUDA (sj_last_error_detail() names the
+ * failing call).  Outputs are undefined on error. */
 sj_status sj_topk_noalloc(const float *A, int64_t nA, const float *B, int64_t nB,
                           int64_t d, int32_t k, int64_t *out_idx, float *out_score,
                           void *stream);
+
+/* Test hook: arm the next sj_topk / sj_threshold / one-job sj_batch call of
+ * this handle to also write what its scoring pass computed, so that the
+ * margin argument can be checked pair by pair: raw[i*nB + j] = s~_ij, the
+ * low-precision score of every pair of the join (float32, in score units,
+ * i.e. E4M3 accumulators already scaled back), and margin[i] = m_i, the
+ * proven bound |s~_ij - s_ij| <= m_i the fused filter relies on.  Both are
+ * DEVICE buffers of the handle's device with room for nA*nB and nA floats.
+ * The armed call runs without graph capture and fails with
+ * SJ_ERR_INVALID_ARG if it holds more than one job; any call disarms the
+ * hook.  Meant for small joins (it writes the whole score matrix).
+ * Errors: SJ_ERR_INVALID_ARG (null, host or other-device buffers). */
+sj_status sj_debug_scores(sj_handle *h, float *raw, float *margin);
 
 /* Static description of a status code. */
 const char *sj_status_string(sj_status s);

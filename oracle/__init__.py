@@ -55,6 +55,8 @@ def _load():
                                       P, P, P]
         lib.sjo_exact_dot.restype = ctypes.c_int
         lib.sjo_exact_dot.argtypes = [P, P, I64, P, P, P]
+        lib.sjo_enclose_all.restype = None
+        lib.sjo_enclose_all.argtypes = [P, P, I64, I64, I64, P, P]
         lib.sjo_exact_dot_minus.restype = ctypes.c_int
         lib.sjo_exact_dot_minus.argtypes = [P, P, I64, ctypes.c_double, P]
         lib.sjo_exact_dot_rounded.restype = None
@@ -166,6 +168,17 @@ def exact_dot(a, b) -> Fraction:
     for t in range(nd.value - 1, -1, -1):
         v = (v << 32) | int(mag[t])
     return sign * Fraction(v) * Fraction(2) ** lsb.value
+
+
+def enclose_all(A, B):
+    """(lo, hi), each nA x nB float64: an interval around the exact s_ij of
+    every pair, from the FP64 naive sum and its rounding-error bound."""
+    A, B = _f32(A), _f32(B)
+    lo = np.empty((A.shape[0], B.shape[0]), np.float64)
+    hi = np.empty_like(lo)
+    if lo.size:
+        _load().sjo_enclose_all(_p(A), _p(B), A.shape[0], B.shape[0], A.shape[1], _p(lo), _p(hi))
+    return lo, hi
 
 
 def exact_dot_minus(a, b, t: float) -> Fraction:

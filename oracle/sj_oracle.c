@@ -216,6 +216,16 @@ static void fp64_enclose(const float *a, const float *b, int64_t d, double *lo,
   *hi = s + w;
 }
 
+/* The enclosure of every pair of a join (step 1 alone): lo/hi are nA x nB,
+ * row-major; the exact s_ij lies in [lo_ij, hi_ij]. */
+void sjo_enclose_all(const float *A, const float *B, int64_t nA, int64_t nB, int64_t d,
+                     double *lo, double *hi) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < nA; ++i)
+    for (int64_t j = 0; j < nB; ++j)
+      fp64_enclose(A + i * d, B + j * d, d, &lo[i * nB + j], &hi[i * nB + j]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Top-k                                                                     */
 /* ------------------------------------------------------------------------ */

@@ -49,15 +49,27 @@ struct Arena {
   }
 };
 
-bool is_device_ptr(const void *p) {
-  if (!p) return false;
+// Where a caller's pointer lives.  Device memory of another GPU is neither
+// usable in place (no peer access is assumed) nor host memory to stage from.
+enum class PtrKind { kHost, kDevice, kOtherDevice };
+
+PtrKind ptr_kind(const void *p, int device) {
+  if (!p) return PtrKind::kHost;
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return PtrKind::kHost;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return PtrKind::kDevice;
+  if (at.type == cudaMemoryTypeDevice)
+    return at.device == device ? PtrKind::kDevice : PtrKind::kOtherDevice;
+  return PtrKind::kHost;
+}
+
+bool is_device_ptr(const void *p, int device) { return p && ptr_kind(p, device) == PtrKind::kDevice; }
+bool is_other_device_ptr(const void *p, int device) {
+  return p && ptr_kind(p, device) == PtrKind::kOtherDevice;
 }
 
 // gamma_n = n u / (1 - n u)
@@ -89,6 +101,8 @@ struct sj_handle {
   cudaEvent_t ev[6]{};
   cudaEvent_t gev[4]{};  // stage events recorded only by captured graphs
   sj::TcContext *tc = nullptr;
+  float *dbg_raw = nullptr;     // sj_debug_scores: armed for the next one-job call
+  float *dbg_margin = nullptr;
 };
 
 namespace {
@@ -102,9 +116,17 @@ sj_status cuda_status(cudaError_t e) {
 // Detail of the last CUDA failure seen by this thread (sj_last_error_detail).
 thread_local char g_err_detail[320] = "";
 
+}  // namespace
+
+void sj::record_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  std::snprintf(g_err_detail, sizeof g_err_detail, "%s at %s:%d (%s): %s",
+                cudaGetErrorName(e), file, line, what, cudaGetErrorString(e));
+}
+
+namespace {
+
 void note_cuda_error(cudaError_t e, const char *what, int line) {
-  std::snprintf(g_err_detail, sizeof g_err_detail, "%s at capi.cu:%d (%s): %s",
-                cudaGetErrorName(e), line, what, cudaGetErrorString(e));
+  sj::record_cuda_error(e, what, "capi.cu", line);
 }
 
 #define SJ_CUDA(call)                          \
@@ -418,11 +440,17 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     // a self-join shares one packed copy, except with the hi/lo split, whose
     // A and B rows are laid out differently
     hh.self = r.A == r.B && r.nA == r.nB && h->cfg.prec != SJ_BF16X3;
-    hh.a_host = r.nA > 0 && !is_device_ptr(r.A);
-    hh.b_host = !hh.self && r.nB > 0 && !is_device_ptr(r.B);
-    hh.ot_host = r.k > 0 && r.nA > 0 && (!is_device_ptr(r.out_idx) || !is_device_ptr(r.out_score));
-    hh.op_host = r.thr && r.capacity > 0 && !is_device_ptr(r.out);
-    hh.nout_dev = r.thr && is_device_ptr(r.n_out);
+    const int dv = h->cfg.device;
+    if (is_other_device_ptr(r.A, dv) || is_other_device_ptr(r.B, dv) ||
+        is_other_device_ptr(r.out_idx, dv) || is_other_device_ptr(r.out_score, dv) ||
+        is_other_device_ptr(r.out, dv) || is_other_device_ptr(r.n_out, dv))
+      return SJ_ERR_INVALID_ARG;
+    hh.a_host = r.nA > 0 && !is_device_ptr(r.A, dv);
+    hh.b_host = !hh.self && r.nB > 0 && !is_device_ptr(r.B, dv);
+    hh.ot_host = r.k > 0 && r.nA > 0 &&
+                 (!is_device_ptr(r.out_idx, dv) || !is_device_ptr(r.out_score, dv));
+    hh.op_host = r.thr && r.capacity > 0 && !is_device_ptr(r.out, dv);
+    hh.nout_dev = r.thr && is_device_ptr(r.n_out, dv);
     jd.row0 = P.rows;
     P.rows += r.nA;
     // packed segments (zero-row segments are left out)
@@ -888,6 +916,8 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
     sa.thr = B.cand;
     sa.thr_cap = thr_cap;
     sa.ctr = B.ctr;
+    sa.raw = h->dbg_raw;
+    sa.raw_m = h->dbg_margin;
     if (h->cfg.prec == SJ_FP32) {
       const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count * 2);
       SJ_CUDA(launch_score_simt(sa, grid, stm));
@@ -1055,7 +1085,7 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
   unsigned long long thr_cap = initial_thr_cap(P);
   bool any_host = false;
   for (const JobHost &hh : P.host) any_host |= hh.a_host || hh.b_host || hh.ot_host || hh.op_host;
-  const bool graphable = !any_host && !(h->cfg.flags & SJ_FLAG_NO_GRAPH);
+  const bool graphable = !any_host && !(h->cfg.flags & SJ_FLAG_NO_GRAPH) && !h->dbg_raw;
   const TableLayout tl = table_layout(P);
   s = ensure_host_tables(h, align_up(tl.bytes, 256) + 16 * (size_t)n);
   if (s != SJ_OK) return s;
@@ -1243,7 +1273,9 @@ sj_status join_batch(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
     const size_t avail = free_b + h->ws_size;
     budget = avail > reserve ? avail - reserve : 0;
   }
-  sj_status s = run_range(h, reqs, 0, n, budget, &acc);
+  sj_status s = (h->dbg_raw && n != 1) ? SJ_ERR_INVALID_ARG
+                                       : run_range(h, reqs, 0, n, budget, &acc);
+  h->dbg_raw = h->dbg_margin = nullptr;  // the test hook arms one call
   if (st) *st = acc;
   return s;
 }
@@ -1503,7 +1535,8 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
                             ContrastivePlan &cp, bool gmat = false) {
   if (!h || !A || !B || N < 1) return SJ_ERR_INVALID_ARG;
   if (N >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
-  if (!is_device_ptr(A) || !is_device_ptr(B)) return SJ_ERR_INVALID_ARG;
+  if (!is_device_ptr(A, h->cfg.device) || !is_device_ptr(B, h->cfg.device))
+    return SJ_ERR_INVALID_ARG;
   SJ_CUDA(cudaSetDevice(h->cfg.device));
   if (h->cc != 103) return SJ_ERR_UNSUPPORTED;
   if (!h->tc) {
@@ -1564,7 +1597,8 @@ extern "C" {
 sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t N, float T,
                              float *loss, float *lse) {
   if (!h || !A || !B || N < 1 || !(T > 0.f) || !loss || !lse) return SJ_ERR_INVALID_ARG;
-  if (!is_device_ptr(loss) || !is_device_ptr(lse)) return SJ_ERR_INVALID_ARG;
+  if (!is_device_ptr(loss, h->cfg.device) || !is_device_ptr(lse, h->cfg.device))
+    return SJ_ERR_INVALID_ARG;
   ContrastivePlan cp;
   sj_status s = contrastive_setup(h, A, B, N, false, cp);
   if (s != SJ_OK) return s;
@@ -1605,7 +1639,9 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
                       const float *lse, const float *grad_loss, float *dA, float *dB) {
   if (!h || !A || !B || N < 1 || !(T > 0.f) || !lse || !grad_loss || !dA || !dB)
     return SJ_ERR_INVALID_ARG;
-  if (!is_device_ptr(lse) || !is_device_ptr(grad_loss) || !is_device_ptr(dA) || !is_device_ptr(dB))
+  const int dv = h->cfg.device;
+  if (!is_device_ptr(lse, dv) || !is_device_ptr(grad_loss, dv) || !is_device_ptr(dA, dv) ||
+      !is_device_ptr(dB, dv))
     return SJ_ERR_INVALID_ARG;
   ContrastivePlan cp;
   // materialise G when the workspace allows, else the fused path
@@ -1676,6 +1712,15 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   a.dX = dB;
   SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mB, cp.mA, cp.mAT, a, grid, h->stream));
   return contrastive_finish(h, cp);
+}
+
+sj_status sj_debug_scores(sj_handle *h, float *raw, float *margin) {
+  if (!h || !raw || !margin) return SJ_ERR_INVALID_ARG;
+  if (!is_device_ptr(raw, h->cfg.device) || !is_device_ptr(margin, h->cfg.device))
+    return SJ_ERR_INVALID_ARG;
+  h->dbg_raw = raw;
+  h->dbg_margin = margin;
+  return SJ_OK;
 }
 
 const char *sj_status_string(sj_status s) {

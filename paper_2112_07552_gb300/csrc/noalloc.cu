@@ -8,10 +8,14 @@
 // device array of fixed size, loaded with the library and kept by every GPU
 // that loads it until the process exits.
 //
-// Computation: for every left row i, a block computes the compensated FP32
-// (Dot2) score interval of every right row j, then ranks all nB candidates
-// exactly with the same block ranker as the main path (rank.cuh), so results
-// equal sj_topk's bit for bit.  Rows are validated as in sj_topk.
+// Computation: a first launch validates every right row once and stores an
+// upper bound on its norm in the scratch; then, for every left row i, a block
+// validates the row, computes the compensated FP32 (Dot2) score interval of
+// every right row j, and ranks all nB candidates exactly with the same block
+// ranker as the main path (rank.cuh), so results equal sj_topk's bit for bit.
+// Rows are validated as in sj_topk.  Cost: one Dot2 per pair on 32 blocks,
+// about nA * nB * d * 2 FP32 FMAs plus the ranking, far slower than sj_topk
+// for large nA; the variant is for small right tables only.
 //
 // Limits: nB <= kNoAllocMaxB right rows (any nA), 1 <= k <= 1024, device
 // pointers only.  The scratch is shared by every call on a device and keeps
@@ -22,6 +26,7 @@
 #include "../../include/sj.h"
 #include "rank.cuh"
 #include "sj_device.cuh"
+#include "sj_internal.h"
 
 namespace sj {
 namespace {
@@ -33,7 +38,9 @@ constexpr int kNoAllocThreads = 256;
 constexpr size_t kSlotBytes = (size_t)kNoAllocMaxB * (8 + 8 + sizeof(Exact) + 6 * 4 + 1);
 constexpr size_t kStatusBytes = 256;  // Counters of the current call, cleared per call
 static_assert(sizeof(Counters) <= kStatusBytes, "status area too small");
-constexpr size_t kScratchBytes = kStatusBytes + (size_t)kNoAllocBlocks * kSlotBytes;  // ~5.2 MB
+constexpr size_t kNormBytes = (size_t)kNoAllocMaxB * sizeof(float);  // right-row norm bounds
+constexpr size_t kScratchBytes =
+    kStatusBytes + kNormBytes + (size_t)kNoAllocBlocks * kSlotBytes;  // ~5.2 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -87,12 +94,26 @@ __device__ __forceinline__ float check_row(const float *x, int64_t d, Counters *
   return __fsqrt_ru(__fmul_ru(fmaxf(n2, 0.f), 1.0f + 0x1p-20f));
 }
 
+// Validation and norm bound of every right row, once per call (warp per row).
+__global__ void __launch_bounds__(kNoAllocThreads)
+    noalloc_norms_kernel(const float *B, int64_t nB, int64_t d, unsigned char *scratch) {
+  Counters *ctr = reinterpret_cast<Counters *>(scratch);
+  float *nrm = reinterpret_cast<float *>(scratch + kStatusBytes);
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = w; j < nB; j += nw) {
+    const float nb = check_row(B + j * d, d, ctr);
+    if ((threadIdx.x & 31) == 0) nrm[j] = nb;
+  }
+}
+
 __global__ void __launch_bounds__(kNoAllocThreads)
     topk_noalloc_kernel(const float *A, int64_t nA, const float *B, int64_t nB, int64_t d, int k,
                         float dot2_coef_key, int64_t *out_idx, float *out_score,
                         unsigned char *scratch) {
   Counters *ctr = reinterpret_cast<Counters *>(scratch);
-  unsigned char *base = scratch + kStatusBytes + (size_t)blockIdx.x * kSlotBytes;
+  const float *nrm_bs = reinterpret_cast<const float *>(scratch + kStatusBytes);
+  unsigned char *base = scratch + kStatusBytes + kNormBytes + (size_t)blockIdx.x * kSlotBytes;
   const int n_pad = next_pow2(nB > 0 ? (int)nB : 1);
   CandArrays c;
   c.U = reinterpret_cast<long long *>(base);
@@ -107,17 +128,24 @@ __global__ void __launch_bounds__(kNoAllocThreads)
   c.flag = reinterpret_cast<uint8_t *>(c.sc + n_pad);
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
   __shared__ float s_nrm_a;
+  __shared__ unsigned s_bad;
   for (int64_t i = blockIdx.x; i < nA; i += gridDim.x) {
     const float *a = A + i * d;
     if (warp == 0) {
       float na = check_row(a, d, ctr);
-      if (lane == 0) s_nrm_a = na;
+      if (lane == 0) {
+        s_nrm_a = na;
+        s_bad = *(volatile unsigned *)&ctr->err_flags & (kErrNonFinite | kErrNotUnit);
+      }
     }
     __syncthreads();
+    // an input failed validation: the call returns an error and its outputs
+    // are undefined, so no row is ranked any more (uniform over the block)
+    if (s_bad) break;
     const float nrm_a = s_nrm_a;
     for (int64_t j = warp; j < nB; j += nwarps) {
       const float *b = B + j * d;
-      const float nrm_b = check_row(b, d, ctr);
+      const float nrm_b = nrm_bs[j];
       float hi, lo;
       dot2_warp(a, b, d, hi, lo);
       if (lane == 0) {
@@ -134,14 +162,29 @@ __global__ void __launch_bounds__(kNoAllocThreads)
   }
 }
 
-bool is_device_memory(const void *p) {
+// Memory the current device `dev` can use in place: its own device memory or
+// managed memory (device memory of another GPU is refused: no peer access is
+// assumed).
+bool is_device_memory(const void *p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
+
+// Returns SJ_ERR_CUDA (or SJ_ERR_OOM) with sj_last_error_detail() set.
+sj_status cuda_fail(cudaError_t e, const char *what, int line) {
+  record_cuda_error(e, what, "noalloc.cu", line);
+  return e == cudaErrorMemoryAllocation ? SJ_ERR_OOM : SJ_ERR_CUDA;
+}
+#define NA_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t e__ = (call);                                  \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call, __LINE__); \
+  } while (0)
 
 }  // namespace
 }  // namespace sj
@@ -156,14 +199,19 @@ extern "C" sj_status sj_topk_noalloc(const float *A, int64_t nA, const float *B,
   if (d > (1 << 20) || nA >= (1ll << 31)) return SJ_ERR_UNSUPPORTED;
   if (nA == 0) return SJ_OK;
   if (!A || !out_idx || !out_score || (nB > 0 && !B)) return SJ_ERR_INVALID_ARG;
-  if (!is_device_memory(A) || !is_device_memory(out_idx) || !is_device_memory(out_score) ||
-      (nB > 0 && !is_device_memory(B)))
-    return SJ_ERR_INVALID_ARG;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SJ_ERR_CUDA;
-  unsigned char *scratch = nullptr;
-  if (scratch_address(dev, &scratch) != cudaSuccess) return SJ_ERR_CUDA;
+  NA_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return SJ_ERR_UNSUPPORTED;
+  if (!is_device_memory(A, dev) || !is_device_memory(out_idx, dev) ||
+      !is_device_memory(out_score, dev) || (nB > 0 && !is_device_memory(B, dev)))
+    return SJ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The call reads its status back and synchronises: it cannot be captured.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  NA_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return SJ_ERR_INVALID_ARG;
+  unsigned char *scratch = nullptr;
+  NA_CUDA(scratch_address(dev, &scratch));
   // Dot2 error coefficient in key units (as in the main path): lane chains of
   // n = ceil(d/32) products plus a 5-level combination.
   const double u = 0x1p-24;
@@ -172,15 +220,19 @@ extern "C" sj_status sj_topk_noalloc(const float *A, int64_t nA, const float *B,
   const double coef = 2.0 * (g * g + 10.0 * u * (g + 5.0 * u)) * (1.0 + 1e-6) * 0x1p60;
   float coef_key = (float)coef;
   if ((double)coef_key < coef) coef_key = nextafterf(coef_key, INFINITY);
-  if (cudaMemsetAsync(scratch, 0, kStatusBytes, st) != cudaSuccess) return SJ_ERR_CUDA;
+  NA_CUDA(cudaMemsetAsync(scratch, 0, kStatusBytes, st));
+  if (nB > 0) {
+    const int ngrid = (int)((nB + kNoAllocThreads / 32 - 1) / (kNoAllocThreads / 32));
+    noalloc_norms_kernel<<<ngrid, kNoAllocThreads, 0, st>>>(B, nB, d, scratch);
+    NA_CUDA(cudaGetLastError());
+  }
   const int grid = (int)(nA < kNoAllocBlocks ? nA : kNoAllocBlocks);
   topk_noalloc_kernel<<<grid, kNoAllocThreads, 0, st>>>(A, nA, B, nB, d, k, coef_key, out_idx,
                                                         out_score, scratch);
-  if (cudaGetLastError() != cudaSuccess) return SJ_ERR_CUDA;
+  NA_CUDA(cudaGetLastError());
   Counters hc;
-  if (cudaMemcpyAsync(&hc, scratch, sizeof(Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return SJ_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return SJ_ERR_CUDA;
+  NA_CUDA(cudaMemcpyAsync(&hc, scratch, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaStreamSynchronize(st));
   if (hc.err_flags & kErrNonFinite) return SJ_ERR_NONFINITE;
   if (hc.err_flags & kErrNotUnit) return SJ_ERR_NOT_UNIT_NORM;
   return SJ_OK;

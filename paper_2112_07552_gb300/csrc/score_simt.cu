@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
     rc.exact = false;  // theta refreshed lazily from the band list
     const bool owner = tid < BM && lrow < jb.nA;
     if (owner) row_begin(rc, a, jb, lrow, un.split);
+    if (a.raw_m != nullptr && owner)
+      a.raw_m[lrow] = row_margin(a.metaA[jb.a_prow0 + lrow], jb.gmaxB, a.acc_coef);
     const int64_t nB = jb.nB;
     const int64_t ct0 = (int64_t)un.split * jb.tiles_per_split;
     const int64_t ct1 = min64(jb.n_col_tiles, ct0 + jb.tiles_per_split);
@@ -124,6 +126,7 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
           const float tmin = fminf(rc.theta, rc.tau_lo);
           for (int c = 0; c < ncol; ++c) {
             const float v = sm.S[tid][c];
+            if (a.raw != nullptr) a.raw[lrow * nB + col0 + c] = v;
             if (v >= tmin) row_push(rc, a, v, (int32_t)(col0 + c));
           }
         }

@@ -152,6 +152,8 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
   if constexpr (KM > 0) topk_regs_init<KM>(h, kj);
   if constexpr (KM < 0) heap_init(heap, kj);
   if (owner) row_begin(rc, a, jb, row, list);
+  if (a.raw_m != nullptr && owner)
+    a.raw_m[row] = row_margin(a.metaA[jb.a_prow0 + row], jb.gmaxB, a.acc_coef);
   if constexpr (FP8) {
     // E4M3 scores come out of the tensor core as acc = s~ 2^(e_i + e_B): the
     // filter works on acc (thresholds scaled exactly by the power of two)
@@ -189,6 +191,14 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
       tmem_ld32_nowait(taddr + c0, v0);
       tmem_ld32_nowait(taddr + c0 + 32, v1);
       tmem_wait_ld(v0, v1);
+      if (a.raw != nullptr && owner) {
+        float *dst = a.raw + row * nB;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {  // static indices: v0/v1 stay in registers
+          if (col0 + c0 + t < nB) dst[col0 + c0 + t] = v0[t] * rc.to_s;
+          if (col0 + c0 + 32 + t < nB) dst[col0 + c0 + 32 + t] = v1[t] * rc.to_s;
+        }
+      }
       if (owner) {
         epilogue_chunk<KM>(rc, h, heap, a, v0, col0 + c0, nB);
         epilogue_chunk<KM>(rc, h, heap, a, v1, col0 + c0 + 32, nB);
@@ -349,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+    // ---------------- epilogue (warps 2..9) ----------------
     const int quarter = warp & 3;        // TMEM lanes this warp may access
     const int half = (warp - 2) >> 2;    // column half of each tile
     const int r_in_tile = quarter * 32 + lane;

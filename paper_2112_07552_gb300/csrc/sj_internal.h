@@ -16,6 +16,10 @@
 
 namespace sj {
 
+// Record the CUDA failure behind an SJ_ERR_CUDA / SJ_ERR_OOM status for
+// sj_last_error_detail() (thread-local; error name, file:line, call, message).
+void record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
 // kBF16X3: rows of 3d bfloat16, [hi | hi | lo] for A rows and [hi | lo | hi]
 // for B rows (x = hi + lo + r, hi = bf16(x), lo = bf16(x - hi)).
 enum class PackFormat { kF32, kBF16, kFP8, kBF16X3 };
@@ -126,6 +130,10 @@ struct ScoreArgs {
   ThrCand *thr;              // threshold candidates
   unsigned long long thr_cap;
   Counters *ctr;
+  // test hook (sj_debug_scores; one job): every raw score s~_ij of the job,
+  // row-major nA x nB, and each row's margin m_i; null in normal calls
+  float *raw;
+  float *raw_m;
 };
 
 // Tile sizes of the scoring kernels (rows x columns of one score tile).

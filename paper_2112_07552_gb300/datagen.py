@@ -5,7 +5,7 @@ Every array is a deterministic function of (seed, stream, shape), drawn with
 NumPy's counter-based Philox generator in fixed-size row chunks, so the result
 does not depend on the number of threads used.
 
-Recipes (the workloads of the join, stated in the design doc):
+Recipes (the workloads of the join):
   * clustered: K centres uniform on the unit sphere (normalised Gaussians);
     each row picks a centre (iid uniform, or Zipf(s) over the centre ranks),
     adds isotropic Gaussian noise whose TOTAL expected squared norm is
@@ -229,3 +229,48 @@ def clustered_batch_device(sizes_a, sizes_b, d: int, sigma: float = 0.1, seed: i
     B, b_off = side(sizes_b)
     del C
     return A, B, a_off, b_off
+
+
+ADVERSARIAL_KINDS = ("cancel_run", "cancel_half", "spread", "alternating")
+
+
+def adversarial(n: int, d: int, kind: str, seed: int = 0, side: int = 0) -> np.ndarray:
+    """n x d float32 unit rows built so that many products <a_i, b_j> of an
+    A side (side=0) and a B side (side=1) cancel: large partial sums and a
+    small result, the hardest case for a long low-precision accumulation.
+
+    * cancel_run: a long run of small same-sign entries and one large entry
+      (at one of 8 positions) holding half the squared norm; on the B side the
+      large entry has the opposite sign, so run and large term cancel.
+    * cancel_half: entries of one magnitude pattern; B rows negate the second
+      half of the coordinates, so the first half's sum (~ +1/2) is cancelled
+      by the second half.
+    * spread: magnitudes 2^-U(0, 20) with random signs (exponents across the
+      whole bfloat16/E4M3 range at unit norm).
+    * alternating: a_k of alternating sign against all-positive b_k.
+    Every row gets a small multiplicative jitter so that no two entries are
+    equal, then is normalised in FP64 and rounded to float32.
+    """
+    if kind not in ADVERSARIAL_KINDS:
+        raise ValueError("unknown kind %r" % kind)
+    rng = _rng(seed, 5000 + 10 * ADVERSARIAL_KINDS.index(kind) + side, 0)
+    jit = 1.0 + 0.05 * rng.standard_normal((n, d))
+    if kind == "cancel_run":
+        x = np.full((n, d), 1.0 / np.sqrt(2.0 * (d - 1)))
+        pos = rng.integers(0, 8, size=n) * (d // 8) + (d // 8 - 1)
+        big = np.sqrt(0.5) * (-1.0 if side else 1.0)
+        x[np.arange(n), pos] = big
+    elif kind == "cancel_half":
+        base = _rng(seed, 5099, 0).uniform(0.5, 1.5, size=d)
+        x = np.tile(base, (n, 1))
+        if side:
+            x[:, d // 2:] *= -1.0
+    elif kind == "spread":
+        e = rng.uniform(0.0, 20.0, size=(n, d))
+        s = rng.choice([-1.0, 1.0], size=(n, d))
+        x = s * np.exp2(-e)
+    else:  # alternating
+        x = rng.uniform(0.5, 1.5, size=(n, d))
+        if side == 0:
+            x[:, 1::2] *= -1.0
+    return _normalise_rows(x * jit)

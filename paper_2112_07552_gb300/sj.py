@@ -44,7 +44,8 @@ SJ_FLAG_DEBUG_TIMEOUT = 0x100
 # every symbol include/sj.h declares
 EXPORTS = ("sj_create", "sj_destroy", "sj_topk", "sj_threshold", "sj_batch",
            "sj_contrastive_fwd", "sj_backward", "sj_topk_noalloc", "sj_status_string",
-           "sj_version", "sj_last_error_detail", "sj_autotune", "sj_autotune_load")
+           "sj_version", "sj_last_error_detail", "sj_autotune", "sj_autotune_load",
+           "sj_debug_scores")
 
 I64, P = ctypes.c_int64, ctypes.c_void_p
 
@@ -128,6 +129,8 @@ def lib() -> ctypes.CDLL:
         L.sj_contrastive_fwd.argtypes = [P, P, P, I64, ctypes.c_float, P, P]
         L.sj_backward.restype = st
         L.sj_backward.argtypes = [P, P, P, I64, ctypes.c_float, P, P, P, P]
+        L.sj_debug_scores.restype = st
+        L.sj_debug_scores.argtypes = [P, P, P]
         L.sj_topk_noalloc.restype = st
         L.sj_topk_noalloc.argtypes = [P, I64, P, I64, I64, ctypes.c_int32, P, P, P]
         L.sj_status_string.restype = ctypes.c_char_p

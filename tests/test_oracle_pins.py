@@ -494,3 +494,17 @@ def test_infonce_rows_match_full():
     l2, dA2 = oracle.infonce_rows(A, B, T, rows, g=1.3)
     assert np.allclose(l2, lse[rows], rtol=1e-14)
     assert np.allclose(dA2, dA[rows], rtol=1e-12, atol=1e-15)
+
+
+def test_enclose_all_contains_the_exact_score():
+    # the FP64 enclosure used for the every-pair margin check: lo <= s <= hi
+    # for the exact s (Fraction), and it is tight (width far below 1e-12 here)
+    rng = np.random.default_rng(11)
+    A = rand_floats(rng, (12, 37), -20, 1)
+    B = rand_floats(rng, (9, 37), -20, 1)
+    lo, hi = oracle.enclose_all(A, B)
+    for i in range(A.shape[0]):
+        for j in range(B.shape[0]):
+            s = fdot(A[i], B[j])
+            assert Fraction(lo[i, j]) <= s <= Fraction(hi[i, j]), (i, j)
+            assert hi[i, j] - lo[i, j] <= 1e-12 * max(1.0, abs(float(s)))
