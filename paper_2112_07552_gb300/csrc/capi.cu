@@ -494,7 +494,7 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     // running k-th is refreshed lazily and needs 4k + 256.
     if (r.k > 0) {
       const int64_t cols = tps * bn / P.bands;
-      const bool exact_running = h->cfg.prec != SJ_FP32 && r.k <= kTcHeapMaxK;
+      const bool exact_running = h->cfg.prec != SJ_FP32 && r.k <= kTcExactMaxK;
       const int64_t slack = std::min<int64_t>(192, std::max<int64_t>(32, cols / 2048));
       jd.cap = (int32_t)(exact_running ? round_up(2 * (int64_t)r.k + 64 + slack, 32)
                                        : round_up(4 * (int64_t)r.k + 256, 32));
@@ -508,7 +508,7 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     P.band_entries += r.nA * jd.lists * (int64_t)jd.cap;
     // exact per-list top-k values (tensor-core epilogue, k <= 32)
     jd.topv0 = -1;
-    if (r.k > 0 && r.k <= kTcHeapMaxK && h->cfg.prec != SJ_FP32) {
+    if (r.k > 0 && r.k <= kTcExactMaxK && h->cfg.prec != SJ_FP32) {
       jd.topv0 = P.topv_entries;
       P.topv_entries += r.nA * jd.lists * (int64_t)r.k;
     }

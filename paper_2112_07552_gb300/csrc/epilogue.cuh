@@ -73,54 +73,6 @@ __device__ __forceinline__ void push_thr(const ScoreArgs &a, int32_t i, int32_t 
   if (slot < a.thr_cap) a.thr[slot] = ThrCand{i, j, v, 0};
 }
 
-// Running k best of a row in shared memory, for 16 < k <= 32: a k-element
-// min-heap stored transposed (element t of heap h at heap[t * kHeapStride +
-// h]) so the heaps of a warp's rows fall in distinct banks; a CTA holds up to
-// kHeapStride heaps.  Cheaper than the register array when insertions are
-// rare (long rows) and k is large.
-constexpr int kHeapStride = 256;
-
-__device__ __forceinline__ void heap_init(float *h, int k) {
-  for (int t = 0; t < k; ++t) h[t * kHeapStride] = -INFINITY;
-}
-
-// Replace the minimum (root) of a k-element min-heap by v and sift down.
-__device__ __forceinline__ void heap_replace_min(float *h, int k, float v) {
-  int p = 0;
-  while (true) {
-    int c = 2 * p + 1;
-    if (c >= k) break;
-    float hc = h[c * kHeapStride];
-    if (c + 1 < k) {
-      const float h2 = h[(c + 1) * kHeapStride];
-      if (h2 < hc) {
-        hc = h2;
-        c += 1;
-      }
-    }
-    if (hc >= v) break;
-    h[p * kHeapStride] = hc;
-    p = c;
-  }
-  h[p * kHeapStride] = v;
-}
-
-// The same visit with the running k best in a shared-memory heap.
-__device__ __forceinline__ void row_push_heap(RowCtx &r, float *heap, const ScoreArgs &a,
-                                              float v, int32_t j) {
-  if (v >= r.theta) {
-    if (!r.overflow) {
-      r.band[r.cnt] = Cand{v * r.to_s, j};
-      r.cnt += 1;
-    }
-    if (v > heap[0]) {
-      heap_replace_min(heap, r.k, v);
-      r.theta = __fsub_rd(heap[0], r.two_m);
-    }
-  }
-  if (v >= r.tau_lo) push_thr(a, r.i, j, v * r.to_s);
-}
-
 // Margin m_i: |s~_ij - s_ij| <= m_i for every j.
 //   <a,b> - <a~,b~> = <a - a~, b> + <a~, b - b~>  (Cauchy-Schwarz on each)
 //   plus the accumulation error of the scoring pass, acc_coef ||a~|| ||b~||.

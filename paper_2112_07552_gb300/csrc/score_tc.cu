@@ -14,8 +14,9 @@
 //              warp may access is its index mod 4), each taking one half of
 //              the tile's columns; tcgen05.ld (one left row per thread),
 //              fused top-k / threshold filter (epilogue.cuh) with one band
-//              list and heap per (row, column half), then release the
-//              accumulator to the MMA warp.
+//              list and register top-k per (row, column half): passing
+//              scores are queued while the accumulator is held and visited
+//              after it is released to the MMA warp.
 // Work unit = (128-row block of A, column split of B); CTAs take units
 // round-robin.  Every wait is bounded (globaltimer); a wait that gives up
 // flags SJ_ERR_TIMEOUT, the CTA drains its in-flight copies and MMAs,
@@ -42,10 +43,12 @@ constexpr int kRowBytes = 128;  // k-block: one 128-byte swizzle row per tile ro
 constexpr int BK = 64;          // k-block elements, BF16 (E4M3: 128)
 constexpr int STAGES = 4;
 constexpr int kEpiChunks = 2;  // 32-column chunks per TMEM round trip
-constexpr int kRegsMaxK = 16;  // k kept in registers; 16 < k <= kTcHeapMaxK in the smem heap
-static_assert(kRegsMaxK <= kTopKRegs, "register top-k size");
+constexpr int kRegsSmallK = 16;  // k <= 16: 16 register slots; 16 < k <= kTcExactMaxK: 32
+static_assert(kTcExactMaxK <= kTopKRegs, "register top-k size");
 constexpr int kEpiWarps = 8;    // two per TMEM lane quarter
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;
+constexpr int kQueueFlush = kTcQueue / 2;  // a warp drains once one of its lanes holds this many
 constexpr uint32_t kTileABytes = BM * BK * 2;
 constexpr uint32_t kTileBBytes = BN * BK * 2;
 constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators
@@ -64,18 +67,43 @@ struct alignas(1024) TcSmem {
   uint64_t tmem_empty[2];
   uint64_t drain;
   uint64_t never;  // debug-timeout hook: nothing ever arrives here
-  float heap[kTcHeapMaxK * kHeapStride];  // per-row top-k min-heaps (16 < k <= 32)
+  // per-thread visit queues (score, column): entry e of epilogue thread t at
+  // [e][t], so a warp's lanes fall in distinct banks
+  float qv[kTcQueue][kEpiThreads];
+  int32_t qj[kTcQueue][kEpiThreads];
   uint32_t tmem_base;
   int abort;
 };
 
+// One visit of a score that passed min(theta, tau_lo): band list, running
+// top-k (KM > 0 register slots; KM == 0: lazy theta) and threshold list.
+template <int KM>
+__device__ __forceinline__ void visit(RowCtx &rc, float (&h)[KM > 0 ? KM : 1], const ScoreArgs &a,
+                                      float v, int32_t j) {
+  if constexpr (KM > 0) row_push_regs<KM>(rc, h, a, v, j);
+  else row_push(rc, a, v, j);
+}
+
+// The thread's queued visits, in arrival order, against the current theta.
+template <int KM>
+__device__ __forceinline__ void drain_queue(RowCtx &rc, float (&h)[KM > 0 ? KM : 1],
+                                            const ScoreArgs &a, const float *qv,
+                                            const int32_t *qj, int &qn) {
+#pragma unroll 1
+  for (int e = 0; e < qn; ++e) visit<KM>(rc, h, a, qv[e * kEpiThreads], qj[e * kEpiThreads]);
+  qn = 0;
+}
+
 // Fused filter over 32 scores of the thread's row, columns jb .. jb+31.
-// KM > 0: the running k best are kept in h (k <= KM); KM < 0: in the row's
-// shared-memory heap rc_heap; KM == 0: lazy theta.
+// Scores >= min(theta, tau_lo) are appended to the thread's queue; a full
+// queue is drained on the spot.  theta only rises, so a queued score that a
+// later theta would reject is rejected when it is drained, and filtering
+// with the theta of the chunk start keeps a superset.
 template <int KM>
 __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? KM : 1],
-                                               float *rc_heap, const ScoreArgs &a,
-                                               const float (&v)[32], int64_t jb, int64_t nB) {
+                                               const ScoreArgs &a, const float (&v)[32],
+                                               int64_t jb, int64_t nB, float *qv, int32_t *qj,
+                                               int &qn) {
   // fast path: one compare per 32 scores (balanced max tree)
   float p16[16], q8[8];
 #pragma unroll
@@ -86,9 +114,8 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? K
                          fmaxf(fmaxf(q8[4], q8[5]), fmaxf(q8[6], q8[7])));
   const float tmin = fminf(rc.theta, rc.tau_lo);
   if (mx >= tmin) {
-    // slow path: loop over the passing quads; a switch picks the quad's
-    // registers by static index (no local memory) and one copy of the push
-    // code serves every value
+    // loop over the passing quads; a switch picks the quad's registers by
+    // static index (no local memory)
     uint32_t qm = 0;
 #pragma unroll
     for (int g = 0; g < 8; ++g) qm |= (q8[g] >= tmin ? 1u : 0u) << g;
@@ -112,10 +139,11 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? K
 #pragma unroll 1
       for (int e = 0; e < 4; ++e) {
         const float x = e == 0 ? x0 : e == 1 ? x1 : e == 2 ? x2 : x3;
-        if (x >= fminf(rc.theta, rc.tau_lo) && jq + e < nB) {
-          if constexpr (KM > 0) row_push_regs<KM>(rc, h, a, x, (int32_t)(jq + e));
-          else if constexpr (KM < 0) row_push_heap(rc, rc_heap, a, x, (int32_t)(jq + e));
-          else row_push(rc, a, x, (int32_t)(jq + e));
+        if (x >= tmin && jq + e < nB) {
+          if (qn == kTcQueue) drain_queue<KM>(rc, h, a, qv, qj, qn);
+          qv[qn * kEpiThreads] = x;
+          qj[qn * kEpiThreads] = (int32_t)(jq + e);
+          ++qn;
         }
       }
     }
@@ -128,9 +156,13 @@ __device__ __forceinline__ void flag_timeout(TcSmem &sm, Counters *ctr) {
 }
 
 // The epilogue warps' share of one unit: the row's running top-k in
-// registers (KM > 0 slots), in a shared-memory heap (KM < 0) or none (KM == 0:
-// lazy theta), every tile of the unit's column range from tensor memory
-// through the fused filter, then the row's band count and exact top-k values.
+// registers (KM > 0 slots) or none (KM == 0: lazy theta), every tile of the
+// unit's column range from tensor memory through the fused filter, then the
+// row's band count and exact top-k values.  While a tile's accumulator is
+// held, passing scores only go to the thread's queue; the warp drains its
+// queues after releasing the accumulator, so the visits (band and threshold
+// pushes, top-k inserts) overlap the next tiles' MMAs and run on all lanes
+// with queued visits at once.
 template <int KM, bool FP8>
 __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, const UnitDev &un,
                                               const JobDev &jb, int64_t row, bool owner,
@@ -138,7 +170,12 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
                                               uint64_t limit_ns, uint64_t &tile, bool &ok) {
   volatile int *abort = &sm.abort;
   const int kj = jb.k;
-  const int limit = jb.cap - 32 * kEpiChunks;  // room for one round of visits
+  // Band room: before a chunk, for its 32 visits plus a full queue; before a
+  // drain, for the queue alone.  (A list whose entries at or above theta do
+  // not fit in that room is marked overflowed and goes to the fallback.)
+  const int limit = jb.cap - 32 - kTcQueue;
+  const int limit_drain = jb.cap - kTcQueue;
+  static_assert(32 + kTcQueue <= 32 * kEpiChunks, "band room of the lists (capacity plan)");
   const int64_t nB = jb.nB;
   RowCtx rc;
   rc.cnt = 0;
@@ -148,9 +185,11 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
   rc.tau_lo = INFINITY;
   rc.exact = KM != 0;
   float h[KM > 0 ? KM : 1];
-  float *heap = sm.heap + half * BM + (row - (int64_t)un.rb * BM);  // this thread's heap
+  const int et = (int)threadIdx.x - 64;  // epilogue thread index
+  float *qv = &sm.qv[0][et];
+  int32_t *qj = &sm.qj[0][et];
+  int qn = 0;
   if constexpr (KM > 0) topk_regs_init<KM>(h, kj);
-  if constexpr (KM < 0) heap_init(heap, kj);
   if (owner) row_begin(rc, a, jb, row, list);
   if (a.raw_m != nullptr && owner)
     a.raw_m[row] = row_margin(a.metaA[jb.a_prow0 + row], jb.gmaxB, a.acc_coef);
@@ -186,7 +225,6 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
     // two 32-column chunks per TMEM round trip
 #pragma unroll 1
     for (int c0 = half * (bn / 2); c0 < (half + 1) * (bn / 2); c0 += 64) {
-      if (kj > 0) warp_compact(rc, owner, kj, limit);
       float v0[32], v1[32];
       tmem_ld32_nowait(taddr + c0, v0);
       tmem_ld32_nowait(taddr + c0 + 32, v1);
@@ -199,25 +237,30 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
           if (col0 + c0 + 32 + t < nB) dst[col0 + c0 + 32 + t] = v1[t] * rc.to_s;
         }
       }
-      if (owner) {
-        epilogue_chunk<KM>(rc, h, heap, a, v0, col0 + c0, nB);
-        epilogue_chunk<KM>(rc, h, heap, a, v1, col0 + c0 + 32, nB);
-      }
+      if (kj > 0) warp_compact(rc, owner, kj, limit);
+      if (owner) epilogue_chunk<KM>(rc, h, a, v0, col0 + c0, nB, qv, qj, qn);
+      if (kj > 0) warp_compact(rc, owner, kj, limit);
+      if (owner) epilogue_chunk<KM>(rc, h, a, v1, col0 + c0 + 32, nB, qv, qj, qn);
     }
     fence_before();
     mbar_arrive(&sm.tmem_empty[acc]);
+    // the accumulator is released: drain once a lane's queue is half full
+    if (__any_sync(0xffffffffu, qn >= kQueueFlush)) {
+      if (kj > 0) warp_compact(rc, owner, kj, limit_drain);
+      if (owner) drain_queue<KM>(rc, h, a, qv, qj, qn);
+    }
   }
+  if (kj > 0) warp_compact(rc, owner, kj, limit_drain);
   if (owner) {
+    drain_queue<KM>(rc, h, a, qv, qj, qn);
     row_end(rc, a);
-    if (jb.topv0 >= 0) {
-      // the list's k best (any order)
-      float *tv = a.topv + jb.topv0 + (row * jb.lists + list) * (int64_t)kj;
-      if constexpr (KM > 0) {
+    if constexpr (KM > 0) {
+      if (jb.topv0 >= 0) {
+        // the list's k best (any order)
+        float *tv = a.topv + jb.topv0 + (row * jb.lists + list) * (int64_t)kj;
 #pragma unroll
         for (int t = 0; t < KM; ++t)
           if (t >= KM - kj) tv[t - (KM - kj)] = h[t] * rc.to_s;
-      } else if constexpr (KM < 0) {
-        for (int t = 0; t < kj; ++t) tv[t] = heap[t * kHeapStride] * rc.to_s;
       }
     }
   }
@@ -380,12 +423,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool owner = row < jb.nA;
       const int kj = jb.k;
       const int list = un.split * a.bands_per_split + half;
-      if (kj > 0 && kj <= kRegsMaxK)
-        epilogue_unit<kRegsMaxK, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns,
-                                 tile, ok);
-      else if (kj > 0 && kj <= kTcHeapMaxK)
-        epilogue_unit<-1, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile,
-                          ok);
+      if (kj > 0 && kj <= kRegsSmallK)
+        epilogue_unit<kRegsSmallK, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half,
+                                        limit_ns, tile, ok);
+      else if (kj > 0 && kj <= kTcExactMaxK)
+        epilogue_unit<kTcExactMaxK, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half,
+                                         limit_ns, tile, ok);
       else
         epilogue_unit<0, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
     }

@@ -139,7 +139,8 @@ struct ScoreArgs {
 // Tile sizes of the scoring kernels (rows x columns of one score tile).
 constexpr int kSimtBM = 128, kSimtBN = 128, kSimtBK = 16;
 constexpr int kTcBM = 128, kTcBN = 256, kTcBNNarrow = 128;
-constexpr int kTcHeapMaxK = 32;  // k tracked exactly by the tensor-core epilogue's heaps
+constexpr int kTcExactMaxK = 32;  // k tracked exactly by the tensor-core epilogue (registers)
+constexpr int kTcQueue = 16;      // tensor-core epilogue: queued visits per thread
 
 cudaError_t launch_score_simt(const ScoreArgs &a, int grid, cudaStream_t st);
 
