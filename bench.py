@@ -50,11 +50,37 @@ ZIPF = {"workload": "topk_join_10Mx1M_d256_k50_zipf1.1", "nA": 10_000_000, "nB":
         "near_dup_sigma": 0.0, "k": 50, "tau": None, "seed": 0, "prec": "bf16x3"}
 METRIC = "pair-scores/s"
 
-# DRAM bytes of one headline score_tc_kernel launch: an ncu capture of an
-# earlier build of the kernel on a one-wave case scaled by pair-scores
-# (profiles/score_tc_kernel_bf16_19456x262144_d768.md); reported as context
-# only until re-taken on the current kernel.
-SCORE_TC_TRAFFIC_BYTES_PER_PAIR = 1.137653e9 / (19456 * 262144)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of score_tc_kernel
+# per pair-score, from one ncu capture of the one-wave join (19,456 x 262,144,
+# d = 768, k = 20, tau = 0.85: 152 row blocks, each sweeping all columns), and
+# a hash of the scoring kernel's sources at that capture.  A full launch's
+# traffic is this figure times its pair-scores (DRAM bytes grow with the
+# waves of row blocks, each re-reading B); the bench reports null when the
+# kernel sources no longer match the capture.
+SCORE_TC_CAPTURE = {"bytes_per_pair_score": (924884480 + 175581952) / (19456 * 262144),
+                    "src_hash": "38b0d5fe021286d6",
+                    "shape": "19456x262144 d=768 k=20 tau=0.85"}
+SCORE_TC_SOURCES = ("score_tc.cu", "epilogue.cuh", "tc_common.cuh", "sj_device.cuh")
+
+
+def score_tc_src_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in SCORE_TC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2112_07552_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def score_tc_traffic(pair_scores):
+    """(traffic bytes of one launch or None, source string)."""
+    cap = SCORE_TC_CAPTURE
+    if cap["bytes_per_pair_score"] is None:
+        return None, "no ncu capture of this kernel"
+    if cap["src_hash"] != score_tc_src_hash():
+        return None, "kernel changed since the ncu capture (%s)" % cap["shape"]
+    return (cap["bytes_per_pair_score"] * pair_scores,
+            "ncu capture of %s scaled by pair-scores" % cap["shape"])
 
 
 def parse():
@@ -71,6 +97,8 @@ def parse():
                    help="scoring precision override (join and zipf workloads); fp32 is "
                         "the CUDA-core comparison form at the same exactness")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-sub", action="store_true",
+                   help="headline only: skip the FP32 form and the other workloads' sub-results")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--workload", choices=["join", "infonce", "batch", "fp8", "zipf"],
                    default="join",
@@ -85,6 +113,7 @@ def parse():
 
 
 def make_data(w, rank):
+    """(A, B, near-duplicate pairs (i of A, j of B) or None)."""
     from paper_2112_07552_gb300 import datagen
     C = datagen.centres(w["clusters"], w["d"], w["seed"])
     zs = w.get("zipf_s")
@@ -93,11 +122,12 @@ def make_data(w, rank):
     B = datagen.clustered(w["nB"], w["d"], w["clusters"], w["sigma"], w["seed"], stream=1,
                           zipf_s=zs, C=C)
     if not w["near_dup_frac"]:
-        return A, B
+        return A, B, None
     A0 = A if rank == 0 else datagen.clustered(w["nA"], w["d"], w["clusters"], w["sigma"],
                                                 w["seed"], stream=0, C=C)
-    datagen.add_near_duplicates(A0, B, w["near_dup_frac"], w["near_dup_sigma"], w["seed"])
-    return A, B
+    dups = datagen.add_near_duplicates(A0, B, w["near_dup_frac"], w["near_dup_sigma"],
+                                       w["seed"])
+    return A, B, dups
 
 
 def measured_peaks():
@@ -161,8 +191,9 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(w, A, B, budget_s, gpu_out=None):
-    """Oracle on a bounded sample of left rows (all of B); returns a dict."""
+def cpu_baseline(w, A, B, budget_s, gpu_out=None, dups=None):
+    """Oracle on a bounded sample of left rows (all of B); returns a dict.
+    With near-duplicate pairs given, half the sample is rows that have one."""
     import oracle
     rng = np.random.default_rng(1234)
     rows = rng.choice(w["nA"], size=min(w["nA"], max(2, oracle.num_threads())), replace=False)
@@ -173,7 +204,17 @@ def cpu_baseline(w, A, B, budget_s, gpu_out=None):
         oracle.threshold(A, B, w["tau"], rows=rows, want_s64=False)
     per_row = (time.perf_counter() - t0) / len(rows)
     n = int(max(2, min(4096, w["nA"], budget_s / max(per_row, 1e-9))))
-    rows = np.sort(rng.choice(w["nA"], size=min(n, w["nA"]), replace=False))
+    n_dup = 0
+    if dups is not None and len(dups):
+        src = np.unique(dups[:, 0])
+        n_dup = min(len(src), n // 2)
+        dup_rows = rng.choice(src, size=n_dup, replace=False)
+        rest = np.setdiff1d(np.arange(w["nA"]), dup_rows)
+        rows = np.sort(np.concatenate(
+            [dup_rows, rng.choice(rest, size=min(n - n_dup, len(rest)), replace=False)]))
+    else:
+        rows = np.sort(rng.choice(w["nA"], size=min(n, w["nA"]), replace=False))
+    n = len(rows)
     t0 = time.perf_counter()
     idx, s32, _ = oracle.topk(A, B, w["k"], rows=rows)
     if thr:
@@ -181,8 +222,9 @@ def cpu_baseline(w, A, B, budget_s, gpu_out=None):
     dt = time.perf_counter() - t0
     res = {"value": n * w["nB"] / dt, "unit": METRIC, "cores": oracle.num_threads(),
            "kind": "oracle",
-           "sample": "%d random left rows x all %d right rows (top-%d%s), %.1f s"
-                     % (n, w["nB"], w["k"], " + tau=%g" % w["tau"] if thr else "", dt)}
+           "sample": "%d left rows (%d with a near duplicate, the rest random) x all %d "
+                     "right rows (top-%d%s), %.1f s"
+                     % (n, n_dup, w["nB"], w["k"], " + tau=%g" % w["tau"] if thr else "", dt)}
     if gpu_out is not None:
         gidx, gsc, gpairs = gpu_out
         ok = bool(np.array_equal(gidx[rows], idx)
@@ -195,17 +237,28 @@ def cpu_baseline(w, A, B, budget_s, gpu_out=None):
     return res
 
 
+def join_config(w, world):
+    """The config object of a join line (both arms)."""
+    in_gb = (w["nA"] + w["nB"]) * w["d"] * 4 / 1e9
+    return {"workload": w["workload"], "nA": w["nA"], "nB": w["nB"], "d": w["d"], "k": w["k"],
+            "tau": w["tau"], "clusters": w["clusters"], "zipf_s": w.get("zipf_s"),
+            "seed": w["seed"],
+            "l2": ("inputs %.1f GB > L2, no flush" % in_gb) if in_gb > 0.13
+                  else "inputs %.3f GB (small debug shape, fits in L2)" % in_gb,
+            "parallelism": "dp%d" % world}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    A, B = make_data(w, 0)
+    A, B, dups = make_data(w, 0)
     import oracle
     oracle.build()
     vals = []
     last = None
     for s in range(args.warmup + args.steps):
-        r = cpu_baseline(w, A, B, max(1.0, args.cpu_seconds / 3))
+        r = cpu_baseline(w, A, B, max(1.0, args.cpu_seconds / 3), dups=dups)
         if s >= args.warmup:
             vals.append(r["value"])
             last = r
@@ -214,8 +267,7 @@ def run_reference(args, w):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {k: w.get(k) for k in ("workload", "nA", "nB", "d", "k", "tau", "clusters",
-                                            "zipf_s")},
+           "config": join_config(w, 1),
            "cpu_baseline": {"value": v, "unit": METRIC, "cores": last["cores"],
                             "kind": "oracle", "sample": last["sample"]},
            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -251,8 +303,12 @@ def infonce_cpu_baseline(A, B, T, budget_s):
                       % (len(rows), n, dt)}
 
 
-def run_infonce(args):
-    """Contrastive join: one step = forward (loss, lse) + backward (dA, dB)."""
+def run_infonce(args, steps=None, warmup=None, cpu_seconds=None, e2e=True):
+    """Contrastive join: one step = forward (loss, lse) + backward (dA, dB).
+    Returns the line (a dict)."""
+    steps = steps or steps
+    warmup = warmup or warmup
+    cpu_seconds = args.cpu_seconds if cpu_seconds is None else cpu_seconds
     import torch
 
     from paper_2112_07552_gb300 import _build, datagen, sj
@@ -274,7 +330,7 @@ def run_infonce(args):
         gA, gB = J.contrastive_backward(Ain, Bin, T, lse, g)
         return loss
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(dA, dB)
     torch.cuda.synchronize()
     clk = ClockSampler(0)
@@ -283,40 +339,42 @@ def run_infonce(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e2 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         J.contrastive_forward(dA, dB, T)
     e1.record(stream)
     loss, lse = J.contrastive_forward(dA, dB, T)
     e1b = torch.cuda.Event(enable_timing=True)
     e1b.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         J.contrastive_backward(dA, dB, T, lse, g)
     e2.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms_fwd = e0.elapsed_time(e1) / args.steps
-    ms_bwd = e1b.elapsed_time(e2) / args.steps
+    ms_fwd = e0.elapsed_time(e1) / steps
+    ms_bwd = e1b.elapsed_time(e2) / steps
     ms = ms_fwd + ms_bwd
     # e2e: pinned host inputs copied in, loss read back, every step
-    hA = torch.from_numpy(A).pin_memory()
-    hB = torch.from_numpy(B).pin_memory()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        xa = hA.to(dev, non_blocking=True)
-        xb = hB.to(dev, non_blocking=True)
-        float(step(xa, xb).item())
-    torch.cuda.synchronize()
-    e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e_ms = None
+    if e2e:
+        hA = torch.from_numpy(A).pin_memory()
+        hB = torch.from_numpy(B).pin_memory()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            xa = hA.to(dev, non_blocking=True)
+            xb = hB.to(dev, non_blocking=True)
+            float(step(xa, xb).item())
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3 / steps
     peaks, src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     flops = 8.0 * n * n * d  # algorithmic: S (2N^2 d) + dA, dB, S-recompute (6N^2 d)
     achieved = flops / (ms / 1e3) / 1e12
     cpu = None
-    if not args.no_cpu:
-        cpu = infonce_cpu_baseline(A, B, T, args.cpu_seconds)
+    if not args.no_cpu and cpu_seconds > 0:
+        cpu = infonce_cpu_baseline(A, B, T, cpu_seconds)
     out = {
         "metric": METRIC, "value": n * n / (ms / 1e3), "unit": METRIC, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
         "config": {"workload": w["workload"], "n": n, "d": d, "T": T,
@@ -329,15 +387,15 @@ def run_infonce(args):
         # forward: two packs, the forward kernel, the merge of its partial row
         # states, the loss reduction; backward: two packs, the dL/dS pass, two
         # GEMMs (K forwards, one more for lse, K backwards in the timed region)
-        "gpu_launches": 5 * (args.steps + 1) + 5 * args.steps,
+        "gpu_launches": 5 * (steps + 1) + 5 * steps,
         "clocks": clocks,
-        "e2e": {"value": n * n / (e_ms / 1e3), "unit": METRIC, "ms_per_step": e_ms,
+        "e2e": None if e_ms is None else
+               {"value": n * n / (e_ms / 1e3), "unit": METRIC, "ms_per_step": e_ms,
                 "h2d_bytes_per_step": int(2 * n * d * 4), "d2h_bytes_per_step": 4},
         "cpu_baseline": cpu,
     }
-    print(json.dumps(out), flush=True)
     J.close()
-    return 0
+    return out
 
 
 BATCH = {"workload": "bf16_batch_4096_jobs_loguniform_100-50000_d384_k10_tau0.8",
@@ -345,9 +403,11 @@ BATCH = {"workload": "bf16_batch_4096_jobs_loguniform_100-50000_d384_k10_tau0.8"
          "sigma": 0.1, "seed": 0}
 
 
-def run_batch(args):
+def run_batch(args, steps=None, warmup=None, e2e=True):
     """Uneven batch: one step = one sj_batch call over every job (top-k and
-    threshold of each job from one scoring pass)."""
+    threshold of each job from one scoring pass).  Returns the line."""
+    steps = steps or steps
+    warmup = warmup or warmup
     import ctypes
 
     import torch
@@ -410,7 +470,7 @@ def run_batch(args):
             raise sj.SJError(code, "sj_batch")
         return st
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(jobs, nj)
     torch.cuda.synchronize()
     clk = ClockSampler(0)
@@ -418,11 +478,11 @@ def run_batch(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    stats = [step(jobs, nj) for _ in range(args.steps)]
+    stats = [step(jobs, nj) for _ in range(steps)]
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     ms_score = statistics.mean(s.ms_score for s in stats)
     n_pairs_all = int(sum(n_out[q] for q in range(nj)))
     padded = float(stats[-1].padded_pair_scores)
@@ -462,7 +522,7 @@ def run_batch(args):
     # end to end on the leading jobs holding a quarter of the rows: pinned host
     # inputs and outputs through the same call
     e2e = None
-    if not args.no_e2e:
+    if e2e and not args.no_e2e:
         rows_tot = np.cumsum(sa + sb)
         qe = int(max(1, np.searchsorted(rows_tot, rows_tot[-1] / 4)))
         hA = A[:int(ao[qe])].cpu().pin_memory()
@@ -477,10 +537,10 @@ def run_batch(args):
         step(hjobs, qe)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             step(hjobs, qe)
         torch.cuda.synchronize()
-        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        e_ms = (time.perf_counter() - t0) * 1e3 / steps
         sub = float(np.sum(sa[:qe].astype(np.float64) * sb[:qe]))
         e2e = {"value": sub / (e_ms / 1e3), "unit": METRIC, "ms_per_step": e_ms,
                "jobs": qe, "pair_scores_per_step": sub,
@@ -492,7 +552,7 @@ def run_batch(args):
     achieved = 2.0 * pair_scores * d / (ms_score / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": pair_scores / (ms / 1e3), "unit": METRIC, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
         "config": {"workload": w["workload"], "n_jobs": nj, "rows_A": int(ao[-1]),
@@ -517,17 +577,45 @@ def run_batch(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(out), flush=True)
     J.close()
-    return 0
+    return out
 
 
-def run_fp8(args):
+def fp8_peak_tflops():
+    """Dense FP8 E4M3 tensor peak measured here: torch._scaled_mm (cuBLASLt)
+    at 8192^3, best of 5 after 3 warm-ups (burst), or None if unavailable."""
+    import torch
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        best = 1e30
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+    except Exception:
+        return None
+
+
+def run_fp8(args, data=None, steps=None, warmup=None):
     """Threshold join of the headline data (1M x 1M, d = 768, tau = 0.85)
     scored in FP8 E4M3 with exact rescoring; the same join in BF16 is timed
     beside it.  (Exact FP8 top-k is not measured: with the rigorous E4M3
     margin the running k-th best stays within 2m of the bulk until a row's
-    best matches appear, so every band list overflows into the rescan.)"""
+    best matches appear, so every band list overflows into the rescan.)
+    `data` = (A, B, dA, dB) reuses the caller's inputs.  Returns the line."""
+    steps = steps or steps
+    warmup = warmup or warmup
     import ctypes
 
     import torch
@@ -540,10 +628,13 @@ def run_fp8(args):
     nA, nB, d, tau = w["nA"], w["nB"], w["d"], w["tau"]
     _build.build()
     L = sj.lib()
-    A, B = make_data(w, 0)
     dev = torch.device("cuda", 0)
-    dA = torch.from_numpy(A).to(dev)
-    dB = torch.from_numpy(B).to(dev)
+    if data is None:
+        A, B, _ = make_data(w, 0)
+        dA = torch.from_numpy(A).to(dev)
+        dB = torch.from_numpy(B).to(dev)
+    else:
+        A, B, dA, dB = data
     stream = torch.cuda.current_stream(dev)
     cap = 40_000_000
     pairs = torch.empty((cap, 3), dtype=torch.int64, device=dev)
@@ -562,7 +653,7 @@ def run_fp8(args):
             if code != sj.SJ_OK:
                 raise sj.SJError(code, "sj_batch")
             return st
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         clk = ClockSampler(0)
@@ -570,11 +661,11 @@ def run_fp8(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        stats = [step() for _ in range(args.steps)]
+        stats = [step() for _ in range(steps)]
         e1.record(stream)
         torch.cuda.synchronize()
         clocks = clk.stop()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         got = (pairs[:n_out.value, 0].cpu().numpy(), pairs[:n_out.value, 1].cpu().numpy(),
                pairs[:n_out.value, 2:3].contiguous().view(torch.float32)[:, 0].cpu().numpy())
         res[prec] = {"ms": ms, "ms_score": statistics.mean(s.ms_score for s in stats),
@@ -596,12 +687,17 @@ def run_fp8(args):
     ok = bool(np.array_equal(gi[sel], ti) and np.array_equal(gj[sel], tj)
               and np.array_equal(gs[sel].view(np.uint32), ts.view(np.uint32)))
     peaks, src = measured_peaks()
-    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))) * 2.0
+    peak8 = fp8_peak_tflops()
+    if peak8:
+        peak, peak_source = peak8, "measured here: torch._scaled_mm E4M3 8192^3, best of 5"
+    else:
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))) * 2.0
+        peak_source = src + " bf16_tflops_sustained x 2 (FP8/BF16 nominal ratio)"
     r8 = res["fp8"]
     achieved = 2.0 * nA * nB * d / (r8["ms_score"] / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": nA * nB / (r8["ms"] / 1e3), "unit": METRIC, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r8["ms"],
+        "steps": steps, "warmup": warmup, "ms_per_step": r8["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp8_e4m3",
         "data": "synthetic",
         "config": {"workload": "fp8_threshold_join_%dx%d_d%d_tau%g" % (nA, nB, d, tau),
@@ -610,8 +706,7 @@ def run_fp8(args):
                    "parallelism": "dp1"},
         "roofline": {"bound": "tensor", "kernel": "score_tc_kernel<fp8>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": src + " bf16_tflops_sustained x 2 (FP8/BF16 nominal ratio)",
-                     "traffic": None, "ms_kernel": r8["ms_score"]},
+                     "peak_source": peak_source, "traffic": None, "ms_kernel": r8["ms_score"]},
         "stages_ms": {"score": r8["ms_score"], "select": r8["ms_select"]},
         "n_pairs": r8["n_pairs"], "n_candidates": r8["n_candidates"], "n_exact": r8["n_exact"],
         "bf16_same_join": {"ms_per_step": res["bf16"]["ms"], "ms_score": res["bf16"]["ms_score"],
@@ -626,8 +721,8 @@ def run_fp8(args):
                                    % (len(rows), nB, tau, cpu_t),
                          "parity_rows_exact": ok},
     }
-    print(json.dumps(out), flush=True)
-    return 0
+    del pairs
+    return out
 
 
 def zipf_fp8_sample(w, A, dB, dev, stream, rows=2048):
@@ -668,6 +763,131 @@ def zipf_fp8_sample(w, A, dB, dev, stream, rows=2048):
     return out
 
 
+def guarded(fn, *a, **kw):
+    """A sub-result of the line: its dict, or the error that stopped it."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001 -- reported in the line, not fatal
+        return {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+
+
+def fp32_same_join(args, w, dA, dB, stream, idx_bf16, sc_bf16, pairs_bf16, value_bf16,
+                   rows=16384, steps=3, warmup=1):
+    """The plain FP32 CUDA-core form of the headline join at the same
+    exactness, on its first `rows` left rows against all of B (a rate does not
+    depend on the number of rows): pair-scores/s, the BF16 headline's speed-up
+    over it, and whether both emit the same top-k and pairs for those rows."""
+    import ctypes
+
+    import torch
+
+    from paper_2112_07552_gb300 import sj
+    L = sj.lib()
+    nB, d, k, tau = w["nB"], w["d"], w["k"], w["tau"]
+    n = min(rows, w["nA"])
+    cap = 4_000_000
+    idx = torch.empty((n, k), dtype=torch.int64, device=dA.device)
+    sc = torch.empty((n, k), dtype=torch.float32, device=dA.device)
+    pairs = torch.empty((cap, 3), dtype=torch.int64, device=dA.device)
+    n_out = sj.I64(0)
+    J = sj.SimilarityJoin(d, prec="fp32", device=dA.device.index, stream=stream)
+    jb = (sj.SjJob * 1)()
+    jb[0].A, jb[0].nA, jb[0].B, jb[0].nB = dA.data_ptr(), n, dB.data_ptr(), nB
+    jb[0].k, jb[0].topk_idx, jb[0].topk_score = k, idx.data_ptr(), sc.data_ptr()
+    jb[0].tau, jb[0].pairs, jb[0].capacity = tau, pairs.data_ptr(), cap
+    jb[0].n_out = ctypes.cast(ctypes.byref(n_out), sj.P)
+    stats = []
+    for it in range(warmup + steps):
+        st = sj.SjStats()
+        code = L.sj_batch(J.handle, jb, 1, ctypes.byref(st))
+        if code != sj.SJ_OK:
+            raise sj.SJError(code, "sj_batch (fp32)")
+        if it >= warmup:
+            stats.append(st)
+    torch.cuda.synchronize()
+    J.close()
+    ms = statistics.mean(s.ms_total for s in stats)
+    ms_score = statistics.mean(s.ms_score for s in stats)
+    v = n * nB / (ms / 1e3)
+    m = int(n_out.value)
+    gi, gj, gs = pairs_bf16
+    sel = gi < n
+    same = bool(torch.equal(idx, idx_bf16[:n])
+                and torch.equal(sc.view(torch.int32), sc_bf16[:n].view(torch.int32))
+                and m == int(sel.sum())
+                and np.array_equal(pairs[:m, 0].cpu().numpy(), gi[sel])
+                and np.array_equal(pairs[:m, 1].cpu().numpy(), gj[sel])
+                and np.array_equal(pairs[:m, 2:3].contiguous().view(torch.float32)[:, 0]
+                                   .cpu().numpy().view(np.uint32), gs[sel].view(np.uint32)))
+    sms = torch.cuda.get_device_properties(dA.device).multi_processor_count
+    return {"rows": n, "value": v, "unit": METRIC, "ms_per_step": ms, "ms_score": ms_score,
+            "score_tflops": 2.0 * n * nB * d / (ms_score / 1e3) / 1e12,
+            "bf16_speedup": value_bf16 / v, "outputs_identical_to_bf16": same,
+            "fp32_lanes_peak_note": "%d SMs x 128 FP32 lanes x 2 flop per clock" % sms}
+
+
+CONFIG1 = {"workload": "fp32_similarity_join_2000x2000_d256_k10_tau0.8", "nA": 2000,
+           "nB": 2000, "d": 256, "clusters": 200, "sigma": 0.1, "near_dup_frac": 0.0,
+           "near_dup_sigma": 0.0, "k": 10, "tau": 0.8, "seed": 0}
+
+
+def run_config1(args, steps=5, warmup=3):
+    """The small join (2,000 x 2,000, d = 256, 200 centres, k = 10 and
+    tau = 0.8) in the FP32 CUDA-core form and in BF16, each checked in full
+    against the oracle (which finishes it in seconds)."""
+    import torch
+
+    import oracle
+    from paper_2112_07552_gb300 import sj
+    w = dict(CONFIG1)
+    A, B, _ = make_data(w, 0)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    t0 = time.perf_counter()
+    w_idx, w_s, _ = oracle.topk(A, B, w["k"])
+    ti, tj, ts, _ = oracle.threshold(A, B, w["tau"], want_s64=False)
+    cpu_t = time.perf_counter() - t0
+    res = {"config": w, "oracle": {"value": w["nA"] * w["nB"] / cpu_t, "unit": METRIC,
+                                   "cores": oracle.num_threads(), "seconds": cpu_t}}
+    for prec in ("fp32", "bf16"):
+        J = sj.SimilarityJoin(w["d"], prec=prec, device=0)
+        for _ in range(warmup):
+            out = J.batch([{"A": dA, "B": dB, "k": w["k"], "tau": w["tau"]}])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            out = J.batch([{"A": dA, "B": dB, "k": w["k"], "tau": w["tau"]}])
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / steps
+        J.close()
+        o = out[0]
+        exact = bool(np.array_equal(o["idx"].cpu().numpy(), w_idx)
+                     and np.array_equal(o["score"].cpu().numpy().view(np.uint32),
+                                        w_s.view(np.uint32))
+                     and np.array_equal(o["i"].cpu().numpy(), ti)
+                     and np.array_equal(o["j"].cpu().numpy(), tj)
+                     and np.array_equal(o["pair_score"].cpu().numpy().view(np.uint32),
+                                        ts.view(np.uint32)))
+        res[prec] = {"value": w["nA"] * w["nB"] / (ms / 1e3), "unit": METRIC,
+                     "ms_per_call": ms, "n_pairs": int(len(o["i"])),
+                     "parity_full_exact": exact,
+                     "timing": "host wall clock per sj_batch call (launch-latency bound)"}
+    return res
+
+
+def run_subs(args, data):
+    """The other workloads, each a few steps, in the headline line."""
+    import torch
+    sub = {"note": "each workload a few steps; see its own bench workload for the full run"}
+    sub["config1_2000x2000"] = guarded(run_config1, args)
+    sub["fp8_threshold_join"] = guarded(run_fp8, args, data=data, steps=3, warmup=2)
+    torch.cuda.empty_cache()
+    sub["infonce_65536"] = guarded(run_infonce, args, steps=3, warmup=3, cpu_seconds=5.0)
+    torch.cuda.empty_cache()
+    sub["batch_4096_jobs"] = guarded(run_batch, args, steps=3, warmup=2, e2e=False)
+    torch.cuda.empty_cache()
+    return sub
+
+
 def main():
     args = parse()
     if args.workload in ("infonce", "batch", "fp8") or (args.workload == "zipf" and args.gpus > 1):
@@ -678,7 +898,9 @@ def main():
         if args.workload == "zipf":
             print(json.dumps({"workload": "zipf", "unavailable": "one-GPU workload"}))
             return 0
-        return {"infonce": run_infonce, "batch": run_batch, "fp8": run_fp8}[args.workload](args)
+        fn = {"infonce": run_infonce, "batch": run_batch, "fp8": run_fp8}[args.workload]
+        print(json.dumps(fn(args)), flush=True)
+        return 0
     if args.workload == "zipf":
         w = dict(ZIPF)
         if args.shape:
@@ -713,7 +935,7 @@ def main():
     _build.build()
     L = sj.lib()
 
-    A, B = make_data(w, rank)
+    A, B, dups = make_data(w, rank)
     nA, nB, d, k = w["nA"], w["nB"], w["d"], w["k"]
     dev = torch.device("cuda", local)
     dA = torch.from_numpy(A).to(dev)
@@ -829,32 +1051,31 @@ def main():
         peak_source = "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sampled)" % (sms, mhz)
     cpu = None
     if world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w, A, B, args.cpu_seconds, gpu_out)
+        cpu = cpu_baseline(w, A, B, args.cpu_seconds, gpu_out, dups)
     fp8_sample = None
     if args.workload == "zipf":
         fp8_sample = zipf_fp8_sample(w, A, dB, dev, stream)
-    headline = args.workload == "join"
-    in_gb = (nA + nB) * d * 4 / 1e9
+    headline = args.workload == "join" and not args.shape and not args.small
+    # algorithmic bytes of one scoring launch: the packed operands read once
+    # plus the band lists written once (the k best of each list and its
+    # margin band); the measured DRAM traffic is compared against it
+    elem = {"fp8": 1, "fp32": 4, "bf16x3": 6}.get(w["prec"], 2)
+    algo_bytes = float((nA + nB) * d * elem + nA * 2 * (2 * k + 64) * 8)
+    traffic, traffic_src = (score_tc_traffic(float(nA) * nB) if w["prec"] == "bf16"
+                            else (None, "not captured for this precision"))
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp8": "e4m3"}.get(w["prec"], w["prec"]), "data": "synthetic",
-        "config": {"workload": w["workload"], "nA": nA, "nB": nB, "d": d, "k": k,
-                   "tau": w["tau"], "clusters": w["clusters"], "zipf_s": w.get("zipf_s"),
-                   "seed": w["seed"], "l2": "inputs %.1f GB > L2, no flush" % in_gb,
-                   "parallelism": "dp%d" % world},
+        "config": join_config(w, world),
         "roofline": {"bound": bound,
                      "kernel": "score_simt_kernel" if w["prec"] == "fp32" else "score_tc_kernel",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "peak_source": peak_source,
-                     # the kernel changed (margin term, row metadata) after the last
-                     # DRAM capture: no traffic figure until it is captured again
-                     "traffic": None,
-                     "traffic_source": ("last capture (earlier kernel): %.3g bytes per launch, "
-                                        "profiles/" % (SCORE_TC_TRAFFIC_BYTES_PER_PAIR * nA * nB))
-                                       if headline else "not captured for this workload",
-                     "ms_kernel": ms_score},
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "traffic_per_algorithmic_byte": (traffic / algo_bytes) if traffic else None,
+                     "algorithmic_bytes": algo_bytes, "ms_kernel": ms_score},
         "stages_ms": {"prepare": statistics.mean(s.ms_prepare for s in stats),
                       "score": ms_score,
                       "select": statistics.mean(s.ms_select for s in stats)},
@@ -875,6 +1096,13 @@ def main():
     }
     if fp8_sample is not None:
         out["fp8_sample"] = fp8_sample
+    if headline and world == 1 and not args.no_sub:
+        out["fp32_same_join"] = guarded(fp32_same_join, args, w, dA, dB, stream, idx, sc,
+                                        gpu_out[2], value)
+        J.close()
+        del idx, sc, pairs
+        torch.cuda.empty_cache()
+        out["sub"] = run_subs(args, (A, B, dA, dB))
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -42,13 +42,13 @@ constexpr int BN = kTcBN;       // 256 columns of B per tile (TMEM columns)
 constexpr int kRowBytes = 128;  // k-block: one 128-byte swizzle row per tile row
 constexpr int BK = 64;          // k-block elements, BF16 (E4M3: 128)
 constexpr int STAGES = 4;
-constexpr int kEpiChunks = 2;  // 32-column chunks per TMEM round trip
+constexpr int kEpiChunks = 1;  // 32-column chunks per TMEM round trip (1: no spills)
 constexpr int kRegsSmallK = 16;  // k <= 16: 16 register slots; 16 < k <= kTcExactMaxK: 32
 static_assert(kTcExactMaxK <= kTopKRegs, "register top-k size");
 constexpr int kEpiWarps = 8;    // two per TMEM lane quarter
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
-constexpr int kQueueFlush = kTcQueue / 2;  // a warp drains once one of its lanes holds this many
+constexpr int kQueueFlush = 2;  // a warp drains once one of its lanes holds this many
 constexpr uint32_t kTileABytes = BM * BK * 2;
 constexpr uint32_t kTileBBytes = BN * BK * 2;
 constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators
@@ -175,7 +175,7 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
   // not fit in that room is marked overflowed and goes to the fallback.)
   const int limit = jb.cap - 32 - kTcQueue;
   const int limit_drain = jb.cap - kTcQueue;
-  static_assert(32 + kTcQueue <= 32 * kEpiChunks, "band room of the lists (capacity plan)");
+  static_assert(32 + kTcQueue <= 64, "band room of the lists (capacity plan)");
   const int64_t nB = jb.nB;
   RowCtx rc;
   rc.cnt = 0;
@@ -222,29 +222,35 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
     const int bn = jb.bn;
     const int64_t col0 = ct * bn;
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
-    // two 32-column chunks per TMEM round trip
+    // kEpiChunks 32-column chunks per TMEM round trip
 #pragma unroll 1
-    for (int c0 = half * (bn / 2); c0 < (half + 1) * (bn / 2); c0 += 64) {
+    for (int c0 = half * (bn / 2); c0 < (half + 1) * (bn / 2); c0 += 32 * kEpiChunks) {
       float v0[32], v1[32];
       tmem_ld32_nowait(taddr + c0, v0);
-      tmem_ld32_nowait(taddr + c0 + 32, v1);
-      tmem_wait_ld(v0, v1);
+      if constexpr (kEpiChunks == 2) {
+        tmem_ld32_nowait(taddr + c0 + 32, v1);
+        tmem_wait_ld(v0, v1);
+      } else {
+        tmem_wait_ld1(v0);
+      }
       if (a.raw != nullptr && owner) {
         float *dst = a.raw + row * nB;
 #pragma unroll
         for (int t = 0; t < 32; ++t) {  // static indices: v0/v1 stay in registers
           if (col0 + c0 + t < nB) dst[col0 + c0 + t] = v0[t] * rc.to_s;
-          if (col0 + c0 + 32 + t < nB) dst[col0 + c0 + 32 + t] = v1[t] * rc.to_s;
+          if (kEpiChunks == 2 && col0 + c0 + 32 + t < nB) dst[col0 + c0 + 32 + t] = v1[t] * rc.to_s;
         }
       }
       if (kj > 0) warp_compact(rc, owner, kj, limit);
       if (owner) epilogue_chunk<KM>(rc, h, a, v0, col0 + c0, nB, qv, qj, qn);
-      if (kj > 0) warp_compact(rc, owner, kj, limit);
-      if (owner) epilogue_chunk<KM>(rc, h, a, v1, col0 + c0 + 32, nB, qv, qj, qn);
+      if constexpr (kEpiChunks == 2) {
+        if (kj > 0) warp_compact(rc, owner, kj, limit);
+        if (owner) epilogue_chunk<KM>(rc, h, a, v1, col0 + c0 + 32, nB, qv, qj, qn);
+      }
     }
     fence_before();
     mbar_arrive(&sm.tmem_empty[acc]);
-    // the accumulator is released: drain once a lane's queue is half full
+    // the accumulator is released: drain once a lane holds kQueueFlush visits
     if (__any_sync(0xffffffffu, qn >= kQueueFlush)) {
       if (kj > 0) warp_compact(rc, owner, kj, limit_drain);
       if (owner) drain_queue<KM>(rc, h, a, qv, qj, qn);
