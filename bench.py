@@ -100,7 +100,8 @@ def parse():
     p.add_argument("--no-sub", action="store_true",
                    help="headline only: skip the FP32 form and the other workloads' sub-results")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--workload", choices=["join", "infonce", "batch", "fp8", "zipf"],
+    p.add_argument("--workload", choices=["join", "infonce", "batch", "fp8", "zipf",
+                                          "relational"],
                    default="join",
                    help="join: the headline similarity join; infonce: the contrastive "
                         "join (65,536 pairs, d = 768, T = 0.05) forward + backward; batch: "
@@ -874,6 +875,73 @@ def run_config1(args, steps=5, warmup=3):
     return res
 
 
+def run_relational(args, steps=3, warmup=1):
+    """The paper's relational patterns at its entity-matching and
+    microbenchmark shapes: blocking of iTunes-Amazon (6,907 x 55,923) on
+    Price (12 distinct values, ~32M pairs) and on all six attributes with
+    >= 3 equal; Q3/Q4 aggregates over 1M x 1M (ID, Val) tables with 1,000
+    distinct IDs.  Wall time per call (host dictionary encoding included),
+    results checked against the relational oracle."""
+    import torch
+
+    from oracle import relational
+    from paper_2112_07552_gb300 import datagen, sj
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "em_blocking_shapes.json")))
+    it = g["itunes_amazon"]
+    J = sj.SimilarityJoin(8, prec="bf16", device=0)
+    res = {}
+
+    def timed(fn):
+        for _ in range(warmup):
+            out = fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) / steps
+
+    for name, attrs, m in (("em_blocking_itunes_price", ["Price"], 1),
+                           ("em_blocking_itunes_6attr_ge3",
+                            ["Price", "Genre", "Time", "Artist", "Copyright", "Album"], 3)):
+        ka = np.stack([datagen.keys(it["rows"][0], it["distinct"][a], t, 0)
+                       for t, a in enumerate(attrs)], axis=1)
+        kb = np.stack([datagen.keys(it["rows"][1], it["distinct"][a], t, 1)
+                       for t, a in enumerate(attrs)], axis=1)
+        dka, dkb = torch.from_numpy(ka).cuda(), torch.from_numpy(kb).cuda()
+        (i, j, sc), t = timed(lambda: J.block(dka, dkb, m, capacity=40_000_000))
+        wi, wj, ws = relational.block(ka, kb, m)
+        res[name] = {"nA": int(ka.shape[0]), "nB": int(kb.shape[0]), "n_attr": len(attrs),
+                     "min_match": m, "n_pairs": int(len(wi)), "seconds_per_call": t,
+                     "pair_scores_per_s": ka.shape[0] * kb.shape[0] / t,
+                     "pairs_out_per_s": len(wi) / t,
+                     "parity_exact": bool(np.array_equal(i.cpu().numpy(), wi)
+                                          and np.array_equal(j.cpu().numpy(), wj)
+                                          and np.array_equal(sc.cpu().numpy().view(np.uint32),
+                                                             ws.view(np.uint32)))}
+        del i, j, sc
+    rng = np.random.default_rng(11)
+    n = 1_000_000
+    a_id = rng.integers(0, 1000, size=n).astype(np.int64)
+    b_id = rng.integers(0, 1000, size=n).astype(np.int64)
+    a_val = rng.integers(-2 ** 31, 2 ** 31, size=n).astype(np.int32)
+    b_val = rng.integers(-2 ** 31, 2 ** 31, size=n).astype(np.int32)
+    b_g = rng.integers(0, 500, size=n).astype(np.int64)
+    d = [torch.from_numpy(x).cuda() for x in (a_id, a_val, b_id, b_val, b_g)]
+    q3, t3 = timed(lambda: J.groupby_sum(d[0], d[1], d[2], d[4]))
+    q4, t4 = timed(lambda: J.sum_product(d[0], d[1], d[2], d[3]))
+    res["q3_groupby_sum_1Mx1M"] = {"seconds_per_call": t3, "rows_per_s": 2 * n / t3,
+                                   "join_pairs": int(sum(c for _, _, c in q3)),
+                                   "parity_exact": q3 == relational.groupby_sum(a_id, a_val,
+                                                                                b_id, b_g)}
+    res["q4_sum_product_1Mx1M"] = {"seconds_per_call": t4, "rows_per_s": 2 * n / t4,
+                                   "join_pairs": q4[1],
+                                   "parity_exact": q4 == relational.sum_product(a_id, a_val,
+                                                                                b_id, b_val)}
+    J.close()
+    return res
+
+
 def run_subs(args, data):
     """The other workloads, each a few steps, in the headline line."""
     import torch
@@ -885,12 +953,15 @@ def run_subs(args, data):
     torch.cuda.empty_cache()
     sub["batch_4096_jobs"] = guarded(run_batch, args, steps=3, warmup=2, e2e=False)
     torch.cuda.empty_cache()
+    sub["relational"] = guarded(run_relational, args)
+    torch.cuda.empty_cache()
     return sub
 
 
 def main():
     args = parse()
-    if args.workload in ("infonce", "batch", "fp8") or (args.workload == "zipf" and args.gpus > 1):
+    if args.workload in ("infonce", "batch", "fp8", "relational") or \
+            (args.workload == "zipf" and args.gpus > 1):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "workload": args.workload,
                               "unavailable": "the reference arm times the join workload"}))
@@ -898,7 +969,8 @@ def main():
         if args.workload == "zipf":
             print(json.dumps({"workload": "zipf", "unavailable": "one-GPU workload"}))
             return 0
-        fn = {"infonce": run_infonce, "batch": run_batch, "fp8": run_fp8}[args.workload]
+        fn = {"infonce": run_infonce, "batch": run_batch, "fp8": run_fp8,
+              "relational": run_relational}[args.workload]
         print(json.dumps(fn(args)), flush=True)
         return 0
     if args.workload == "zipf":

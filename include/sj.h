@@ -250,6 +250,64 @@ sj_status sj_topk_noalloc(const float *A, int64_t nA, const float *B, int64_t nB
                           int64_t d, int32_t k, int64_t *out_idx, float *out_score,
                           void *stream);
 
+/* ---- Relational join patterns (Sec. 3.1 "Two-way natural join", Sec. 3.3
+ * "Group-by aggregates over joins"; the entity-matching blocking of
+ * Sec. 6.3.2) ---- */
+
+/* Blocking / equi-join on key attributes.  Rows of A and B carry n_attr int64
+ * key attributes (row-major: ka[i*n_attr + a], nA x n_attr and nB x n_attr;
+ * device or host memory).  As in Sec. 3.1 every row becomes a one-hot row,
+ * one block per attribute over that attribute's shared domain (values seen on
+ * one side only get a column of their own side), scaled by
+ * c = fl32(1/sqrt(n_attr)) so rows have unit norm, and C = mat(A) mat(B)^T
+ * runs through the tensor-core threshold join of this library (bfloat16
+ * scoring, exact rescoring) at tau = (min_match - 1/2) / n_attr.
+ * Result: every (i, j) whose keys agree in at least min_match attributes
+ * (n_attr = min_match = 1: the equi-join Q1, C_ij > 0), sorted by (i, j),
+ * score = RN_fp32(matches * c^2) (= matches / n_attr for n_attr = 1 and 4).
+ * Outputs and capacity rules as sj_threshold (out may be device or host).
+ * The handle's d and precision are not used: the call runs through an
+ * internal handle of the one-hot width, kept in h between calls.
+ * Errors: SJ_ERR_INVALID_ARG (null, n_attr outside 1..64, min_match outside
+ * 1..n_attr), SJ_ERR_CAPACITY, SJ_ERR_OOM, SJ_ERR_CUDA. */
+sj_status sj_block(sj_handle *h, const int64_t *ka, int64_t nA, const int64_t *kb, int64_t nB,
+                   int32_t n_attr, int32_t min_match, sj_pair *out, int64_t capacity,
+                   int64_t *n_out, sj_stats *st);
+
+/* One group of a join aggregate: its value, the exact SUM as a two's
+ * complement 128-bit integer (sum_lo + 2^64 sum_hi) and COUNT(*). */
+typedef struct {
+  int64_t group;
+  uint64_t sum_lo;
+  int64_t sum_hi;
+  int64_t count;
+} sj_group;
+
+/* Q3 of Sec. 3.3: SELECT B.G, SUM(A.Val), COUNT(*) FROM A, B
+ * WHERE A.ID = B.ID GROUP BY B.G.  Every pair of the join counts (bag
+ * semantics; the paper's 0/1 mat(B) gives the same result when B holds no
+ * duplicate (ID, G) tuple).  Evaluated as the paper's product
+ * 1 x mat(A) x mat(B)^T in its cheap association order: the per-key sums
+ * 1 x mat(A) first, then one scatter per row of B; on GB300 both are atomic,
+ * memory-bound kernels (a matrix product of one-hot operands would multiply
+ * the work), with exact integer accumulation.  a_id, a_val (int32), b_id,
+ * b_group: device or host arrays.  Writes the groups that have at least one
+ * join pair, ordered by value, to out[0 .. *n_groups); with more groups than
+ * `capacity` returns SJ_ERR_CAPACITY with *n_groups = the required count.
+ * Errors: SJ_ERR_INVALID_ARG, SJ_ERR_CAPACITY, SJ_ERR_OOM, SJ_ERR_CUDA. */
+sj_status sj_join_groupby_sum(sj_handle *h, const int64_t *a_id, const int32_t *a_val,
+                              int64_t nA, const int64_t *b_id, const int64_t *b_group,
+                              int64_t nB, sj_group *out, int64_t capacity, int64_t *n_groups);
+
+/* Q4 of Sec. 3.3: SELECT SUM(A.Val * B.Val), COUNT(*) FROM A, B
+ * WHERE A.ID = B.ID, i.e. 1 x mat(A) mat(B)^T x 1, evaluated as the per-key
+ * sums of A dotted with B's values; exact 128-bit result in out->sum_lo /
+ * out->sum_hi, the pair count in out->count (out->group = 0).
+ * Errors: SJ_ERR_INVALID_ARG, SJ_ERR_OOM, SJ_ERR_CUDA. */
+sj_status sj_join_sum_product(sj_handle *h, const int64_t *a_id, const int32_t *a_val,
+                              int64_t nA, const int64_t *b_id, const int32_t *b_val, int64_t nB,
+                              sj_group *out);
+
 /* Test hook: arm the next sj_topk / sj_threshold / one-job sj_batch call of
  * this handle to also write what its scoring pass computed, so that the
  * margin argument can be checked pair by pair: raw[i*nB + j] = s~_ij, the

@@ -51,15 +51,15 @@ def block(ka, kb, min_match: int = 1):
         ka, kb = ka[:, None], kb[:, None]
     n_attr = ka.shape[1]
     nB = kb.shape[0]
-    counts = {}
+    # every (pair, attribute) with equal values, as the pair's index i * nB + j;
+    # a pair's number of equal attributes is how often its index occurs
+    per_attr = []
     for a in range(n_attr):
         i, j = _pairs_equal(ka[:, a], kb[:, a])
-        key = i * nB + j
-        u, c = np.unique(key, return_counts=True)
-        for kk, cc in zip(u.tolist(), c.tolist()):
-            counts[kk] = counts.get(kk, 0) + cc
-    keys = np.array(sorted(k for k, c in counts.items() if c >= min_match), np.int64)
-    m = np.array([counts[k] for k in keys.tolist()], np.int64)
+        per_attr.append(i * nB + j)
+    allk = np.concatenate(per_attr) if per_attr else np.zeros(0, np.int64)
+    u, cnt = np.unique(allk, return_counts=True)
+    keys, m = u[cnt >= min_match], cnt[cnt >= min_match].astype(np.int64)
     c = float(np.float32(1.0 / np.sqrt(n_attr)))
     s64 = m.astype(np.float64) * (c * c)  # exact: a 48-bit square times a small count
     return keys // max(nB, 1), keys % max(nB, 1), s64.astype(np.float32)

@@ -103,7 +103,29 @@ struct sj_handle {
   sj::TcContext *tc = nullptr;
   float *dbg_raw = nullptr;     // sj_debug_scores: armed for the next one-job call
   float *dbg_margin = nullptr;
+  sj_handle *aux = nullptr;     // relational calls: a handle of their one-hot width
 };
+
+sj_status sj::aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle **out) {
+  if (h->aux && (h->aux->cfg.d != d || h->aux->cfg.prec != prec)) {
+    sj_destroy(h->aux);
+    h->aux = nullptr;
+  }
+  if (!h->aux) {
+    sj_config c = h->cfg;
+    c.d = d;
+    c.prec = prec;
+    c.flags &= ~(uint32_t)SJ_FLAG_SYM_INFONCE;
+    sj_status s = sj_create(&h->aux, &c);
+    if (s != SJ_OK) return s;
+  }
+  *out = h->aux;
+  return SJ_OK;
+}
+
+int sj::handle_device(const sj_handle *h) { return h->cfg.device; }
+void *sj::handle_stream(const sj_handle *h) { return h->stream; }
+int sj::handle_sm_count(const sj_handle *h) { return h->sm_count; }
 
 namespace {
 
@@ -1480,6 +1502,7 @@ sj_status sj_destroy(sj_handle *h) {
   for (int t = 0; t < 4; ++t)
     if (h->gev[t]) cudaEventDestroy(h->gev[t]);
   if (h->tc) tc_destroy(h->tc);
+  if (h->aux) sj_destroy(h->aux);
   delete h;
   return SJ_OK;
 }

@@ -12,9 +12,19 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/sj.h"
 #include "sj_device.cuh"
 
 namespace sj {
+
+// A second handle inside h with the same device, stream and workspace limit
+// but width d and precision prec (created on first use, replaced when d or
+// prec change, destroyed with h): the relational calls run their one-hot
+// joins through it.
+sj_status aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle **out);
+int handle_device(const sj_handle *h);
+void *handle_stream(const sj_handle *h);
+int handle_sm_count(const sj_handle *h);
 
 // Record the CUDA failure behind an SJ_ERR_CUDA / SJ_ERR_OOM status for
 // sj_last_error_detail() (thread-local; error name, file:line, call, message).

@@ -45,7 +45,7 @@ SJ_FLAG_DEBUG_TIMEOUT = 0x100
 EXPORTS = ("sj_create", "sj_destroy", "sj_topk", "sj_threshold", "sj_batch",
            "sj_contrastive_fwd", "sj_backward", "sj_topk_noalloc", "sj_status_string",
            "sj_version", "sj_last_error_detail", "sj_autotune", "sj_autotune_load",
-           "sj_debug_scores")
+           "sj_debug_scores", "sj_block", "sj_join_groupby_sum", "sj_join_sum_product")
 
 I64, P = ctypes.c_int64, ctypes.c_void_p
 
@@ -76,6 +76,14 @@ class SjJob(ctypes.Structure):
     _fields_ = [("A", P), ("nA", I64), ("B", P), ("nB", I64), ("k", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("topk_idx", P), ("topk_score", P), ("pairs", P),
                 ("capacity", I64), ("n_out", P)]
+
+
+class SjGroup(ctypes.Structure):
+    _fields_ = [("group", I64), ("sum_lo", ctypes.c_uint64), ("sum_hi", I64), ("count", I64)]
+
+    def exact_sum(self) -> int:
+        """The 128-bit two's complement SUM as a Python int."""
+        return (int(self.sum_hi) << 64) + int(self.sum_lo)
 
 
 class SJError(RuntimeError):
@@ -129,6 +137,13 @@ def lib() -> ctypes.CDLL:
         L.sj_contrastive_fwd.argtypes = [P, P, P, I64, ctypes.c_float, P, P]
         L.sj_backward.restype = st
         L.sj_backward.argtypes = [P, P, P, I64, ctypes.c_float, P, P, P, P]
+        L.sj_block.restype = st
+        L.sj_block.argtypes = [P, P, I64, P, I64, ctypes.c_int32, ctypes.c_int32, P, I64,
+                               ctypes.POINTER(I64), ctypes.POINTER(SjStats)]
+        L.sj_join_groupby_sum.restype = st
+        L.sj_join_groupby_sum.argtypes = [P, P, P, I64, P, P, I64, P, I64, ctypes.POINTER(I64)]
+        L.sj_join_sum_product.restype = st
+        L.sj_join_sum_product.argtypes = [P, P, P, I64, P, P, I64, ctypes.POINTER(SjGroup)]
         L.sj_debug_scores.restype = st
         L.sj_debug_scores.argtypes = [P, P, P]
         L.sj_topk_noalloc.restype = st
@@ -269,6 +284,62 @@ class SimilarityJoin:
             s = buf[:m, 2:3].view(torch.float32)[:, 0]
             return (i, j, s, st.as_dict()) if with_stats else (i, j, s)
         raise SJError(SJ_ERR_CAPACITY, "sj_threshold")
+
+    def block(self, ka, kb, min_match: int = 1, capacity: int | None = None,
+              with_stats: bool = False):
+        """(i, j, score) of every pair whose n_attr int64 key attributes (the
+        columns of ka, kb; 1-D for one attribute) agree in >= min_match of
+        them, sorted by (i, j) (sj_block)."""
+        import torch
+        if ka.ndim == 1:
+            ka, kb = ka.reshape(-1, 1), kb.reshape(-1, 1)
+        n_attr = int(ka.shape[1])
+        if kb.shape[1] != n_attr:
+            raise ValueError("ka and kb need the same attributes")
+        nA, nB = int(ka.shape[0]), int(kb.shape[0])
+        if capacity is None:
+            capacity = max(1024, 8 * nA)
+        for _ in range(2):
+            buf = self._out_like(ka, (max(int(capacity), 1), 3), torch.int64)
+            n = I64(0)
+            st = SjStats()
+            code = lib().sj_block(self._h, _ptr(ka), nA, _ptr(kb), nB, n_attr, int(min_match),
+                                  _ptr(buf), int(capacity), ctypes.byref(n), ctypes.byref(st))
+            if code == SJ_ERR_CAPACITY:
+                capacity = int(n.value)
+                continue
+            _check(code, "sj_block")
+            m = int(n.value)
+            out = (buf[:m, 0], buf[:m, 1], buf[:m, 2:3].view(torch.float32)[:, 0])
+            return out + (st.as_dict(),) if with_stats else out
+        raise SJError(SJ_ERR_CAPACITY, "sj_block")
+
+    def groupby_sum(self, a_id, a_val, b_id, b_group):
+        """Q3: [(group, SUM(A.Val) as an exact int, COUNT(*))] over the join
+        A.ID = B.ID, groups by value (sj_join_groupby_sum).  a_id, b_id,
+        b_group int64 and a_val int32 arrays (device or host)."""
+        nA, nB = int(a_id.shape[0]), int(b_id.shape[0])
+        cap = nB
+        for _ in range(2):
+            out = (SjGroup * max(1, cap))()
+            n = I64(0)
+            code = lib().sj_join_groupby_sum(self._h, _ptr(a_id), _ptr(a_val), nA, _ptr(b_id),
+                                             _ptr(b_group), nB, out, cap, ctypes.byref(n))
+            if code == SJ_ERR_CAPACITY:
+                cap = int(n.value)
+                continue
+            _check(code, "sj_join_groupby_sum")
+            return [(int(g.group), g.exact_sum(), int(g.count)) for g in out[:int(n.value)]]
+        raise SJError(SJ_ERR_CAPACITY, "sj_join_groupby_sum")
+
+    def sum_product(self, a_id, a_val, b_id, b_val):
+        """Q4: (SUM(A.Val * B.Val) as an exact int, COUNT(*)) over A.ID = B.ID
+        (sj_join_sum_product)."""
+        r = SjGroup()
+        _check(lib().sj_join_sum_product(self._h, _ptr(a_id), _ptr(a_val), int(a_id.shape[0]),
+                                         _ptr(b_id), _ptr(b_val), int(b_id.shape[0]),
+                                         ctypes.byref(r)), "sj_join_sum_product")
+        return r.exact_sum(), int(r.count)
 
     def contrastive_forward(self, A, B, T: float):
         """(loss [1], lse [N] or [2N] with the symmetric flag) on CUDA tensors.

@@ -65,6 +65,17 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sj.SjPair) == 24
     assert ctypes.sizeof(sj.SjConfig) == 48
     assert ctypes.sizeof(sj.SjStats) == 4 * 8 + 5 * 8 + 2 * 8 + 3 * 8 + 8
+    assert ctypes.sizeof(sj.SjGroup) == 32 and sj.SjGroup.sum_hi.offset == 16
+
+
+def test_relational_calls_reject_bad_arguments_without_device(L):
+    n = sj.I64(0)
+    assert L.sj_block(None, None, 0, None, 0, 1, 1, None, 0, ctypes.byref(n), None) == \
+        sj.SJ_ERR_INVALID_ARG
+    assert L.sj_join_groupby_sum(None, None, None, 0, None, None, 0, None, 0,
+                                 ctypes.byref(n)) == sj.SJ_ERR_INVALID_ARG
+    assert L.sj_join_sum_product(None, None, None, 0, None, None, 0, None) == \
+        sj.SJ_ERR_INVALID_ARG
 
 
 def test_header_is_plain_c():
