@@ -1171,6 +1171,8 @@ def main():
     if headline and world == 1 and not args.no_sub:
         out["fp32_same_join"] = guarded(fp32_same_join, args, w, dA, dB, stream, idx, sc,
                                         gpu_out[2], value)
+        out["planner"] = guarded(lambda: dict(J.plan(dA, dB, k, w["tau"]),
+                                              measured_ms_bf16=ms))
         J.close()
         del idx, sc, pairs
         torch.cuda.empty_cache()

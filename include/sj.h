@@ -250,6 +250,40 @@ sj_status sj_topk_noalloc(const float *A, int64_t nA, const float *B, int64_t nB
                           int64_t d, int32_t k, int64_t *out_idx, float *out_score,
                           void *stream);
 
+/* ---- Precision planner (the paper's cost-based optimizer idea, Sec. 4.2:
+ * feasibility test and cost estimation with Eq. (cost), CT ~ 2MNK / peak) ---- */
+
+/* What sj_plan found.  Arrays are indexed by sj_precision. */
+typedef struct {
+  sj_precision choice;    /* the precision with the smallest est_ms */
+  int32_t _pad;
+  double est_ms[4];       /* predicted milliseconds of the whole join */
+  double score_ms[4];     /* its scoring part: 2 nA nB d_p / (eff_p peak_p), Eq. (cost) */
+  double select_ms[4];    /* its rescoring part, from the census (scaled by rows) */
+  double cand_per_row[4]; /* census: candidates per sampled row that were rescored */
+  double overflow_frac[4];/* census: sampled rows that took the rescan fallback */
+  int64_t sample_rows;    /* rows of A in the census */
+} sj_plan_info;
+
+/* Choose the scoring precision of a join before running it.  Every precision
+ * gives the same results (exact rescoring); they differ in tensor-core
+ * cost (E4M3 issues twice the BF16 rate, the BF16 hi/lo split three times
+ * the BF16 work, FP32 runs on the CUDA cores) and in how many candidates
+ * their error margin lets through, which the data decides (a dense band
+ * near the k-th score can overflow the candidate lists into a rescan of all
+ * of B).  sj_plan runs a census: `sample_rows` evenly spaced rows of A
+ * (0: 512) joined against all of B in each precision (k and/or tau as the
+ * real join; k = 0 for none, tau = NaN for none), then predicts
+ *   est_ms[p] = 2 nA nB d_p / (eff_p peak_p) + select_ms_sample[p] nA / s,
+ * with peak_p = SMs x (8,192 BF16 | 16,384 E4M3 | 256 FP32) flop per clock
+ * x the device's clock and eff_p the fraction of it this library's scoring
+ * kernels reached on GB300 (bf16 0.71, e4m3 0.74, bf16x3 0.65, fp32 0.31).
+ * A, B follow the sj_topk rules.  The handle's precision is not used.
+ * Errors: SJ_ERR_INVALID_ARG (null, k < 0, neither k nor tau), the errors of
+ * sj_batch. */
+sj_status sj_plan(sj_handle *h, const float *A, int64_t nA, const float *B, int64_t nB,
+                  int32_t k, double tau, int64_t sample_rows, sj_plan_info *info);
+
 /* ---- Relational join patterns (Sec. 3.1 "Two-way natural join", Sec. 3.3
  * "Group-by aggregates over joins"; the entity-matching blocking of
  * Sec. 6.3.2) ---- */

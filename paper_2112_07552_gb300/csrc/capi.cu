@@ -98,6 +98,7 @@ struct sj_handle {
   std::vector<GraphEntry> graphs;
   std::map<std::pair<int, int>, int> tile_width;  // (k, right-side size class) -> tile width
   int force_bn = 0;                               // autotuner: width under test
+  int64_t force_tps = 0;                          // planner census: a full join's split plan
   cudaEvent_t ev[6]{};
   cudaEvent_t gev[4]{};  // stage events recorded only by captured graphs
   sj::TcContext *tc = nullptr;
@@ -124,6 +125,8 @@ sj_status sj::aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle *
 }
 
 int sj::handle_device(const sj_handle *h) { return h->cfg.device; }
+const sj_config *sj::handle_config(const sj_handle *h) { return &h->cfg; }
+
 void *sj::handle_stream(const sj_handle *h) { return h->stream; }
 int sj::handle_sm_count(const sj_handle *h) { return h->sm_count; }
 
@@ -495,6 +498,7 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     if (rb > 0 && ct > 0) {
       // tps_target counts tiles of BN columns
       tps = (h->cfg.flags & SJ_FLAG_SINGLE_SPLIT) ? ct : std::min(ct, tps_target * (BN / bn));
+      if (h->force_tps > 0) tps = std::min<int64_t>(ct, h->force_tps);
       if ((ct + tps - 1) / tps > 256) tps = (ct + 255) / 256;
       S = (ct + tps - 1) / tps;
     }
@@ -1614,6 +1618,15 @@ sj_status contrastive_finish(sj_handle *h, const ContrastivePlan &cp) {
 }
 
 }  // namespace
+
+int64_t sj::planned_tiles_per_split(sj_handle *h, int64_t nA, int64_t nB, int k, bool thr) {
+  JoinReq r{nullptr, nA, nullptr, nB, k, nullptr, nullptr, thr, 0.5, nullptr, 0, nullptr};
+  BatchPlan P;
+  if (make_batch_plan(h, &r, 1, P) != SJ_OK || P.jobs.empty()) return 0;
+  return P.jobs[0].tiles_per_split;
+}
+
+void sj::set_tiles_per_split(sj_handle *h, int64_t tps) { h->force_tps = tps; }
 
 extern "C" {
 

@@ -23,6 +23,13 @@ namespace sj {
 // joins through it.
 sj_status aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle **out);
 int handle_device(const sj_handle *h);
+const sj_config *handle_config(const sj_handle *h);
+// Column tiles per split the planner gives a one-job join of these sizes on h,
+// and an override of it for h's later calls (0: none): the precision
+// planner's census runs a sample of rows with the full join's split plan, so
+// its candidate lists cover as many columns as the real join's.
+int64_t planned_tiles_per_split(sj_handle *h, int64_t nA, int64_t nB, int k, bool thr);
+void set_tiles_per_split(sj_handle *h, int64_t tps);
 void *handle_stream(const sj_handle *h);
 int handle_sm_count(const sj_handle *h);
 

@@ -45,7 +45,8 @@ SJ_FLAG_DEBUG_TIMEOUT = 0x100
 EXPORTS = ("sj_create", "sj_destroy", "sj_topk", "sj_threshold", "sj_batch",
            "sj_contrastive_fwd", "sj_backward", "sj_topk_noalloc", "sj_status_string",
            "sj_version", "sj_last_error_detail", "sj_autotune", "sj_autotune_load",
-           "sj_debug_scores", "sj_block", "sj_join_groupby_sum", "sj_join_sum_product")
+           "sj_debug_scores", "sj_block", "sj_join_groupby_sum", "sj_join_sum_product",
+           "sj_plan")
 
 I64, P = ctypes.c_int64, ctypes.c_void_p
 
@@ -84,6 +85,21 @@ class SjGroup(ctypes.Structure):
     def exact_sum(self) -> int:
         """The 128-bit two's complement SUM as a Python int."""
         return (int(self.sum_hi) << 64) + int(self.sum_lo)
+
+
+class SjPlanInfo(ctypes.Structure):
+    _fields_ = [("choice", ctypes.c_int), ("_pad", ctypes.c_int32),
+                ("est_ms", ctypes.c_double * 4), ("score_ms", ctypes.c_double * 4),
+                ("select_ms", ctypes.c_double * 4), ("cand_per_row", ctypes.c_double * 4),
+                ("overflow_frac", ctypes.c_double * 4), ("sample_rows", I64)]
+
+    def as_dict(self):
+        names = {v: k for k, v in PRECISIONS.items()}
+        per = lambda arr: {names[p]: float(arr[p]) for p in range(4)}
+        return {"choice": names[int(self.choice)], "est_ms": per(self.est_ms),
+                "score_ms": per(self.score_ms), "select_ms": per(self.select_ms),
+                "cand_per_row": per(self.cand_per_row),
+                "overflow_frac": per(self.overflow_frac), "sample_rows": int(self.sample_rows)}
 
 
 class SJError(RuntimeError):
@@ -144,6 +160,9 @@ def lib() -> ctypes.CDLL:
         L.sj_join_groupby_sum.argtypes = [P, P, P, I64, P, P, I64, P, I64, ctypes.POINTER(I64)]
         L.sj_join_sum_product.restype = st
         L.sj_join_sum_product.argtypes = [P, P, P, I64, P, P, I64, ctypes.POINTER(SjGroup)]
+        L.sj_plan.restype = st
+        L.sj_plan.argtypes = [P, P, I64, P, I64, ctypes.c_int32, ctypes.c_double, I64,
+                              ctypes.POINTER(SjPlanInfo)]
         L.sj_debug_scores.restype = st
         L.sj_debug_scores.argtypes = [P, P, P]
         L.sj_topk_noalloc.restype = st
@@ -284,6 +303,15 @@ class SimilarityJoin:
             s = buf[:m, 2:3].view(torch.float32)[:, 0]
             return (i, j, s, st.as_dict()) if with_stats else (i, j, s)
         raise SJError(SJ_ERR_CAPACITY, "sj_threshold")
+
+    def plan(self, A, B, k: int = 0, tau: float | None = None, sample_rows: int = 0):
+        """sj_plan: the census and cost estimate of each scoring precision for
+        this join; returns a dict (choice, est_ms, ... per precision name)."""
+        info = SjPlanInfo()
+        _check(lib().sj_plan(self._h, _ptr(A), _rows(A, self.d), _ptr(B), _rows(B, self.d),
+                             int(k), float("nan") if tau is None else float(tau),
+                             int(sample_rows), ctypes.byref(info)), "sj_plan")
+        return info.as_dict()
 
     def block(self, ka, kb, min_match: int = 1, capacity: int | None = None,
               with_stats: bool = False):
