@@ -828,6 +828,80 @@ sj_status topk_fallback(sj_handle *h, Counters *ctr, const RowMeta *meta, const 
   return redo_rows.empty() ? SJ_OK : SJ_ERR_INTERNAL;  // a list of all of B cannot be cut off
 }
 
+// The rows of one job to re-join, gathered into a dense matrix.
+__global__ void gather_rows_kernel(const float *src, const int *rows, int n, int64_t d,
+                                   float *dst) {
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const float *sr = src + (int64_t)rows[r] * d;
+    float *o = dst + (int64_t)r * d;
+    for (int64_t c = threadIdx.x; c < d; c += blockDim.x) o[c] = sr[c];
+  }
+}
+
+// Top-k rows of the re-join back to their places in the job's outputs.
+__global__ void scatter_topk_kernel(const int *rows, int n, int k, const int64_t *ii,
+                                    const float *ss, int64_t *oi, float *os) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * k;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t dst = (int64_t)rows[t / k] * k + t % k;
+    oi[dst] = ii[t];
+    os[dst] = ss[t];
+  }
+}
+
+// Overflowed rows from this many up are re-joined by the FP32 form instead of
+// rescanned one by one (a 128-row FFMA tile serves them together).
+constexpr int kRejoinMinRows = 64;
+
+struct DevMem {
+  void *p = nullptr;
+  ~DevMem() {
+    if (p) cudaFree(p);
+  }
+};
+
+// Cascade step for rows whose band lists overflowed on a tensor-core pass:
+// the dense band of near-ties below their k-th score, wider than the lists,
+// comes from the margin of the low precision (BF16 (d + 32) 2^-21, E4M3
+// (d + 32) 2^-13, the hi/lo split (3d + 32) 2^-21, times the norms).  The
+// FP32 form's margin, 2 gamma_d, is two to four orders of magnitude
+// narrower, so the same rows re-joined against all of B in FP32 give short
+// candidate lists again; that costs 2 nB d flops per row on the FFMA tiles,
+// instead of a Dot2 rescan of all of B per row.  The re-join runs through
+// the handle's auxiliary FP32 handle (its own workspace: this call's buffers
+// stay intact), in chunks of rows, and writes the rows' outputs in place.
+sj_status rejoin_fp32(sj_handle *h, const JobDev &jd, int64_t d, const int *rows, int n,
+                      int64_t &launches) {
+  sj_handle *ax = nullptr;
+  sj_status s = sj::aux_handle(h, d, SJ_FP32, &ax);
+  if (s != SJ_OK) return s;
+  cudaStream_t stm = h->stream;
+  const int k = jd.k;
+  const int chunk = std::min(n, 1 << 20);
+  DevMem ag, ii, ss;
+  SJ_CUDA(cudaMalloc(&ag.p, (size_t)chunk * d * 4));
+  SJ_CUDA(cudaMalloc(&ii.p, (size_t)chunk * k * 8));
+  SJ_CUDA(cudaMalloc(&ss.p, (size_t)chunk * k * 4));
+  for (int c0 = 0; c0 < n; c0 += chunk) {
+    const int nc = std::min(chunk, n - c0);
+    gather_rows_kernel<<<std::min(nc, 8192), 256, 0, stm>>>(jd.A, rows + c0, nc, d,
+                                                          static_cast<float *>(ag.p));
+    SJ_CUDA(cudaGetLastError());
+    sj_stats st;
+    s = sj_topk(ax, static_cast<const float *>(ag.p), nc, jd.B, jd.nB, k,
+                static_cast<int64_t *>(ii.p), static_cast<float *>(ss.p), &st);
+    if (s != SJ_OK) return s;
+    const int64_t tot = (int64_t)nc * k;
+    scatter_topk_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, stm>>>(
+        rows + c0, nc, k, static_cast<int64_t *>(ii.p), static_cast<float *>(ss.p), jd.out_idx,
+        jd.out_score);
+    SJ_CUDA(cudaGetLastError());
+    launches += 2 + st.n_launches;
+  }
+  SJ_CUDA(cudaStreamSynchronize(stm));
+  return SJ_OK;
+}
+
 // Fallback rows of the whole batch, grouped by job.
 sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, unsigned n_ovf,
                             Arena &ar, int64_t &launches) {
@@ -865,10 +939,14 @@ sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, uns
     while (t1 < n_ovf && by_job[t1].first == by_job[t0].first) ++t1;
     const JobDev &jd = P.jobs[by_job[t0].first / 2];
     const bool band = (by_job[t0].first & 1) != 0;
-    sj_status s = topk_fallback(h, B.ctr, B.meta, jd, P.d, static_cast<int *>(rows_s.p) + t0,
-                                static_cast<long long *>(keys_s.p) + t0, lrow.data() + t0,
-                                lkey.data() + t0, (int)(t1 - t0), band ? B.band : nullptr,
-                                B.band_cnt, ar, launches);
+    sj_status s;
+    if (!band && h->cfg.prec != SJ_FP32 && (int)(t1 - t0) >= kRejoinMinRows)
+      s = rejoin_fp32(h, jd, P.d, static_cast<int *>(rows_s.p) + t0, (int)(t1 - t0), launches);
+    else
+      s = topk_fallback(h, B.ctr, B.meta, jd, P.d, static_cast<int *>(rows_s.p) + t0,
+                        static_cast<long long *>(keys_s.p) + t0, lrow.data() + t0,
+                        lkey.data() + t0, (int)(t1 - t0), band ? B.band : nullptr, B.band_cnt,
+                        ar, launches);
     if (s != SJ_OK) return s;
     t0 = t1;
   }

@@ -203,7 +203,14 @@ __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int
       r.theta = theta / to_s;
       r.cnt = w;
       r.last = w;
-      if (w > limit) r.overflow = 1;  // the band near the k-th score is too dense
+      if (w > limit) {
+        // the band near the k-th score is too dense: the row goes to the
+        // fallback, which needs only the entries kept so far (their k-th
+        // largest bounds the row's k-th score from below), so the rest of
+        // its columns make no more top-k visits (threshold visits go on)
+        r.overflow = 1;
+        r.theta = INFINITY;
+      }
     }
   }
 }
