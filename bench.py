@@ -97,6 +97,8 @@ def parse():
                    help="scoring precision override (join and zipf workloads); fp32 is "
                         "the CUDA-core comparison form at the same exactness")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--parity-rows", type=int, default=2000,
+                   help="zipf workload: cluster-stratified rows checked against the oracle")
     p.add_argument("--no-sub", action="store_true",
                    help="headline only: skip the FP32 form and the other workloads' sub-results")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -726,42 +728,65 @@ def run_fp8(args, data=None, steps=None, warmup=None):
     return out
 
 
-def zipf_fp8_sample(w, A, dB, dev, stream, rows=2048):
-    """E4M3 scoring of a sample of left rows against all of B (top-k): the
-    largest observed |s~ - s| over rescored candidates, the largest proven
-    margin, and how many rows' candidate bands overflowed."""
-    import ctypes
+def zipf_parity(w, A, B, gidx, gsc, n_rows=2000):
+    """Oracle parity of the top-k on cluster-stratified rows: the clusters are
+    ranked by size (Zipf rank), cut into four strata holding a quarter of
+    the rows each (the few largest clusters first), and n_rows/4 rows are
+    drawn from each, so the dense bands of the big clusters are covered."""
+    import oracle
+    from paper_2112_07552_gb300 import datagen
+    asg = datagen.assignments(w["nA"], w["clusters"], w["seed"], 0, w.get("zipf_s"))
+    sizes = np.bincount(asg, minlength=w["clusters"])
+    order = np.argsort(-sizes, kind="stable")
+    rank = np.empty_like(order)
+    rank[order] = np.arange(len(order))
+    row_rank = rank[asg]
+    cum = np.cumsum(sizes[order]) / w["nA"]
+    cuts = [int(np.searchsorted(cum, q)) for q in (0.25, 0.5, 0.75)]
+    edges = [0] + cuts + [w["clusters"]]
+    rng = np.random.default_rng(77)
+    rows, strata = [], []
+    for t in range(4):
+        cand = np.nonzero((row_rank >= edges[t]) & (row_rank < edges[t + 1]))[0]
+        take = min(len(cand), n_rows // 4)
+        rows.append(rng.choice(cand, size=take, replace=False))
+        strata.append({"cluster_ranks": [int(edges[t]), int(edges[t + 1])], "rows": take})
+    rows = np.sort(np.concatenate(rows))
+    t0 = time.perf_counter()
+    idx, s32, _ = oracle.topk(A, B, w["k"], rows=rows)
+    dt = time.perf_counter() - t0
+    ok = bool(np.array_equal(gidx[rows], idx)
+              and np.array_equal(gsc[rows].view(np.uint32), s32.view(np.uint32)))
+    return {"rows": int(len(rows)), "strata": strata, "exact": ok, "oracle_seconds": dt,
+            "oracle_cores": oracle.num_threads(),
+            "oracle_pair_scores_per_s": len(rows) * w["nB"] / dt}
 
+
+def fp8_error_sample(w, A, B, dB, rows=16):
+    """E4M3 scoring error against FP64 on every pair of a row sample: the raw
+    E4M3 scores of `rows` rows against all of B (sj_debug_scores) against the
+    oracle's FP64 enclosure of each exact score, with the proven margins."""
     import torch
 
+    import oracle
     from paper_2112_07552_gb300 import sj
-    rng = np.random.default_rng(99)
-    sel = np.sort(rng.choice(w["nA"], size=min(rows, w["nA"]), replace=False))
-    dS = torch.from_numpy(A[sel]).to(dev)
-    k = w["k"]
-    idx = torch.empty((len(sel), k), dtype=torch.int64, device=dev)
-    sc = torch.empty((len(sel), k), dtype=torch.float32, device=dev)
-    out = {"rows": int(len(sel))}
-    for prec in ("fp8", "bf16"):
-        J = sj.SimilarityJoin(w["d"], prec=prec, device=dev.index, stream=stream)
-        jb = (sj.SjJob * 1)()
-        jb[0].A, jb[0].nA, jb[0].B, jb[0].nB = dS.data_ptr(), len(sel), dB.data_ptr(), w["nB"]
-        jb[0].k = k
-        jb[0].topk_idx, jb[0].topk_score = idx.data_ptr(), sc.data_ptr()
-        st = sj.SjStats()
-        t0 = time.perf_counter()
-        code = sj.lib().sj_batch(J.handle, jb, 1, ctypes.byref(st))
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        J.close()
-        if code != sj.SJ_OK:
-            out[prec] = {"status": int(code)}
-            continue
-        out[prec] = {"max_abs_err": float(st.max_abs_err_lowprec),
-                     "margin_max": float(st.margin_max),
-                     "n_candidates": int(st.n_candidates),
-                     "n_overflow_rows": int(st.n_overflow_rows), "seconds": dt}
-    return out
+    sel = np.linspace(0, w["nA"] - 1, rows).astype(np.int64)
+    As = np.ascontiguousarray(A[sel])
+    dA = torch.from_numpy(As).cuda()
+    raw = torch.empty((rows, w["nB"]), dtype=torch.float32, device="cuda")
+    marg = torch.empty(rows, dtype=torch.float32, device="cuda")
+    with sj.SimilarityJoin(w["d"], prec="fp8", device=0) as J:
+        sj._check(sj.lib().sj_debug_scores(J.handle, raw.data_ptr(), marg.data_ptr()),
+                  "sj_debug_scores")
+        J.topk(dA, dB, w["k"])
+    torch.cuda.synchronize()
+    lo, hi = oracle.enclose_all(As, B)
+    r = raw.cpu().numpy().astype(np.float64)
+    m = marg.cpu().numpy().astype(np.float64)
+    err = np.maximum(r - lo, hi - r)
+    return {"rows": rows, "pairs": int(r.size), "max_abs_err": float(err.max()),
+            "mean_abs_err": float(np.abs(r - 0.5 * (lo + hi)).mean()),
+            "margin_max": float(m.max()), "max_err_over_margin": float((err / m[:, None]).max())}
 
 
 def guarded(fn, *a, **kw):
@@ -1122,11 +1147,13 @@ def main():
         bound, peak = "alu", sms * 128 * 2 * mhz * 1e6 / 1e12
         peak_source = "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (sampled)" % (sms, mhz)
     cpu = None
-    if world == 1 and not args.no_cpu:
+    if world == 1 and not args.no_cpu and args.workload != "zipf":
         cpu = cpu_baseline(w, A, B, args.cpu_seconds, gpu_out, dups)
-    fp8_sample = None
-    if args.workload == "zipf":
-        fp8_sample = zipf_fp8_sample(w, A, dB, dev, stream)
+    fp8_sample = zipf_par = None
+    if args.workload == "zipf" and world == 1:
+        fp8_sample = guarded(fp8_error_sample, w, A, B, dB)
+        if not args.no_cpu:
+            zipf_par = guarded(zipf_parity, w, A, B, gpu_out[0], gpu_out[1], args.parity_rows)
     headline = args.workload == "join" and not args.shape and not args.small
     # algorithmic bytes of one scoring launch: the packed operands read once
     # plus the band lists written once (the k best of each list and its
@@ -1167,7 +1194,20 @@ def main():
         "margin_max": float(stats[-1].margin_max),
     }
     if fp8_sample is not None:
-        out["fp8_sample"] = fp8_sample
+        out["fp8_error_vs_fp64"] = fp8_sample
+    if zipf_par is not None:
+        out["parity_stratified"] = zipf_par
+        if "oracle_pair_scores_per_s" in zipf_par:
+            out["cpu_baseline"] = {"value": zipf_par["oracle_pair_scores_per_s"], "unit": METRIC,
+                                   "cores": zipf_par["oracle_cores"], "kind": "oracle",
+                                   "sample": "%d cluster-stratified left rows x all %d right rows "
+                                             "(top-%d), %.1f s" % (zipf_par["rows"], nB, k,
+                                                                   zipf_par["oracle_seconds"]),
+                                   "parity_rows_exact": zipf_par["exact"]}
+    if args.workload == "zipf":
+        out["fallback_share"] = {"rows": int(stats[-1].n_overflow_rows),
+                                 "fraction": stats[-1].n_overflow_rows / nA,
+                                 "how": "rows whose band lists overflowed, re-joined in FP32"}
     if headline and world == 1 and not args.no_sub:
         out["fp32_same_join"] = guarded(fp32_same_join, args, w, dA, dB, stream, idx, sc,
                                         gpu_out[2], value)
