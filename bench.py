@@ -309,8 +309,8 @@ def infonce_cpu_baseline(A, B, T, budget_s):
 def run_infonce(args, steps=None, warmup=None, cpu_seconds=None, e2e=True):
     """Contrastive join: one step = forward (loss, lse) + backward (dA, dB).
     Returns the line (a dict)."""
-    steps = steps or steps
-    warmup = warmup or warmup
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
     cpu_seconds = args.cpu_seconds if cpu_seconds is None else cpu_seconds
     import torch
 
@@ -409,8 +409,8 @@ BATCH = {"workload": "bf16_batch_4096_jobs_loguniform_100-50000_d384_k10_tau0.8"
 def run_batch(args, steps=None, warmup=None, e2e=True):
     """Uneven batch: one step = one sj_batch call over every job (top-k and
     threshold of each job from one scoring pass).  Returns the line."""
-    steps = steps or steps
-    warmup = warmup or warmup
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
     import ctypes
 
     import torch
@@ -617,8 +617,8 @@ def run_fp8(args, data=None, steps=None, warmup=None):
     margin the running k-th best stays within 2m of the bulk until a row's
     best matches appear, so every band list overflows into the rescan.)
     `data` = (A, B, dA, dB) reuses the caller's inputs.  Returns the line."""
-    steps = steps or steps
-    warmup = warmup or warmup
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
     import ctypes
 
     import torch

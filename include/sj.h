@@ -219,6 +219,28 @@ sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t
 sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, float T,
                       const float *lse, const float *grad_loss, float *dA, float *dB);
 
+/* Row shard of the contrastive join, for data parallelism over rows (one
+ * GPU per shard): A_rows are rows [r0, r0 + n_rows) of A (n_rows x d, DEVICE
+ * float32), B all N rows of B, the positive of local row i is B row r0 + i,
+ * and the loss keeps the global 1/N.  Writes lse_rows[n_rows] and
+ * loss_part[0] = (1/N) sum_i (lse_i - S_i,r0+i): the shards' loss_part sum to
+ * the loss of sj_contrastive_fwd (an all-reduce of one float).
+ * One-directional loss only (SJ_FLAG_SYM_INFONCE: SJ_ERR_UNSUPPORTED).
+ * Errors: SJ_ERR_INVALID_ARG (r0 + n_rows > N, ...) and those of
+ * sj_contrastive_fwd. */
+sj_status sj_contrastive_fwd_rows(sj_handle *h, const void *A_rows, int64_t n_rows, int64_t r0,
+                                  const void *B, int64_t N, float T, float *loss_part,
+                                  float *lse_rows);
+
+/* Backward of sj_contrastive_fwd_rows: dA_rows (n_rows x d) is the gradient of
+ * the shard's rows, dB_part (N x d) the shard's contribution to the gradient
+ * of B (G_rows^T A_rows / T); the shards' dB_part sum to sj_backward's dB (an
+ * all-reduce of N x d floats).  Same two paths (materialised or fused) as
+ * sj_backward.  Errors as sj_backward, plus those of the forward's rows. */
+sj_status sj_backward_rows(sj_handle *h, const void *A_rows, int64_t n_rows, int64_t r0,
+                           const void *B, int64_t N, float T, const float *lse_rows,
+                           const float *grad_loss, float *dA_rows, float *dB_part);
+
 /* Exact top-k join that allocates nothing, for callers that cannot allocate
  * device memory at call time (their HBM is reserved in full by another
  * allocator's pool, or they must not call cudaMalloc/cudaFree, which can

@@ -1624,22 +1624,22 @@ namespace {
 // Shared set-up of the contrastive calls: BF16 packing (and transposes for the
 // backward) of A and B into the workspace, and their tensor maps.
 struct ContrastivePlan {
-  int64_t n, d, np, dp;
+  int64_t nx, ny, d, npx, npy, dp;  // rows of A (the call's row operand) and of B, padded
   void *Ap, *Bp, *AT, *BT;
-  void *G;       // materialised backward: dL/dS (np x np BF16)
-  float *part;   // forward: partial row states (3 x 2 n_splits x np) and S_ii (np)
+  void *G;       // materialised backward: dL/dS (npx x npy BF16)
+  float *part;   // forward: partial row states (3 x 2 n_splits x npx) and S_ii (npx)
   int n_splits, tiles_per_split;
   Counters *ctr;
-  float *scratch;  // 2n floats (per-row loss terms)
+  float *scratch;  // nx + ny floats (per-row loss terms)
   unsigned char mA[128], mB[128], mAT[128], mBT[128], mG[128];
 };
 
 // `gmat`: also reserve and map G (fails with SJ_ERR_OOM before any launch
-// when the workspace cannot hold it).
-sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t N, bool bwd,
-                            ContrastivePlan &cp, bool gmat = false) {
-  if (!h || !A || !B || N < 1) return SJ_ERR_INVALID_ARG;
-  if (N >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
+// when the workspace cannot hold it).  A has nx rows, B ny rows.
+sj_status contrastive_setup(sj_handle *h, const void *A, int64_t nx, const void *B, int64_t ny,
+                            bool bwd, ContrastivePlan &cp, bool gmat = false) {
+  if (!h || !A || !B || nx < 1 || ny < 1) return SJ_ERR_INVALID_ARG;
+  if (nx >= (1ll << 31) - 1024 || ny >= (1ll << 31) - 1024) return SJ_ERR_UNSUPPORTED;
   if (!is_device_ptr(A, h->cfg.device) || !is_device_ptr(B, h->cfg.device))
     return SJ_ERR_INVALID_ARG;
   SJ_CUDA(cudaSetDevice(h->cfg.device));
@@ -1648,25 +1648,27 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
     sj_status s = tc_create(&h->tc);
     if (s != SJ_OK) return s;
   }
-  cp.n = N;
+  cp.nx = nx;
+  cp.ny = ny;
   cp.d = h->cfg.d;
-  cp.np = round_up(N, 256);
+  cp.npx = round_up(nx, 256);
+  cp.npy = round_up(ny, 256);
   cp.dp = round_up(cp.d, 64);
-  contrastive_splits(cp.np, &cp.n_splits, &cp.tiles_per_split);
-  const size_t op = (size_t)cp.np * cp.dp * 2;
-  const size_t gsz = (size_t)cp.np * cp.np * 2;
-  const size_t psz = ((size_t)6 * cp.n_splits + 1) * cp.np * 4;
-  size_t bytes = 2 * op + (bwd ? 2 * op : 0) + sizeof(Counters) + (size_t)2 * N * 4 + 8 * 256 +
-                 (gmat ? gsz + 256 : 0) + (bwd ? 0 : psz + 256);
+  contrastive_splits(cp.npy, &cp.n_splits, &cp.tiles_per_split);
+  const size_t opa = (size_t)cp.npx * cp.dp * 2, opb = (size_t)cp.npy * cp.dp * 2;
+  const size_t gsz = (size_t)cp.npx * cp.npy * 2;
+  const size_t psz = ((size_t)6 * cp.n_splits + 1) * std::max(cp.npx, cp.npy) * 4;
+  size_t bytes = (opa + opb) * (bwd ? 2 : 1) + sizeof(Counters) + (size_t)(nx + ny) * 4 +
+                 8 * 256 + (gmat ? gsz + 256 : 0) + (bwd ? 0 : psz + 256);
   sj_status s = ensure_ws(h, bytes);
   if (s != SJ_OK) return s;
   Arena ar{static_cast<unsigned char *>(h->ws), h->ws_size, 0};
   cp.ctr = static_cast<Counters *>(ar.take(sizeof(Counters)));
-  cp.scratch = static_cast<float *>(ar.take((size_t)2 * N * 4));
-  cp.Ap = ar.take(op);
-  cp.Bp = ar.take(op);
-  cp.AT = bwd ? ar.take(op) : nullptr;
-  cp.BT = bwd ? ar.take(op) : nullptr;
+  cp.scratch = static_cast<float *>(ar.take((size_t)(nx + ny) * 4));
+  cp.Ap = ar.take(opa);
+  cp.Bp = ar.take(opb);
+  cp.AT = bwd ? ar.take(opa) : nullptr;
+  cp.BT = bwd ? ar.take(opb) : nullptr;
   cp.G = gmat ? ar.take(gsz) : nullptr;
   cp.part = bwd ? nullptr : static_cast<float *>(ar.take(psz));
   if (!cp.ctr || !cp.scratch || !cp.Ap || !cp.Bp || (bwd && (!cp.AT || !cp.BT)) ||
@@ -1674,15 +1676,15 @@ sj_status contrastive_setup(sj_handle *h, const void *A, const void *B, int64_t 
     return SJ_ERR_INTERNAL;
   cudaStream_t st = h->stream;
   SJ_CUDA(cudaMemsetAsync(cp.ctr, 0, sizeof(Counters), st));
-  SJ_CUDA(launch_contrastive_pack(static_cast<const float *>(A), N, cp.d, cp.Ap, cp.AT, cp.np, cp.dp,
-                                  &cp.ctr->err_flags, st));
-  SJ_CUDA(launch_contrastive_pack(static_cast<const float *>(B), N, cp.d, cp.Bp, cp.BT, cp.np, cp.dp,
-                                  &cp.ctr->err_flags, st));
-  s = tc_encode_2d(h->tc, cp.Ap, cp.dp, cp.np, 64, 128, cp.mA);
-  if (s == SJ_OK) s = tc_encode_2d(h->tc, cp.Bp, cp.dp, cp.np, 64, 128, cp.mB);
-  if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.AT, cp.np, cp.dp, 64, 64, cp.mAT);
-  if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.BT, cp.np, cp.dp, 64, 64, cp.mBT);
-  if (s == SJ_OK && gmat) s = tc_encode_2d(h->tc, cp.G, cp.np, cp.np, 64, 128, cp.mG);
+  SJ_CUDA(launch_contrastive_pack(static_cast<const float *>(A), nx, cp.d, cp.Ap, cp.AT, cp.npx,
+                                  cp.dp, &cp.ctr->err_flags, st));
+  SJ_CUDA(launch_contrastive_pack(static_cast<const float *>(B), ny, cp.d, cp.Bp, cp.BT, cp.npy,
+                                  cp.dp, &cp.ctr->err_flags, st));
+  s = tc_encode_2d(h->tc, cp.Ap, cp.dp, cp.npx, 64, 128, cp.mA);
+  if (s == SJ_OK) s = tc_encode_2d(h->tc, cp.Bp, cp.dp, cp.npy, 64, 128, cp.mB);
+  if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.AT, cp.npx, cp.dp, 64, 64, cp.mAT);
+  if (s == SJ_OK && bwd) s = tc_encode_2d(h->tc, cp.BT, cp.npy, cp.dp, 64, 64, cp.mBT);
+  if (s == SJ_OK && gmat) s = tc_encode_2d(h->tc, cp.G, cp.npy, cp.npx, 64, 128, cp.mG);
   return s;
 }
 
@@ -1708,19 +1710,28 @@ void sj::set_tiles_per_split(sj_handle *h, int64_t tps) { h->force_tps = tps; }
 
 extern "C" {
 
-sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t N, float T,
-                             float *loss, float *lse) {
-  if (!h || !A || !B || N < 1 || !(T > 0.f) || !loss || !lse) return SJ_ERR_INVALID_ARG;
-  if (!is_device_ptr(loss, h->cfg.device) || !is_device_ptr(lse, h->cfg.device))
-    return SJ_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Forward over rows [r0, r0 + nx) of a paired set of N rows: A holds those nx
+// rows, B all N; the positive of local row i is B row r0 + i; the loss is
+// normalised by N.  With r0 = 0 and nx = N it is the whole join (and the
+// symmetric flag adds the column term).
+sj_status contrastive_fwd_impl(sj_handle *h, const void *A, int64_t nx, int64_t r0,
+                               const void *B, int64_t N, float T, bool sym, float *loss,
+                               float *lse) {
   ContrastivePlan cp;
-  sj_status s = contrastive_setup(h, A, B, N, false, cp);
+  sj_status s = contrastive_setup(h, A, nx, B, N, false, cp);
   if (s != SJ_OK) return s;
-  const bool sym = (h->cfg.flags & SJ_FLAG_SYM_INFONCE) != 0;
   ContrastiveArgs a{};
-  a.n = N;
+  a.n = nx;
   a.d = cp.d;
-  a.np = cp.np;
+  a.np = cp.npx;
+  a.ny = N;
+  a.npy = cp.npy;
+  a.diag_off = r0;
+  a.n_norm = N;
   a.dp = cp.dp;
   a.T = T;
   a.n_chunks = 1;
@@ -1730,23 +1741,134 @@ sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t
   // partial row states are merged by a second launch
   a.n_splits = cp.n_splits;
   a.tiles_per_split = cp.tiles_per_split;
-  const size_t pn = (size_t)2 * cp.n_splits * cp.np;
+  const size_t pn = (size_t)2 * cp.n_splits * cp.npx;
   a.part_m = cp.part;
   a.part_l = cp.part + pn;
   a.part_c = cp.part + 2 * pn;
   a.diag_out = cp.part + 3 * pn;
-  const int grid = (int)std::min<int64_t>((cp.np / 128) * cp.n_splits, h->sm_count);
+  const int grid = (int)std::min<int64_t>((cp.npx / 128) * cp.n_splits, h->sm_count);
   a.lse_out = lse;
   a.term_out = cp.scratch;
   SJ_CUDA(launch_contrastive(kContrastiveFwd, cp.mA, cp.mB, nullptr, a, grid, h->stream));
-  if (sym) {
+  if (sym) {  // square only: rows of B against the columns of A
     a.lse_out = lse + N;
     a.term_out = cp.scratch + N;
     SJ_CUDA(launch_contrastive(kContrastiveFwd, cp.mB, cp.mA, nullptr, a, grid, h->stream));
   }
-  SJ_CUDA(launch_contrastive_loss(cp.scratch, sym ? cp.scratch + N : nullptr, N, sym ? 0.5f : 1.f,
-                                  0.5f, loss, h->stream));
+  SJ_CUDA(launch_contrastive_loss(cp.scratch, sym ? cp.scratch + N : nullptr, nx, N,
+                                  sym ? 0.5f : 1.f, 0.5f, loss, h->stream));
   return contrastive_finish(h, cp);
+}
+
+// Backward of contrastive_fwd_impl: dA (nx x d) for the call's rows and dB
+// (N x d), the rows' contribution to the gradient of B (the whole of it when
+// nx = N).
+sj_status backward_impl(sj_handle *h, const void *A, int64_t nx, int64_t r0, const void *B,
+                        int64_t N, float T, bool sym, const float *lse, const float *grad_loss,
+                        float *dA, float *dB) {
+  ContrastivePlan cp;
+  // materialise G when the workspace allows, else the fused path
+  bool gmat = (h->cfg.flags & SJ_FLAG_FUSED_BACKWARD) == 0;
+  sj_status s = gmat ? contrastive_setup(h, A, nx, B, N, true, cp, true) : SJ_ERR_OOM;
+  if (s == SJ_ERR_OOM) {
+    gmat = false;
+    s = contrastive_setup(h, A, nx, B, N, true, cp, false);
+  }
+  if (s != SJ_OK) return s;
+  ContrastiveArgs a{};
+  a.n = nx;
+  a.d = cp.d;
+  a.np = cp.npx;
+  a.ny = N;
+  a.npy = cp.npy;
+  a.diag_off = r0;
+  a.n_norm = N;
+  a.dp = cp.dp;
+  a.T = T;
+  a.n_chunks = (int)((cp.dp + 383) / 384);
+  a.n_splits = 1;
+  a.tiles_per_split = (int)(cp.npy / 128);
+  a.grad_loss = grad_loss;
+  a.ctr = cp.ctr;
+  a.debug_timeout = (h->cfg.flags & SJ_FLAG_DEBUG_TIMEOUT) ? 1 : 0;
+  // G = w_r (P - I) + w_c (Q - I): the row softmax P of A's rows, the column
+  // softmax Q (symmetric loss only)
+  a.lse_r = lse;
+  a.wr = sym ? 0.5f : 1.f;
+  a.lse_c = sym ? lse + N : lse;
+  a.wc = sym ? 0.5f : 0.f;
+  const int64_t n_rb = cp.npx / 128;
+  if (gmat) {
+    // G pass: units = (row block, column split) for balance; G written
+    // through its tensor map (TMA stores)
+    a.n_splits = cp.n_splits;
+    a.tiles_per_split = cp.tiles_per_split;
+    const int grid = (int)std::min<int64_t>(n_rb * a.n_splits, h->sm_count);
+    SJ_CUDA(launch_contrastive(kContrastiveGprime, cp.mA, cp.mB, cp.mG, a, grid, h->stream));
+    ContrastiveGemmArgs g{};
+    g.d = cp.d;
+    g.dp = cp.dp;
+    g.n_norm = N;
+    g.T = T;
+    g.n_chunks = a.n_chunks;
+    g.grad_loss = grad_loss;
+    g.ctr = cp.ctr;
+    g.n = nx;  // dA = G B / T: rows of A, K over the rows of B
+    g.np = cp.npx;
+    g.kp = cp.npy;
+    g.dX = dA;
+    SJ_CUDA(launch_contrastive_gemm(false, cp.mG, cp.mBT, g,
+                                    (int)std::min<int64_t>(n_rb * g.n_chunks, h->sm_count),
+                                    h->stream));
+    g.n = N;  // dB = G^T A / T: rows of B, K over the rows of A
+    g.np = cp.npy;
+    g.kp = cp.npx;
+    g.dX = dB;
+    // G^T as an MN-major operand: boxes of 64 columns x 64 rows of G
+    unsigned char mG64[128];
+    sj_status ms = tc_encode_2d(h->tc, cp.G, cp.npy, cp.npx, 64, 64, mG64);
+    if (ms != SJ_OK) return ms;
+    SJ_CUDA(launch_contrastive_gemm(true, mG64, cp.mAT, g,
+                                    (int)std::min<int64_t>((cp.npy / 128) * g.n_chunks,
+                                                           h->sm_count),
+                                    h->stream));
+    return contrastive_finish(h, cp);
+  }
+  // dA: rows of A against columns (rows of B); row term = softmax over j
+  a.dX = dA;
+  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mA, cp.mB, cp.mBT, a,
+                             (int)std::min<int64_t>(n_rb * a.n_chunks, h->sm_count), h->stream));
+  // dB: rows of B against columns (rows of A); the row softmax term is indexed
+  // by the kernel's columns, the column softmax term by its rows; B row j's
+  // positive is A row j - r0
+  a.n = N;
+  a.np = cp.npy;
+  a.ny = nx;
+  a.npy = cp.npx;
+  a.diag_off = -r0;
+  a.tiles_per_split = (int)(cp.npx / 128);
+  a.lse_r = sym ? lse + N : lse;
+  a.wr = sym ? 0.5f : 0.f;
+  a.lse_c = lse;
+  a.wc = sym ? 0.5f : 1.f;
+  a.dX = dB;
+  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mB, cp.mA, cp.mAT, a,
+                             (int)std::min<int64_t>((cp.npy / 128) * a.n_chunks, h->sm_count),
+                             h->stream));
+  return contrastive_finish(h, cp);
+}
+
+}  // namespace
+
+extern "C" {
+
+sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t N, float T,
+                             float *loss, float *lse) {
+  if (!h || !A || !B || N < 1 || !(T > 0.f) || !loss || !lse) return SJ_ERR_INVALID_ARG;
+  if (!is_device_ptr(loss, h->cfg.device) || !is_device_ptr(lse, h->cfg.device))
+    return SJ_ERR_INVALID_ARG;
+  return contrastive_fwd_impl(h, A, N, 0, B, N, T, (h->cfg.flags & SJ_FLAG_SYM_INFONCE) != 0,
+                              loss, lse);
 }
 
 sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, float T,
@@ -1757,75 +1879,35 @@ sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, flo
   if (!is_device_ptr(lse, dv) || !is_device_ptr(grad_loss, dv) || !is_device_ptr(dA, dv) ||
       !is_device_ptr(dB, dv))
     return SJ_ERR_INVALID_ARG;
-  ContrastivePlan cp;
-  // materialise G when the workspace allows, else the fused path
-  bool gmat = (h->cfg.flags & SJ_FLAG_FUSED_BACKWARD) == 0;
-  sj_status s = gmat ? contrastive_setup(h, A, B, N, true, cp, true) : SJ_ERR_OOM;
-  if (s == SJ_ERR_OOM) {
-    gmat = false;
-    s = contrastive_setup(h, A, B, N, true, cp, false);
-  }
-  if (s != SJ_OK) return s;
-  const bool sym = (h->cfg.flags & SJ_FLAG_SYM_INFONCE) != 0;
-  ContrastiveArgs a{};
-  a.n = N;
-  a.d = cp.d;
-  a.np = cp.np;
-  a.dp = cp.dp;
-  a.T = T;
-  a.n_chunks = (int)((cp.dp + 383) / 384);
-  a.n_splits = 1;
-  a.tiles_per_split = (int)(cp.np / 128);
-  a.grad_loss = grad_loss;
-  a.ctr = cp.ctr;
-  a.debug_timeout = (h->cfg.flags & SJ_FLAG_DEBUG_TIMEOUT) ? 1 : 0;
-  // G = w_r (P - I) + w_c (Q - I): the row softmax P of A's rows, the column
-  // softmax Q (symmetric loss only)
-  a.lse_r = lse;
-  a.wr = sym ? 0.5f : 1.f;
-  a.lse_c = sym ? lse + N : lse;
-  a.wc = sym ? 0.5f : 0.f;
-  const int64_t n_rb = cp.np / 128;
-  if (gmat) {
-    // G pass: units = (row block, column split) for balance; G written
-    // through its tensor map (TMA stores)
-    a.n_splits = cp.n_splits;
-    a.tiles_per_split = cp.tiles_per_split;
-    const int grid = (int)std::min<int64_t>(n_rb * a.n_splits, h->sm_count);
-    SJ_CUDA(launch_contrastive(kContrastiveGprime, cp.mA, cp.mB, cp.mG, a, grid, h->stream));
-    ContrastiveGemmArgs g{};
-    g.n = N;
-    g.d = cp.d;
-    g.np = cp.np;
-    g.dp = cp.dp;
-    g.T = T;
-    g.n_chunks = a.n_chunks;
-    g.grad_loss = grad_loss;
-    g.ctr = cp.ctr;
-    const int ggrid = (int)std::min<int64_t>(n_rb * g.n_chunks, h->sm_count);
-    g.dX = dA;  // dA = G B / T
-    SJ_CUDA(launch_contrastive_gemm(false, cp.mG, cp.mBT, g, ggrid, h->stream));
-    g.dX = dB;  // dB = G^T A / T
-    // G^T as an MN-major operand: boxes of 64 columns x 64 rows of G
-    unsigned char mG64[128];
-    sj_status ms = tc_encode_2d(h->tc, cp.G, cp.np, cp.np, 64, 64, mG64);
-    if (ms != SJ_OK) return ms;
-    SJ_CUDA(launch_contrastive_gemm(true, mG64, cp.mAT, g, ggrid, h->stream));
-    return contrastive_finish(h, cp);
-  }
-  const int grid = (int)std::min<int64_t>(n_rb * a.n_chunks, h->sm_count);
-  // dA: rows of A against columns (rows of B); row term = softmax over j
-  a.dX = dA;
-  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mA, cp.mB, cp.mBT, a, grid, h->stream));
-  // dB: rows of B against columns (rows of A); the row softmax term is indexed
-  // by the kernel's columns, the column softmax term by its rows
-  a.lse_r = sym ? lse + N : lse;
-  a.wr = sym ? 0.5f : 0.f;
-  a.lse_c = lse;
-  a.wc = sym ? 0.5f : 1.f;
-  a.dX = dB;
-  SJ_CUDA(launch_contrastive(kContrastiveBwdFused, cp.mB, cp.mA, cp.mAT, a, grid, h->stream));
-  return contrastive_finish(h, cp);
+  return backward_impl(h, A, N, 0, B, N, T, (h->cfg.flags & SJ_FLAG_SYM_INFONCE) != 0, lse,
+                       grad_loss, dA, dB);
+}
+
+sj_status sj_contrastive_fwd_rows(sj_handle *h, const void *A_rows, int64_t n_rows, int64_t r0,
+                                  const void *B, int64_t N, float T, float *loss_part,
+                                  float *lse_rows) {
+  if (!h || !A_rows || !B || n_rows < 1 || r0 < 0 || r0 + n_rows > N || !(T > 0.f) ||
+      !loss_part || !lse_rows)
+    return SJ_ERR_INVALID_ARG;
+  if (h->cfg.flags & SJ_FLAG_SYM_INFONCE) return SJ_ERR_UNSUPPORTED;
+  if (!is_device_ptr(loss_part, h->cfg.device) || !is_device_ptr(lse_rows, h->cfg.device))
+    return SJ_ERR_INVALID_ARG;
+  return contrastive_fwd_impl(h, A_rows, n_rows, r0, B, N, T, false, loss_part, lse_rows);
+}
+
+sj_status sj_backward_rows(sj_handle *h, const void *A_rows, int64_t n_rows, int64_t r0,
+                           const void *B, int64_t N, float T, const float *lse_rows,
+                           const float *grad_loss, float *dA_rows, float *dB_part) {
+  if (!h || !A_rows || !B || n_rows < 1 || r0 < 0 || r0 + n_rows > N || !(T > 0.f) ||
+      !lse_rows || !grad_loss || !dA_rows || !dB_part)
+    return SJ_ERR_INVALID_ARG;
+  if (h->cfg.flags & SJ_FLAG_SYM_INFONCE) return SJ_ERR_UNSUPPORTED;
+  const int dv = h->cfg.device;
+  if (!is_device_ptr(lse_rows, dv) || !is_device_ptr(grad_loss, dv) ||
+      !is_device_ptr(dA_rows, dv) || !is_device_ptr(dB_part, dv))
+    return SJ_ERR_INVALID_ARG;
+  return backward_impl(h, A_rows, n_rows, r0, B, N, T, false, lse_rows, grad_loss, dA_rows,
+                       dB_part);
 }
 
 sj_status sj_debug_scores(sj_handle *h, float *raw, float *margin) {

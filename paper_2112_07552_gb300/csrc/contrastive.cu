@@ -167,8 +167,8 @@ __global__ void __launch_bounds__(kCThreads, 1)
   fence_after();
   const uint32_t tmem = sm.tmem_base;
   const int nkb = (int)(a.dp / BK);
-  const int n_tiles = (int)(a.np / TN);
-  const int n_rb = (int)(a.np / TM);
+  const int n_tiles = (int)(a.npy / TN);  // column tiles (rows of Y)
+  const int n_rb = (int)(a.np / TM);      // row blocks (rows of X)
   const int n_chunks = BWD ? a.n_chunks : 1;
   // the forward and the G' pass also split a row block's column tiles
   const int n_splits = BWD ? 1 : a.n_splits;
@@ -373,21 +373,22 @@ __global__ void __launch_bounds__(kCThreads, 1)
         mbar_arrive(&sm.s_empty[buf]);  // S buffer free for the next tile
         const int64_t col0 = (int64_t)t * TN;
         if constexpr (MODE == kModeFwd) {
-          const bool cols_full = col0 + TN <= a.n;
+          const bool cols_full = col0 + TN <= a.ny;
+          const int64_t pos = row + a.diag_off;  // the row's positive column
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             // in place: scores -> log2-domain logits -> exponentials -> sum
             const int64_t jb = col0 + (cb + c) * 32;
-            if (valid && row >= jb && row < jb + 32) {
+            if (valid && pos >= jb && pos < jb + 32) {
 #pragma unroll
               for (int q = 0; q < 32; ++q)
-                if (jb + q == row) a.diag_out[row] = v[c][q];
+                if (jb + q == pos) a.diag_out[row] = v[c][q];
             }
             float cm = -INFINITY;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
               float x = v[c][q] * c1;
-              if (!cols_full && jb + q >= a.n) x = -INFINITY;
+              if (!cols_full && jb + q >= a.ny) x = -INFINITY;
               v[c][q] = x;
               cm = fmaxf(cm, x);
             }
@@ -419,14 +420,14 @@ __global__ void __launch_bounds__(kCThreads, 1)
           // value per lane and is broadcast by shuffles; the diagonal and the
           // ragged last tile are fixed up apart from the element loop
           const float wr = a.wr, wc = a.wc;
-          const bool cols_full = col0 + TN <= a.n;
-          const int64_t dr = row - col0;  // position of the diagonal in the tile
+          const bool cols_full = col0 + TN <= a.ny;
+          const int64_t dr = row + a.diag_off - col0;  // the positive's column in the tile
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             float lcq = INFINITY;
             if (wc != 0.f) {
               const int64_t jj = col0 + (cb + c) * 32 + lane;
-              if (jj < a.n) lcq = __ldg(a.lse_c + jj) * kLog2e;
+              if (jj < a.ny) lcq = __ldg(a.lse_c + jj) * kLog2e;
             }
             const int dq = (int)(dr - (cb + c) * 32);  // 0..31 when the diagonal is in this chunk
 #pragma unroll
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(kCThreads, 1)
             for (int c = 0; c < NC; ++c)
 #pragma unroll
               for (int q = 0; q < 32; ++q)
-                if (!valid || col0 + (cb + c) * 32 + q >= a.n) v[c][q] = 0.f;
+                if (!valid || col0 + (cb + c) * 32 + q >= a.ny) v[c][q] = 0.f;
           }
           // G' into the shared tile (128B-swizzled K-major k-blocks of 64
           // columns): the fused backward's MMA operand, or the G' pass's
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(kCThreads, 1)
           break;
         }
         fence_after();
-        const float scale = __ldg(a.grad_loss) / ((float)a.n * a.T);
+        const float scale = __ldg(a.grad_loss) / ((float)a.n_norm * a.T);
         const int c0 = ch * kMaxChunk;
         const int cw = (int)min64(kMaxChunk, a.dp - c0);
         // each epilogue warp of a lane quarter stores its half of the chunk
@@ -630,7 +631,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm.tmem_base;
-  const int nkb = (int)(a.np / BK);
+  const int nkb = (int)(a.kp / BK);
   const int64_t n_units = (a.np / TM) * a.n_chunks;
 
   if (warp == 0) {
@@ -714,7 +715,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
   } else {
     const int quarter = warp & 3;
-    const float scale = __ldg(a.grad_loss) / ((float)a.n * a.T);
+    const float scale = __ldg(a.grad_loss) / ((float)a.n_norm * a.T);
     uint64_t unit_n = 0;
     for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++unit_n) {
       const int rb = (int)(u / a.n_chunks), ch = (int)(u % a.n_chunks);
@@ -779,8 +780,8 @@ __global__ void contrastive_pack_kernel(const float *__restrict__ X, int64_t n, 
 }
 
 // loss = (w1 sum term1 + w2 sum term2) / N, compensated summation, one block.
-__global__ void contrastive_loss_kernel(const float *t1, const float *t2, int64_t n, float w1,
-                                        float w2, float *loss) {
+__global__ void contrastive_loss_kernel(const float *t1, const float *t2, int64_t n,
+                                        int64_t n_norm, float w1, float w2, float *loss) {
   __shared__ float sh_s[32];
   float s = 0.f, c = 0.f;  // Kahan-compensated per-thread partial sum
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -797,7 +798,7 @@ __global__ void contrastive_loss_kernel(const float *t1, const float *t2, int64_
   if (threadIdx.x == 0) {
     float tot = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh_s[w];
-    *loss = tot / (float)n;
+    *loss = tot / (float)n_norm;
   }
 }
 
@@ -829,9 +830,9 @@ cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *
   return cudaGetLastError();
 }
 
-cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n, float w1, float w2,
-                                    float *loss, cudaStream_t st) {
-  contrastive_loss_kernel<<<1, 1024, 0, st>>>(t1, t2, n, w1, w2, loss);
+cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n, int64_t n_norm,
+                                    float w1, float w2, float *loss, cudaStream_t st) {
+  contrastive_loss_kernel<<<1, 1024, 0, st>>>(t1, t2, n, n_norm, w1, w2, loss);
   return cudaGetLastError();
 }
 

@@ -9,9 +9,12 @@
 namespace sj {
 
 struct ContrastiveArgs {
-  int64_t n;            // paired rows
+  int64_t n;            // rows of the kernel's row operand X
   int64_t d;            // embedding width
-  int64_t np, dp;       // padded rows (multiple of 256) and width (multiple of 64)
+  int64_t np, dp;       // padded rows of X (multiple of 256) and width (multiple of 64)
+  int64_t ny, npy;      // rows of the column operand Y (score columns), padded
+  int64_t diag_off;     // the positive of X row i is column i + diag_off (if in range)
+  int64_t n_norm;       // N of the loss (1/N scale): all paired rows, over every shard
   float T;              // temperature
   int n_chunks;         // fused backward: output-dimension chunks of <= 384
   int n_splits;         // forward and G' pass: column splits of a row block
@@ -39,7 +42,9 @@ constexpr int kContrastiveGprime = 2;    // G' written to memory through tmZ
 
 // dX = (g / (N T)) G Z from a materialised G (np x np BF16) and Z^T (dp x np).
 struct ContrastiveGemmArgs {
-  int64_t n, d, np, dp;
+  int64_t n, d, np, dp;    // output rows (valid, padded) and width
+  int64_t kp;              // padded K (rows of Z)
+  int64_t n_norm;          // N of the 1/N scale
   float T;
   int n_chunks;            // output-dimension chunks of <= 384
   const float *grad_loss;  // device scalar
@@ -53,8 +58,9 @@ void contrastive_splits(int64_t np, int *n_splits, int *tiles_per_split);
 size_t contrastive_gemm_smem_bytes();
 cudaError_t launch_contrastive_pack(const float *X, int64_t n, int64_t d, void *Xp, void *XT,
                                     int64_t np, int64_t dp, unsigned *err, cudaStream_t st);
-cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n, float w1,
-                                    float w2, float *loss, cudaStream_t st);
+// loss = (w1 sum t1 + w2 sum t2) / n_norm over n terms each
+cudaError_t launch_contrastive_loss(const float *t1, const float *t2, int64_t n, int64_t n_norm,
+                                    float w1, float w2, float *loss, cudaStream_t st);
 // tmX/tmY/tmZ: 128-byte CUtensorMap objects (X, Y: box 64 x 128; Z: Z^T with
 // box 64 x 64 in the fused backward, the G' map with box 64 x 128 in the G'
 // pass, null in the forward).  The forward also launches the merge of its

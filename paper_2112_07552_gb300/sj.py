@@ -46,7 +46,7 @@ EXPORTS = ("sj_create", "sj_destroy", "sj_topk", "sj_threshold", "sj_batch",
            "sj_contrastive_fwd", "sj_backward", "sj_topk_noalloc", "sj_status_string",
            "sj_version", "sj_last_error_detail", "sj_autotune", "sj_autotune_load",
            "sj_debug_scores", "sj_block", "sj_join_groupby_sum", "sj_join_sum_product",
-           "sj_plan")
+           "sj_plan", "sj_contrastive_fwd_rows", "sj_backward_rows")
 
 I64, P = ctypes.c_int64, ctypes.c_void_p
 
@@ -160,6 +160,10 @@ def lib() -> ctypes.CDLL:
         L.sj_join_groupby_sum.argtypes = [P, P, P, I64, P, P, I64, P, I64, ctypes.POINTER(I64)]
         L.sj_join_sum_product.restype = st
         L.sj_join_sum_product.argtypes = [P, P, P, I64, P, P, I64, ctypes.POINTER(SjGroup)]
+        L.sj_contrastive_fwd_rows.restype = st
+        L.sj_contrastive_fwd_rows.argtypes = [P, P, I64, I64, P, I64, ctypes.c_float, P, P]
+        L.sj_backward_rows.restype = st
+        L.sj_backward_rows.argtypes = [P, P, I64, I64, P, I64, ctypes.c_float, P, P, P, P]
         L.sj_plan.restype = st
         L.sj_plan.argtypes = [P, P, I64, P, I64, ctypes.c_int32, ctypes.c_double, I64,
                               ctypes.POINTER(SjPlanInfo)]
@@ -394,6 +398,32 @@ class SimilarityJoin:
         g = grad_loss.reshape(1).to(torch.float32).contiguous()
         _check(lib().sj_backward(self._h, _ptr(A), _ptr(B), N, float(T), _ptr(lse), _ptr(g),
                                  _ptr(dA), _ptr(dB)), "sj_backward")
+        return dA, dB
+
+    def contrastive_forward_rows(self, A_rows, r0: int, B, T: float):
+        """Row shard rows [r0, r0 + n) of the contrastive join against all of
+        B: (loss_part [1], lse_rows [n]); loss_part sums over shards to the
+        loss (sj_contrastive_fwd_rows)."""
+        import torch
+        n, N = _rows(A_rows, self.d), _rows(B, self.d)
+        loss = torch.empty(1, dtype=torch.float32, device=A_rows.device)
+        lse = torch.empty(n, dtype=torch.float32, device=A_rows.device)
+        _check(lib().sj_contrastive_fwd_rows(self._h, _ptr(A_rows), n, int(r0), _ptr(B), N,
+                                             float(T), _ptr(loss), _ptr(lse)),
+               "sj_contrastive_fwd_rows")
+        return loss, lse
+
+    def contrastive_backward_rows(self, A_rows, r0: int, B, T: float, lse_rows, grad_loss):
+        """(dA_rows, dB_part) of the row shard; dB_part sums over shards to dB
+        (sj_backward_rows)."""
+        import torch
+        n, N = _rows(A_rows, self.d), _rows(B, self.d)
+        dA = torch.empty_like(A_rows, dtype=torch.float32)
+        dB = torch.empty_like(B, dtype=torch.float32)
+        g = grad_loss.reshape(1).to(torch.float32).contiguous()
+        _check(lib().sj_backward_rows(self._h, _ptr(A_rows), n, int(r0), _ptr(B), N, float(T),
+                                      _ptr(lse_rows), _ptr(g), _ptr(dA), _ptr(dB)),
+               "sj_backward_rows")
         return dA, dB
 
     def batch(self, jobs, with_stats: bool = False):

@@ -90,6 +90,64 @@ def test_row_sharded_join_and_contrastive_reductions(tmp_path):
     assert np.allclose(np.load(tmp_path / "lse_col.npy"), lse_col, rtol=1e-13, atol=1e-12)
 
 
+def _infonce_worker(rank, world, port, out_dir):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import oracle
+    from paper_2112_07552_gb300 import datagen, shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    N, d, T = 90, 12, 0.1
+    Ap, Bp = datagen.paired(N, d, 6, seed=53)
+    a64, b64 = Ap.astype(np.float64), Bp.astype(np.float64)
+
+    # stand-ins for the library's row-shard calls: FP64, from the oracle's
+    # row statistics (lse, dA rows) and the rows' dB contribution written out
+    def fwd(A_rows, r0, B, T_):
+        rows = np.arange(r0, r0 + A_rows.shape[0])
+        lse, _ = oracle.infonce_rows(a64, b64, T_, rows, grads=True)
+        S = A_rows.numpy() @ B.numpy().T / T_
+        part = (lse - S[np.arange(len(rows)), rows]).sum() / N
+        return torch.tensor([part], dtype=torch.float64), torch.from_numpy(lse)
+
+    def bwd(A_rows, r0, B, T_, lse):
+        rows = np.arange(r0, r0 + A_rows.shape[0])
+        _, dA = oracle.infonce_rows(a64, b64, T_, rows, grads=True)
+        S = A_rows.numpy() @ B.numpy().T / T_
+        G = np.exp(S - lse.numpy()[:, None])
+        G[np.arange(len(rows)), rows] -= 1.0
+        dB = G.T @ A_rows.numpy() / (N * T_)
+        return torch.from_numpy(dA), torch.from_numpy(dB)
+
+    r0, r1 = shard.row_range(N, rank, world)
+    loss, lse, dA, dB = shard.infonce_step(fwd, bwd, torch.from_numpy(a64[r0:r1]), r0,
+                                           torch.from_numpy(b64), T)
+    gathered = shard.all_gather_object((r0, dA.numpy()))
+    if rank == 0:
+        np.save(os.path.join(out_dir, "inf_loss.npy"), loss.numpy())
+        np.save(os.path.join(out_dir, "inf_dB.npy"), dB.numpy())
+        np.save(os.path.join(out_dir, "inf_dA.npy"),
+                np.concatenate([g[1] for g in sorted(gathered, key=lambda g: g[0])]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_row_sharded_infonce_reductions(tmp_path):
+    # the loss all-reduce and the dB all-reduce of shard.infonce_step over two
+    # gloo ranks give the unsharded oracle's loss, dA and dB
+    import oracle
+    from paper_2112_07552_gb300 import datagen
+    mp.spawn(_infonce_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    N, d, T = 90, 12, 0.1
+    Ap, Bp = datagen.paired(N, d, 6, seed=53)
+    loss, _, _, dA, dB = oracle.infonce(Ap.astype(np.float64), Bp.astype(np.float64), T)
+    assert abs(np.load(tmp_path / "inf_loss.npy")[0] - loss) <= 1e-12 * max(1.0, abs(loss))
+    assert np.allclose(np.load(tmp_path / "inf_dA.npy"), dA, rtol=1e-10, atol=1e-13)
+    assert np.allclose(np.load(tmp_path / "inf_dB.npy"), dB, rtol=1e-10, atol=1e-13)
+
+
 def test_row_range_partitions():
     from paper_2112_07552_gb300 import shard
     for n in (0, 1, 7, 100, 1001):
