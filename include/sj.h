@@ -79,6 +79,17 @@ typedef enum {
 #define SJ_FLAG_NO_GRAPH 0x4u      /* never replay joins from a captured CUDA graph */
 #define SJ_FLAG_NARROW_TILES 0x8u  /* test hook: 128-column score tiles for every job */
 #define SJ_FLAG_FUSED_BACKWARD 0x10u /* sj_backward: never materialise dL/dS (see there) */
+#define SJ_FLAG_BLOCK_SPARSE 0x20u  /* tensor-core scoring skips zero blocks: the packing
+                                       pass records which 128-byte k-blocks of each
+                                       128-row group hold a nonzero; a score tile loads
+                                       and multiplies only the k-blocks nonzero on both
+                                       sides (exact: a zero block adds exactly 0), and a
+                                       threshold-only job skips the epilogue of an
+                                       all-zero tile when tau exceeds its margin (the
+                                       paper's block-sparse path for low density,
+                                       Sec. 4.3).  Pays off for one-hot or sparse rows
+                                       clustered by key; dense rows only pay the
+                                       occupancy pass */
 #define SJ_FLAG_DEBUG_TIMEOUT 0x100u /* test hook: device waits give up at once */
 
 typedef struct {

@@ -107,8 +107,10 @@ struct sj_handle {
   sj_handle *aux = nullptr;     // relational calls: a handle of their one-hot width
 };
 
-sj_status sj::aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle **out) {
-  if (h->aux && (h->aux->cfg.d != d || h->aux->cfg.prec != prec)) {
+sj_status sj::aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle **out,
+                         uint32_t extra_flags) {
+  const uint32_t flags = (h->cfg.flags & ~(uint32_t)SJ_FLAG_SYM_INFONCE) | extra_flags;
+  if (h->aux && (h->aux->cfg.d != d || h->aux->cfg.prec != prec || h->aux->cfg.flags != flags)) {
     sj_destroy(h->aux);
     h->aux = nullptr;
   }
@@ -116,7 +118,7 @@ sj_status sj::aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle *
     sj_config c = h->cfg;
     c.d = d;
     c.prec = prec;
-    c.flags &= ~(uint32_t)SJ_FLAG_SYM_INFONCE;
+    c.flags = flags;
     sj_status s = sj_create(&h->aux, &c);
     if (s != SJ_OK) return s;
   }
@@ -419,6 +421,7 @@ struct BatchPlan {
   int64_t rows = 0, prows = 0, slots = 0, band_entries = 0, topv_entries = 0;
   int64_t rows_thr = 0, cap_sum = 0;
   double padded_pairs = 0.0;  // pair-scores the score tiles compute (incl. padding)
+  int occ_words = 0;          // block-sparse scoring: bitmap words per 128-row group (0: dense)
   bool any_topk = false, any_thr = false, any_op_host = false;
 };
 
@@ -448,6 +451,11 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
   P.d = h->cfg.d;
   P.pp = plan_prec(h->cfg.prec, P.d);
   P.bands = h->cfg.prec == SJ_FP32 ? 1 : 2;
+  if ((h->cfg.flags & SJ_FLAG_BLOCK_SPARSE) && h->cfg.prec != SJ_FP32) {
+    const int64_t nkb = P.pp.dp * P.pp.elem / 128;
+    const int64_t words = (nkb + 31) / 32;
+    if (words <= kOccMaxWords) P.occ_words = (int)words;
+  }
   const int64_t BM = P.pp.BM, BN = P.pp.BN, edge = std::max(BM, BN);
   int64_t total_tiles = 0;
   for (int q = 0; q < n; ++q)
@@ -605,6 +613,7 @@ struct Bufs {
   RowMeta *meta = nullptr;
   void *packed = nullptr;
   std::vector<float *> stA, stB;
+  uint32_t *occ = nullptr;
   Cand *band = nullptr;
   float *topv = nullptr;
   int *band_cnt = nullptr, *defer = nullptr, *tier2 = nullptr, *ovf = nullptr;
@@ -640,6 +649,8 @@ bool layout(Arena &ar, const BatchPlan &P, const JoinReq *reqs, unsigned long lo
   B.units = reinterpret_cast<UnitDev *>(tab + tl.units);
   B.meta = static_cast<RowMeta *>(take(sizeof(RowMeta) * std::max<int64_t>(P.prows, 1)));
   B.packed = take((size_t)std::max<int64_t>(P.prows, 1) * P.pp.dp * P.pp.elem);
+  if (P.occ_words > 0)
+    B.occ = static_cast<uint32_t *>(take((size_t)(P.prows / 128 + 1) * P.occ_words * 4));
   B.stA.assign(n, nullptr);
   B.stB.assign(n, nullptr);
   B.st_idx.assign(n, nullptr);
@@ -999,6 +1010,10 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
   SJ_CUDA(launch_prepare(B.segs, (int)P.segs.size(), B.jobs, P.prows, P.d, P.pp.fmt, B.packed,
                          P.pp.dp, B.meta, B.ctr, stm));
   launches += P.prows > 0 ? (P.pp.fmt == PackFormat::kFP8 ? 2 : 1) : 0;
+  if (B.occ && P.prows > 0) {
+    SJ_CUDA(launch_occupancy(B.packed, P.prows, P.pp.dp * P.pp.elem, B.occ, P.occ_words, stm));
+    launches += 1;
+  }
   ev.rec(1);
   // ---- scoring pass with the fused filter ----
   if (P.any_topk && P.slots > 0) SJ_CUDA(cudaMemsetAsync(B.band_cnt, 0, (size_t)P.slots * 4, stm));
@@ -1022,6 +1037,8 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
     sa.ctr = B.ctr;
     sa.raw = h->dbg_raw;
     sa.raw_m = h->dbg_margin;
+    sa.occ = B.occ;
+    sa.occ_words = P.occ_words;
     if (h->cfg.prec == SJ_FP32) {
       const int grid = (int)std::min<int64_t>(sa.n_units, (int64_t)h->sm_count * 2);
       SJ_CUDA(launch_score_simt(sa, grid, stm));
@@ -1101,6 +1118,7 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
 // Kernels issue_group launches for this plan.
 void issue_count(const BatchPlan &P, int64_t &l) {
   l += P.prows > 0 ? (P.pp.fmt == PackFormat::kFP8 ? 2 : 1) : 0;
+  l += P.prows > 0 && P.occ_words > 0 ? 1 : 0;
   l += P.units.empty() ? 0 : 1;
   l += P.any_topk && P.rows > 0 ? 3 : 0;
   l += P.any_thr && P.rows > 0 ? 9 : 0;

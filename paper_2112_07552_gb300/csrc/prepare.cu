@@ -297,7 +297,47 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
   }
 }
 
+// One block per 128-row group: which 128-byte k-blocks hold a nonzero byte in
+// any of the group's rows (each warp scans 16 rows, 512 bytes per step; the
+// four k-blocks of a step are decided by ballots of 8 lanes each).
+__global__ void __launch_bounds__(256)
+    occupancy_kernel(const unsigned char *Xp, int64_t row_bytes, uint32_t *occ, int words) {
+  __shared__ uint32_t s_occ[kOccMaxWords];
+  for (int w = threadIdx.x; w < words; w += blockDim.x) s_occ[w] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t g = blockIdx.x;
+  for (int r = wib; r < 128; r += 8) {
+    const unsigned char *row = Xp + (g * 128 + r) * row_bytes;
+    for (int64_t off = 0; off < row_bytes; off += 512) {
+      const int64_t o = off + lane * 16;
+      bool nz = false;
+      if (o < row_bytes) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(row + o);
+        nz = (v.x | v.y | v.z | v.w) != 0u;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, nz);
+      if (lane < 4 && ((bal >> (lane * 8)) & 0xffu)) {
+        const int64_t kb = off / 128 + lane;
+        atomicOr(&s_occ[kb >> 5], 1u << (kb & 31));
+      }
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < words; w += blockDim.x) occ[g * words + w] = s_occ[w];
+}
+
 }  // namespace
+
+cudaError_t launch_occupancy(const void *Xp, int64_t prows, int64_t row_bytes, uint32_t *occ,
+                             int words, cudaStream_t st) {
+  if (prows == 0) return cudaSuccess;
+  if (words > kOccMaxWords || prows % 128 != 0 || row_bytes % 128 != 0)
+    return cudaErrorInvalidValue;
+  occupancy_kernel<<<(unsigned)(prows / 128), 256, 0, st>>>(
+      static_cast<const unsigned char *>(Xp), row_bytes, occ, words);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows,
                            int64_t d, PackFormat fmt, void *Xp, int64_t dp, RowMeta *meta,

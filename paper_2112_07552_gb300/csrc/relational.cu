@@ -3,7 +3,9 @@
 // sj_block (Sec. 3.1 "Two-way natural join", the entity-matching blocking of
 // Sec. 6.3.2): key attributes become one-hot rows (one block per attribute,
 // scaled to unit norm) and the join C = mat(A) mat(B)^T runs through the
-// tensor-core threshold join at tau = (min_match - 1/2) / n_attr.
+// tensor-core threshold join at tau = (min_match - 1/2) / n_attr, with the
+// block-sparse scoring of SJ_FLAG_BLOCK_SPARSE (tables clustered by key leave
+// most k-blocks and tiles without a common nonzero).
 //
 // sj_join_groupby_sum / sj_join_sum_product (Sec. 3.3, Q3 and Q4): the
 // paper writes them as 1 x mat(A) x mat(B)^T (x 1).  Associated from the
@@ -286,7 +288,8 @@ extern "C" sj_status sj_block(sj_handle *h, const int64_t *ka, int64_t nA, const
     d += K + 1;
   }
   sj_handle *ax = nullptr;
-  s = aux_handle(h, std::max<int64_t>(d, 1), SJ_BF16, &ax);
+  // one-hot rows are sparse: score only the blocks with a common nonzero
+  s = aux_handle(h, std::max<int64_t>(d, 1), SJ_BF16, &ax, SJ_FLAG_BLOCK_SPARSE);
   if (s != SJ_OK) return s;
   DevBuf xa, xb, dca, dcb;
   RL_CUDA(xa.alloc((size_t)nA * d * 4));

@@ -150,6 +150,37 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? K
   }
 }
 
+// The k-blocks of one score tile, in increasing order, handed to f (which
+// returns false to stop): every k-block when scoring dense; with occupancy
+// bitmaps, the k-blocks nonzero in the A row group and in one of the B tile's
+// row groups.  A skipped k-block contributes exactly 0 to every score of the
+// tile, so the accumulators equal the dense ones; a tile with no k-block left
+// is all zeros (the epilogue then reads no accumulator).  Returns the count,
+// -1 when f stopped.
+template <class F>
+__device__ __forceinline__ int tile_kblocks(const ScoreArgs &a, int64_t nkb, int64_t arow,
+                                            int64_t brow, int bn, F &&f) {
+  if (a.occ == nullptr) {
+    for (int64_t kb = 0; kb < nkb; ++kb)
+      if (!f(kb)) return -1;
+    return (int)nkb;
+  }
+  const uint32_t *oa = a.occ + (arow / 128) * a.occ_words;
+  const uint32_t *ob0 = a.occ + (brow / 128) * a.occ_words;
+  const uint32_t *ob1 = bn > 128 ? ob0 + a.occ_words : ob0;
+  int n = 0;
+  for (int w = 0; w < a.occ_words; ++w) {
+    uint32_t m = __ldg(oa + w) & (__ldg(ob0 + w) | __ldg(ob1 + w));
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      if (!f((int64_t)w * 32 + b)) return -1;
+      ++n;
+    }
+  }
+  return n;
+}
+
 __device__ __forceinline__ void flag_timeout(TcSmem &sm, Counters *ctr) {
   *(volatile int *)&sm.abort = 1;
   atomicOr(&ctr->err_flags, kErrTimeout);
@@ -222,16 +253,28 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
     const int bn = jb.bn;
     const int64_t col0 = ct * bn;
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+    // block-sparse: a tile without a common nonzero k-block is all zeros and
+    // its accumulator was not written
+    const bool zero_tile =
+        a.occ != nullptr &&
+        tile_kblocks(a, a.dp * 2 / 128 /* any count: only the bitmaps are read */,
+                     jb.a_prow0 + (int64_t)un.rb * BM, jb.b_prow0 + col0, bn,
+                     [](int64_t) { return false; }) == 0;
     // kEpiChunks 32-column chunks per TMEM round trip
 #pragma unroll 1
     for (int c0 = half * (bn / 2); c0 < (half + 1) * (bn / 2); c0 += 32 * kEpiChunks) {
       float v0[32], v1[32];
-      tmem_ld32_nowait(taddr + c0, v0);
-      if constexpr (kEpiChunks == 2) {
-        tmem_ld32_nowait(taddr + c0 + 32, v1);
-        tmem_wait_ld(v0, v1);
+      if (zero_tile) {
+#pragma unroll
+        for (int t = 0; t < 32; ++t) v0[t] = v1[t] = 0.f;
       } else {
-        tmem_wait_ld1(v0);
+        tmem_ld32_nowait(taddr + c0, v0);
+        if constexpr (kEpiChunks == 2) {
+          tmem_ld32_nowait(taddr + c0 + 32, v1);
+          tmem_wait_ld(v0, v1);
+        } else {
+          tmem_wait_ld1(v0);
+        }
       }
       if (a.raw != nullptr && owner) {
         float *dst = a.raw + row * nB;
@@ -329,19 +372,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t ct = ct0; ct < ct1 && ok; ++ct) {
           const bool narrow = jb.bn == kTcBNNarrow;
           const int brow = (int)(jb.b_prow0 + ct * jb.bn);
-          for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
+          const int n = tile_kblocks(a, nkb, arow, brow, jb.bn, [&](int64_t kb) {
             const int s = (int)(it % STAGES);
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
             if (!mbar_wait(&sm.empty[s], ph ^ 1, limit_ns, abort)) {
               flag_timeout(sm, a.ctr);
-              ok = false;
-              break;
+              return false;
             }
+            ++it;
             mbar_arrive_expect_tx(&sm.full[s],
                                   kTileABytes + (narrow ? kTileBBytes / 2 : kTileBBytes));
             tma_load_2d(sm.a[s], &tmA, (int)(kb * BKE), arow, &sm.full[s]);
             tma_load_2d(sm.b[s], narrow ? &tmB128 : &tmB, (int)(kb * BKE), brow, &sm.full[s]);
-          }
+            return true;
+          });
+          if (n < 0) ok = false;
         }
       }
       // Drain: the last load issued into each stage must have landed before the
@@ -376,27 +421,33 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           fence_after();
           const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
-          for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
+          const int arow = (int)(jb.a_prow0 + (int64_t)un.rb * BM);
+          const int brow = (int)(jb.b_prow0 + ct * jb.bn);
+          bool first = true;  // the tile's first MMA overwrites the accumulator
+          const int n = tile_kblocks(a, nkb, arow, brow, jb.bn, [&](int64_t) {
             const int s = (int)(it % STAGES);
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
             if (!mbar_wait(&sm.full[s], ph, limit_ns, abort)) {
               flag_timeout(sm, a.ctr);
-              ok = false;
-              break;
+              return false;
             }
+            ++it;
             fence_after();
             const uint32_t a0 = su32(sm.a[s]), b0 = su32(sm.b[s]);
 #pragma unroll
             for (int kk = 0; kk < kMmaPerStage; ++kk) {
               if constexpr (FP8)
                 mma_e4m3(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
-                         (kb > 0 || kk > 0) ? 1u : 0u);
+                         (!first || kk > 0) ? 1u : 0u);
               else
                 mma_bf16(d_tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
-                         (kb > 0 || kk > 0) ? 1u : 0u);
+                         (!first || kk > 0) ? 1u : 0u);
             }
+            first = false;
             mma_commit(&sm.empty[s]);  // frees the smem stage once these MMAs finish
-          }
+            return true;
+          });
+          if (n < 0) ok = false;
           if (!ok) break;
           mma_commit(&sm.tmem_full[acc]);  // accumulator ready for the epilogue
         }

@@ -18,10 +18,12 @@
 namespace sj {
 
 // A second handle inside h with the same device, stream and workspace limit
-// but width d and precision prec (created on first use, replaced when d or
-// prec change, destroyed with h): the relational calls run their one-hot
-// joins through it.
-sj_status aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle **out);
+// but width d, precision prec and h's flags plus extra_flags (created on
+// first use, replaced when any of them change, destroyed with h): the
+// relational calls run their one-hot joins through it, the cascade its FP32
+// re-joins.
+sj_status aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle **out,
+                     uint32_t extra_flags = 0);
 int handle_device(const sj_handle *h);
 const sj_config *handle_config(const sj_handle *h);
 // Column tiles per split the planner gives a one-job join of these sizes on h,
@@ -126,6 +128,13 @@ __device__ __forceinline__ int find_job_row0_hint(const JobDev *jobs, int n_jobs
 // row is stored as q = RNE_sat(x 2^e) with its own e (largest with max|x| 2^e
 // <= 448), a B row with its job's common eB (from the maxima), a self-join
 // segment with eB in both roles.  meta.sexp holds the row's exponent.
+// Occupancy bitmaps of a packed buffer (prows rows of row_bytes bytes, prows
+// a multiple of 128): occ[g * words + kb / 32] bit kb % 32 for 128-row group g
+// and 128-byte k-block kb.
+constexpr int kOccMaxWords = 128;  // k-blocks tracked: up to 4,096 (wider rows run dense)
+cudaError_t launch_occupancy(const void *Xp, int64_t prows, int64_t row_bytes, uint32_t *occ,
+                             int words, cudaStream_t st);
+
 cudaError_t launch_prepare(const PackSeg *segs, int n_segs, JobDev *jobs, int64_t prows,
                            int64_t d, PackFormat fmt, void *Xp, int64_t dp, RowMeta *meta,
                            Counters *ctr, cudaStream_t st);
@@ -147,6 +156,11 @@ struct ScoreArgs {
   ThrCand *thr;              // threshold candidates
   unsigned long long thr_cap;
   Counters *ctr;
+  // block-sparse scoring (SJ_FLAG_BLOCK_SPARSE): per 128-row group of the
+  // packed buffer, occ_words words of bits, bit kb set when a row of the
+  // group has a nonzero byte in 128-byte k-block kb; null: dense
+  const uint32_t *occ;
+  int occ_words;
   // test hook (sj_debug_scores; one job): every raw score s~_ij of the job,
   // row-major nA x nB, and each row's margin m_i; null in normal calls
   float *raw;

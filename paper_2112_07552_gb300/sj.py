@@ -39,6 +39,7 @@ SJ_FLAG_SINGLE_SPLIT = 0x2
 SJ_FLAG_NO_GRAPH = 0x4
 SJ_FLAG_NARROW_TILES = 0x8
 SJ_FLAG_FUSED_BACKWARD = 0x10
+SJ_FLAG_BLOCK_SPARSE = 0x20
 SJ_FLAG_DEBUG_TIMEOUT = 0x100
 
 # every symbol include/sj.h declares
