@@ -230,6 +230,28 @@ sj_status sj_contrastive_fwd(sj_handle *h, const void *A, const void *B, int64_t
 sj_status sj_backward(sj_handle *h, const void *A, const void *B, int64_t N, float T,
                       const float *lse, const float *grad_loss, float *dA, float *dB);
 
+/* Joins whose right table B stays in HOST memory (larger than the device's,
+ * or simply not resident): B is streamed through the device in chunks of
+ * `chunk_rows` rows (0: 1,048,576), the copy of the next chunk overlapping
+ * the join of the current one on a second stream; the paper's pipelined
+ * blocking for data larger than device memory (Sec. 4.3, MSplitGEMM).
+ * Results are exactly those of sj_topk / sj_threshold on the whole of B:
+ * threshold pairs are the chunks' pairs (columns offset by the chunk start)
+ * merged by row; the top-k of a row is ranked exactly from the union of the
+ * chunks' top-k lists (Dot2 intervals and the fixed-point accumulator, which
+ * settles equal float32 scores of different chunks), reading those B rows
+ * through B's mapped host address.  B is page-locked for the call
+ * (cudaHostRegister) unless it already is.  A: device or host; top-k
+ * outputs: device memory; threshold outputs: device or host.
+ * Errors: SJ_ERR_INVALID_ARG (B not host memory, null, sizes), those of
+ * sj_topk / sj_threshold. */
+sj_status sj_topk_streamed(sj_handle *h, const float *A, int64_t nA, const float *B, int64_t nB,
+                           int32_t k, int64_t chunk_rows, int64_t *out_idx, float *out_score,
+                           sj_stats *st);
+sj_status sj_threshold_streamed(sj_handle *h, const float *A, int64_t nA, const float *B,
+                                int64_t nB, double tau, int64_t chunk_rows, sj_pair *out,
+                                int64_t capacity, int64_t *n_out, sj_stats *st);
+
 /* Row shard of the contrastive join, for data parallelism over rows (one
  * GPU per shard): A_rows are rows [r0, r0 + n_rows) of A (n_rows x d, DEVICE
  * float32), B all N rows of B, the positive of local row i is B row r0 + i,

@@ -47,7 +47,8 @@ EXPORTS = ("sj_create", "sj_destroy", "sj_topk", "sj_threshold", "sj_batch",
            "sj_contrastive_fwd", "sj_backward", "sj_topk_noalloc", "sj_status_string",
            "sj_version", "sj_last_error_detail", "sj_autotune", "sj_autotune_load",
            "sj_debug_scores", "sj_block", "sj_join_groupby_sum", "sj_join_sum_product",
-           "sj_plan", "sj_contrastive_fwd_rows", "sj_backward_rows")
+           "sj_plan", "sj_contrastive_fwd_rows", "sj_backward_rows", "sj_topk_streamed",
+           "sj_threshold_streamed")
 
 I64, P = ctypes.c_int64, ctypes.c_void_p
 
@@ -165,6 +166,12 @@ def lib() -> ctypes.CDLL:
         L.sj_contrastive_fwd_rows.argtypes = [P, P, I64, I64, P, I64, ctypes.c_float, P, P]
         L.sj_backward_rows.restype = st
         L.sj_backward_rows.argtypes = [P, P, I64, I64, P, I64, ctypes.c_float, P, P, P, P]
+        L.sj_topk_streamed.restype = st
+        L.sj_topk_streamed.argtypes = [P, P, I64, P, I64, ctypes.c_int32, I64, P, P,
+                                       ctypes.POINTER(SjStats)]
+        L.sj_threshold_streamed.restype = st
+        L.sj_threshold_streamed.argtypes = [P, P, I64, P, I64, ctypes.c_double, I64, P, I64,
+                                            ctypes.POINTER(I64), ctypes.POINTER(SjStats)]
         L.sj_plan.restype = st
         L.sj_plan.argtypes = [P, P, I64, P, I64, ctypes.c_int32, ctypes.c_double, I64,
                               ctypes.POINTER(SjPlanInfo)]
@@ -308,6 +315,42 @@ class SimilarityJoin:
             s = buf[:m, 2:3].view(torch.float32)[:, 0]
             return (i, j, s, st.as_dict()) if with_stats else (i, j, s)
         raise SJError(SJ_ERR_CAPACITY, "sj_threshold")
+
+    def topk_streamed(self, A, B_host, k: int, chunk_rows: int = 0, with_stats: bool = False):
+        """Top-k against a B held in host memory, streamed in row chunks
+        (sj_topk_streamed); outputs on A's device (A may be host: cuda:0)."""
+        import torch
+        nA, nB = _rows(A, self.d), _rows(B_host, self.d)
+        dev = A.device if hasattr(A, "device") and A.is_cuda else torch.device("cuda", self.device)
+        idx = torch.empty((nA, k), dtype=torch.int64, device=dev)
+        sc = torch.empty((nA, k), dtype=torch.float32, device=dev)
+        st = SjStats()
+        _check(lib().sj_topk_streamed(self._h, _ptr(A), nA, _ptr(B_host), nB, int(k),
+                                      int(chunk_rows), _ptr(idx), _ptr(sc), ctypes.byref(st)),
+               "sj_topk_streamed")
+        return (idx, sc, st.as_dict()) if with_stats else (idx, sc)
+
+    def threshold_streamed(self, A, B_host, tau: float, chunk_rows: int = 0,
+                           capacity: int | None = None):
+        """(i, j, score) host tensors of every pair with s_ij >= tau against a
+        B held in host memory (sj_threshold_streamed)."""
+        import torch
+        nA, nB = _rows(A, self.d), _rows(B_host, self.d)
+        if capacity is None:
+            capacity = max(1024, 8 * nA)
+        for _ in range(2):
+            buf = torch.empty((max(int(capacity), 1), 3), dtype=torch.int64)
+            n = I64(0)
+            code = lib().sj_threshold_streamed(self._h, _ptr(A), nA, _ptr(B_host), nB,
+                                               float(tau), int(chunk_rows), _ptr(buf),
+                                               int(capacity), ctypes.byref(n), None)
+            if code == SJ_ERR_CAPACITY:
+                capacity = int(n.value)
+                continue
+            _check(code, "sj_threshold_streamed")
+            m = int(n.value)
+            return buf[:m, 0], buf[:m, 1], buf[:m, 2:3].view(torch.float32)[:, 0]
+        raise SJError(SJ_ERR_CAPACITY, "sj_threshold_streamed")
 
     def plan(self, A, B, k: int = 0, tau: float | None = None, sample_rows: int = 0):
         """sj_plan: the census and cost estimate of each scoring precision for
