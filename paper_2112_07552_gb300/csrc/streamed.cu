@@ -11,11 +11,12 @@
 //     start, merged by row in chunk order (each chunk's pairs are sorted by
 //     (i, j) and the chunks' columns increase);
 //   * top-k: row i's global top-k lies in the union of the chunks' top-k
-//     lists.  A block per row ranks that union with the same exact ranker as
-//     the fallback path (Dot2 key intervals, then the fixed-point accumulator
-//     for any group of overlapping intervals, e.g. equal float32 scores of
-//     different chunks), reading the candidates' B rows through the mapped
-//     host pointer (NVLink-C2C on GB300).
+//     lists.  A warp per row merges them by (float32 score desc, column asc),
+//     which is exact wherever no two chunks meet with equal float32 scores
+//     (each chunk's list is in exact order and rounding is monotone); a row
+//     where they do is ranked by the same exact ranker as the fallback path
+//     (Dot2 key intervals, then the fixed-point accumulator), reading those B
+//     rows through the mapped host pointer (NVLink-C2C on GB300).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -94,13 +95,80 @@ __host__ __device__ constexpr size_t merge_slot_bytes(int n_pad) {
   return ((size_t)n_pad * (8 + 8 + sizeof(Exact) + 6 * 4 + 1) + 511) / 256 * 256;
 }
 
-// Row i's candidates: the chunks' top-k lists (columns offset by the chunk
-// starts), ranked exactly into the global top-k.
+// Fast merge, a warp per row (at most 32 chunks, one per lane): each chunk's
+// list is already in exact order with exact float32 scores, and float32
+// rounding is monotone, so a k-way merge by (float32 score desc, column asc)
+// is exact -- except where equal float32 scores of different chunks meet,
+// whose exact order is unknown.  A row with such a meeting among its first
+// k + 1 merged entries goes to `slow` (the exact ranker); the others are
+// written out here, without reading B.
+__global__ void __launch_bounds__(256)
+    merge_fast_kernel(int64_t nA, int k, int n_chunks, const int64_t *chunk0,
+                      const int64_t *cidx, const float *csc, int64_t *out_idx,
+                      float *out_score, int *slow, unsigned *n_slow) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < nA; i += nw) {
+    const int64_t *li = cidx + ((int64_t)lane * nA + i) * k;
+    const float *ls = csc + ((int64_t)lane * nA + i) * k;
+    int pos = 0;
+    // the lane's head as an order key: larger score first, then lower column
+    auto head = [&](float &sc, int64_t &j) {
+      sc = -INFINITY;
+      j = INT64_MAX;
+      if (lane < n_chunks && pos < k) {
+        const int64_t jj = li[pos];
+        if (jj >= 0) {
+          sc = ls[pos];
+          j = jj + chunk0[lane];
+        }
+      }
+    };
+    float prev_s = 0.f;
+    int prev_c = -1;
+    bool need_exact = false;
+    for (int r = 0; r <= k && !need_exact; ++r) {
+      float sc;
+      int64_t j;
+      head(sc, j);
+      // warp arg-best: (sc desc, j asc)
+      float bs = sc;
+      int64_t bj = j;
+      int bl = lane;
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, bs, off);
+        const int64_t oj = __shfl_xor_sync(0xffffffffu, bj, off);
+        const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+        if (os > bs || (os == bs && oj < bj)) {
+          bs = os;
+          bj = oj;
+          bl = ol;
+        }
+      }
+      const bool valid = bs != -INFINITY;
+      if (valid && r > 0 && prev_c >= 0 && bs == prev_s && bl != prev_c) need_exact = true;
+      if (r < k && lane == 0) {
+        out_idx[i * k + r] = valid ? bj : -1;
+        out_score[i * k + r] = valid ? bs : -INFINITY;
+      }
+      if (lane == bl && valid) ++pos;
+      prev_s = bs;
+      prev_c = valid ? bl : -1;
+    }
+    if (need_exact && lane == 0) slow[atomicAdd(n_slow, 1u)] = (int)i;
+  }
+}
+
+// Exact merge of the listed rows: the chunks' top-k lists (columns offset by
+// the chunk starts) ranked into the global top-k.
 __global__ void __launch_bounds__(kMergeThreads)
-    merge_topk_kernel(const float *A, int64_t nA, const float *Bm, int64_t d, int k,
-                      int n_chunks, const int64_t *chunk0, const int64_t *cidx,
-                      const float *csc, float coef_key, int64_t *out_idx, float *out_score,
-                      unsigned char *scratch, size_t slot_bytes, Counters *ctr) {
+    merge_topk_kernel(const int *rows, const unsigned *n_rows, const float *A, const float *Bm,
+                      int64_t nA, int64_t d, int k, int n_chunks, const int64_t *chunk0,
+                      const int64_t *cidx, const float *csc, float coef_key, int64_t *out_idx,
+                      float *out_score, unsigned char *scratch, size_t slot_bytes,
+                      Counters *ctr) {
   const int n_max = k * n_chunks;
   const int n_pad = next_pow2(n_max > 0 ? n_max : 1);
   unsigned char *base = scratch + (size_t)blockIdx.x * slot_bytes;
@@ -118,7 +186,9 @@ __global__ void __launch_bounds__(kMergeThreads)
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
   __shared__ int s_n;
   __shared__ float s_nrm_a;
-  for (int64_t i = blockIdx.x; i < nA; i += gridDim.x) {
+  const unsigned nr = *n_rows;
+  for (unsigned r = blockIdx.x; r < nr; r += gridDim.x) {
+    const int64_t i = rows[r];
     const float *a = A + i * d;
     if (threadIdx.x == 0) {
       // compact the chunks' (valid) entries in chunk order
@@ -294,19 +364,39 @@ extern "C" sj_status sj_topk_streamed(sj_handle *h, const float *A, int64_t nA, 
     if (s != SJ_OK) return s;
     add_chunk_stats(&acc, one);
   }
-  // exact merge of the chunks' lists
+  // merge of the chunks' lists: the fast k-way merge (up to 32 chunks), the
+  // exact ranker for the rows it leaves (all rows with more chunks)
   int n_pad = 1;
   while (n_pad < k * nch) n_pad <<= 1;
   const size_t slot = merge_slot_bytes(n_pad);
   const int grid = (int)std::min<int64_t>(nA, (int64_t)handle_sm_count(h) * 4);
+  DMem slow;
   ST_CUDA(cudaMalloc(&scratch.p, slot * grid));
-  ST_CUDA(cudaMalloc(&ctr.p, sizeof(Counters)));
-  ST_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), stm));
+  ST_CUDA(cudaMalloc(&ctr.p, sizeof(Counters) + 16));
+  ST_CUDA(cudaMalloc(&slow.p, (size_t)nA * 4));
+  ST_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters) + 16, stm));
+  unsigned *n_slow = reinterpret_cast<unsigned *>(static_cast<unsigned char *>(ctr.p) +
+                                                  sizeof(Counters));
+  if (nch <= 32) {
+    merge_fast_kernel<<<(unsigned)std::min<int64_t>((nA + 7) / 8, 65535), 256, 0, stm>>>(
+        nA, k, nch, static_cast<int64_t *>(c0d.p), static_cast<int64_t *>(cidx.p),
+        static_cast<float *>(csc.p), out_idx, out_score, static_cast<int *>(slow.p), n_slow);
+    ST_CUDA(cudaGetLastError());
+  } else {
+    std::vector<int> all((size_t)nA);
+    for (int64_t i = 0; i < nA; ++i) all[i] = (int)i;
+    const unsigned na = (unsigned)nA;
+    ST_CUDA(cudaMemcpyAsync(slow.p, all.data(), (size_t)nA * 4, cudaMemcpyHostToDevice, stm));
+    ST_CUDA(cudaMemcpyAsync(n_slow, &na, 4, cudaMemcpyHostToDevice, stm));
+    ST_CUDA(cudaStreamSynchronize(stm));
+  }
   merge_topk_kernel<<<grid, kMergeThreads, 0, stm>>>(
-      sp.Adev, nA, sp.mb.dev, d, k, nch, static_cast<int64_t *>(c0d.p),
-      static_cast<int64_t *>(cidx.p), static_cast<float *>(csc.p), dot2_coef_key_of(d), out_idx,
-      out_score, static_cast<unsigned char *>(scratch.p), slot, static_cast<Counters *>(ctr.p));
+      static_cast<int *>(slow.p), n_slow, sp.Adev, sp.mb.dev, nA, d, k, nch,
+      static_cast<int64_t *>(c0d.p), static_cast<int64_t *>(cidx.p),
+      static_cast<float *>(csc.p), dot2_coef_key_of(d), out_idx, out_score,
+      static_cast<unsigned char *>(scratch.p), slot, static_cast<Counters *>(ctr.p));
   ST_CUDA(cudaGetLastError());
+  acc.n_launches += 1;
   Counters hc;
   ST_CUDA(cudaMemcpyAsync(&hc, ctr.p, sizeof hc, cudaMemcpyDeviceToHost, stm));
   ST_CUDA(cudaStreamSynchronize(stm));
