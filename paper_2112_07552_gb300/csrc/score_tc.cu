@@ -157,10 +157,10 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? K
 // tile, so the accumulators equal the dense ones; a tile with no k-block left
 // is all zeros (the epilogue then reads no accumulator).  Returns the count,
 // -1 when f stopped.
-template <class F>
+template <bool SPARSE, class F>
 __device__ __forceinline__ int tile_kblocks(const ScoreArgs &a, int64_t nkb, int64_t arow,
                                             int64_t brow, int bn, F &&f) {
-  if (a.occ == nullptr) {
+  if constexpr (!SPARSE) {
     for (int64_t kb = 0; kb < nkb; ++kb)
       if (!f(kb)) return -1;
     return (int)nkb;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void flag_timeout(TcSmem &sm, Counters *ctr) {
 // queues after releasing the accumulator, so the visits (band and threshold
 // pushes, top-k inserts) overlap the next tiles' MMAs and run on all lanes
 // with queued visits at once.
-template <int KM, bool FP8>
+template <int KM, bool FP8, bool SPARSE>
 __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, const UnitDev &un,
                                               const JobDev &jb, int64_t row, bool owner,
                                               int list, uint32_t tmem, int quarter, int half,
@@ -255,16 +255,16 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
     const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
     // block-sparse: a tile without a common nonzero k-block is all zeros and
     // its accumulator was not written
-    const bool zero_tile =
-        a.occ != nullptr &&
-        tile_kblocks(a, a.dp * 2 / 128 /* any count: only the bitmaps are read */,
-                     jb.a_prow0 + (int64_t)un.rb * BM, jb.b_prow0 + col0, bn,
-                     [](int64_t) { return false; }) == 0;
+    bool zero_tile = false;
+    if constexpr (SPARSE)
+      zero_tile = tile_kblocks<true>(a, 0 /* only the bitmaps are read */,
+                                     jb.a_prow0 + (int64_t)un.rb * BM, jb.b_prow0 + col0, bn,
+                                     [](int64_t) { return false; }) == 0;
     // kEpiChunks 32-column chunks per TMEM round trip
 #pragma unroll 1
     for (int c0 = half * (bn / 2); c0 < (half + 1) * (bn / 2); c0 += 32 * kEpiChunks) {
       float v0[32], v1[32];
-      if (zero_tile) {
+      if (SPARSE && zero_tile) {
 #pragma unroll
         for (int t = 0; t < 32; ++t) v0[t] = v1[t] = 0.f;
       } else {
@@ -315,7 +315,7 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
   }
 }
 
-template <bool FP8>
+template <bool FP8, bool SPARSE>
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                     const __grid_constant__ CUtensorMap tmB,
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t ct = ct0; ct < ct1 && ok; ++ct) {
           const bool narrow = jb.bn == kTcBNNarrow;
           const int brow = (int)(jb.b_prow0 + ct * jb.bn);
-          const int n = tile_kblocks(a, nkb, arow, brow, jb.bn, [&](int64_t kb) {
+          const int n = tile_kblocks<SPARSE>(a, nkb, arow, brow, jb.bn, [&](int64_t kb) {
             const int s = (int)(it % STAGES);
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
             if (!mbar_wait(&sm.empty[s], ph ^ 1, limit_ns, abort)) {
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int arow = (int)(jb.a_prow0 + (int64_t)un.rb * BM);
           const int brow = (int)(jb.b_prow0 + ct * jb.bn);
           bool first = true;  // the tile's first MMA overwrites the accumulator
-          const int n = tile_kblocks(a, nkb, arow, brow, jb.bn, [&](int64_t) {
+          const int n = tile_kblocks<SPARSE>(a, nkb, arow, brow, jb.bn, [&](int64_t) {
             const int s = (int)(it % STAGES);
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
             if (!mbar_wait(&sm.full[s], ph, limit_ns, abort)) {
@@ -481,13 +481,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int kj = jb.k;
       const int list = un.split * a.bands_per_split + half;
       if (kj > 0 && kj <= kRegsSmallK)
-        epilogue_unit<kRegsSmallK, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half,
+        epilogue_unit<kRegsSmallK, FP8, SPARSE>(sm, a, un, jb, row, owner, list, tmem, quarter, half,
                                         limit_ns, tile, ok);
       else if (kj > 0 && kj <= kTcExactMaxK)
-        epilogue_unit<kTcExactMaxK, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half,
+        epilogue_unit<kTcExactMaxK, FP8, SPARSE>(sm, a, un, jb, row, owner, list, tmem, quarter, half,
                                          limit_ns, tile, ok);
       else
-        epilogue_unit<0, FP8>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
+        epilogue_unit<0, FP8, SPARSE>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
     }
   }
 
@@ -565,7 +565,9 @@ cudaError_t launch_score_tc(const ScoreArgs &a, int grid, const TcMaps *maps, ui
   if (a.n_units == 0) return cudaSuccess;
   if (a.bands_per_split != 2) return cudaErrorInvalidValue;  // one list per column half
   const size_t smem = sizeof(TcSmem) + 1024;
-  auto kern = fp8 ? score_tc_kernel<true> : score_tc_kernel<false>;
+  // the dense instantiations carry none of the block-sparse code
+  auto kern = a.occ != nullptr ? (fp8 ? score_tc_kernel<true, true> : score_tc_kernel<false, true>)
+                               : (fp8 ? score_tc_kernel<true, false> : score_tc_kernel<false, false>);
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
