@@ -1205,9 +1205,14 @@ def main():
                                                                    zipf_par["oracle_seconds"]),
                                    "parity_rows_exact": zipf_par["exact"]}
     if args.workload == "zipf":
-        out["fallback_share"] = {"rows": int(stats[-1].n_overflow_rows),
-                                 "fraction": stats[-1].n_overflow_rows / nA,
-                                 "how": "rows whose band lists overflowed, re-joined in FP32"}
+        nxt = "the BF16 hi/lo split with band lists sized by their columns"
+        out["fallback_share"] = {
+            "rows": int(stats[-1].n_overflow_rows),
+            "fraction": stats[-1].n_overflow_rows / nA,
+            "how": "rows whose band lists overflowed on the first pass, re-joined in " + nxt,
+            "rejoined_rows": int(stats[-1].n_rejoined_rows),
+            "rejoined_again": int(stats[-1].n_rejoined_again),
+            "rejoined_again_how": "lists overflowed there too: re-joined in FP32"}
     if headline and world == 1 and not args.no_sub:
         out["fp32_same_join"] = guarded(fp32_same_join, args, w, dA, dB, stream, idx, sc,
                                         gpu_out[2], value)

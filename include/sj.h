@@ -119,7 +119,8 @@ typedef struct {
   int64_t n_candidates;      /* pairs that passed the low-precision filter */
   int64_t n_rescored;        /* pairs rescored with the compensated FP32 dot */
   int64_t n_exact;           /* pairs evaluated with the exact accumulator */
-  int64_t n_overflow_rows;   /* rows re-ranked against all of B (fallback) */
+  int64_t n_overflow_rows;   /* rows whose band lists overflowed (re-joined, or re-ranked
+                                against all of B) */
   int64_t n_pairs;           /* threshold: pairs emitted */
   double margin_max;         /* max proven bound m_i >= |s~ - s| over the rows whose
                                 top-k were finalised (0 without a top-k part) */
@@ -128,6 +129,13 @@ typedef struct {
   int64_t n_tier2_rows;      /* rows finalised with the large candidate tier */
   int64_t graph_replayed;    /* job groups run from a captured CUDA graph */
   double padded_pair_scores; /* pair-scores the score tiles computed, padding included */
+  int64_t n_rejoined_rows;   /* overflowed rows (64 or more of a job) re-joined against
+                                all of B by the next stage of the cascade: the BF16
+                                hi/lo split with band lists sized by the columns they
+                                cover, then FP32 */
+  int64_t n_rejoined_again;  /* of those, rows whose lists overflowed there as well and
+                                were re-joined by the stage after it (rows whose lists
+                                were complete but long are ranked within the stage) */
 } sj_stats;
 
 typedef struct sj_handle sj_handle;

@@ -104,7 +104,11 @@ struct sj_handle {
   sj::TcContext *tc = nullptr;
   float *dbg_raw = nullptr;     // sj_debug_scores: armed for the next one-job call
   float *dbg_margin = nullptr;
-  sj_handle *aux = nullptr;     // relational calls: a handle of their one-hot width
+  sj_handle *aux = nullptr;     // relational calls: a handle of their one-hot width;
+                                // cascade re-joins: a handle of the next precision
+  bool wide_lists = false;      // cascade stage: band lists sized by the columns they cover
+  int64_t rejoin_rows = 0;      // this call: rows re-joined by the next precision
+  int64_t rejoin_rows_next = 0; // of those, rows the next stage re-joined once more
 };
 
 sj_status sj::aux_handle(sj_handle *h, int64_t d, sj_precision prec, sj_handle **out,
@@ -526,12 +530,21 @@ sj_status make_batch_plan(const sj_handle *h, const JoinReq *reqs, int n, BatchP
     // rows x 2) compete with the operand tiles for L2, and a list that still
     // overflows after compaction goes to the rescan fallback.  Otherwise the
     // running k-th is refreshed lazily and needs 4k + 256.
+    // A cascade stage (wide_lists) re-joins rows whose bands overflowed the
+    // lists of a coarser precision: its lists grow with the columns they
+    // cover (1/8 of them, at most 2,048 more entries), as the dense band of
+    // those rows does: each list tracks its own k-th best, below the row's, so
+    // its band holds a fixed share of its columns (about 6% for the rows of
+    // one tight cluster under the hi/lo split's margin).
     if (r.k > 0) {
       const int64_t cols = tps * bn / P.bands;
       const bool exact_running = h->cfg.prec != SJ_FP32 && r.k <= kTcExactMaxK;
-      const int64_t slack = std::min<int64_t>(192, std::max<int64_t>(32, cols / 2048));
+      const int64_t slack =
+          h->wide_lists ? std::min<int64_t>(2048, std::max<int64_t>(32, cols / 8))
+                        : std::min<int64_t>(192, std::max<int64_t>(32, cols / 2048));
       jd.cap = (int32_t)(exact_running ? round_up(2 * (int64_t)r.k + 64 + slack, 32)
-                                       : round_up(4 * (int64_t)r.k + 256, 32));
+                                       : round_up(4 * (int64_t)r.k + 256 +
+                                                      (h->wide_lists ? slack : 0), 32));
     } else {
       jd.cap = 0;
     }
@@ -860,8 +873,9 @@ __global__ void scatter_topk_kernel(const int *rows, int n, int k, const int64_t
   }
 }
 
-// Overflowed rows from this many up are re-joined by the FP32 form instead of
-// rescanned one by one (a 128-row FFMA tile serves them together).
+// Overflowed rows from this many up are re-joined by the next precision of
+// the cascade instead of rescanned one by one (a 128-row tile serves them
+// together).
 constexpr int kRejoinMinRows = 64;
 
 struct DevMem {
@@ -874,21 +888,31 @@ struct DevMem {
 // Cascade step for rows whose band lists overflowed on a tensor-core pass:
 // the dense band of near-ties below their k-th score, wider than the lists,
 // comes from the margin of the low precision (BF16 (d + 32) 2^-21, E4M3
-// (d + 32) 2^-13, the hi/lo split (3d + 32) 2^-21, times the norms).  The
-// FP32 form's margin, 2 gamma_d, is two to four orders of magnitude
-// narrower, so the same rows re-joined against all of B in FP32 give short
-// candidate lists again; that costs 2 nB d flops per row on the FFMA tiles,
-// instead of a Dot2 rescan of all of B per row.  The re-join runs through
-// the handle's auxiliary FP32 handle (its own workspace: this call's buffers
-// stay intact), in chunks of rows, and writes the rows' outputs in place.
-sj_status rejoin_fp32(sj_handle *h, const JobDev &jd, int64_t d, const int *rows, int n,
+// (d + 32) 2^-13, the hi/lo split (3d + 32) 2^-21, times the norms and the
+// quantisation terms).  The same rows re-joined against all of B in a
+// precision with a narrower margin, or with longer lists, give complete
+// candidate lists again:
+//   * after a BF16, E4M3 or hi/lo-split pass with the usual lists, the BF16
+//     hi/lo split on the tensor cores (quantisation terms near 2^-16 instead
+//     of 2^-8 or 2^-4; three times the BF16 work) with band lists sized by
+//     the columns they cover;
+//   * after that, the FP32 form on the CUDA cores (2 gamma_d, about ten times
+//     narrower again; 2 nB d flops per row on the FFMA tiles).
+// Rows that overflow again go on down the cascade inside the re-join call.
+// Either step replaces a Dot2 rescan of all of B per row.  The re-join runs
+// through the handle's auxiliary handle (its own workspace: this call's
+// buffers stay intact), in chunks of rows, and writes the rows' outputs in
+// place.
+sj_status rejoin_rows(sj_handle *h, const JobDev &jd, int64_t d, const int *rows, int n,
                       int64_t &launches) {
+  const sj_precision next = h->cfg.prec == SJ_BF16X3 && h->wide_lists ? SJ_FP32 : SJ_BF16X3;
   sj_handle *ax = nullptr;
-  sj_status s = sj::aux_handle(h, d, SJ_FP32, &ax);
+  sj_status s = sj::aux_handle(h, d, next, &ax);
   if (s != SJ_OK) return s;
+  ax->wide_lists = next != SJ_FP32;
   cudaStream_t stm = h->stream;
   const int k = jd.k;
-  const int chunk = std::min(n, 1 << 20);
+  const int chunk = std::min(n, 1 << 19);  // bounds the next stage's band lists
   DevMem ag, ii, ss;
   SJ_CUDA(cudaMalloc(&ag.p, (size_t)chunk * d * 4));
   SJ_CUDA(cudaMalloc(&ii.p, (size_t)chunk * k * 8));
@@ -908,6 +932,8 @@ sj_status rejoin_fp32(sj_handle *h, const JobDev &jd, int64_t d, const int *rows
         jd.out_score);
     SJ_CUDA(cudaGetLastError());
     launches += 2 + st.n_launches;
+    h->rejoin_rows += nc;
+    h->rejoin_rows_next += st.n_rejoined_rows;
   }
   SJ_CUDA(cudaStreamSynchronize(stm));
   return SJ_OK;
@@ -952,7 +978,7 @@ sj_status topk_fallback_all(sj_handle *h, const BatchPlan &P, const Bufs &B, uns
     const bool band = (by_job[t0].first & 1) != 0;
     sj_status s;
     if (!band && h->cfg.prec != SJ_FP32 && (int)(t1 - t0) >= kRejoinMinRows)
-      s = rejoin_fp32(h, jd, P.d, static_cast<int *>(rows_s.p) + t0, (int)(t1 - t0), launches);
+      s = rejoin_rows(h, jd, P.d, static_cast<int *>(rows_s.p) + t0, (int)(t1 - t0), launches);
     else
       s = topk_fallback(h, B.ctr, B.meta, jd, P.d, static_cast<int *>(rows_s.p) + t0,
                         static_cast<long long *>(keys_s.p) + t0, lrow.data() + t0,
@@ -1081,6 +1107,14 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
     SJ_CUDA(cudaMemsetAsync(B.row_count, 0, (size_t)P.rows * 8, stm));
     SJ_CUDA(cudaMemsetAsync(B.row_fill, 0, (size_t)P.rows * 8, stm));
     SJ_CUDA(cudaMemsetAsync(B.n_big, 0, sizeof(int), stm));
+    // candidates grouped by row into B.acc (counts in row_fill, offsets in
+    // row_off; both are reset or rewritten below), then rescored from there
+    // with the accepted pairs written over B.cand
+    const int g_sc = (int)std::min<unsigned long long>((thr_cap + 255) / 256,
+                                                       (unsigned long long)h->sm_count * 16);
+    SJ_CUDA(launch_thr_bucket(B.cand, &B.ctr->thr_count, (int64_t)thr_cap, B.ctr, P.rows,
+                              B.row_fill, B.row_off, B.total, B.scan, B.acc, g_sc, stm));
+    SJ_CUDA(cudaMemsetAsync(B.row_fill, 0, (size_t)P.rows * 8, stm));
     ThrFinalArgs ta{};
     ta.jobs = B.jobs;
     ta.n_jobs = n;
@@ -1088,26 +1122,24 @@ sj_status issue_group(sj_handle *h, cudaStream_t stm, bool capturing, const Batc
     ta.metaA = B.meta;
     ta.metaB = B.meta;
     ta.dot2_coef_key = dot2_coef_key(P.d);
-    ta.cand = B.cand;
+    ta.cand = B.acc;
     ta.n_cand = &B.ctr->thr_count;
     ta.cand_cap = (int64_t)thr_cap;
     ta.row_count = B.row_count;
-    ta.accepted = B.acc;
+    ta.accepted = B.cand;
     ta.ctr = B.ctr;
     const int g_res = (int)std::min<unsigned long long>((thr_cap + 31) / 32,
                                                         (unsigned long long)h->sm_count * 16);
     SJ_CUDA(launch_thr_rescore(ta, g_res, stm));
     SJ_CUDA(launch_exclusive_scan(B.row_count, B.row_off, P.rows, B.total, B.scan, stm));
     SJ_CUDA(launch_job_pairs(B.jobs, n, P.rows, B.row_off, B.total, B.job_info, stm));
-    const int g_sc = (int)std::min<unsigned long long>((thr_cap + 255) / 256,
-                                                       (unsigned long long)h->sm_count * 16);
-    SJ_CUDA(launch_thr_scatter(B.jobs, n, B.acc, &B.ctr->n_pairs, (int64_t)thr_cap, B.row_off,
+    SJ_CUDA(launch_thr_scatter(B.jobs, n, B.cand, &B.ctr->n_pairs, (int64_t)thr_cap, B.row_off,
                                B.row_fill, B.staging, g_sc, stm));
     SJ_CUDA(launch_thr_sort_rows(B.jobs, n, P.rows, B.row_off, B.row_count, B.staging,
                                  B.big_rows, B.n_big, stm));
     SJ_CUDA(launch_thr_sort_big(B.jobs, n, B.staging, B.tmp, B.row_off, B.row_count, B.big_rows,
                                 B.n_big, 2 * h->sm_count, stm));
-    launches += 9;
+    launches += 14;
     SJ_CUDA(cudaMemcpyAsync(h_info, B.job_info, 16 * (size_t)n, cudaMemcpyDeviceToHost, stm));
   }
   SJ_CUDA(cudaMemcpyAsync(h->h_ctr, B.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, stm));
@@ -1198,6 +1230,7 @@ sj_status run_group_device(sj_handle *h, const BatchPlan &P, const Bufs &B, cons
 sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
   if (st) std::memset(st, 0, sizeof *st);
   if (n == 0) return SJ_OK;
+  h->rejoin_rows = h->rejoin_rows_next = 0;
   cudaStream_t stm = h->stream;
   Events ev{h, stm};
   int64_t launches = 0;
@@ -1307,6 +1340,8 @@ sj_status join_group(sj_handle *h, const JoinReq *reqs, int n, sj_stats *st) {
       st->ms_total = ev.ms(0, 3);
       st->graph_replayed = used_graph ? 1 : 0;
       st->padded_pair_scores = P.padded_pairs;
+      st->n_rejoined_rows = h->rejoin_rows;
+      st->n_rejoined_again = h->rejoin_rows_next;
     }
     s = flags_status(h->h_ctr->err_flags);
     if (s != SJ_OK) return s;
@@ -1341,6 +1376,8 @@ void add_stats(sj_stats *acc, const sj_stats &one) {
   acc->n_tier2_rows += one.n_tier2_rows;
   acc->graph_replayed += one.graph_replayed;
   acc->padded_pair_scores += one.padded_pair_scores;
+  acc->n_rejoined_rows += one.n_rejoined_rows;
+  acc->n_rejoined_again += one.n_rejoined_again;
   acc->max_abs_err_lowprec = std::max(acc->max_abs_err_lowprec, one.max_abs_err_lowprec);
   acc->margin_max = std::max(acc->margin_max, one.margin_max);
 }

@@ -331,16 +331,15 @@ __global__ void __launch_bounds__(kFinWarps * 32)
     float err = 0.f;
     constexpr int NC = 4;
     for (int p0 = 0; p0 < n; p0 += NC) {
-      const float *ap[NC], *bp[NC];
+      const float *bp[NC];
       int32_t jq[NC];
 #pragma unroll
       for (int t = 0; t < NC; ++t) {
         jq[t] = w.j[p0 + t < n ? p0 + t : p0];
-        ap[t] = a_src;
         bp[t] = B + (int64_t)jq[t] * d;
       }
       float hi[NC], lo[NC];
-      dot2_warp_n<NC>(ap, bp, d, hi, lo);
+      dot2_warp_sa<NC>(a_src, bp, d, hi, lo);
       // lane t < NC finishes candidate p0 + t
 #pragma unroll
       for (int t = 0; t < NC; ++t) {
@@ -646,6 +645,35 @@ __global__ void __launch_bounds__(1024) topk_rank_global_kernel(RankListArgs a, 
 // ---------------------------------------------------------------------------
 // Threshold
 
+// Threshold candidates bucketed by left row before rescoring.  The scoring
+// CTAs push candidates of many jobs at once, so in push order the Dot2
+// gathers touch the B rows of many jobs together (far more than L2 holds).
+// In row order the rows of one job are contiguous: the warps in flight read
+// one or two jobs' B rows, which stay in L2, and share each A row.
+// Counting pass, then (after an exclusive scan of the counts) placement.
+__global__ void thr_count_kernel(const ThrCand *cand, const unsigned long long *n_cand,
+                                 int64_t cap, const Counters *ctr, int64_t *cnt) {
+  const int64_t n = ctr->err_flags ? 0 : min64((int64_t)*n_cand, cap);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(reinterpret_cast<unsigned long long *>(cnt + cand[c].i), 1ull);
+}
+
+// cursor[i] starts at row i's exclusive offset; the order inside a row is
+// arbitrary (the accepted pairs are sorted by j afterwards).
+__global__ void thr_bucket_kernel(const ThrCand *cand, const unsigned long long *n_cand,
+                                  int64_t cap, const Counters *ctr, int64_t *cursor,
+                                  ThrCand *out) {
+  const int64_t n = ctr->err_flags ? 0 : min64((int64_t)*n_cand, cap);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const ThrCand cd = cand[c];
+    const unsigned long long slot =
+        atomicAdd(reinterpret_cast<unsigned long long *>(cursor + cd.i), 1ull);
+    out[slot] = cd;
+  }
+}
+
 // One warp evaluates four candidates at a time (Dot2 gathers interleaved).
 __global__ void thr_rescore_kernel(ThrFinalArgs a) {
   constexpr int NC = 4;
@@ -671,9 +699,19 @@ __global__ void thr_rescore_kernel(ThrFinalArgs a) {
       bp[q] = jq[q]->B + (int64_t)t[q].j * d;
     }
     float hi[NC], lo[NC];
-    dot2_warp_n<NC>(ap, bp, d, hi, lo);
+    bool same_a = true;
+#pragma unroll
+    for (int q = 1; q < NC; ++q) same_a = same_a && ap[q] == ap[0];
+    if (same_a)  // the common case: candidates are grouped by row
+      dot2_warp_sa<NC>(ap[0], bp, d, hi, lo);
+    else
+      dot2_warp_n<NC>(ap, bp, d, hi, lo);
+    // decisions are warp-uniform (every lane holds the reduced hi, lo)
+    unsigned acc = 0;
+    float sq[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
+      sq[q] = 0.f;
       if (c0 + q >= n_cand) break;
       const JobDev &jb = *jq[q];
       const long long K = dot2_key(hi[q], lo[q]);
@@ -701,10 +739,21 @@ __global__ void thr_rescore_kernel(ThrFinalArgs a) {
         }
         s = exact_to_float(ex);
       }
-      if (lane == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(a.row_count + t[q].i), 1ull);
-        unsigned long long slot = atomicAdd(&a.ctr->n_pairs, 1ull);
-        a.accepted[slot] = ThrCand{t[q].i, t[q].j, s, 0};
+      sq[q] = s;
+      acc |= 1u << q;
+    }
+    // one slot reservation per warp and group of candidates; lane q stores
+    // candidate q
+    if (acc) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&a.ctr->n_pairs, (unsigned long long)__popc(acc));
+      base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        if (lane == q && ((acc >> q) & 1u)) {
+          atomicAdd(reinterpret_cast<unsigned long long *>(a.row_count + t[q].i), 1ull);
+          a.accepted[base + __popc(acc & ((1u << q) - 1u))] = ThrCand{t[q].i, t[q].j, sq[q], 0};
+        }
       }
     }
   }
@@ -992,6 +1041,18 @@ cudaError_t launch_topk_rank_global(const RankListArgs &a, const int *big, int n
                                     void *scratch, size_t per_row, cudaStream_t st) {
   if (n_big == 0) return cudaSuccess;
   topk_rank_global_kernel<<<n_big, 1024, 0, st>>>(a, big, scratch, per_row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thr_bucket(const ThrCand *cand, const unsigned long long *n_cand,
+                              int64_t cap, const Counters *ctr, int64_t rows, int64_t *cnt,
+                              int64_t *off, int64_t *total, void *scan_scratch, ThrCand *out,
+                              int grid, cudaStream_t st) {
+  if (grid <= 0 || rows == 0) return cudaSuccess;
+  thr_count_kernel<<<(unsigned)grid, 256, 0, st>>>(cand, n_cand, cap, ctr, cnt);
+  cudaError_t e = launch_exclusive_scan(cnt, off, rows, total, scan_scratch, st);
+  if (e != cudaSuccess) return e;
+  thr_bucket_kernel<<<(unsigned)grid, 256, 0, st>>>(cand, n_cand, cap, ctr, off, out);
   return cudaGetLastError();
 }
 

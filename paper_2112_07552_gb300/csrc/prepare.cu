@@ -66,6 +66,23 @@ __device__ __forceinline__ int find_seg(const PackSeg *segs, int n_segs, int64_t
 
 constexpr int kPrepWarps = 8;
 
+// Four packed elements at dst (aligned to four elements) in one store.
+__device__ __forceinline__ void store4(float *dst, float a, float b, float c, float d) {
+  *reinterpret_cast<float4 *>(dst) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(__nv_bfloat16 *dst, __nv_bfloat16 a, __nv_bfloat16 b,
+                                       __nv_bfloat16 c, __nv_bfloat16 d) {
+  uint2 w;
+  w.x = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+  w.y = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
+  *reinterpret_cast<uint2 *>(dst) = w;
+}
+__device__ __forceinline__ void store4(__nv_fp8_e4m3 *dst, __nv_fp8_e4m3 a, __nv_fp8_e4m3 b,
+                                       __nv_fp8_e4m3 c, __nv_fp8_e4m3 d) {
+  *reinterpret_cast<uint32_t *>(dst) = (uint32_t)a.__x | ((uint32_t)b.__x << 8) |
+                                       ((uint32_t)c.__x << 16) | ((uint32_t)d.__x << 24);
+}
+
 // E4M3 scale exponent: the largest e with mx 2^e <= 448 (the largest finite
 // E4M3 value, 0.875 2^9), clamped to [-60, 60]; 0 for mx == 0.
 __device__ __forceinline__ int e4m3_exponent(float mx) {
@@ -219,6 +236,44 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
       float qs = 0.f, qc = 0.f;   // ||x~||^2
       float es = 0.f, ec = 0.f;   // ||x~ - x||^2
       bool bad = false;
+      // one element of the row: validity, rounding, the three sums of squares
+      auto pack1 = [&](float x) -> OutT {
+        if (!isfinite(x)) { bad = true; x = 0.f; }
+        OutT qv;
+        float qf;
+        if constexpr (kE4M3) {
+          qv = OutT(x * up);  // round to nearest even, saturating
+          qf = float(qv) * down;
+        } else {
+          qv = OutT(x);
+          qf = float(qv);
+        }
+        acc_sq(x, ns, nc);
+        acc_sq(qf, qs, qc);
+        acc_sq(__fsub_rn(qf, x), es, ec);  // exact difference of x and its rounding
+        return qv;
+      };
+      if ((d & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        // 16-byte loads: lane l takes entries 4l .. 4l+3 of each 128-entry
+        // block (a group of four lies wholly inside or outside the row)
+        for (int64_t k0 = 0; k0 < dp; k0 += 512) {
+          float4 xv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + 128 * u + 4 * lane;
+            xv[u] = k < d ? *reinterpret_cast<const float4 *>(src + k)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + 128 * u + 4 * lane;
+            if (k >= dp) break;
+            const OutT q0 = pack1(xv[u].x), q1 = pack1(xv[u].y);
+            const OutT q2 = pack1(xv[u].z), q3 = pack1(xv[u].w);
+            store4(dst + k, q0, q1, q2, q3);
+          }
+        }
+      } else {
       for (int64_t k0 = 0; k0 < dp; k0 += 128) {
         float xv[4];
 #pragma unroll
@@ -230,22 +285,9 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
         for (int u = 0; u < 4; ++u) {
           const int64_t k = k0 + 32 * u + lane;
           if (k >= dp) break;
-          float x = xv[u];
-          if (!isfinite(x)) { bad = true; x = 0.f; }
-          OutT qv;
-          float qf;
-          if constexpr (kE4M3) {
-            qv = OutT(x * up);  // round to nearest even, saturating
-            qf = float(qv) * down;
-          } else {
-            qv = OutT(x);
-            qf = float(qv);
-          }
-          dst[k] = qv;
-          acc_sq(x, ns, nc);
-          acc_sq(qf, qs, qc);
-          acc_sq(__fsub_rn(qf, x), es, ec);  // exact difference of x and its rounding
+          dst[k] = pack1(xv[u]);
         }
+      }
       }
       bool any_bad = __any_sync(0xffffffffu, bad);
       float n2 = warp_sumsq2(ns, nc);

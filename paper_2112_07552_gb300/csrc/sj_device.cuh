@@ -133,6 +133,76 @@ __device__ __forceinline__ void dot2_warp(const float *a, const float *b, int64_
   lo = c;
 }
 
+// NC Dot2 evaluations of one row a against NC rows b[q], by one warp.  With
+// d a multiple of 128 and every row 16-byte aligned, lane l takes the
+// entries 4l .. 4l+3 of each 128-entry block through one 16-byte load per
+// row, a shared by the NC evaluations; otherwise the lane chains of
+// dot2_warp_n.  Either way each lane chain holds at most ceil(d/32) products
+// summed in index order and the combination tree is that of dot2_warp, so
+// the error bound of dot2_warp holds (the values may differ from it in the
+// last bits, within that bound).
+template <int NC>
+__device__ __forceinline__ void dot2_warp_sa(const float *a, const float *const (&b)[NC],
+                                             int64_t d, float (&hi)[NC], float (&lo)[NC]) {
+  const int lane = threadIdx.x & 31;
+  float s[NC], c[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) s[q] = c[q] = 0.f;
+  uintptr_t al = reinterpret_cast<uintptr_t>(a);
+#pragma unroll
+  for (int q = 0; q < NC; ++q) al |= reinterpret_cast<uintptr_t>(b[q]);
+  if ((d & 127) == 0 && (al & 15) == 0) {
+#pragma unroll 4
+    for (int64_t k = 4 * lane; k < d; k += 128) {
+      const float4 x = *reinterpret_cast<const float4 *>(a + k);
+      float4 y[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) y[q] = __ldg(reinterpret_cast<const float4 *>(b[q] + k));
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        dot2_step(x.x, y[q].x, s[q], c[q]);
+        dot2_step(x.y, y[q].y, s[q], c[q]);
+        dot2_step(x.z, y[q].z, s[q], c[q]);
+        dot2_step(x.w, y[q].w, s[q], c[q]);
+      }
+    }
+  } else {
+    int64_t k = lane;
+    for (; k + 96 < d; k += 128) {
+      float x[4], y[NC][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = a[k + 32 * u];
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[q][u] = __ldg(b[q] + k + 32 * u);
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dot2_step(x[u], y[q][u], s[q], c[q]);
+    }
+    for (; k < d; k += 32) {
+      const float x = a[k];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) dot2_step(x, __ldg(b[q] + k), s[q], c[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      float s2 = __shfl_xor_sync(0xffffffffu, s[q], off);
+      float c2 = __shfl_xor_sync(0xffffffffu, c[q], off);
+      float t, e;
+      two_sum(s[q], s2, t, e);
+      s[q] = t;
+      c[q] = __fadd_rn(__fadd_rn(c[q], c2), e);
+    }
+    hi[q] = s[q];
+    lo[q] = c[q];
+  }
+}
+
 // NC independent Dot2 evaluations by one warp, interleaved so that 4 * NC
 // gathers per lane are in flight.  Each evaluation has exactly the lane chains
 // and combination tree of dot2_warp (same values, same error bound).

@@ -264,6 +264,15 @@ struct ThrFinalArgs {
   Counters *ctr;
 };
 cudaError_t launch_thr_rescore(const ThrFinalArgs &a, int grid, cudaStream_t st);
+// Candidates cand[0 .. min(*n_cand, cap)) placed into `out` grouped by left
+// row (rows in increasing order): counts into cnt (zeroed by the caller), an
+// exclusive scan into off (off[i] ends as the end of row i's group), then
+// placement.  Skips its work once an input was flagged.
+cudaError_t launch_thr_bucket(const ThrCand *cand, const unsigned long long *n_cand,
+                              int64_t cap, const Counters *ctr, int64_t rows, int64_t *cnt,
+                              int64_t *off, int64_t *total, void *scan_scratch, ThrCand *out,
+                              int grid, cudaStream_t st);
+
 
 // Exclusive scan of n int64 values (in place allowed); total written to *total.
 size_t scan_scratch_bytes(int64_t n);

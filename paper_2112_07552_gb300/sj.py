@@ -65,7 +65,8 @@ class SjStats(ctypes.Structure):
                 ("n_overflow_rows", I64), ("n_pairs", I64),
                 ("margin_max", ctypes.c_double), ("max_abs_err_lowprec", ctypes.c_double),
                 ("n_launches", I64), ("n_tier2_rows", I64), ("graph_replayed", I64),
-                ("padded_pair_scores", ctypes.c_double)]
+                ("padded_pair_scores", ctypes.c_double), ("n_rejoined_rows", I64),
+                ("n_rejoined_again", I64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -64,7 +64,7 @@ def test_invalid_arguments_are_rejected_without_device(L):
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(sj.SjPair) == 24
     assert ctypes.sizeof(sj.SjConfig) == 48
-    assert ctypes.sizeof(sj.SjStats) == 4 * 8 + 5 * 8 + 2 * 8 + 3 * 8 + 8
+    assert ctypes.sizeof(sj.SjStats) == 4 * 8 + 5 * 8 + 2 * 8 + 3 * 8 + 8 + 2 * 8
     assert ctypes.sizeof(sj.SjGroup) == 32 and sj.SjGroup.sum_hi.offset == 16
     assert ctypes.sizeof(sj.SjPlanInfo) == 8 + 5 * 4 * 8 + 8
 

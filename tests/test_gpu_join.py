@@ -470,3 +470,40 @@ def test_bf16x3_narrows_dense_bands(sjmod):
     assert out["bf16"]["n_overflow_rows"] > 0
     assert out["bf16x3"]["n_overflow_rows"] < out["bf16"]["n_overflow_rows"]
     assert out["bf16x3"]["n_rescored"] < out["bf16"]["n_rescored"]
+
+
+def test_cascade_reaches_every_stage_on_massive_ties(sjmod):
+    """200 one-hot rows over 2 keys against 1,300: every row has ~650 exact
+    ties at its k-th score, more than any band list holds.  The BF16 pass
+    overflows, the rows are re-joined in the hi/lo split (overflow again:
+    the ties are exact), then in FP32 (again), and finally re-ranked against
+    all of B by the rescan; the results stay exact throughout."""
+    keys, k = 2, 10
+    A = datagen.one_hot(datagen.keys(200, keys, 61, 0), keys)
+    B = datagen.one_hot(datagen.keys(1300, keys, 61, 1), keys)
+    J = sjmod.SimilarityJoin(keys, prec="bf16", device=0, flags=sjmod.SJ_FLAG_SINGLE_SPLIT)
+    idx, sc, st = J.topk(dev(A), dev(B), k, with_stats=True)
+    J.close()
+    assert_topk(idx, sc, A, B, k)
+    assert st["n_overflow_rows"] == 200
+    assert st["n_rejoined_rows"] == 200 and st["n_rejoined_again"] == 200
+
+
+@pytest.mark.parametrize("prec", ("fp8", "bf16"))
+def test_cascade_dense_cluster_top50(sjmod, prec):
+    """One dense cluster, k = 50, one column split per row block (each row's
+    candidates in two lists, as in joins of many rows): the E4M3 (or BF16)
+    margin band overflows the lists of every row; the re-join in the hi/lo
+    split, with band lists sized by the columns they cover, settles almost
+    all of them on the tensor cores."""
+    nA, nB, d, k = 300, 20000, 256, 50
+    C = datagen.centres(1, d, 74)
+    A = datagen.clustered(nA, d, 1, 0.1, seed=74, stream=0, C=C)
+    B = datagen.clustered(nB, d, 1, 0.1, seed=74, stream=1, C=C)
+    J = sjmod.SimilarityJoin(d, prec=prec, device=0, flags=sjmod.SJ_FLAG_SINGLE_SPLIT)
+    idx, sc, st = J.topk(dev(A), dev(B), k, with_stats=True)
+    J.close()
+    assert_topk(idx, sc, A, B, k)
+    assert st["n_overflow_rows"] >= 64
+    assert st["n_rejoined_rows"] == st["n_overflow_rows"]
+    assert st["n_rejoined_again"] < st["n_rejoined_rows"] // 4
