@@ -242,7 +242,9 @@ __device__ __forceinline__ uint32_t warp_kth_key(int n, int k, Get get) {
   return T;
 }
 
-__global__ void __launch_bounds__(kFinWarps * 32)
+// Four blocks (32 warps) per SM: the kernel is bound by the latency of its
+// gathers, so occupancy matters more than registers.
+__global__ void __launch_bounds__(kFinWarps * 32, 4)
     topk_finalize_warp_kernel(TopkFinalArgs a, int *defer, unsigned *n_defer) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const unsigned FULL = 0xffffffffu;

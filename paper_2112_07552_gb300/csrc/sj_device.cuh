@@ -152,7 +152,7 @@ __device__ __forceinline__ void dot2_warp_sa(const float *a, const float *const 
 #pragma unroll
   for (int q = 0; q < NC; ++q) al |= reinterpret_cast<uintptr_t>(b[q]);
   if ((d & 127) == 0 && (al & 15) == 0) {
-#pragma unroll 4
+#pragma unroll 1
     for (int64_t k = 4 * lane; k < d; k += 128) {
       const float4 x = *reinterpret_cast<const float4 *>(a + k);
       float4 y[NC];
