@@ -151,15 +151,20 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 
 // Warp-cooperative refresh of theta and compaction of every row of this warp
 // whose band list holds more than `limit` entries, or at least k entries and
-// kRefresh more than after its last refresh (keeps theta close to the running
-// k-th best, so few scores reach the slow path).  Must be called by all 32
-// lanes (each lane owning at most one row; non-owners pass has_row = false).
+// twice as many as right after its last refresh (at least kRefresh more).  A
+// refresh is a 32-step bisection over the whole list, so refreshes are spaced
+// geometrically: a list whose band is dense (hundreds of near-ties) is
+// refreshed a few times, not once per 32 entries; a stale theta only lets
+// more scores into the list, which the next refresh drops.  Must be called
+// by all 32 lanes (each lane owning at most one row; non-owners pass
+// has_row = false).
 constexpr int kRefresh = 32;
 __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int limit) {
   const int lane = threadIdx.x & 31;
   // with an exact theta: compact only when the list is full
   const bool due = r.exact ? r.cnt > limit
-                          : (r.cnt > limit || (r.cnt >= k && r.cnt >= r.last + kRefresh));
+                          : (r.cnt > limit ||
+                             (r.cnt >= k && r.cnt >= r.last + max(kRefresh, r.last)));
   unsigned need = __ballot_sync(0xffffffffu, has_row && !r.overflow && due);
   while (need) {
     const int src = __ffs(need) - 1;
