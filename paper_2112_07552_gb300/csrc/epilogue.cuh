@@ -134,7 +134,8 @@ __device__ __forceinline__ void row_push_regs(RowCtx &r, float (&h)[KM], const S
     }
     if (v > h[KM - 1]) {
       topk_regs_insert<KM>(h, v);
-      r.theta = __fsub_rd(h[KM - 1], r.two_m);
+      // never below a bound adopted from the row's other list
+      r.theta = fmaxf(r.theta, __fsub_rd(h[KM - 1], r.two_m));
     }
   }
   if (v >= r.tau_lo) push_thr(a, r.i, j, v * r.to_s);

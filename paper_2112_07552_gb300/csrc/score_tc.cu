@@ -71,9 +71,35 @@ struct alignas(1024) TcSmem {
   // [e][t], so a warp's lanes fall in distinct banks
   float qv[kTcQueue][kEpiThreads];
   int32_t qj[kTcQueue][kEpiThreads];
+  // each (column half, tile row)'s latest theta, tagged with its unit:
+  // (tag << 32) | float bits
+  unsigned long long kpub[2][BM];
   uint32_t tmem_base;
   int abort;
 };
+
+// The two column halves of a row share their thresholds.  Each half's theta
+// is at most (k-th best of the columns it has seen) - 2m, and the k-th best
+// of any subset of a row's columns is at most the row's, so either half may
+// filter with the larger of the two: its band list still holds every final
+// candidate of its columns, and the row's top-k members it holds are among
+// its k best visited scores, so the finaliser's k-th (from the lists' top-k
+// or by bisection over the lists) is unchanged.  The tag (unit + 1) keeps a
+// half from adopting a value its partner published for the previous unit's
+// row; an overflowed list (theta = +inf) publishes nothing.
+__device__ __forceinline__ void theta_publish(TcSmem &sm, int half, int r, uint32_t tag,
+                                              const RowCtx &rc) {
+  if (rc.overflow || !(rc.theta > -INFINITY)) return;
+  *reinterpret_cast<volatile unsigned long long *>(&sm.kpub[half][r]) =
+      ((unsigned long long)tag << 32) | __float_as_uint(rc.theta);
+}
+__device__ __forceinline__ void theta_adopt(TcSmem &sm, int half, int r, uint32_t tag,
+                                            RowCtx &rc) {
+  const unsigned long long p =
+      *reinterpret_cast<volatile unsigned long long *>(&sm.kpub[half ^ 1][r]);
+  if ((uint32_t)(p >> 32) == tag && !rc.overflow)
+    rc.theta = fmaxf(rc.theta, __uint_as_float((uint32_t)p));
+}
 
 // One visit of a score that passed min(theta, tau_lo): band list, running
 // top-k (KM > 0 register slots; KM == 0: lazy theta) and threshold list.
@@ -198,8 +224,10 @@ template <int KM, bool FP8, bool SPARSE>
 __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, const UnitDev &un,
                                               const JobDev &jb, int64_t row, bool owner,
                                               int list, uint32_t tmem, int quarter, int half,
-                                              uint64_t limit_ns, uint64_t &tile, bool &ok) {
+                                              uint64_t limit_ns, uint64_t &tile, bool &ok,
+                                              uint32_t tag) {
   volatile int *abort = &sm.abort;
+  const int rt = quarter * 32 + (int)(threadIdx.x & 31);  // row within the tile
   const int kj = jb.k;
   // Band room: before a chunk, for its 32 visits plus a full queue; before a
   // drain, for the queue alone.  (A list whose entries at or above theta do
@@ -260,6 +288,7 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
       zero_tile = tile_kblocks<true>(a, 0 /* only the bitmaps are read */,
                                      jb.a_prow0 + (int64_t)un.rb * BM, jb.b_prow0 + col0, bn,
                                      [](int64_t) { return false; }) == 0;
+    if (owner && kj > 0) theta_adopt(sm, half, rt, tag, rc);
     // kEpiChunks 32-column chunks per TMEM round trip
 #pragma unroll 1
     for (int c0 = half * (bn / 2); c0 < (half + 1) * (bn / 2); c0 += 32 * kEpiChunks) {
@@ -291,12 +320,14 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
         if (owner) epilogue_chunk<KM>(rc, h, a, v1, col0 + c0 + 32, nB, qv, qj, qn);
       }
     }
+    if (owner && kj > 0) theta_publish(sm, half, rt, tag, rc);
     fence_before();
     mbar_arrive(&sm.tmem_empty[acc]);
     // the accumulator is released: drain once a lane holds kQueueFlush visits
     if (__any_sync(0xffffffffu, qn >= kQueueFlush)) {
       if (kj > 0) warp_compact(rc, owner, kj, limit_drain);
       if (owner) drain_queue<KM>(rc, h, a, qv, qj, qn);
+      if (owner && kj > 0) theta_publish(sm, half, rt, tag, rc);
     }
   }
   if (kj > 0) warp_compact(rc, owner, kj, limit_drain);
@@ -344,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     sm.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int t = threadIdx.x; t < 2 * BM; t += kThreads) (&sm.kpub[0][0])[t] = 0ull;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(&sm.tmem_base)),
@@ -480,14 +512,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool owner = row < jb.nA;
       const int kj = jb.k;
       const int list = un.split * a.bands_per_split + half;
+      const uint32_t tag = (uint32_t)unit + 1u;  // never 0, the cleared value
       if (kj > 0 && kj <= kRegsSmallK)
         epilogue_unit<kRegsSmallK, FP8, SPARSE>(sm, a, un, jb, row, owner, list, tmem, quarter, half,
-                                        limit_ns, tile, ok);
+                                        limit_ns, tile, ok, tag);
       else if (kj > 0 && kj <= kTcExactMaxK)
         epilogue_unit<kTcExactMaxK, FP8, SPARSE>(sm, a, un, jb, row, owner, list, tmem, quarter, half,
-                                         limit_ns, tile, ok);
+                                         limit_ns, tile, ok, tag);
       else
-        epilogue_unit<0, FP8, SPARSE>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns, tile, ok);
+        epilogue_unit<0, FP8, SPARSE>(sm, a, un, jb, row, owner, list, tmem, quarter, half, limit_ns,
+                                      tile, ok, tag);
     }
   }
 

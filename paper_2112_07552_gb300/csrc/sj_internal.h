@@ -171,7 +171,7 @@ struct ScoreArgs {
 constexpr int kSimtBM = 128, kSimtBN = 128, kSimtBK = 16;
 constexpr int kTcBM = 128, kTcBN = 256, kTcBNNarrow = 128;
 constexpr int kTcExactMaxK = 32;  // k tracked exactly by the tensor-core epilogue (registers)
-constexpr int kTcQueue = 16;      // tensor-core epilogue: queued visits per thread
+constexpr int kTcQueue = 15;      // tensor-core epilogue: queued visits per thread
 
 cudaError_t launch_score_simt(const ScoreArgs &a, int grid, cudaStream_t st);
 
