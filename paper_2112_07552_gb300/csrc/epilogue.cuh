@@ -127,17 +127,17 @@ __device__ __forceinline__ void row_push(RowCtx &r, const ScoreArgs &a, float v,
 template <int KM>
 __device__ __forceinline__ void row_push_regs(RowCtx &r, float (&h)[KM], const ScoreArgs &a,
                                               float v, int32_t j) {
-  if (v >= r.theta) {
-    if (!r.overflow) {
-      r.band[r.cnt] = Cand{v * r.to_s, j};
-      r.cnt += 1;
-    }
-    if (v > h[KM - 1]) {
-      topk_regs_insert<KM>(h, v);
-      // never below a bound adopted from the row's other list
-      r.theta = fmaxf(r.theta, __fsub_rd(h[KM - 1], r.two_m));
-    }
+  // branch-free apart from the stores: lanes of a warp visit different
+  // scores at once, and an insert of -inf (a score below theta) leaves the
+  // array, and so theta, unchanged
+  const bool in = v >= r.theta;
+  if (in && !r.overflow) {
+    r.band[r.cnt] = Cand{v * r.to_s, j};
+    r.cnt += 1;
   }
+  topk_regs_insert<KM>(h, in ? v : -INFINITY);
+  // never below a bound adopted from the row's other list
+  r.theta = fmaxf(r.theta, __fsub_rd(h[KM - 1], r.two_m));
   if (v >= r.tau_lo) push_thr(a, r.i, j, v * r.to_s);
 }
 

@@ -140,33 +140,31 @@ __device__ __forceinline__ void epilogue_chunk(RowCtx &rc, float (&h)[KM > 0 ? K
                          fmaxf(fmaxf(q8[4], q8[5]), fmaxf(q8[6], q8[7])));
   const float tmin = fminf(rc.theta, rc.tau_lo);
   if (mx >= tmin) {
-    // loop over the passing quads; a switch picks the quad's registers by
-    // static index (no local memory)
+    // loop over the passing quads; the quad's registers are picked by a
+    // select tree on the bits of its index (static register indices, no
+    // indirect branch: lanes with different quads do not serialise)
     uint32_t qm = 0;
 #pragma unroll
     for (int g = 0; g < 8; ++g) qm |= (q8[g] >= tmin ? 1u : 0u) << g;
     while (qm) {
       const int g = __ffs(qm) - 1;
       qm &= qm - 1;
-      float x0, x1, x2, x3;
-      switch (g) {
-#define SJ_QUAD(G)     \
-  case G:              \
-    x0 = v[4 * G];     \
-    x1 = v[4 * G + 1]; \
-    x2 = v[4 * G + 2]; \
-    x3 = v[4 * G + 3]; \
-    break;
-        SJ_QUAD(0) SJ_QUAD(1) SJ_QUAD(2) SJ_QUAD(3) SJ_QUAD(4) SJ_QUAD(5) SJ_QUAD(6)
-        default: SJ_QUAD(7)
-#undef SJ_QUAD
+      float xs[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const bool g0 = (g & 1) != 0, g1 = (g & 2) != 0, g2 = (g & 4) != 0;
+        const float s0 = g0 ? v[4 + e] : v[e], s1 = g0 ? v[12 + e] : v[8 + e];
+        const float s2 = g0 ? v[20 + e] : v[16 + e], s3 = g0 ? v[28 + e] : v[24 + e];
+        const float t0 = g1 ? s1 : s0, t1 = g1 ? s3 : s2;
+        xs[e] = g2 ? t1 : t0;
       }
       const int64_t jq = jb + 4 * g;
-#pragma unroll 1
+      // room for the quad first, then four predicated appends
+      if (qn > kTcQueue - 4) drain_queue<KM>(rc, h, a, qv, qj, qn);
+#pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float x = e == 0 ? x0 : e == 1 ? x1 : e == 2 ? x2 : x3;
+        const float x = xs[e];
         if (x >= tmin && jq + e < nB) {
-          if (qn == kTcQueue) drain_queue<KM>(rc, h, a, qv, qj, qn);
           qv[qn * kEpiThreads] = x;
           qj[qn * kEpiThreads] = (int32_t)(jq + e);
           ++qn;
