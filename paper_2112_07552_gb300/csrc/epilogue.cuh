@@ -38,6 +38,7 @@ struct RowCtx {
   int overflow;   // band list could not be compacted below the limit
   Cand *band;     // cap entries
   bool exact;     // theta tracks the running k-th best exactly (kept by the caller)
+  uint32_t kth_key;  // lazy theta: key of the list's k-th entry at the last refresh
   float to_s;     // stored score = visited value * to_s (a power of two; E4M3 scoring
                   // visits accumulator units, with theta, tau_lo, two_m in those units)
   int32_t i;      // global left row
@@ -104,6 +105,7 @@ __device__ __forceinline__ void row_begin(RowCtx &r, const ScoreArgs &a, const J
   r.slot = jb.slot0 + local * jb.lists + list;
   r.band = a.band + jb.band0 + (local * jb.lists + list) * (int64_t)jb.cap;
   r.theta = jb.k > 0 ? -INFINITY : INFINITY;
+  r.kth_key = 0;
   r.to_s = 1.f;
 }
 
@@ -159,13 +161,18 @@ __device__ __forceinline__ float fkey_inv(uint32_t k) {
 // more scores into the list, which the next refresh drops.  Must be called
 // by all 32 lanes (each lane owning at most one row; non-owners pass
 // has_row = false).
+// LAZY: theta is refreshed from the list (r.exact false); otherwise the
+// caller tracks the running k-th exactly (r.exact true) and the list is only
+// compacted when full.  A template parameter, so that the exact kernels carry
+// no bisection code (registers).
 constexpr int kRefresh = 32;
+template <bool LAZY>
 __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int limit) {
   const int lane = threadIdx.x & 31;
   // with an exact theta: compact only when the list is full
-  const bool due = r.exact ? r.cnt > limit
-                          : (r.cnt > limit ||
-                             (r.cnt >= k && r.cnt >= r.last + max(kRefresh, r.last)));
+  const bool due = !LAZY ? r.cnt > limit
+                         : (r.cnt > limit ||
+                            (r.cnt >= k && r.cnt >= r.last + max(kRefresh, r.last)));
   unsigned need = __ballot_sync(0xffffffffu, has_row && !r.overflow && due);
   while (need) {
     const int src = __ffs(need) - 1;
@@ -179,18 +186,29 @@ __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int
     const float to_s = __shfl_sync(0xffffffffu, r.to_s, src);
     const float two_m = __shfl_sync(0xffffffffu, r.two_m, src) * to_s;
     const float theta_old = __shfl_sync(0xffffffffu, r.theta, src) * to_s;
-    const bool exact = __shfl_sync(0xffffffffu, r.exact ? 1 : 0, src) != 0;
     float theta = theta_old;
-    if (!exact) {
-      // k-th largest banded score: the largest key T with #{key >= T} >= k
-      uint32_t T = 0;
-      for (int b = 31; b >= 0; --b) {
-        const uint32_t t = T | (1u << b);
+    uint32_t T = 0;
+    if constexpr (LAZY) {
+      // k-th largest banded score: the largest key T with #{key >= T} >= k,
+      // by bisection between the k-th of the last refresh (the list's k-th
+      // only rises: entries are only added, and compaction drops entries
+      // below theta, which stays below it) and the list's largest key.  A
+      // result without k entries at or above it can only be that earlier
+      // k-th, itself a lower bound of the row's k-th score, so theta stays
+      // valid either way.
+      uint32_t lo = __shfl_sync(0xffffffffu, r.kth_key, src), hi = 0;
+      for (int q = lane; q < n; q += 32) hi = max(hi, fkey(band[q].v));
+      hi = __reduce_max_sync(0xffffffffu, hi);
+      if (hi < lo) hi = lo;
+      while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1) + 1;  // in (lo, hi]
         unsigned c = 0;
-        for (int q = lane; q < n; q += 32) c += fkey(band[q].v) >= t;
+        for (int q = lane; q < n; q += 32) c += fkey(band[q].v) >= mid;
         c = __reduce_add_sync(0xffffffffu, c);
-        if (c >= (unsigned)k) T = t;
+        if (c >= (unsigned)k) lo = mid;
+        else hi = mid - 1;
       }
+      T = lo;
       theta = fmaxf(theta_old, __fsub_rd(fkey_inv(T), two_m));
     }
     // stable in-place compaction: a chunk is read fully before it is written
@@ -206,6 +224,7 @@ __device__ __forceinline__ void warp_compact(RowCtx &r, bool has_row, int k, int
     }
     __syncwarp();
     if (lane == src) {
+      if (LAZY) r.kth_key = T;
       r.theta = theta / to_s;
       r.cnt = w;
       r.last = w;

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, 2) score_simt_kernel(ScoreArgs a) {
       __syncthreads();
       if (tid < BM) {
         // the whole of warps 0-3 (the row owners) refreshes and compacts
-        if (rc.k > 0) warp_compact(rc, owner, rc.k, jb.cap - BN);
+        if (rc.k > 0) warp_compact<true>(rc, owner, rc.k, jb.cap - BN);
         if (owner) {
           const int ncol = (int)min64(BN, nB - col0);
           const float tmin = fminf(rc.theta, rc.tau_lo);

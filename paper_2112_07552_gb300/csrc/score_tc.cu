@@ -311,10 +311,10 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
           if (kEpiChunks == 2 && col0 + c0 + 32 + t < nB) dst[col0 + c0 + 32 + t] = v1[t] * rc.to_s;
         }
       }
-      if (kj > 0) warp_compact(rc, owner, kj, limit);
+      if (kj > 0) warp_compact<KM == 0>(rc, owner, kj, limit);
       if (owner) epilogue_chunk<KM>(rc, h, a, v0, col0 + c0, nB, qv, qj, qn);
       if constexpr (kEpiChunks == 2) {
-        if (kj > 0) warp_compact(rc, owner, kj, limit);
+        if (kj > 0) warp_compact<KM == 0>(rc, owner, kj, limit);
         if (owner) epilogue_chunk<KM>(rc, h, a, v1, col0 + c0 + 32, nB, qv, qj, qn);
       }
     }
@@ -323,12 +323,12 @@ __device__ __forceinline__ void epilogue_unit(TcSmem &sm, const ScoreArgs &a, co
     mbar_arrive(&sm.tmem_empty[acc]);
     // the accumulator is released: drain once a lane holds kQueueFlush visits
     if (__any_sync(0xffffffffu, qn >= kQueueFlush)) {
-      if (kj > 0) warp_compact(rc, owner, kj, limit_drain);
+      if (kj > 0) warp_compact<KM == 0>(rc, owner, kj, limit_drain);
       if (owner) drain_queue<KM>(rc, h, a, qv, qj, qn);
       if (owner && kj > 0) theta_publish(sm, half, rt, tag, rc);
     }
   }
-  if (kj > 0) warp_compact(rc, owner, kj, limit_drain);
+  if (kj > 0) warp_compact<KM == 0>(rc, owner, kj, limit_drain);
   if (owner) {
     drain_queue<KM>(rc, h, a, qv, qj, qn);
     row_end(rc, a);
