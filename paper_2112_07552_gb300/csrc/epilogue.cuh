@@ -9,15 +9,15 @@
 //
 // Top-k filter.  |s~_ij - s_ij| <= m_i for every j.  With s~_(k) the k-th
 // largest s~ of the row, every exact top-k member has s~ >= s~_(k) - 2 m_i
-// (k rows have s >= s~_(k) - m_i).  theta_i is s~_(k) - 2 m_i over the
-// columns seen so far, which never exceeds the final value, so the band list
-// is a superset of the final candidates.  theta_i is refreshed only when the
-// list is nearly full: the warp then finds the exact k-th largest banded score
-// (bisection on order-preserving integer keys) and compacts the list, unless
-// the kernel tracks the running k best exactly (a sorted register array in the
-// tensor-core epilogue), in which case theta is always exact.  The row's k
-// best scores always pass and are never compacted away, so the final list
-// holds them and the finaliser recomputes s~_(k) from it.
+// (k rows have s >= s~_(k) - m_i).  theta_i is at most s~_(k) - 2 m_i over
+// the columns seen so far, which never exceeds the final value, so the band
+// list is a superset of the final candidates.  The tensor-core epilogue
+// tracks the running k best exactly for k <= 32 (a sorted register array);
+// otherwise theta_i is refreshed from the list when it has doubled since the
+// last refresh or is full: the warp finds the k-th largest banded score
+// (bisection on order-preserving integer keys) and compacts the list.  The
+// row's k best scores always pass and are never compacted away, so the final
+// list holds them and the finaliser recomputes s~_(k) from it.
 #pragma once
 
 #include <cooperative_groups.h>
