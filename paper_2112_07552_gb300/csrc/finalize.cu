@@ -282,7 +282,14 @@ __global__ void __launch_bounds__(kFinWarps * 32, 4)
     float kth = -INFINITY;
     if (jb.topv0 >= 0) {
       const float *tv = a.topv + jb.topv0 + i * S * (int64_t)k;
-      kth = fkey_inv(warp_kth_key(S * k, k, [&](int e) { return tv[e]; }));
+      if (S * k <= 32) {
+        // one value per lane, loaded once (-inf padding adds to no count
+        // above the smallest real value)
+        const float mine = lane < S * k ? tv[lane] : -INFINITY;
+        kth = fkey_inv(warp_kth_key(32, k, [&](int) { return mine; }));
+      } else {
+        kth = fkey_inv(warp_kth_key(S * k, k, [&](int e) { return tv[e]; }));
+      }
     } else if (n_all >= k) {
       // bisection over the band entries, list by list (uniform list loop)
       uint32_t T = 0;
@@ -342,16 +349,22 @@ __global__ void __launch_bounds__(kFinWarps * 32, 4)
       }
       float hi[NC], lo[NC];
       dot2_warp_sa<NC>(a_src, bp, d, hi, lo);
-      // lane t < NC finishes candidate p0 + t
+      // lane t < NC finishes candidate p0 + t, all NC lanes at once (each
+      // picks its candidate's values by a select chain: static indices)
+      float hm = hi[0], lm = lo[0];
+      int32_t jm = jq[0];
 #pragma unroll
-      for (int t = 0; t < NC; ++t) {
-        if (lane == t && p0 + t < n) {
-          const long long K = dot2_key(hi[t], lo[t]);
-          const long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, metaB[jq[t]].nrm);
-          w.U[p0 + t] = K + D;
-          w.L[p0 + t] = K - D;
-          err = fmaxf(err, fabsf(__fsub_rn(__fsub_rn(w.v[p0 + t], hi[t]), lo[t])));
-        }
+      for (int t = 1; t < NC; ++t) {
+        hm = lane == t ? hi[t] : hm;
+        lm = lane == t ? lo[t] : lm;
+        jm = lane == t ? jq[t] : jm;
+      }
+      if (lane < NC && p0 + lane < n) {
+        const long long K = dot2_key(hm, lm);
+        const long long D = dot2_halfwidth(a.dot2_coef_key, nrm_a, metaB[jm].nrm);
+        w.U[p0 + lane] = K + D;
+        w.L[p0 + lane] = K - D;
+        err = fmaxf(err, fabsf(__fsub_rn(__fsub_rn(w.v[p0 + lane], hm), lm)));
       }
     }
     // sort candidate indices by (U desc, j asc); padding indices sort last
