@@ -36,3 +36,32 @@ def test_reference_arm_line():
 def test_reference_arm_other_workloads_say_unavailable():
     r = run_bench("--impl", "reference", "--workload", "infonce")
     assert r["impl"] == "reference" and "unavailable" in r
+
+
+def test_traffic_guard_ignores_comments_only():
+    """The bench reports the scoring kernel's DRAM traffic only while the
+    kernel sources match the ncu capture; the guard's hash leaves comments
+    out, so a comment edit keeps it and a code edit voids it."""
+    import shutil
+    import tempfile
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_2112_07552_gb300", "csrc")
+    with tempfile.TemporaryDirectory() as td:
+        for f in bench.SCORE_TC_SOURCES:
+            shutil.copy(os.path.join(src, f), td)
+        h0 = bench.score_tc_src_hash(td)
+        assert h0 == bench.score_tc_src_hash()
+        p = os.path.join(td, "score_tc.cu")
+        with open(p, "a") as fh:
+            fh.write("\n// a comment\n/* another\n   comment */\n")
+        assert bench.score_tc_src_hash(td) == h0
+        with open(p, "a") as fh:
+            fh.write("static const int sj_probe_constant = 1;\n")
+        assert bench.score_tc_src_hash(td) != h0
+    # with a matching hash the traffic scales with the pair-scores
+    tr, how = bench.score_tc_traffic(1e12)
+    if bench.SCORE_TC_CAPTURE["src_hash"] == bench.score_tc_src_hash():
+        assert tr is not None and abs(tr / bench.score_tc_traffic(2e12)[0] - 0.5) < 1e-12, how
+    else:
+        assert tr is None
